@@ -1,0 +1,180 @@
+"""FP64 CPU oracle for cell integration and global assembly (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The CUDA product path never calls it, and
+the two share no code: the oracle is the plain C file ``fe_oracle.c`` compiled
+with gcc and reached through ctypes.
+
+Each wrapper names the passage of the FEMPAR paper it follows (see the header of
+``fe_oracle.c``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fe_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+_i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
+_i64p = np.ctypeslib.ndpointer(dtype=np.int64, flags="C_CONTIGUOUS")
+_f64p = np.ctypeslib.ndpointer(dtype=np.float64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile fe_oracle.c into liboracle.so next to it (gcc, plain -O2)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.or_gauss_legendre.argtypes = [ctypes.c_int, _f64p, _f64p]
+        L.or_gauss_legendre.restype = ctypes.c_int
+        L.or_lagrange_1d.argtypes = [ctypes.c_int, ctypes.c_double, _f64p, _f64p]
+        L.or_lagrange_1d.restype = None
+        L.or_cell_matrix.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _f64p, ctypes.c_double,
+                                     ctypes.c_double, _f64p, _f64p, _f64p]
+        L.or_cell_matrix.restype = ctypes.c_int
+        L.or_min_det_jacobian.argtypes = [ctypes.c_int, ctypes.c_int64, _i32p, _f64p]
+        L.or_min_det_jacobian.restype = ctypes.c_double
+        L.or_dof_numbering.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i32p, _i32p]
+        L.or_dof_numbering.restype = ctypes.c_int64
+        vp = ctypes.c_void_p
+        L.or_assemble_csr.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i32p, _f64p,
+                                      _i32p, ctypes.c_int64, _f64p, ctypes.c_double, _f64p, vp, vp, vp, vp]
+        L.or_assemble_csr.restype = ctypes.c_int64
+        L.or_assemble_rows.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i32p, _f64p,
+                                       _i32p, ctypes.c_int64, _f64p, ctypes.c_double, _f64p, ctypes.c_int64,
+                                       _i64p, ctypes.c_int64, _i64p, _i32p, _f64p, _f64p]
+        L.or_assemble_rows.restype = ctypes.c_int64
+        L.or_cell_energies.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i32p, _f64p,
+                                       _i32p, ctypes.c_double, _f64p, _f64p]
+        L.or_cell_energies.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _c(a, dt):
+    return np.ascontiguousarray(a, dtype=dt)
+
+
+def gauss_legendre(n: int):
+    """n-point Gauss-Legendre rule on [0,1] (Sect. Numerical integration)."""
+    x = np.zeros(n)
+    w = np.zeros(n)
+    rc = lib().or_gauss_legendre(n, x, w)
+    if rc:
+        raise ValueError(f"or_gauss_legendre({n}) -> {rc}")
+    return x, w
+
+
+def lagrange_1d(p: int, x: float):
+    """Values and derivatives of the p+1 equidistant Lagrange polynomials (Eq. lagbas)."""
+    v = np.zeros(p + 1)
+    d = np.zeros(p + 1)
+    lib().or_lagrange_1d(p, float(x), v, d)
+    return v, d
+
+
+def cell_matrix(problem: int, p: int, nq1d: int, xv, coef: float, nu: float, force):
+    """Cell matrix and vector of one hexahedron given its 8 vertices [8,3]."""
+    ncomp = 3 if problem == 1 else 1
+    nl = ncomp * (p + 1) ** 3
+    Ke = np.zeros(nl * nl)
+    fe = np.zeros(nl)
+    f = _c(np.resize(np.asarray(force, dtype=np.float64), 3), np.float64)
+    rc = lib().or_cell_matrix(problem, p, nq1d, _c(xv, np.float64).ravel(), float(coef), float(nu), f, Ke, fe)
+    if rc:
+        raise ValueError(f"or_cell_matrix -> {rc}")
+    return Ke.reshape(nl, nl), fe
+
+
+def min_det_jacobian(mesh, nq1d: int) -> float:
+    return float(lib().or_min_det_jacobian(nq1d, mesh.n_cells, _c(mesh.cell_vertices, np.int32),
+                                           _c(mesh.coords, np.float64).ravel()))
+
+
+def dof_numbering(mesh, p: int, ncomp: int):
+    """Global DOF numbering by the list_dofs algorithm; returns (cell_dofs, n_dofs)."""
+    nl = ncomp * (p + 1) ** 3
+    cd = np.zeros((mesh.n_cells, nl), dtype=np.int32)
+    n = lib().or_dof_numbering(p, ncomp, mesh.n_cells, _c(mesh.cell_vertices, np.int32), cd.reshape(-1))
+    if n < 0:
+        raise ValueError(f"or_dof_numbering -> {n}")
+    return cd, int(n)
+
+
+def _force3(force):
+    return _c(np.resize(np.asarray(force, dtype=np.float64), 3), np.float64)
+
+
+def assemble_csr(prob, cell_dofs=None, n_dofs=None):
+    """Full CSR matrix + RHS by COO push-back and compress (Eq. assembly)."""
+    L = lib()
+    mesh = prob.mesh
+    if cell_dofs is None:
+        cell_dofs, n_dofs = dof_numbering(mesh, prob.order, prob.ncomp)
+    cv = _c(mesh.cell_vertices, np.int32)
+    xyz = _c(mesh.coords, np.float64).ravel()
+    cd = _c(cell_dofs, np.int32).reshape(-1)
+    coef = _c(prob.coef, np.float64)
+    f = _force3(prob.force)
+    nnz = L.or_assemble_csr(prob.problem, prob.order, prob.quad_1d, mesh.n_cells, cv, xyz, cd, n_dofs,
+                            coef, prob.nu, f, None, None, None, None)
+    if nnz < 0:
+        raise ValueError(f"or_assemble_csr -> {nnz}")
+    row_ptr = np.zeros(n_dofs + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz, dtype=np.float64)
+    rhs = np.zeros(n_dofs, dtype=np.float64)
+    nnz2 = L.or_assemble_csr(prob.problem, prob.order, prob.quad_1d, mesh.n_cells, cv, xyz, cd, n_dofs,
+                             coef, prob.nu, f, row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data,
+                             rhs.ctypes.data)
+    assert nnz2 == nnz
+    return row_ptr, col, val, rhs
+
+
+def assemble_rows(prob, rows, cell_dofs, n_dofs):
+    """Selected rows of the assembled matrix and RHS: (ptr, col, val, rhs)."""
+    L = lib()
+    mesh = prob.mesh
+    rows = _c(rows, np.int64)
+    nl = prob.ncomp * (prob.order + 1) ** 3
+    cap = int(rows.size) * 8 * nl
+    ptr = np.zeros(rows.size + 1, dtype=np.int64)
+    col = np.zeros(cap, dtype=np.int32)
+    val = np.zeros(cap, dtype=np.float64)
+    rhs = np.zeros(rows.size, dtype=np.float64)
+    tot = L.or_assemble_rows(prob.problem, prob.order, prob.quad_1d, mesh.n_cells,
+                             _c(mesh.cell_vertices, np.int32), _c(mesh.coords, np.float64).ravel(),
+                             _c(cell_dofs, np.int32).reshape(-1), n_dofs, _c(prob.coef, np.float64),
+                             prob.nu, _force3(prob.force), rows.size, rows, cap, ptr, col, val, rhs)
+    if tot < 0:
+        raise ValueError(f"or_assemble_rows -> {tot}")
+    assert tot <= cap
+    return ptr, col[:tot], val[:tot], rhs
+
+
+def cell_energies(prob, u, cell_dofs):
+    """g_K = u_K^T (A^K / coef_K) u_K for every cell (compliance sensitivity)."""
+    mesh = prob.mesh
+    g = np.zeros(mesh.n_cells)
+    rc = lib().or_cell_energies(prob.problem, prob.order, prob.quad_1d, mesh.n_cells,
+                                _c(mesh.cell_vertices, np.int32), _c(mesh.coords, np.float64).ravel(),
+                                _c(cell_dofs, np.int32).reshape(-1), prob.nu, _c(u, np.float64), g)
+    if rc:
+        raise ValueError(f"or_cell_energies -> {rc}")
+    return g

@@ -1,0 +1,193 @@
+"""Seeded synthetic inputs shared by the CUDA path, the oracle and the benchmark.
+
+This module draws meshes, coefficients and displacement fields. It holds none of
+the finite element arithmetic (no shape functions, Jacobians or quadrature):
+both sides of every parity check receive exactly the arrays built here.
+
+Mesh convention (the paper's lexicographic node numbering, Sect. "Node
+generation and indexing", Eq. nodes_set): the local vertex ``v`` of a hexahedron
+sits at reference corner ``(v & 1, (v >> 1) & 1, (v >> 2) & 1)`` of [0,1]^3, so
+local vertex order is x-fastest lexicographic. Cells of a structured brick are
+numbered x-fastest as well, like the structured mesh generator of the paper
+(Sect. "A triangulation implementation").
+
+Workloads (the paper runs no experiments; these stand in for its "structural"
+problems, all synthetic):
+
+* ``poisson_q1_8``      Poisson Q1, 8^3 cells of the unit cube, interior vertices
+  shifted by up to 0.2h per coordinate, conductivity 10^U[-1,1], f = 1, 2^3 Gauss.
+* ``elasticity_q2_beam`` Elasticity Q2, 32x32x32 cells of the beam [0,4]x[0,1]^2,
+  shifts up to 0.15h_d, E ~ U[1,10], nu = 0.3, f = (0,0,-1), 3^3 Gauss.
+* ``elasticity_q1_128`` Elasticity Q1, 128^3 cells of the unit cube, shifts up to
+  0.2h, E = 10^U[log10 0.5, log10 5], nu = 0.3, f = (0,0,-1), 2^3 Gauss.
+* ``batched64``        64 unit-cube meshes with n ~ U{10..40} cells per axis,
+  p ~ U{1,2,3}, problem ~ Bernoulli(1/2), (p+1)^3 Gauss, shifts up to 0.2h.
+* ``cantilever_q1_64`` Elasticity Q1, 64^3 cells of the unit cube, E ~ U[0.1,1],
+  nu = 0.3, shifts up to 0.2h, u ~ N(0,1) per DOF rescaled to unit RMS.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 20171773
+
+POISSON = 0
+ELASTICITY = 1
+
+
+@dataclass
+class Mesh:
+    """A conforming hexahedral mesh: vertex coordinates and cell connectivity."""
+
+    coords: np.ndarray          # [n_vertices, 3] float64
+    cell_vertices: np.ndarray   # [n_cells, 8] int32, x-fastest local order
+    shape: tuple = ()           # (nx, ny, nz) for structured bricks
+    extent: tuple = ()          # (Lx, Ly, Lz)
+
+    @property
+    def n_cells(self) -> int:
+        return int(self.cell_vertices.shape[0])
+
+    @property
+    def n_vertices(self) -> int:
+        return int(self.coords.shape[0])
+
+
+@dataclass
+class Problem:
+    """One assembly workload: mesh + discretisation + coefficients."""
+
+    name: str
+    mesh: Mesh
+    order: int
+    quad_1d: int
+    problem: int                 # POISSON or ELASTICITY
+    coef: np.ndarray             # [n_cells] float64 (kappa_K or E_K)
+    force: np.ndarray            # [ncomp] float64, constant body force / source
+    nu: float = 0.3
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def ncomp(self) -> int:
+        return 3 if self.problem == ELASTICITY else 1
+
+
+def brick(nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 1.0, lz: float = 1.0) -> Mesh:
+    """Structured brick [0,lx]x[0,ly]x[0,lz] with nx*ny*nz hexahedra."""
+    xs = np.linspace(0.0, lx, nx + 1)
+    ys = np.linspace(0.0, ly, ny + 1)
+    zs = np.linspace(0.0, lz, nz + 1)
+    Z, Y, X = np.meshgrid(zs, ys, xs, indexing="ij")
+    coords = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1).astype(np.float64)
+    i = np.arange(nx)
+    j = np.arange(ny)
+    k = np.arange(nz)
+    K, J, I = np.meshgrid(k, j, i, indexing="ij")
+    base = (I + J * (nx + 1) + K * (nx + 1) * (ny + 1)).ravel().astype(np.int64)
+    cv = np.empty((base.size, 8), dtype=np.int64)
+    for v in range(8):
+        bx, by, bz = v & 1, (v >> 1) & 1, (v >> 2) & 1
+        cv[:, v] = base + bx + by * (nx + 1) + bz * (nx + 1) * (ny + 1)
+    return Mesh(coords=coords, cell_vertices=cv.astype(np.int32), shape=(nx, ny, nz), extent=(lx, ly, lz))
+
+
+def perturb_interior(mesh: Mesh, alpha: float, rng: np.random.Generator) -> Mesh:
+    """Shift every interior vertex coordinate by an independent U[-alpha h_d, alpha h_d].
+
+    Boundary vertices stay put, so the domain and its volume are unchanged.
+    """
+    nx, ny, nz = mesh.shape
+    lx, ly, lz = mesh.extent
+    h = np.array([lx / nx, ly / ny, lz / nz])
+    shift = rng.uniform(-1.0, 1.0, size=mesh.coords.shape) * (alpha * h)[None, :]
+    idx = np.arange(mesh.n_vertices)
+    vi = idx % (nx + 1)
+    vj = (idx // (nx + 1)) % (ny + 1)
+    vk = idx // ((nx + 1) * (ny + 1))
+    interior = (vi > 0) & (vi < nx) & (vj > 0) & (vj < ny) & (vk > 0) & (vk < nz)
+    coords = mesh.coords.copy()
+    coords[interior] += shift[interior]
+    return Mesh(coords=coords, cell_vertices=mesh.cell_vertices, shape=mesh.shape, extent=mesh.extent)
+
+
+def _log_uniform(rng, lo, hi, n):
+    return 10.0 ** rng.uniform(np.log10(lo), np.log10(hi), size=n)
+
+
+def poisson_q1_8(n: int = 8, seed_offset: int = 1) -> Problem:
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    mesh = perturb_interior(brick(n, n, n), 0.2, rng)
+    coef = _log_uniform(rng, 0.1, 10.0, mesh.n_cells)
+    return Problem("poisson_q1_8", mesh, 1, 2, POISSON, coef, np.array([1.0]))
+
+
+def elasticity_q2_beam(n: int = 32, seed_offset: int = 2) -> Problem:
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    mesh = perturb_interior(brick(n, n, n, 4.0, 1.0, 1.0), 0.15, rng)
+    coef = rng.uniform(1.0, 10.0, size=mesh.n_cells)
+    return Problem("elasticity_q2_beam", mesh, 2, 3, ELASTICITY, coef, np.array([0.0, 0.0, -1.0]))
+
+
+def elasticity_q1_128(n: int = 128, seed_offset: int = 3) -> Problem:
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    mesh = perturb_interior(brick(n, n, n), 0.2, rng)
+    coef = _log_uniform(rng, 0.5, 5.0, mesh.n_cells)
+    return Problem("elasticity_q1_128", mesh, 1, 2, ELASTICITY, coef, np.array([0.0, 0.0, -1.0]))
+
+
+def batched64(n_meshes: int = 64, n_lo: int = 10, n_hi: int = 40, seed_offset: int = 4) -> list[Problem]:
+    """Independent meshes of uneven size and mixed order, one child seed each."""
+    children = np.random.SeedSequence(SEED_BASE + seed_offset).spawn(n_meshes)
+    out = []
+    for m, ss in enumerate(children):
+        rng = np.random.default_rng(ss)
+        n = int(rng.integers(n_lo, n_hi + 1))
+        p = int(rng.integers(1, 4))
+        prob = int(rng.integers(0, 2))
+        mesh = perturb_interior(brick(n, n, n), 0.2, rng)
+        if prob == POISSON:
+            coef = _log_uniform(rng, 0.1, 10.0, mesh.n_cells)
+            force = np.array([1.0])
+        else:
+            coef = rng.uniform(1.0, 10.0, size=mesh.n_cells)
+            force = np.array([0.0, 0.0, -1.0])
+        out.append(Problem(f"batch{m}_p{p}_{'ela' if prob else 'poi'}_n{n}", mesh, p, p + 1, prob, coef, force))
+    return out
+
+
+def cantilever_q1_64(n: int = 64, seed_offset: int = 5) -> Problem:
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    mesh = perturb_interior(brick(n, n, n), 0.2, rng)
+    coef = rng.uniform(0.1, 1.0, size=mesh.n_cells)
+    return Problem("cantilever_q1_64", mesh, 1, 2, ELASTICITY, coef, np.array([0.0, 0.0, -1.0]))
+
+
+def unit_rms_field(n_dofs: int, seed: int) -> np.ndarray:
+    """u_i ~ N(0,1) i.i.d., rescaled so that sqrt(mean(u^2)) = 1."""
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal(n_dofs)
+    return u / np.sqrt(np.mean(u * u))
+
+
+def small_problem(n: tuple, order: int, problem: int, alpha: float = 0.2, seed: int = 7,
+                  extent: tuple = (1.0, 1.0, 1.0)) -> Problem:
+    """A small seeded problem for parity tests (several tiles plus a ragged tail)."""
+    rng = np.random.default_rng(SEED_BASE + 100 + seed)
+    mesh = perturb_interior(brick(*n, *extent), alpha, rng)
+    if problem == POISSON:
+        coef = _log_uniform(rng, 0.1, 10.0, mesh.n_cells)
+        force = np.array([1.0])
+    else:
+        coef = rng.uniform(1.0, 10.0, size=mesh.n_cells)
+        force = np.array([0.0, 0.0, -1.0])
+    return Problem(f"small_{n}_p{order}_{problem}", mesh, order, order + 1, problem, coef, force)
+
+
+WORKLOADS = {
+    "poisson_q1_8": poisson_q1_8,
+    "elasticity_q2_beam": elasticity_q2_beam,
+    "elasticity_q1_128": elasticity_q1_128,
+    "cantilever_q1_64": cantilever_q1_64,
+}

@@ -1,0 +1,488 @@
+"""Pins of the FP64 oracle against facts the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: each test checks a closed form,
+an exactness statement, an invariant or a brute-force computation written
+independently in numpy. A plausible slip in the oracle (a dropped term, a wrong
+sign, a transposed J, a swapped index) fails at least one of them.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_01773_gb300 import inputs
+
+NU = 0.3
+
+
+# ---------------------------------------------------------------- helpers
+def lame_hat(nu):
+    return nu / ((1 + nu) * (1 - 2 * nu)), 1.0 / (2 * (1 + nu))
+
+
+def node_positions(prob, cell_dofs, n_dofs):
+    """Physical position of every DOF: Phi_K(alpha/p) with the trilinear map,
+    checked to agree between all cells sharing the DOF (conformity)."""
+    p = prob.order
+    n1 = p + 1
+    mesh = prob.mesh
+    al = np.array([[a % n1, (a // n1) % n1, a // (n1 * n1)] for a in range(n1 ** 3)]) / p
+    N = np.ones((n1 ** 3, 8))
+    for v in range(8):
+        b = [(v >> d) & 1 for d in range(3)]
+        for d in range(3):
+            N[:, v] *= al[:, d] if b[d] else 1 - al[:, d]
+    xv = mesh.coords[mesh.cell_vertices]                     # [cells, 8, 3]
+    xn = np.einsum("av,evk->eak", N, xv)                     # [cells, nb, 3]
+    pos = np.full((n_dofs, 3), np.nan)
+    nb = n1 ** 3
+    for c in range(prob.ncomp):
+        d = cell_dofs[:, c * nb:(c + 1) * nb]
+        pos[d.ravel()] = xn.reshape(-1, 3)
+    # every cell must agree with the stored position
+    for c in range(prob.ncomp):
+        d = cell_dofs[:, c * nb:(c + 1) * nb]
+        np.testing.assert_allclose(pos[d.ravel()], xn.reshape(-1, 3), atol=1e-13)
+    comp = np.zeros(n_dofs, dtype=np.int64)
+    for c in range(prob.ncomp):
+        comp[cell_dofs[:, c * nb:(c + 1) * nb].ravel()] = c
+    return pos, comp
+
+
+def csr_to_dense(row_ptr, col, val, n):
+    A = np.zeros((n, n))
+    for r in range(n):
+        A[r, col[row_ptr[r]:row_ptr[r + 1]]] = val[row_ptr[r]:row_ptr[r + 1]]
+    return A
+
+
+def boundary_dofs(pos, tol=1e-12, extent=(1.0, 1.0, 1.0)):
+    b = np.zeros(pos.shape[0], dtype=bool)
+    for d in range(3):
+        b |= np.abs(pos[:, d]) < tol
+        b |= np.abs(pos[:, d] - extent[d]) < tol
+    return b
+
+
+# ---------------------------------------------------------------- Gauss rule
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 8, 12])
+def test_gauss_exactness(n):
+    """An n-point rule integrates x^k on [0,1] exactly for k <= 2n-1 and not for 2n."""
+    x, w = oracle.gauss_legendre(n)
+    assert np.all(np.diff(x) > 0) and np.all((x > 0) & (x < 1)) and np.all(w > 0)
+    for k in range(2 * n):
+        assert abs(np.dot(w, x ** k) - 1.0 / (k + 1)) < 1e-14
+    # degree 2n is not exact: the rule gives 0 for P_n(2x-1)^2 (it vanishes at the nodes),
+    # whose integral over [0,1] is 1/(2n+1)
+    Pn = np.polynomial.legendre.Legendre.basis(n)(2 * x - 1)
+    assert np.abs(Pn).max() < 1e-13 and abs(np.dot(w, Pn ** 2)) < 1e-25
+
+
+def test_gauss_closed_forms():
+    x, w = oracle.gauss_legendre(2)
+    np.testing.assert_allclose(x, [0.5 - 0.5 / math.sqrt(3), 0.5 + 0.5 / math.sqrt(3)], atol=1e-15)
+    np.testing.assert_allclose(w, [0.5, 0.5], atol=1e-15)
+    x, w = oracle.gauss_legendre(3)
+    s = 0.5 * math.sqrt(3 / 5)
+    np.testing.assert_allclose(x, [0.5 - s, 0.5, 0.5 + s], atol=1e-15)
+    np.testing.assert_allclose(w, [5 / 18, 8 / 18, 5 / 18], atol=1e-15)
+    x, w = oracle.gauss_legendre(4)
+    t = np.array([-math.sqrt(3 / 7 + 2 / 7 * math.sqrt(6 / 5)), -math.sqrt(3 / 7 - 2 / 7 * math.sqrt(6 / 5))])
+    t = np.concatenate([t, -t[::-1]])
+    wt = np.array([(18 - math.sqrt(30)) / 36, (18 + math.sqrt(30)) / 36])
+    wt = np.concatenate([wt, wt[::-1]])
+    np.testing.assert_allclose(x, 0.5 * (t + 1), atol=1e-15)
+    np.testing.assert_allclose(w, 0.5 * wt, atol=1e-15)
+
+
+# ---------------------------------------------------------------- Lagrange basis
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_lagrange_kronecker_and_partition(p):
+    for l in range(p + 1):
+        v, _ = oracle.lagrange_1d(p, l / p)
+        np.testing.assert_allclose(v, np.eye(p + 1)[l], atol=1e-15)
+    rng = np.random.default_rng(0)
+    for x in rng.uniform(-0.2, 1.2, 10):
+        v, d = oracle.lagrange_1d(p, x)
+        assert abs(v.sum() - 1) < 1e-13 and abs(d.sum()) < 1e-12
+        # derivative vs a central difference of the values
+        h = 1e-6
+        vp, _ = oracle.lagrange_1d(p, x + h)
+        vm, _ = oracle.lagrange_1d(p, x - h)
+        np.testing.assert_allclose(d, (vp - vm) / (2 * h), atol=1e-8)
+        # reproduces x^k for k <= p
+        for k in range(p + 1):
+            nodes = np.arange(p + 1) / p
+            assert abs(np.dot(v, nodes ** k) - x ** k) < 1e-12
+
+
+# ---------------------------------------------------------------- closed-form unit cube
+UNIT = np.array([[(v & 1), (v >> 1) & 1, (v >> 2) & 1] for v in range(8)], dtype=float)
+
+
+def test_q1_unit_cube_laplacian_closed_form():
+    """K = K1(x)M1(x)M1 + ...: 1/3 on the diagonal, 0 / -1/12 / -1/12 at Hamming distance 1/2/3."""
+    K, f = oracle.cell_matrix(0, 1, 2, UNIT, 1.0, NU, [1.0])
+    for a in range(8):
+        for b in range(8):
+            h = bin(a ^ b).count("1")
+            assert abs(K[a, b] - [1 / 3, 0.0, -1 / 12, -1 / 12][h]) < 1e-15
+    np.testing.assert_allclose(f, np.full(8, 1 / 8), atol=1e-15)
+    K2, _ = oracle.cell_matrix(0, 1, 2, UNIT, 3.5, NU, [1.0])
+    np.testing.assert_allclose(K2, 3.5 * K, atol=1e-14)
+
+
+def test_q1_unit_cube_elasticity_closed_form():
+    """Elasticity on the unit cube from 1D factor integrals (independent of the oracle's
+    stress/strain contraction): G^{ij}_{ab} = prod_d (K1 | C1 | C1^T | M1)."""
+    M1 = np.array([[1 / 3, 1 / 6], [1 / 6, 1 / 3]])
+    K1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
+    C1 = np.array([[-0.5, -0.5], [0.5, 0.5]])    # C1[a,b] = int l_a' l_b
+
+    def G(i, j, a, b):
+        val = 1.0
+        for d in range(3):
+            ad, bd = (a >> d) & 1, (b >> d) & 1
+            if d == i and d == j:
+                val *= K1[ad, bd]
+            elif d == i:
+                val *= C1[ad, bd]
+            elif d == j:
+                val *= C1[bd, ad]
+            else:
+                val *= M1[ad, bd]
+        return val
+
+    E = 2.7
+    lh, mh = lame_hat(NU)
+    Kref = np.zeros((24, 24))
+    for i, j, a, b in itertools.product(range(3), range(3), range(8), range(8)):
+        v = lh * G(i, j, a, b) + mh * G(j, i, a, b)
+        if i == j:
+            v += mh * sum(G(k, k, a, b) for k in range(3))
+        Kref[i * 8 + a, j * 8 + b] = E * v
+    K, f = oracle.cell_matrix(1, 1, 2, UNIT, E, NU, [0.0, 0.0, -1.0])
+    np.testing.assert_allclose(K, Kref, atol=1e-14)
+    np.testing.assert_allclose(f, np.concatenate([np.zeros(16), -np.full(8, 1 / 8)]), atol=1e-15)
+
+
+# ---------------------------------------------------------------- affine cells: exact quadrature
+def affine_cell(rng, scale=1.0):
+    A = np.eye(3) + 0.3 * rng.uniform(-1, 1, (3, 3))
+    b = rng.uniform(-1, 1, 3)
+    return scale * (UNIT @ A.T) + b, A
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("problem", [0, 1])
+def test_affine_cell_exact_vs_brute_force(p, problem):
+    """On a parallelepiped the (p+1)-point rule is exact: a 12-point rule must agree."""
+    rng = np.random.default_rng(10 * p + problem)
+    xv, _ = affine_cell(rng)
+    K, f = oracle.cell_matrix(problem, p, p + 1, xv, 1.7, NU, [0.3, -0.2, 1.1])
+    Kb, fb = oracle.cell_matrix(problem, p, 12, xv, 1.7, NU, [0.3, -0.2, 1.1])
+    sc = np.abs(Kb).max()
+    assert np.abs(K - Kb).max() < 1e-13 * sc
+    assert np.abs(f - fb).max() < 1e-13 * np.abs(fb).max()
+
+
+@pytest.mark.parametrize("problem", [0, 1])
+def test_scaling_and_rotation(problem):
+    """3D stiffness scales linearly with the cell size; Poisson is rotation invariant and
+    the elasticity blocks transform with R (comp-major local index i*nb + a)."""
+    rng = np.random.default_rng(3)
+    p = 2
+    xv = UNIT + 0.1 * rng.uniform(-1, 1, (8, 3))
+    K, _ = oracle.cell_matrix(problem, p, 3, xv, 1.0, NU, [0, 0, 0])
+    Ks, _ = oracle.cell_matrix(problem, p, 3, 2.5 * xv, 1.0, NU, [0, 0, 0])
+    np.testing.assert_allclose(Ks, 2.5 * K, atol=1e-12 * np.abs(K).max())
+    th = 0.7
+    R = np.array([[math.cos(th), -math.sin(th), 0], [math.sin(th), math.cos(th), 0], [0, 0, 1]])
+    R = R @ np.array([[1, 0, 0], [0, math.cos(0.4), -math.sin(0.4)], [0, math.sin(0.4), math.cos(0.4)]])
+    Kr, _ = oracle.cell_matrix(problem, p, 3, xv @ R.T, 1.0, NU, [0, 0, 0])
+    if problem == 0:
+        np.testing.assert_allclose(Kr, K, atol=1e-12 * np.abs(K).max())
+    else:
+        nb = (p + 1) ** 3
+        Q = np.kron(R, np.eye(nb))
+        np.testing.assert_allclose(Kr, Q @ K @ Q.T, atol=1e-12 * np.abs(K).max())
+
+
+def test_distorted_cell_converges_with_quadrature():
+    """On a distorted cell the (p+1) rule is the method's value, not the exact integral;
+    increasing the rule must converge (sanity check)."""
+    rng = np.random.default_rng(5)
+    xv = UNIT + 0.2 * rng.uniform(-1, 1, (8, 3))
+    ref, _ = oracle.cell_matrix(1, 2, 14, xv, 1.0, NU, [0, 0, 0])
+    errs = [np.abs(oracle.cell_matrix(1, 2, n, xv, 1.0, NU, [0, 0, 0])[0] - ref).max() for n in (3, 5, 8)]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-6 * np.abs(ref).max()
+
+
+# ---------------------------------------------------------------- independent numpy brute force
+def numpy_cell_matrix(problem, p, nq1d, xv, coef, nu):
+    """Second implementation: einsum over quadrature points, Gram-block form of
+    elasticity, numpy's Gauss-Legendre nodes on [-1,1] mapped to [0,1]."""
+    t, wt = np.polynomial.legendre.leggauss(nq1d)
+    x1, w1 = 0.5 * (t + 1), 0.5 * wt
+    n1 = p + 1
+    nodes = np.arange(n1) / p
+
+    def lag(x):
+        V = np.ones((len(x), n1))
+        D = np.zeros((len(x), n1))
+        for m in range(n1):
+            for s in range(n1):
+                if s != m:
+                    V[:, m] *= (x - nodes[s]) / (nodes[m] - nodes[s])
+            for r in range(n1):
+                if r == m:
+                    continue
+                term = np.full(len(x), 1 / (nodes[m] - nodes[r]))
+                for s in range(n1):
+                    if s != m and s != r:
+                        term *= (x - nodes[s]) / (nodes[m] - nodes[s])
+                D[:, m] += term
+        return V, D
+
+    V, D = lag(x1)
+    Vg, Dg = np.array([[1 - x, x] for x in x1]), np.tile([-1.0, 1.0], (nq1d, 1))
+    qi = np.array(list(itertools.product(range(nq1d), repeat=3)))[:, ::-1]   # x fastest
+    ai = np.array(list(itertools.product(range(n1), repeat=3)))[:, ::-1]
+    vi = np.array(list(itertools.product(range(2), repeat=3)))[:, ::-1]
+    w = w1[qi[:, 0]] * w1[qi[:, 1]] * w1[qi[:, 2]]
+
+    def grads(Vt, Dt, idx):
+        g = np.empty((len(qi), len(idx), 3))
+        for d in range(3):
+            f = np.ones((len(qi), len(idx)))
+            for e in range(3):
+                T = Dt if e == d else Vt
+                f *= T[qi[:, e]][:, idx[:, e]]
+            g[:, :, d] = f
+        return g
+
+    gref = grads(V, D, ai)
+    gN = grads(Vg, Dg, vi)
+    J = np.einsum("vk,qvd->qkd", xv, gN)
+    det = np.linalg.det(J)
+    Jinv = np.linalg.inv(J)
+    g = np.einsum("qad,qdk->qak", gref, Jinv)
+    c = w * det
+    Gm = np.einsum("q,qai,qbj->ijab", c, g, g)
+    nb = n1 ** 3
+    if problem == 0:
+        return coef * (Gm[0, 0] + Gm[1, 1] + Gm[2, 2])
+    lh, mh = lame_hat(nu)
+    K = np.zeros((3 * nb, 3 * nb))
+    tr = Gm[0, 0] + Gm[1, 1] + Gm[2, 2]
+    for i in range(3):
+        for j in range(3):
+            blk = lh * Gm[i, j] + mh * Gm[j, i] + (mh * tr if i == j else 0)
+            K[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb] = coef * blk
+    return K
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("problem", [0, 1])
+def test_distorted_cell_vs_numpy_brute_force(p, problem):
+    rng = np.random.default_rng(100 + p)
+    xv = UNIT * np.array([1.3, 0.7, 1.0]) + 0.2 * rng.uniform(-1, 1, (8, 3))
+    K, _ = oracle.cell_matrix(problem, p, p + 1, xv, 2.3, NU, [0, 0, 0])
+    Kn = numpy_cell_matrix(problem, p, p + 1, xv, 2.3, NU)
+    np.testing.assert_allclose(K, Kn, atol=1e-13 * np.abs(Kn).max())
+
+
+# ---------------------------------------------------------------- DOF numbering
+def test_dof_numbering_list_dofs_order_single_q2_cell():
+    """One Q2 cell: the interior node is numbered first, then the 8 vertices, then
+    x-, y-, z-edges (anchors ascending), then the faces (xy, xz, yz)."""
+    mesh = inputs.brick(1, 1, 1)
+    cd, n = oracle.dof_numbering(mesh, 2, 1)
+    assert n == 27
+    lex = lambda i, j, k: i + 3 * j + 9 * k
+    expected_order = [lex(1, 1, 1)]
+    expected_order += [lex(2 * (v & 1), 2 * ((v >> 1) & 1), 2 * ((v >> 2) & 1)) for v in range(8)]
+    expected_order += [lex(1, 0, 0), lex(1, 2, 0), lex(1, 0, 2), lex(1, 2, 2)]   # x-edges
+    expected_order += [lex(0, 1, 0), lex(2, 1, 0), lex(0, 1, 2), lex(2, 1, 2)]   # y-edges
+    expected_order += [lex(0, 0, 1), lex(2, 0, 1), lex(0, 2, 1), lex(2, 2, 1)]   # z-edges
+    expected_order += [lex(1, 1, 0), lex(1, 1, 2)]                               # xy faces
+    expected_order += [lex(1, 0, 1), lex(1, 2, 1)]                               # xz faces
+    expected_order += [lex(0, 1, 1), lex(2, 1, 1)]                               # yz faces
+    got = np.empty(27, dtype=int)
+    got[cd[0]] = np.arange(27)
+    assert list(got) == expected_order
+
+
+def test_dof_numbering_two_cells_share_face():
+    mesh = inputs.brick(2, 1, 1)
+    cd, n = oracle.dof_numbering(mesh, 1, 3)
+    assert n == 12 * 3
+    # cell 0: vertices in local order, 3 consecutive ids per node, local index c*8 + a
+    np.testing.assert_array_equal(cd[0].reshape(3, 8), np.arange(24).reshape(8, 3).T)
+    # cell 1 shares its x=0 face (local 0,2,4,6) with cell 0's x=1 face (local 1,3,5,7)
+    np.testing.assert_array_equal(cd[1].reshape(3, 8)[:, [0, 2, 4, 6]], cd[0].reshape(3, 8)[:, [1, 3, 5, 7]])
+    np.testing.assert_array_equal(cd[1].reshape(3, 8)[:, [1, 3, 5, 7]], 24 + np.arange(12).reshape(4, 3).T)
+
+
+@pytest.mark.parametrize("p,ncomp,shape", [(1, 1, (3, 2, 2)), (2, 3, (2, 3, 2)), (3, 1, (2, 2, 3)), (3, 3, (2, 1, 2))])
+def test_dof_numbering_conformity(p, ncomp, shape):
+    """(s,K) ~ (s',K') iff x_s = x_s': every DOF has one position, DOF count is the
+    structured node count, and distinct DOFs of one component sit at distinct points."""
+    prob = inputs.small_problem(shape, p, 1 if ncomp == 3 else 0, seed=p)
+    cd, n = oracle.dof_numbering(prob.mesh, p, ncomp)
+    nx, ny, nz = shape
+    assert n == ncomp * (p * nx + 1) * (p * ny + 1) * (p * nz + 1)
+    pos, comp = node_positions(prob, cd, n)
+    for c in range(ncomp):
+        pts = np.round(pos[comp == c], 12)
+        assert len(np.unique(pts, axis=0)) == len(pts)
+    # a node's components carry consecutive ids
+    if ncomp == 3:
+        nb = (p + 1) ** 3
+        np.testing.assert_array_equal(cd[:, nb:2 * nb], cd[:, :nb] + 1)
+        np.testing.assert_array_equal(cd[:, 2 * nb:], cd[:, :nb] + 2)
+
+
+def test_dof_numbering_rotated_cells():
+    """Cells given with a rotated local vertex order (same geometry) must keep the
+    space conforming: node keys are orientation free."""
+    prob = inputs.small_problem((2, 2, 1), 3, 0, seed=11)
+    mesh = prob.mesh
+    cv = mesh.cell_vertices.copy()
+    # rotate cell 1 by 180 degrees about z: local (x,y,z) -> (1-x, 1-y, z)
+    perm = [(1 - (v & 1)) + 2 * (1 - ((v >> 1) & 1)) + 4 * ((v >> 2) & 1) for v in range(8)]
+    cv[1] = cv[1][perm]
+    m2 = inputs.Mesh(mesh.coords, cv, mesh.shape, mesh.extent)
+    prob2 = inputs.Problem("rot", m2, 3, 4, 0, prob.coef, prob.force)
+    cd, n = oracle.dof_numbering(m2, 3, 1)
+    assert n == (3 * 2 + 1) * (3 * 2 + 1) * (3 * 1 + 1)
+    node_positions(prob2, cd, n)
+
+
+# ---------------------------------------------------------------- assembled-system invariants
+def assembled(prob):
+    cd, n = oracle.dof_numbering(prob.mesh, prob.order, prob.ncomp)
+    rp, col, val, rhs = oracle.assemble_csr(prob, cd, n)
+    return cd, n, rp, col, val, rhs
+
+
+def test_poisson_q1_8_invariants():
+    prob = inputs.poisson_q1_8()
+    assert oracle.min_det_jacobian(prob.mesh, 2) > 0
+    cd, n, rp, col, val, rhs = assembled(prob)
+    assert n == 729 and rp[-1] == 15625                     # (3n+1)^3 pattern
+    A = csr_to_dense(rp, col, val, n)
+    assert np.array_equal(A, A.T)                           # bitwise symmetric
+    assert np.abs(A @ np.ones(n)).max() < 1e-13 * np.abs(A).max()   # zero row sums
+    assert abs(rhs.sum() - 1.0) < 1e-13                     # sum f = vol = 1 for f = 1
+    assert np.all(np.diag(A) > 0)
+
+
+def _lin_fields(pos, comp, ncomp):
+    """The linear fields used by the patch test and the rigid-body check."""
+    out = []
+    for c in range(ncomp):
+        for d in range(3):
+            u = np.where(comp == c, pos[:, d], 0.0)
+            out.append(((c, d), u))
+    return out
+
+
+@pytest.mark.parametrize("p,shape", [(1, (3, 3, 3)), (2, (3, 2, 2)), (3, (2, 2, 2))])
+def test_poisson_patch_test(p, shape):
+    """Constant conductivity: A u_lin vanishes on interior rows and u^T A u = kappa |a|^2 vol."""
+    prob = inputs.small_problem(shape, p, 0, seed=20 + p)
+    prob.coef[:] = 2.0
+    cd, n, rp, col, val, rhs = assembled(prob)
+    A = csr_to_dense(rp, col, val, n)
+    pos, comp = node_positions(prob, cd, n)
+    interior = ~boundary_dofs(pos)
+    a = np.array([0.3, -1.1, 0.7])
+    u = pos @ a + 0.5
+    r = A @ u
+    assert np.abs(r[interior]).max() < 1e-12 * np.abs(A).max()
+    assert abs(u @ r - 2.0 * (a @ a) * 1.0) < 1e-12
+    assert abs(rhs.sum() - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("p,shape", [(1, (3, 2, 3)), (2, (2, 2, 2)), (3, (2, 1, 2))])
+def test_elasticity_rigid_modes_and_patch(p, shape):
+    """Six rigid-body modes lie in the kernel (any E, any geometry); a uniform strain
+    gives the closed-form energy with constant E; RHS z-rows sum to -vol."""
+    prob = inputs.small_problem(shape, p, 1, seed=30 + p)
+    cd, n, rp, col, val, rhs = assembled(prob)
+    A = csr_to_dense(rp, col, val, n)
+    sc = np.abs(A).max()
+    assert np.abs(A - A.T).max() < 1e-15 * sc               # symmetric to rounding
+    pos, comp = node_positions(prob, cd, n)
+    for c in range(3):                                       # translations
+        t = (comp == c).astype(float)
+        assert np.abs(A @ t).max() < 1e-12 * sc
+    for w in np.eye(3):                                      # rotations w x x
+        r = np.zeros(n)
+        disp = np.cross(w[None, :], pos)
+        for c in range(3):
+            r[comp == c] = disp[comp == c, c]
+        assert np.abs(A @ r).max() < 1e-12 * sc
+    # uniform strain with constant E: u = eps0 x
+    prob.coef[:] = 3.0
+    _, _, rp2, col2, val2, _ = assembled(prob)
+    A2 = csr_to_dense(rp2, col2, val2, n)
+    eps0 = np.array([[0.2, 0.05, -0.1], [0.05, -0.3, 0.15], [-0.1, 0.15, 0.4]])
+    disp = pos @ eps0.T
+    u = np.zeros(n)
+    for c in range(3):
+        u[comp == c] = disp[comp == c, c]
+    lh, mh = lame_hat(NU)
+    exact = 3.0 * (lh * np.trace(eps0) ** 2 + 2 * mh * np.sum(eps0 * eps0)) * 1.0
+    assert abs(u @ A2 @ u - exact) < 1e-12 * exact
+    r = A2 @ u
+    assert np.abs(r[~boundary_dofs(pos)]).max() < 1e-11 * np.abs(A2).max()
+    zsum = rhs[comp == 2].sum()
+    assert abs(zsum + 1.0) < 1e-13 and abs(rhs[comp == 0].sum()) < 1e-14 and abs(rhs[comp == 1].sum()) < 1e-14
+
+
+def test_assemble_rows_matches_full():
+    prob = inputs.small_problem((3, 2, 2), 2, 1, seed=41)
+    cd, n, rp, col, val, rhs = assembled(prob)
+    rows = np.array([0, 5, n // 2, n - 1], dtype=np.int64)
+    ptr, c2, v2, r2 = oracle.assemble_rows(prob, rows, cd, n)
+    for q, r in enumerate(rows):
+        np.testing.assert_array_equal(c2[ptr[q]:ptr[q + 1]], col[rp[r]:rp[r + 1]])
+        np.testing.assert_allclose(v2[ptr[q]:ptr[q + 1]], val[rp[r]:rp[r + 1]], rtol=0, atol=1e-14)
+    np.testing.assert_allclose(r2, rhs[rows], atol=1e-15)
+
+
+@pytest.mark.parametrize("problem", [0, 1])
+def test_cell_energies_euler_and_fd(problem):
+    """c(E) = u^T A(E) u is linear in E: sum_K E_K g_K = c, and central differences agree."""
+    prob = inputs.small_problem((2, 2, 2), 2, problem, seed=50 + problem)
+    cd, n, rp, col, val, rhs = assembled(prob)
+    A = csr_to_dense(rp, col, val, n)
+    u = inputs.unit_rms_field(n, 5)
+    g = oracle.cell_energies(prob, u, cd)
+    c = u @ A @ u
+    assert abs(np.dot(prob.coef, g) - c) < 1e-12 * abs(c)
+    for e in (0, 3, 7):
+        h = 1e-6 * prob.coef[e]
+        cp = prob.coef.copy(); cp[e] += h
+        cm = prob.coef.copy(); cm[e] -= h
+        pp = inputs.Problem("p", prob.mesh, prob.order, prob.quad_1d, problem, cp, prob.force)
+        pm = inputs.Problem("m", prob.mesh, prob.order, prob.quad_1d, problem, cm, prob.force)
+        Ap = csr_to_dense(*oracle.assemble_csr(pp, cd, n)[:3], n)
+        Am = csr_to_dense(*oracle.assemble_csr(pm, cd, n)[:3], n)
+        fd = (u @ Ap @ u - u @ Am @ u) / (2 * h)
+        assert abs(fd - g[e]) < 1e-6 * abs(g[e])
+
+
+def test_workload_meshes_valid_and_patterns():
+    """The seeded workloads have positive Jacobians everywhere (the generator does not
+    redraw) and the structured pattern sizes of the paper-shaped configs."""
+    prob = inputs.elasticity_q2_beam(n=8)
+    assert oracle.min_det_jacobian(prob.mesh, 3) > 0
+    cd, n = oracle.dof_numbering(prob.mesh, 2, 3)
+    assert n == 3 * 17 ** 3
+    pc = inputs.cantilever_q1_64(n=16)
+    assert oracle.min_det_jacobian(pc.mesh, 2) > 0
