@@ -1,0 +1,379 @@
+"""Benchmark: cell integration + global CSR assembly on one GB300 (per rank).
+
+One step = one fe_assemble call (geometry, gradients, cell-matrix contraction,
+cell vectors, deterministic scatter into CSR + RHS) on the 32x32x32 Q2
+linear-elasticity beam (32,768 cells, 823,875 DOFs, 152,771,337 nonzeros),
+mixed FP32 contraction with FP64 geometry and FP64 CSR accumulation. Inputs are
+seeded synthetic meshes; the working set (cell matrices 0.86 GB, CSR values
+1.22 GB) is far larger than L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|bf16|fp64]
+  python bench.py --impl reference     # the FP64 CPU oracle on the host cores
+
+Prints one JSON line (rank 0). Under torchrun every rank assembles its own
+replica (weak scaling, no collective on the data path); the barrier and the
+max over ranks are for timing only.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cells/s integrate+assemble (elasticity Q2 32^3 beam), mixed-prec vs FP64 at <=1e-6 rel err"
+UNIT = "cells/s"
+WORKLOAD = "elasticity_q2_beam"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp64"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-comparators", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ----------------------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("bf16_tflops", 1900.0)), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            time.sleep(0.1)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def kernel_traffic(kernel: str):
+    """DRAM traffic per launch from a committed ncu summary, if the kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_1708_01773_gb300", "csrc", d["source"])
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d["bytes_per_launch"] if sha == d["source_sha"] else None
+
+
+def scatter_bytes(sp, prec: str) -> int:
+    """Algorithmic bytes of one scatter launch: every cell-matrix entry read once, one
+    16-bit code per contribution, one count byte per nonzero, the FP64 values written,
+    the row/slot tables and the cell vectors read, the RHS written."""
+    ke = 8 if prec == "fp64" else 4
+    nl = sp.nl
+    return int(sp.n_cells * nl * nl * ke + sp.n_contrib * 2 + sp.nnz * (1 + 8)
+               + sp.n_cells * nl * (4 + 8) + (sp.n_dofs + 1) * 8 * 3 + sp.n_dofs * 8)
+
+
+def cell_bytes(sp, prec: str) -> int:
+    """Algorithmic bytes of one cell-integration launch: vertex coordinates and the
+    coefficient read, cell matrices and cell vectors written."""
+    ke = 8 if prec == "fp64" else 4
+    nl = sp.nl
+    return int(sp.n_cells * (24 * 8 + 8) + sp.n_cells * nl * nl * ke + sp.n_cells * nl * 8)
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+def oracle_rate(prob, target_s: float, max_cells: int | None = None):
+    """Times the FP64 CPU oracle (numbering + cell loop + COO compress) on the first
+    cells of the workload, sized to take about target_s seconds. Returns
+    (cells/s, cells in the sample, seconds)."""
+    import oracle
+    from paper_1708_01773_gb300 import inputs
+
+    def sample(n):
+        cv = prob.mesh.cell_vertices[:n]
+        sub = inputs.Problem(prob.name, inputs.Mesh(prob.mesh.coords, cv), prob.order, prob.quad_1d,
+                             prob.problem, prob.coef[:n], prob.force, prob.nu)
+        t = time.perf_counter()
+        oracle.assemble_csr(sub)
+        return time.perf_counter() - t
+
+    n = 4
+    dt = sample(n)
+    while dt < 0.5 and n < prob.mesh.n_cells:
+        n = min(prob.mesh.n_cells, n * 4)
+        dt = sample(n)
+    n_target = int(min(prob.mesh.n_cells, max(1, n * target_s / max(dt, 1e-6))))
+    if max_cells:
+        n_target = min(n_target, max_cells)
+    dt = sample(n_target)
+    return n_target / dt, n_target, dt
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1708_01773_gb300 import inputs
+    import oracle
+    oracle.build()
+    prob = inputs.WORKLOADS[args.workload]()
+    # size one step so that warmup + steps take about two minutes in total
+    per_step = max(0.5, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    rate, n, _ = oracle_rate(prob, per_step)
+    import oracle as _o  # noqa: F401
+    times = []
+    from paper_1708_01773_gb300 import inputs as _i
+    cv = prob.mesh.cell_vertices[:n]
+    sub = _i.Problem(prob.name, _i.Mesh(prob.mesh.coords, cv), prob.order, prob.quad_1d, prob.problem,
+                     prob.coef[:n], prob.force, prob.nu)
+    for s in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        oracle.assemble_csr(sub)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t)
+    step = float(np.mean(times))
+    value = n / step
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cells": int(prob.mesh.n_cells), "sample_cells": int(n),
+                   "l2": "n/a (CPU)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"first {n} cells of {args.workload}, single-threaded C oracle, "
+                                   f"numbering + cell loop + COO compress per step"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    from paper_1708_01773_gb300 import build, feasm, inputs
+    build.build()
+
+    prob = inputs.WORKLOADS[args.workload]()
+    t0 = time.perf_counter()
+    sp = feasm.FESpace(prob)
+    setup_s = time.perf_counter() - t0
+    prec = feasm.PRECISIONS[args.prec]
+    dev = torch.device("cuda", local)
+    coef = torch.tensor(prob.coef, device=dev)
+    vals = torch.empty(sp.nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(sp.n_dofs, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev_mid=None):
+        if ev_mid is None:
+            feasm.fe_assemble(sp.handle, coef, prob.force, vals, rhs, prec, stream)
+        else:
+            feasm.fe_assemble_ex(sp.handle, coef, prob.force, vals, rhs, prec, stream, ev_mid.cuda_event)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    if sp.status() != 0:
+        raise RuntimeError("device error during warm-up")
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(K)] for _ in range(3)]
+    for e in ev[1]:
+        e.record(stream)  # materialise the event handles before handing them to the library
+    torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            ev[0][k].record(stream)
+            step(ev[1][k])
+            ev[2][k].record(stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if sp.status() != 0:
+        raise RuntimeError("device error in the timed region")
+    total_ms = ev[0][0].elapsed_time(ev[2][K - 1])
+    cell_ms = [ev[0][k].elapsed_time(ev[1][k]) for k in range(K)]
+    scat_ms = [ev[1][k].elapsed_time(ev[2][k]) for k in range(K)]
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t)
+    ms_per_step = total_ms / K
+    value = ws * sp.n_cells * K / (total_ms / 1e3)
+
+    # end to end through the host-buffer entry point (pinned memory, copies timed)
+    Ke2e = max(3, min(K, 20))
+    hc = torch.tensor(prob.coef).pin_memory()
+    hv = torch.empty(sp.nnz, dtype=torch.float64).pin_memory()
+    hr = torch.empty(sp.n_dofs, dtype=torch.float64).pin_memory()
+    feasm.fe_assemble_host(sp.handle, hc, prob.force, hv, hr, prec, stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(Ke2e):
+        feasm.fe_assemble_host(sp.handle, hc, prob.force, hv, hr, prec, stream)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / Ke2e
+    if ws > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t)
+
+    # same-GPU comparators (plain FP64 assembler, BF16 form)
+    comparators = {}
+    if not args.no_comparators:
+        for name in ("fp64", "fp32", "bf16"):
+            if name == args.prec:
+                continue
+            p2 = feasm.PRECISIONS[name]
+            for _ in range(3):
+                feasm.fe_assemble(sp.handle, coef, prob.force, vals, rhs, p2, stream)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            n2 = 20
+            a.record(stream)
+            for _ in range(n2):
+                feasm.fe_assemble(sp.handle, coef, prob.force, vals, rhs, p2, stream)
+            b.record(stream)
+            torch.cuda.synchronize()
+            comparators[name] = {"cells_per_s": sp.n_cells * n2 / (a.elapsed_time(b) / 1e3),
+                                 "ms_per_step": a.elapsed_time(b) / n2}
+
+    hbm, bf16_tf, peak_src = measured_peaks()
+    cell_avg, scat_avg = float(np.mean(cell_ms)), float(np.mean(scat_ms))
+    kernels = {
+        "k_scatter": {"ms": scat_avg, "bytes": scatter_bytes(sp, args.prec)},
+        "k_cell": {"ms": cell_avg, "bytes": cell_bytes(sp, args.prec)},
+    }
+    for k in kernels.values():
+        k["gbs"] = k["bytes"] / (k["ms"] / 1e3) / 1e9
+        k["frac"] = k["gbs"] / hbm
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm, "unit": "GB/s",
+            "frac": kernels[dom]["frac"], "traffic": kernel_traffic(dom),
+            "algorithmic_bytes": kernels[dom]["bytes"], "peak_source": peak_src + " (burst copy)"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, n, dt = oracle_rate(prob, 12.0)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"first {n} cells of {args.workload} ({dt:.1f} s), single-threaded C oracle: "
+                         f"numbering + cell loop + COO compress"}
+
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": K, "warmup": args.warmup,
+            "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16": "bf16", "fp64": "f64"}[args.prec], "data": "synthetic",
+            "config": {"workload": args.workload, "cells": int(sp.n_cells), "dofs": int(sp.n_dofs),
+                       "nnz": int(sp.nnz), "contributions": int(sp.n_contrib), "order": prob.order,
+                       "precision": f"{args.prec} contraction, fp64 geometry + fp64 CSR accumulation",
+                       "l2": "working set > L2 (no flush)", "parallelism": f"replicas x{ws}",
+                       "setup_s": setup_s},
+            "nnz_per_s": value / sp.n_cells * sp.nnz,
+            "e2e": {"value": ws * sp.n_cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(sp.n_cells * 8),
+                    "d2h_bytes_per_step": int((sp.nnz + sp.n_dofs) * 8)},
+            "gpu_launches": 2 * K,
+            "roofline": roof,
+            "kernels": kernels,
+            "comparators": comparators,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(out), flush=True)
+    sp.close()
+    if ws > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,197 @@
+/*
+ * feasm.h -- C ABI of the GB300 cell-integration and global-assembly library
+ * (libfeasm.so) for grad-conforming Lagrangian Q_p hexahedra, p = 1..3,
+ * Poisson and linear elasticity, after the FEMPAR paper (arXiv 1708.01773).
+ *
+ * Conventions shared by every entry point
+ *   - All functions return 0 (FE_OK) or a negative FE_ERR_* code; no C++
+ *     exception crosses the ABI. fe_last_error() returns a thread-local message
+ *     for the last failure of the calling thread.
+ *   - "host" pointers are ordinary CPU memory; "device" pointers are CUDA global
+ *     memory of the current device (for instance torch tensors' data_ptr()).
+ *   - Device buffers passed in or out are owned by the caller; the library owns
+ *     only what an fe_space / fe_batch holds (tables, DOF map, sparsity
+ *     pattern, assembly permutation, cell-matrix scratch), allocated at create
+ *     time and freed by the matching destroy.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Compute calls
+ *     are asynchronous on it and allocate nothing.
+ *   - Errors found on the device (a non-positive Jacobian determinant, a
+ *     persistent-kernel wait that gave up) are recorded in a device error word
+ *     and reported by fe_status(); kernels never trap.
+ *   - Local DOF order in a cell: component-major, index i*nb + a, with the
+ *     scalar nodes a in x-fastest lexicographic order (nb = (p+1)^3).
+ *   - Mesh vertex order in a cell: x-fastest lexicographic, local vertex v at
+ *     reference corner (v&1, (v>>1)&1, (v>>2)&1) of [0,1]^3.
+ */
+#ifndef FEASM_H
+#define FEASM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fe_space fe_space; /* opaque, library-owned */
+typedef struct fe_batch fe_batch; /* opaque, library-owned */
+
+typedef enum { FE_POISSON = 0, FE_ELASTICITY = 1 } fe_problem;
+
+/* Arithmetic of the cell-matrix contraction. The geometry (Jacobian,
+ * determinant, cofactors) and the global CSR accumulation are always FP64.
+ *   FE_PREC_FP64: all FP64 (the plain FP64 GPU assembler).
+ *   FE_PREC_FP32: FP32 operands and FP32 accumulation of the contraction.
+ *   FE_PREC_BF16: BF16 operands, FP32 accumulation. */
+typedef enum { FE_PREC_FP64 = 0, FE_PREC_FP32 = 1, FE_PREC_BF16 = 2 } fe_precision;
+
+enum {
+  FE_OK = 0,
+  FE_ERR_INVALID_ARG = -1,
+  FE_ERR_CUDA = -2,
+  FE_ERR_OOM = -3,
+  FE_ERR_NEG_JACOBIAN = -4,
+  FE_ERR_TIMEOUT = -5,
+  FE_ERR_UNSUPPORTED = -6
+};
+
+typedef struct {
+  int64_t n_vertices;
+  const double* coords;         /* host [n_vertices*3], copied at create */
+  int64_t n_cells;
+  const int32_t* cell_vertices; /* host [n_cells*8], x-fastest local order, copied */
+} fe_mesh_desc;
+
+/* Builds an FE space on a conforming hexahedral mesh: reference tables of the
+ * Q_p Lagrangian element at a tensor Gauss-Legendre rule (paper, Sect.
+ * "Numerical integration", Eq. lagbas / Eq. lagbasmd), the global DOF
+ * numbering by the list_dofs algorithm (Sect. "Global DOF numbering
+ * generation"), the CSR sparsity pattern (every DOF pair sharing a cell, columns
+ * ascending; Sect. "Linear algebra": pattern built once and reused) and the
+ * cell-to-nonzero assembly permutation used by fe_assemble.
+ *   order           p in 1..3.
+ *   quad_points_1d  Gauss points per direction, 0 = p+1 (exact mass matrix on
+ *                   affine cells), else 1..6.
+ *   problem         FE_POISSON (1 component) or FE_ELASTICITY (3 components).
+ *   nu              Poisson ratio (elasticity only, 0 <= nu < 0.5).
+ *   out             receives the new space; destroy with fe_space_destroy.
+ * Uses the current CUDA device. Host work is multi-threaded. Errors:
+ * FE_ERR_INVALID_ARG (bad sizes, vertex ids out of range), FE_ERR_UNSUPPORTED
+ * (index widths exceeded, more than 255 cells around one DOF), FE_ERR_OOM,
+ * FE_ERR_CUDA. */
+int fe_space_create(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem,
+                    double nu, fe_space** out);
+
+/* Same host-side setup as fe_space_create without touching any GPU (for
+ * inspection of the numbering and the pattern on machines without one). The
+ * result supports fe_space_sizes, fe_space_cell_dofs_host,
+ * fe_space_csr_pattern_host and fe_space_destroy only. */
+int fe_space_create_host(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem,
+                         double nu, fe_space** out);
+
+/* Sizes of the space: number of global DOFs, CSR nonzeros, cells, and
+ * per-contribution counts (n_cells * n_loc^2). Any pointer may be NULL. */
+int fe_space_sizes(const fe_space* s, int64_t* n_dofs, int64_t* nnz, int64_t* n_cells,
+                   int64_t* n_contrib);
+
+/* Copies the cell-to-DOF map [n_cells * n_loc] (host, int32, local order
+ * i*nb + a) into caller memory (Sect. "Global DOF numbering generation"). */
+int fe_space_cell_dofs_host(const fe_space* s, int32_t* cell_dofs);
+
+/* Copies the CSR pattern into caller memory: row_ptr [n_dofs+1] int64 and
+ * col_idx [nnz] int32. _host: host pointers; plain: device pointers, copied
+ * asynchronously on `stream`. */
+int fe_space_csr_pattern_host(const fe_space* s, int64_t* row_ptr, int32_t* col_idx);
+int fe_space_csr_pattern(const fe_space* s, int64_t* row_ptr, int32_t* col_idx, void* stream);
+
+/* Copies the assembly permutation of a host-only space into caller memory
+ * (host): cnt [nnz] uint8 contributions per nonzero; code_ptr [n_dofs+1] int64
+ * first code of each row; codes [n_contrib] uint16; slot_ptr [n_dofs+1] int64;
+ * slots [n_cells * n_loc] int32. Row r has the cells ("slots", ascending) given
+ * by slots[slot_ptr[r] .. slot_ptr[r+1]), each entry e * n_loc + (local index
+ * of DOF r in cell e). Nonzero k of row r sums, in code order, the cell-matrix
+ * entries K^{e_s}[local row][m] for the codes (s << 8) | m of its segment; the
+ * segments of a row are consecutive from code_ptr[r], nonzeros in column order.
+ * This is the deterministic gather form of Eq. assembly. Only spaces made by
+ * fe_space_create_host keep these arrays on the host (FE_ERR_INVALID_ARG
+ * otherwise). */
+int fe_space_permutation_host(const fe_space* s, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
+                              int64_t* slot_ptr, int32_t* slots);
+
+/* Integrates every cell and assembles the global matrix and right-hand side
+ * (paper Eq. linear_system, Eq. assembly, Eq. fematrix, Eq. shape_grad; the
+ * element loop of the Listing "element_matrix_entries_computation").
+ *   coefficients  device [n_cells] FP64: conductivity kappa_K (Poisson) or
+ *                 Young's modulus E_K (elasticity), constant per cell.
+ *   body_force    host [ncomp] FP64: constant source f (Poisson) or body
+ *                 force (elasticity).
+ *   csr_values    device [nnz] FP64, overwritten (pattern of fe_space_csr_pattern).
+ *   rhs           device [n_dofs] FP64, overwritten; may be NULL.
+ *   prec          arithmetic of the cell-matrix contraction (see fe_precision).
+ * The result is deterministic: every CSR value is the sum of its cell
+ * contributions in ascending cell order, in FP64, without atomics. No
+ * boundary conditions are applied (the unconstrained, singular operator). */
+int fe_assemble(fe_space* s, const double* coefficients, const double* body_force, double* csr_values,
+                double* rhs, fe_precision prec, void* stream);
+
+/* fe_assemble that also records `event_mid` (a cudaEvent_t, or NULL) on
+ * `stream` between the cell-integration kernel and the scatter kernel, so that
+ * a caller can time the two kernels separately with CUDA events. */
+int fe_assemble_ex(fe_space* s, const double* coefficients, const double* body_force, double* csr_values,
+                   double* rhs, fe_precision prec, void* stream, void* event_mid);
+
+/* fe_assemble with HOST buffers: coefficients [n_cells], csr_values [nnz] and
+ * rhs [n_dofs] (may be NULL) are host memory (pinned memory gives full copy
+ * speed). The copies run on `stream` through device staging buffers that the
+ * space allocates on its first host-buffer call; the call returns after the
+ * results are in host memory. */
+int fe_assemble_host(fe_space* s, const double* coefficients, const double* body_force,
+                     double* csr_values, double* rhs, fe_precision prec, void* stream);
+
+/* Compliance sensitivity. For a fixed nodal field u, c(coef) = u^T A(coef) u
+ * is linear in the cell coefficients (Eq. assembly), so
+ *   dc/dcoef_K = u_K^T (A^K / coef_K) u_K,
+ * computed per quadrature point from the strain of u without forming A^K:
+ * elasticity lambda^ (div u)^2 + 2 mu^ eps(u):eps(u), Poisson |grad u|^2,
+ * times w_q det J_q (Eq. fematrix), with lambda^, mu^ the Lame parameters per
+ * unit Young's modulus.
+ *   u             device [n_dofs] FP64 nodal values.
+ *   coefficients  device [n_cells] FP64; needed only for `compliance`.
+ *   grad_scale    multiplies dc_dcoef (the incoming gradient of a backward pass).
+ *   dc_dcoef      device [n_cells] FP64, overwritten with grad_scale * dc/dcoef.
+ *   compliance    device scalar FP64 or NULL: receives c = sum_K coef_K dc/dcoef_K
+ *                 (unscaled), reduced in a fixed order (deterministic).
+ *   prec          FE_PREC_FP64 or FE_PREC_FP32 (FP32 strain arithmetic, FP64
+ *                 geometry and FP64 sums). */
+int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients, double grad_scale,
+                        double* dc_dcoef, double* compliance, fe_precision prec, void* stream);
+
+/* Synchronises `stream`, returns and clears the device error word:
+ * FE_OK, FE_ERR_NEG_JACOBIAN (some det J <= 0 at a quadrature point) or
+ * FE_ERR_TIMEOUT (a bounded persistent-kernel wait gave up). */
+int fe_status(fe_space* s, void* stream);
+
+void fe_space_destroy(fe_space* s);
+
+/* Thread-local description of the last error of the calling thread. */
+const char* fe_last_error(void);
+
+/* Batched assembly: several independent spaces (any order, problem and size)
+ * assembled by one persistent launch pair over a shared work list of
+ * (space, cell tile) and (space, row block) items. The batch keeps pointers to
+ * the spaces, which must outlive it.
+ *   cells_per_item  cells per contraction work item, 0 = autotuned default. */
+int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch** out);
+
+/* coefficients[i], csr_values[i], rhs[i] are the device buffers of space i
+ * (rhs[i] may be NULL); body_force is host [n*3] (force of space i at 3*i).
+ * Same semantics and determinism as fe_assemble for every space. */
+int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const double* body_force,
+                      double* const* csr_values, double* const* rhs, fe_precision prec, void* stream);
+
+void fe_batch_destroy(fe_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FEASM_H */

@@ -1,0 +1,287 @@
+// C-ABI entry points of libfeasm: space creation (host setup + upload),
+// assembly, adjoint, status, and the host-buffer variant.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "fe_launch.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA;
+}
+
+#define FE_CUDA(call)                                 \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <typename T>
+cudaError_t upload(T** dst, const T* src, size_t n) {
+  *dst = nullptr;
+  if (n == 0) return cudaSuccess;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), n * sizeof(T));
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+void free_device(fe_space* s) {
+  void* ptrs[] = {s->d_xv, s->d_w, s->d_xq, s->d_phi, s->d_dphi, s->d_dphi32, s->d_cell_dofs, s->d_row_ptr,
+                  s->d_col, s->d_cnt, s->d_code_ptr, s->d_codes, s->d_slot_ptr, s->d_slots, s->d_ke, s->d_fe,
+                  s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+}
+
+int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem, double nu,
+                  bool host_only, fe_space** out) {
+  if (!out) return fail(FE_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!mesh || mesh->n_cells < 0 || mesh->n_vertices < 0 || (mesh->n_cells > 0 && !mesh->cell_vertices) ||
+      (mesh->n_vertices > 0 && !mesh->coords))
+    return fail(FE_ERR_INVALID_ARG, "invalid mesh descriptor");
+  if (order < 1 || order > feasm::kMaxOrder) return fail(FE_ERR_INVALID_ARG, "order must be 1..3");
+  const int nq1d = quad_points_1d == 0 ? order + 1 : quad_points_1d;
+  if (nq1d < 1 || nq1d > feasm::kMaxQ1d) return fail(FE_ERR_INVALID_ARG, "quad_points_1d must be 0 or 1..6");
+  if (problem != FE_POISSON && problem != FE_ELASTICITY) return fail(FE_ERR_INVALID_ARG, "unknown problem");
+  if (problem == FE_ELASTICITY && !(nu >= 0.0 && nu < 0.5)) return fail(FE_ERR_INVALID_ARG, "nu must be in [0, 0.5)");
+  if (mesh->n_vertices > INT32_MAX) return fail(FE_ERR_UNSUPPORTED, "more than 2^31-1 vertices");
+  fe_space* s = new (std::nothrow) fe_space();
+  if (!s) return fail(FE_ERR_OOM, "host allocation failed");
+  s->order = order;
+  s->nq1d = nq1d;
+  s->problem = problem;
+  s->ncomp = problem == FE_ELASTICITY ? 3 : 1;
+  s->nu = nu;
+  s->n_cells = mesh->n_cells;
+  s->n_vertices = mesh->n_vertices;
+  s->host_only = host_only;
+  feasm::build_ref_tables(order, nq1d, &s->tab);
+  s->nb = s->tab.nb;
+  s->nq = s->tab.nq;
+  s->nl = s->ncomp * s->nb;
+  std::string err;
+  int rc;
+  try {
+    rc = feasm::build_host_setup(order, s->ncomp, mesh->n_cells, mesh->n_vertices, mesh->cell_vertices, &s->hs, &err);
+  } catch (const std::bad_alloc&) {
+    rc = FE_ERR_OOM;
+    err = "host allocation failed during setup";
+  }
+  if (rc) {
+    delete s;
+    return fail(rc, err);
+  }
+  if (!host_only) {
+    const long smem = feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP64, feasm::cells_per_block(s->nb));
+    if (smem < 0) {
+      delete s;
+      return fail(FE_ERR_UNSUPPORTED, "quadrature too large for one block at this order");
+    }
+    cudaError_t e = cudaGetDevice(&s->device);
+    std::vector<double> xv;
+    if (e == cudaSuccess) {
+      xv.resize(size_t(s->n_cells) * 24);
+      for (int64_t c = 0; c < s->n_cells; ++c)
+        for (int v = 0; v < 8; ++v)
+          for (int k = 0; k < 3; ++k)
+            xv[size_t(c) * 24 + v * 3 + k] = mesh->coords[3 * int64_t(mesh->cell_vertices[8 * c + v]) + k];
+    }
+    std::vector<float> dphi32(s->tab.dphi.begin(), s->tab.dphi.end());
+    const auto& hs = s->hs;
+    if (e == cudaSuccess) e = upload(&s->d_xv, xv.data(), xv.size());
+    if (e == cudaSuccess) e = upload(&s->d_w, s->tab.w.data(), s->tab.w.size());
+    if (e == cudaSuccess) e = upload(&s->d_xq, s->tab.xq.data(), s->tab.xq.size());
+    if (e == cudaSuccess) e = upload(&s->d_phi, s->tab.phi.data(), s->tab.phi.size());
+    if (e == cudaSuccess) e = upload(&s->d_dphi, s->tab.dphi.data(), s->tab.dphi.size());
+    if (e == cudaSuccess) e = upload(&s->d_dphi32, dphi32.data(), dphi32.size());
+    if (e == cudaSuccess) e = upload(&s->d_cell_dofs, hs.cell_dofs.data(), hs.cell_dofs.size());
+    if (e == cudaSuccess) e = upload(&s->d_row_ptr, hs.row_ptr.data(), hs.row_ptr.size());
+    if (e == cudaSuccess) e = upload(&s->d_col, hs.col.data(), hs.col.size());
+    if (e == cudaSuccess) e = upload(&s->d_cnt, hs.cnt.data(), hs.cnt.size());
+    if (e == cudaSuccess) e = upload(&s->d_code_ptr, hs.code_ptr.data(), hs.code_ptr.size());
+    if (e == cudaSuccess) e = upload(&s->d_codes, hs.codes.data(), hs.codes.size());
+    if (e == cudaSuccess) e = upload(&s->d_slot_ptr, hs.slot_ptr.data(), hs.slot_ptr.size());
+    if (e == cudaSuccess) e = upload(&s->d_slots, hs.slots.data(), hs.slots.size());
+    const size_t nke = size_t(s->n_cells) * s->nl * s->nl;
+    if (e == cudaSuccess && nke) e = cudaMalloc(&s->d_ke, nke * sizeof(double));
+    if (e == cudaSuccess && s->n_cells) e = cudaMalloc(&s->d_fe, size_t(s->n_cells) * s->nl * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(s->d_err, 0, sizeof(int));
+    s->n_partials = int((s->n_cells + 127) / 128) + 1;
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_partials, size_t(s->n_partials) * sizeof(double));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+      free_device(s);
+      delete s;
+      return cuda_fail(e, "fe_space_create upload");
+    }
+    // the large host arrays are no longer needed (cell_dofs, row_ptr and col are kept for inspection)
+    std::vector<uint8_t>().swap(s->hs.cnt);
+    std::vector<uint16_t>().swap(s->hs.codes);
+    std::vector<int64_t>().swap(s->hs.code_ptr);
+    std::vector<int32_t>().swap(s->hs.slots);
+  }
+  *out = s;
+  return FE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* fe_last_error(void) { return g_last_error.c_str(); }
+
+int fe_space_create(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem, double nu,
+                    fe_space** out) {
+  return create_common(mesh, order, quad_points_1d, problem, nu, false, out);
+}
+
+int fe_space_create_host(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem, double nu,
+                         fe_space** out) {
+  return create_common(mesh, order, quad_points_1d, problem, nu, true, out);
+}
+
+int fe_space_sizes(const fe_space* s, int64_t* n_dofs, int64_t* nnz, int64_t* n_cells, int64_t* n_contrib) {
+  if (!s) return fail(FE_ERR_INVALID_ARG, "space is NULL");
+  if (n_dofs) *n_dofs = s->hs.n_dofs;
+  if (nnz) *nnz = s->hs.nnz;
+  if (n_cells) *n_cells = s->n_cells;
+  if (n_contrib) *n_contrib = s->hs.n_contrib;
+  return FE_OK;
+}
+
+int fe_space_cell_dofs_host(const fe_space* s, int32_t* cell_dofs) {
+  if (!s || !cell_dofs) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(cell_dofs, s->hs.cell_dofs.data(), s->hs.cell_dofs.size() * sizeof(int32_t));
+  return FE_OK;
+}
+
+int fe_space_csr_pattern_host(const fe_space* s, int64_t* row_ptr, int32_t* col_idx) {
+  if (!s || !row_ptr || (!col_idx && s->hs.nnz)) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(row_ptr, s->hs.row_ptr.data(), s->hs.row_ptr.size() * sizeof(int64_t));
+  if (s->hs.nnz) std::memcpy(col_idx, s->hs.col.data(), s->hs.col.size() * sizeof(int32_t));
+  return FE_OK;
+}
+
+int fe_space_permutation_host(const fe_space* s, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
+                              int64_t* slot_ptr, int32_t* slots) {
+  if (!s || !cnt || !code_ptr || !codes || !slot_ptr || !slots) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+  if (!s->host_only) return fail(FE_ERR_INVALID_ARG, "the permutation is kept on the host only for host-only spaces");
+  const auto& hs = s->hs;
+  std::memcpy(cnt, hs.cnt.data(), hs.cnt.size());
+  std::memcpy(code_ptr, hs.code_ptr.data(), hs.code_ptr.size() * sizeof(int64_t));
+  std::memcpy(codes, hs.codes.data(), hs.codes.size() * sizeof(uint16_t));
+  std::memcpy(slot_ptr, hs.slot_ptr.data(), hs.slot_ptr.size() * sizeof(int64_t));
+  std::memcpy(slots, hs.slots.data(), hs.slots.size() * sizeof(int32_t));
+  return FE_OK;
+}
+
+int fe_space_csr_pattern(const fe_space* s, int64_t* row_ptr, int32_t* col_idx, void* stream) {
+  if (!s || !row_ptr || (!col_idx && s->hs.nnz)) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+  if (s->host_only) return fail(FE_ERR_INVALID_ARG, "host-only space");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FE_CUDA(cudaMemcpyAsync(row_ptr, s->d_row_ptr, (s->hs.n_dofs + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+  if (s->hs.nnz)
+    FE_CUDA(cudaMemcpyAsync(col_idx, s->d_col, s->hs.nnz * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return FE_OK;
+}
+
+static int check_compute_space(const fe_space* s) {
+  if (!s) return fail(FE_ERR_INVALID_ARG, "space is NULL");
+  if (s->host_only) return fail(FE_ERR_INVALID_ARG, "host-only space cannot compute");
+  return FE_OK;
+}
+
+int fe_assemble(fe_space* s, const double* coefficients, const double* body_force, double* csr_values, double* rhs,
+                fe_precision prec, void* stream) {
+  return fe_assemble_ex(s, coefficients, body_force, csr_values, rhs, prec, stream, nullptr);
+}
+
+int fe_assemble_ex(fe_space* s, const double* coefficients, const double* body_force, double* csr_values,
+                   double* rhs, fe_precision prec, void* stream, void* event_mid) {
+  if (int rc = check_compute_space(s)) return rc;
+  if (prec != FE_PREC_FP64 && prec != FE_PREC_FP32 && prec != FE_PREC_BF16)
+    return fail(FE_ERR_INVALID_ARG, "unknown precision");
+  if ((s->n_cells && !coefficients) || (s->hs.nnz && !csr_values))
+    return fail(FE_ERR_INVALID_ARG, "NULL coefficients or csr_values");
+  if (rhs && !body_force) return fail(FE_ERR_INVALID_ARG, "rhs requested without body_force");
+  double f[3] = {0.0, 0.0, 0.0};
+  if (body_force)
+    for (int k = 0; k < s->ncomp; ++k) f[k] = body_force[k];
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  FE_CUDA(feasm::launch_cell_integration(s, coefficients, f, prec, st));
+  if (event_mid) FE_CUDA(cudaEventRecord(static_cast<cudaEvent_t>(event_mid), st));
+  FE_CUDA(feasm::launch_scatter(s, prec, csr_values, rhs, st));
+  return FE_OK;
+}
+
+int fe_assemble_host(fe_space* s, const double* coefficients, const double* body_force, double* csr_values,
+                     double* rhs, fe_precision prec, void* stream) {
+  if (int rc = check_compute_space(s)) return rc;
+  if ((s->n_cells && !coefficients) || (s->hs.nnz && !csr_values))
+    return fail(FE_ERR_INVALID_ARG, "NULL coefficients or csr_values");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!s->d_stage_coef) {
+    FE_CUDA(cudaMalloc(&s->d_stage_coef, std::max<int64_t>(1, s->n_cells) * sizeof(double)));
+    FE_CUDA(cudaMalloc(&s->d_stage_vals, std::max<int64_t>(1, s->hs.nnz) * sizeof(double)));
+    FE_CUDA(cudaMalloc(&s->d_stage_rhs, std::max<int64_t>(1, s->hs.n_dofs) * sizeof(double)));
+  }
+  FE_CUDA(cudaMemcpyAsync(s->d_stage_coef, coefficients, s->n_cells * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = fe_assemble(s, s->d_stage_coef, body_force, s->d_stage_vals, rhs ? s->d_stage_rhs : nullptr, prec, stream);
+  if (rc) return rc;
+  FE_CUDA(cudaMemcpyAsync(csr_values, s->d_stage_vals, s->hs.nnz * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (rhs) FE_CUDA(cudaMemcpyAsync(rhs, s->d_stage_rhs, s->hs.n_dofs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaStreamSynchronize(st));
+  return FE_OK;
+}
+
+int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients, double grad_scale,
+                        double* dc_dcoef, double* compliance, fe_precision prec, void* stream) {
+  if (int rc = check_compute_space(s)) return rc;
+  if (s->n_cells && (!u || !dc_dcoef)) return fail(FE_ERR_INVALID_ARG, "NULL u or dc_dcoef");
+  if (compliance && !coefficients) return fail(FE_ERR_INVALID_ARG, "compliance requested without coefficients");
+  if (prec != FE_PREC_FP64 && prec != FE_PREC_FP32) return fail(FE_ERR_INVALID_ARG, "adjoint precision must be FP64 or FP32");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (s->n_cells == 0) {
+    if (compliance) FE_CUDA(cudaMemsetAsync(compliance, 0, sizeof(double), st));
+    return FE_OK;
+  }
+  FE_CUDA(feasm::launch_adjoint(s, u, coefficients, grad_scale, dc_dcoef, compliance, prec, st));
+  return FE_OK;
+}
+
+int fe_status(fe_space* s, void* stream) {
+  if (int rc = check_compute_space(s)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int h = 0;
+  FE_CUDA(cudaMemcpyAsync(&h, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FE_CUDA(cudaStreamSynchronize(st));
+  FE_CUDA(cudaMemsetAsync(s->d_err, 0, sizeof(int), st));
+  FE_CUDA(cudaStreamSynchronize(st));
+  if (h & feasm::kErrNegJacobian) return fail(FE_ERR_NEG_JACOBIAN, "non-positive Jacobian determinant at a quadrature point");
+  if (h & feasm::kErrTimeout) return fail(FE_ERR_TIMEOUT, "a bounded device wait gave up");
+  return FE_OK;
+}
+
+void fe_space_destroy(fe_space* s) {
+  if (!s) return;
+  if (!s->host_only) free_device(s);
+  delete s;
+}
+
+}  // extern "C"

@@ -1,0 +1,81 @@
+// Internal data structures of libfeasm: the FE space (host setup products and
+// their device copies) and the host-side setup routines.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/feasm.h"
+
+namespace feasm {
+
+constexpr int kMaxOrder = 3;
+constexpr int kMaxQ1d = 6;
+constexpr int kMaxSlots = 255;  // cells around one DOF (8 bits of a code)
+
+// Reference tables of the Q_p element at a tensor Gauss-Legendre rule on
+// [0,1]^3. Point q = q0 + n q1 + n^2 q2, node a = a0 + (p+1) a1 + (p+1)^2 a2.
+struct RefTables {
+  int p = 0, nq1d = 0, nb = 0, nq = 0;
+  std::vector<double> w;      // [nq]
+  std::vector<double> xq;     // [nq][3]
+  std::vector<double> phi;    // [nq][nb]
+  std::vector<double> dphi;   // [nq][nb][3]
+};
+
+// Products of the host setup of one space.
+struct HostSetup {
+  int64_t n_dofs = 0, nnz = 0, n_contrib = 0;
+  int max_slots = 0;
+  std::vector<int32_t> cell_dofs;   // [n_cells][nl]
+  std::vector<int64_t> row_ptr;     // [n_dofs+1]
+  std::vector<int32_t> col;         // [nnz]
+  std::vector<uint8_t> cnt;         // [nnz] contributions per nonzero
+  std::vector<int64_t> code_ptr;    // [n_dofs+1] first code of each row
+  std::vector<uint16_t> codes;      // [n_contrib] (slot << 8) | local column
+  std::vector<int64_t> slot_ptr;    // [n_dofs+1]
+  std::vector<int32_t> slots;       // [n_cells*nl] e*nl + local row, cells ascending
+};
+
+void build_ref_tables(int p, int nq1d, RefTables* t);
+// Returns 0 or an FE_ERR_* code (message in *err).
+int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
+                     HostSetup* hs, std::string* err);
+
+}  // namespace feasm
+
+struct fe_space {
+  int order = 0, nq1d = 0, problem = 0, ncomp = 1, nb = 0, nq = 0, nl = 0;
+  double nu = 0.0;
+  int64_t n_cells = 0, n_vertices = 0;
+  bool host_only = false;
+  int device = 0;
+  feasm::RefTables tab;
+  feasm::HostSetup hs;  // host arrays (pattern arrays are released after upload)
+  bool host_pattern_kept = true;
+  // device data
+  double* d_xv = nullptr;        // [n_cells][8][3] cell vertex coordinates
+  double* d_w = nullptr;         // [nq]
+  double* d_xq = nullptr;        // [nq][3]
+  double* d_phi = nullptr;       // [nq][nb]
+  double* d_dphi = nullptr;      // [nq][nb][3]
+  float* d_dphi32 = nullptr;     // [nq][nb][3]
+  int32_t* d_cell_dofs = nullptr;
+  int64_t* d_row_ptr = nullptr;
+  int32_t* d_col = nullptr;
+  uint8_t* d_cnt = nullptr;
+  int64_t* d_code_ptr = nullptr;
+  uint16_t* d_codes = nullptr;
+  int64_t* d_slot_ptr = nullptr;
+  int32_t* d_slots = nullptr;
+  void* d_ke = nullptr;          // cell matrices, [n_cells][nl][nl] FP64 or FP32
+  double* d_fe = nullptr;        // cell vectors [n_cells][nl]
+  int* d_err = nullptr;          // device error word
+  double* d_partials = nullptr;  // reduction scratch for the compliance
+  int n_partials = 0;
+  // staging buffers of fe_assemble_host
+  double* d_stage_coef = nullptr;
+  double* d_stage_vals = nullptr;
+  double* d_stage_rhs = nullptr;
+};

@@ -1,0 +1,524 @@
+// CUDA kernels of libfeasm (sm_103a): cell integration (geometry, physical
+// gradients, cell-matrix contraction, cell vectors), the deterministic
+// segmented scatter into CSR, and the compliance adjoint.
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
+#include "fe_launch.h"
+
+namespace feasm {
+
+constexpr int kCellThreads = 256;
+constexpr int kScatterWarps = 8;
+
+int cells_per_block(int nb) {
+  const int pairs = nb * nb;
+  return pairs >= kCellThreads ? 1 : kCellThreads / pairs;
+}
+
+// Shared memory of k_cell: vertex coordinates [cpb][24], trilinear
+// coefficients [cpb][21], per-point geometry [cpb][nq][11] (cofactor matrix,
+// w/det, w*det) in FP64, and the cofactor-scaled reference gradients
+// [cpb][nq][3][nb] in the operand type.
+long cell_smem_bytes(int nb, int nq, fe_precision prec, int cpb) {
+  const long tsz = prec == FE_PREC_FP64 ? 8 : 4;
+  const long bytes = long(cpb) * (24 + 21) * 8 + long(cpb) * nq * 11 * 8 + long(cpb) * nq * 3 * nb * tsz;
+  return bytes <= 227 * 1024 ? bytes : -1;
+}
+
+struct CellParams {
+  int64_t n_cells;
+  int nq, cpb;
+  const double* xv;
+  const double* w;
+  const double* xq;
+  const double* phi;
+  const double* dphi;
+  const double* coef;
+  double f[3];
+  double lam_hat, mu_hat;
+  void* ke;
+  double* fe;
+  int* err;
+};
+
+__device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// Trilinear map Phi(x) = a0 + a1 x + a2 y + a3 z + a4 xy + a5 xz + a6 yz + a7 xyz
+// (the Q1 geometry of the cell written in monomials). Its Jacobian at a
+// point, the cofactor matrix and the determinant, all FP64:
+//   J[k][d] = dPhi_k / dxhat_d,  cof[k][d] = cofactor of J[k][d],
+//   det J = sum_d J[0][d] cof[0][d],  J^{-T} = cof / det.
+__device__ __forceinline__ void geometry_at(const double* a, double x, double y, double z, double cof[9],
+                                            double* det) {
+  double J[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const double a1 = a[0 + k], a2 = a[3 + k], a3 = a[6 + k], a4 = a[9 + k], a5 = a[12 + k], a6 = a[15 + k],
+                 a7 = a[18 + k];
+    J[k][0] = a1 + a4 * y + a5 * z + a7 * (y * z);
+    J[k][1] = a2 + a4 * x + a6 * z + a7 * (x * z);
+    J[k][2] = a3 + a5 * x + a6 * y + a7 * (x * y);
+  }
+  cof[0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+  cof[1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+  cof[2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+  cof[3] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+  cof[4] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+  cof[5] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+  cof[6] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+  cof[7] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+  cof[8] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  *det = J[0][0] * cof[0] + J[0][1] * cof[1] + J[0][2] * cof[2];
+}
+
+// Monomial coefficients a1..a7 (3 components each) from the 8 vertices in
+// x-fastest order.
+__device__ __forceinline__ void trilinear_coefficients(const double* x, int k, double* a) {
+  const double x0 = x[k], x1 = x[3 + k], x2 = x[6 + k], x3 = x[9 + k], x4 = x[12 + k], x5 = x[15 + k],
+               x6 = x[18 + k], x7 = x[21 + k];
+  const double d10 = x1 - x0, d32 = x3 - x2, d54 = x5 - x4, d76 = x7 - x6, d20 = x2 - x0, d64 = x6 - x4;
+  a[0 + k] = d10;
+  a[3 + k] = d20;
+  a[6 + k] = x4 - x0;
+  a[9 + k] = d32 - d10;
+  a[12 + k] = d54 - d10;
+  a[15 + k] = d64 - d20;
+  a[18 + k] = (d76 - d54) - (d32 - d10);
+}
+
+// One block integrates `cpb` cells. Steps (paper: Eq. fematrix, Eq.
+// shape_grad, the element loop of the Listing
+// "element_matrix_entries_computation"):
+//   1. geometry at every quadrature point (FP64),
+//   2. cofactor gradients gh_a = cof(J) gradhat(phihat_a), so that
+//      grad(phi_a) = gh_a / det J,
+//   3. G^{ij}_{ab} = sum_q (w_q / det J_q) gh_{a,i} gh_{b,j}, and
+//      Poisson   K_ab = kappa sum_i G^{ii}_{ab},
+//      elasticity K_(a,i),(b,j) = E (lam^ G^{ij}_ab + mu^ G^{ji}_ab + mu^ d_ij sum_k G^{kk}_ab),
+//   4. cell vector f_(a,i) = f_i sum_q w_q det J_q phihat_a(x_q).
+// PREC 0: FP64 throughout. PREC 1: FP32 gradients and contraction. PREC 2:
+// BF16-rounded operands with FP32 products and sums.
+template <int P, int NC, int PREC>
+__global__ void __launch_bounds__(kCellThreads) k_cell(CellParams prm) {
+  constexpr int NB = (P + 1) * (P + 1) * (P + 1);
+  constexpr int NL = NC * NB;
+  using T = typename std::conditional<PREC == 0, double, float>::type;
+  extern __shared__ __align__(16) double smem[];
+  const int cpb = prm.cpb, nq = prm.nq;
+  double* sx = smem;
+  double* sa = sx + cpb * 24;
+  double* geo = sa + cpb * 21;
+  T* g = reinterpret_cast<T*>(geo + cpb * nq * 11);
+  const int64_t e0 = int64_t(blockIdx.x) * cpb;
+  const int tid = threadIdx.x;
+  const int ncell = int(prm.n_cells - e0 < cpb ? prm.n_cells - e0 : cpb);
+
+  for (int i = tid; i < ncell * 24; i += blockDim.x) sx[i] = prm.xv[e0 * 24 + i];
+  __syncthreads();
+  for (int i = tid; i < ncell * 3; i += blockDim.x) trilinear_coefficients(sx + (i / 3) * 24, i % 3, sa + (i / 3) * 21);
+  __syncthreads();
+  for (int i = tid; i < ncell * nq; i += blockDim.x) {
+    const int c = i / nq, q = i % nq;
+    double cof[9], det;
+    geometry_at(sa + c * 21, prm.xq[3 * q], prm.xq[3 * q + 1], prm.xq[3 * q + 2], cof, &det);
+    if (!(det > 0.0)) atomicOr(prm.err, kErrNegJacobian);
+    const double wq = prm.w[q];
+    double* gm = geo + size_t(i) * 11;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) gm[t] = cof[t];
+    gm[9] = wq / det;
+    gm[10] = wq * det;
+  }
+  __syncthreads();
+  for (int i = tid; i < ncell * nq * NB; i += blockDim.x) {
+    const int a = i % NB, cq = i / NB, q = cq % nq;
+    const double* gm = geo + size_t(cq) * 11;
+    const double* dp = prm.dphi + (size_t(q) * NB + a) * 3;
+    T* gg = g + size_t(cq) * 3 * NB;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (PREC == 0) {
+        gg[k * NB + a] = gm[3 * k] * dp[0] + gm[3 * k + 1] * dp[1] + gm[3 * k + 2] * dp[2];
+      } else {
+        float v = float(gm[3 * k]) * float(dp[0]);
+        v = fmaf(float(gm[3 * k + 1]), float(dp[1]), v);
+        v = fmaf(float(gm[3 * k + 2]), float(dp[2]), v);
+        gg[k * NB + a] = T(v);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < ncell * NB * NB; i += blockDim.x) {
+    const int c = i / (NB * NB), ab = i % (NB * NB), a = ab / NB, b = ab % NB;
+    const T* gc = g + size_t(c) * nq * 3 * NB;
+    const double* gm = geo + size_t(c) * nq * 11;
+    const int64_t e = e0 + c;
+    const double coef = prm.coef[e];
+    if (NC == 1) {
+      T acc = T(0);
+      for (int q = 0; q < nq; ++q) {
+        const T* gq = gc + size_t(q) * 3 * NB;
+        const T s = T(gm[q * 11 + 9]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          T ga = s * gq[k * NB + a], gb = gq[k * NB + b];
+          if (PREC == 2) { ga = round_bf16(ga); gb = round_bf16(gb); }
+          acc += ga * gb;
+        }
+      }
+      T* K = reinterpret_cast<T*>(prm.ke) + e * NL * NL;
+      K[a * NB + b] = T(coef) * acc;
+    } else {
+      T G[3][3];
+#pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] = T(0);
+      for (int q = 0; q < nq; ++q) {
+        const T* gq = gc + size_t(q) * 3 * NB;
+        const T s = T(gm[q * 11 + 9]);
+        T ga[3], gb[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          ga[k] = s * gq[k * NB + a];
+          gb[k] = gq[k * NB + b];
+          if (PREC == 2) { ga[k] = round_bf16(ga[k]); gb[k] = round_bf16(gb[k]); }
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+          for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] += ga[i2] * gb[j2];
+      }
+      const T lh = T(prm.lam_hat), mh = T(prm.mu_hat), E = T(coef);
+      const T tr = G[0][0] + G[1][1] + G[2][2];
+      T* K = reinterpret_cast<T*>(prm.ke) + e * NL * NL;
+#pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2) {
+          T v = lh * G[i2][j2] + mh * G[j2][i2];
+          if (i2 == j2) v += mh * tr;
+          K[size_t(i2 * NB + a) * NL + j2 * NB + b] = E * v;
+        }
+    }
+  }
+  for (int i = tid; i < ncell * NB; i += blockDim.x) {
+    const int c = i / NB, a = i % NB;
+    const double* gm = geo + size_t(c) * nq * 11;
+    double f = 0.0;
+    for (int q = 0; q < nq; ++q) f += gm[q * 11 + 10] * prm.phi[size_t(q) * NB + a];
+    double* fe = prm.fe + (e0 + c) * NL;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) fe[k * NB + a] = prm.f[k] * f;
+  }
+}
+
+template <int P, int NC, int PREC>
+static cudaError_t launch_cell_t(const fe_space* s, const CellParams& prm, long smem, cudaStream_t st) {
+  auto kern = k_cell<P, NC, PREC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  const int64_t blocks = (s->n_cells + prm.cpb - 1) / prm.cpb;
+  kern<<<dim3(unsigned(blocks)), kCellThreads, size_t(smem), st>>>(prm);
+  return cudaGetLastError();
+}
+
+template <int P, int NC>
+static cudaError_t launch_cell_p(const fe_space* s, const CellParams& prm, long smem, fe_precision prec,
+                                 cudaStream_t st) {
+  switch (prec) {
+    case FE_PREC_FP64: return launch_cell_t<P, NC, 0>(s, prm, smem, st);
+    case FE_PREC_FP32: return launch_cell_t<P, NC, 1>(s, prm, smem, st);
+    default: return launch_cell_t<P, NC, 2>(s, prm, smem, st);
+  }
+}
+
+cudaError_t launch_cell_integration(const fe_space* s, const double* coef, const double force[3],
+                                    fe_precision prec, cudaStream_t st) {
+  if (s->n_cells == 0) return cudaSuccess;
+  CellParams prm;
+  prm.n_cells = s->n_cells;
+  prm.nq = s->nq;
+  prm.cpb = cells_per_block(s->nb);
+  prm.xv = s->d_xv;
+  prm.w = s->d_w;
+  prm.xq = s->d_xq;
+  prm.phi = s->d_phi;
+  prm.dphi = s->d_dphi;
+  prm.coef = coef;
+  for (int k = 0; k < 3; ++k) prm.f[k] = force[k];
+  prm.lam_hat = s->nu / ((1.0 + s->nu) * (1.0 - 2.0 * s->nu));
+  prm.mu_hat = 1.0 / (2.0 * (1.0 + s->nu));
+  prm.ke = s->d_ke;
+  prm.fe = s->d_fe;
+  prm.err = s->d_err;
+  const long smem = cell_smem_bytes(s->nb, s->nq, prec, prm.cpb);
+  if (smem < 0) return cudaErrorInvalidConfiguration;
+  const int key = s->order * 10 + s->ncomp;
+  switch (key) {
+    case 11: return launch_cell_p<1, 1>(s, prm, smem, prec, st);
+    case 13: return launch_cell_p<1, 3>(s, prm, smem, prec, st);
+    case 21: return launch_cell_p<2, 1>(s, prm, smem, prec, st);
+    case 23: return launch_cell_p<2, 3>(s, prm, smem, prec, st);
+    case 31: return launch_cell_p<3, 1>(s, prm, smem, prec, st);
+    case 33: return launch_cell_p<3, 3>(s, prm, smem, prec, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic scatter (Eq. assembly): one warp per CSR row. The row's cells
+// ("slots", ascending) are staged in shared memory as offsets of their cell
+// matrix rows. Lane l owns nonzero k = k0 + l of a 32-wide chunk; a warp
+// inclusive scan of the contribution counts gives each lane the start of its
+// contiguous segment of codes, and the lane sums its segment in FP64 in code
+// order (= ascending cell), then stores values[k] (coalesced across lanes).
+struct ScatterParams {
+  int64_t n_rows;
+  int nl;
+  const int64_t* row_ptr;
+  const uint8_t* cnt;
+  const int64_t* code_ptr;
+  const uint16_t* codes;
+  const int64_t* slot_ptr;
+  const int32_t* slots;
+  const void* ke;
+  const double* fe;
+  double* values;
+  double* rhs;
+};
+
+template <typename TK>
+__global__ void __launch_bounds__(kScatterWarps * 32) k_scatter(ScatterParams p) {
+  __shared__ int64_t sbase[kScatterWarps][kMaxSlots + 1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const TK* ke = reinterpret_cast<const TK*>(p.ke);
+  for (int64_t r = int64_t(blockIdx.x) * kScatterWarps + warp; r < p.n_rows;
+       r += int64_t(gridDim.x) * kScatterWarps) {
+    const int64_t s0 = p.slot_ptr[r];
+    const int ns = int(p.slot_ptr[r + 1] - s0);
+    for (int s = lane; s < ns; s += 32) sbase[warp][s] = int64_t(p.slots[s0 + s]) * p.nl;
+    __syncwarp();
+    if (p.rhs != nullptr && lane == 0) {
+      double f = 0.0;
+      for (int s = 0; s < ns; ++s) f += p.fe[p.slots[s0 + s]];
+      p.rhs[r] = f;
+    }
+    const int64_t k0 = p.row_ptr[r], k1 = p.row_ptr[r + 1];
+    int64_t c = p.code_ptr[r];
+    for (int64_t kb = k0; kb < k1; kb += 32) {
+      const int64_t k = kb + lane;
+      const int n = k < k1 ? int(p.cnt[k]) : 0;
+      int incl = n;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += t;
+      }
+      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const uint16_t* cp = p.codes + c + (incl - n);
+      double v = 0.0;
+      for (int t = 0; t < n; ++t) {
+        const unsigned code = cp[t];
+        v += double(ke[sbase[warp][code >> 8] + (code & 255u)]);
+      }
+      if (k < k1) p.values[k] = v;
+      c += total;
+    }
+    __syncwarp();
+  }
+}
+
+cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st) {
+  if (s->hs.n_dofs == 0) return cudaSuccess;
+  ScatterParams p;
+  p.n_rows = s->hs.n_dofs;
+  p.nl = s->nl;
+  p.row_ptr = s->d_row_ptr;
+  p.cnt = s->d_cnt;
+  p.code_ptr = s->d_code_ptr;
+  p.codes = s->d_codes;
+  p.slot_ptr = s->d_slot_ptr;
+  p.slots = s->d_slots;
+  p.ke = s->d_ke;
+  p.fe = s->d_fe;
+  p.values = values;
+  p.rhs = rhs;
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
+  const int64_t need = (p.n_rows + kScatterWarps - 1) / kScatterWarps;
+  const int blocks = int(std::min<int64_t>(need, int64_t(nsm) * 8));
+  if (prec == FE_PREC_FP64)
+    k_scatter<double><<<blocks, kScatterWarps * 32, 0, st>>>(p);
+  else
+    k_scatter<float><<<blocks, kScatterWarps * 32, 0, st>>>(p);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Compliance adjoint: one thread per cell. For fixed u the sensitivity of
+// c = u^T A u to the cell coefficient is the cell energy of u per unit
+// coefficient, evaluated per quadrature point from grad u (Eq. fematrix,
+// Eq. shape_grad) without forming A^K:
+//   Poisson    |grad u|^2,
+//   elasticity lam^ (div u)^2 + 2 mu^ eps(u):eps(u),
+// times w_q det J_q. T is the arithmetic of the strain (FP64 or FP32); the
+// geometry and the sums over points are FP64.
+struct AdjParams {
+  int64_t n_cells;
+  int nq;
+  const double* xv;
+  const double* w;
+  const double* xq;
+  const double* dphi;
+  const int32_t* cell_dofs;
+  const double* u;
+  const double* coef;
+  double grad_scale, lam_hat, mu_hat;
+  double* g;
+  double* partials;
+  int* err;
+};
+
+constexpr int kAdjThreads = 128;
+
+template <int P, int NC, typename T>
+__global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjParams p) {
+  constexpr int NB = (P + 1) * (P + 1) * (P + 1);
+  constexpr int NL = NC * NB;
+  __shared__ double red[kAdjThreads];
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  double energy = 0.0;
+  if (e < p.n_cells) {
+    double x[24], a[21];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) x[i] = p.xv[e * 24 + i];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) trilinear_coefficients(x, k, a);
+    T ue[NL];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) ue[l] = T(p.u[p.cell_dofs[e * NL + l]]);
+    for (int q = 0; q < p.nq; ++q) {
+      double cof[9], det;
+      geometry_at(a, p.xq[3 * q], p.xq[3 * q + 1], p.xq[3 * q + 2], cof, &det);
+      if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
+      // reference gradient of each component of u
+      T gr[NC][3];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) gr[c][0] = gr[c][1] = gr[c][2] = T(0);
+      const double* dq = p.dphi + size_t(q) * NB * 3;
+#pragma unroll 4
+      for (int b = 0; b < NB; ++b) {
+        const T d0 = T(dq[3 * b]), d1 = T(dq[3 * b + 1]), d2 = T(dq[3 * b + 2]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const T uc = ue[c * NB + b];
+          gr[c][0] += uc * d0;
+          gr[c][1] += uc * d1;
+          gr[c][2] += uc * d2;
+        }
+      }
+      // physical gradient: (grad u)_{c,k} = sum_d gr[c][d] cof[k][d] / det
+      const double inv = 1.0 / det;
+      T cs[9];
+#pragma unroll
+      for (int t = 0; t < 9; ++t) cs[t] = T(cof[t] * inv);
+      T gu[NC][3];
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gu[c][k] = gr[c][0] * cs[3 * k] + gr[c][1] * cs[3 * k + 1] + gr[c][2] * cs[3 * k + 2];
+      double dens;
+      if (NC == 1) {
+        dens = double(gu[0][0] * gu[0][0] + gu[0][1] * gu[0][1] + gu[0][2] * gu[0][2]);
+      } else {
+        const T div = gu[0][0] + gu[1 % NC][1] + gu[2 % NC][2];
+        T ee = T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int l = 0; l < 3; ++l) {
+            const T eps = T(0.5) * (gu[k % NC][l] + gu[l % NC][k]);
+            ee += eps * eps;
+          }
+        dens = p.lam_hat * double(div * div) + 2.0 * p.mu_hat * double(ee);
+      }
+      energy += p.w[q] * det * dens;
+    }
+    p.g[e] = p.grad_scale * energy;
+  }
+  if (p.partials != nullptr) {
+    red[threadIdx.x] = (e < p.n_cells) ? p.coef[e] * energy : 0.0;
+    __syncthreads();
+    for (int off = kAdjThreads / 2; off > 0; off >>= 1) {
+      if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) p.partials[blockIdx.x] = red[0];
+  }
+}
+
+// Sums the per-block partials in a fixed order (one block).
+__global__ void k_sum_partials(const double* partials, int n, double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += 256) s += partials[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 128; off > 0; off >>= 1) {
+    if (threadIdx.x < off) red[threadIdx.x] += red[threadIdx.x + off];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
+template <int P, int NC>
+static cudaError_t launch_adj_p(const AdjParams& prm, bool fp32, int blocks, cudaStream_t st) {
+  if (fp32)
+    k_adjoint<P, NC, float><<<blocks, kAdjThreads, 0, st>>>(prm);
+  else
+    k_adjoint<P, NC, double><<<blocks, kAdjThreads, 0, st>>>(prm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint(const fe_space* s, const double* u, const double* coef, double grad_scale, double* g,
+                           double* compliance, fe_precision prec, cudaStream_t st) {
+  if (s->n_cells == 0) return cudaSuccess;
+  AdjParams prm;
+  prm.n_cells = s->n_cells;
+  prm.nq = s->nq;
+  prm.xv = s->d_xv;
+  prm.w = s->d_w;
+  prm.xq = s->d_xq;
+  prm.dphi = s->d_dphi;
+  prm.cell_dofs = s->d_cell_dofs;
+  prm.u = u;
+  prm.coef = coef;
+  prm.grad_scale = grad_scale;
+  prm.lam_hat = s->nu / ((1.0 + s->nu) * (1.0 - 2.0 * s->nu));
+  prm.mu_hat = 1.0 / (2.0 * (1.0 + s->nu));
+  prm.g = g;
+  prm.err = s->d_err;
+  const int blocks = int((s->n_cells + kAdjThreads - 1) / kAdjThreads);
+  const bool want_c = compliance != nullptr && coef != nullptr;
+  prm.partials = want_c ? s->d_partials : nullptr;
+  if (want_c && blocks > s->n_partials) return cudaErrorInvalidValue;
+  const bool fp32 = prec != FE_PREC_FP64;
+  cudaError_t e;
+  switch (s->order * 10 + s->ncomp) {
+    case 11: e = launch_adj_p<1, 1>(prm, fp32, blocks, st); break;
+    case 13: e = launch_adj_p<1, 3>(prm, fp32, blocks, st); break;
+    case 21: e = launch_adj_p<2, 1>(prm, fp32, blocks, st); break;
+    case 23: e = launch_adj_p<2, 3>(prm, fp32, blocks, st); break;
+    case 31: e = launch_adj_p<3, 1>(prm, fp32, blocks, st); break;
+    case 33: e = launch_adj_p<3, 3>(prm, fp32, blocks, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess || !want_c) return e;
+  k_sum_partials<<<1, 256, 0, st>>>(s->d_partials, blocks, compliance);
+  return cudaGetLastError();
+}
+
+}  // namespace feasm

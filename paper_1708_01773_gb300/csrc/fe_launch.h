@@ -1,0 +1,32 @@
+// Kernel launchers of libfeasm (defined in fe_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fe_internal.h"
+
+namespace feasm {
+
+// Error bits of the device error word.
+constexpr int kErrNegJacobian = 1;
+constexpr int kErrTimeout = 2;
+
+// Cell integration: geometry (FP64), physical gradients, cell-matrix
+// contraction in the arithmetic of `prec`, cell vectors (FP64). Writes
+// s->d_ke (FP64 for FE_PREC_FP64, FP32 otherwise) and s->d_fe.
+cudaError_t launch_cell_integration(const fe_space* s, const double* coef, const double force[3],
+                                    fe_precision prec, cudaStream_t st);
+
+// Deterministic scatter of the cell matrices/vectors into CSR values / RHS.
+cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st);
+
+// Compliance sensitivities and (optionally) the compliance.
+cudaError_t launch_adjoint(const fe_space* s, const double* u, const double* coef, double grad_scale,
+                           double* g, double* compliance, fe_precision prec, cudaStream_t st);
+
+// Dynamic shared memory needed by the cell-integration kernel (bytes), or -1
+// if the combination does not fit one block.
+long cell_smem_bytes(int nb, int nq, fe_precision prec, int cells_per_block);
+int cells_per_block(int nb);
+
+}  // namespace feasm

@@ -1,0 +1,349 @@
+// Host-side setup of an FE space (runs once, untimed): reference tables,
+// global DOF numbering, CSR sparsity pattern and the cell-to-nonzero assembly
+// permutation consumed by the scatter kernel.
+#include <algorithm>
+#include <functional>
+#include <cmath>
+#include <cstring>
+#include <thread>
+#include <unordered_map>
+
+#include "fe_internal.h"
+
+namespace feasm {
+
+// ---------------------------------------------------------------------------
+// Gauss-Legendre rule with n points on [0,1] (paper, Sect. "Numerical
+// integration": an n-point rule is exact up to degree 2n-1). Roots of P_n by
+// Newton's method from Chebyshev-like initial guesses; weights from P_n'.
+static void gauss_rule_01(int n, double* x, double* w) {
+  for (int k = 0; k < n; ++k) {
+    // k-th root counted from the left end of [-1,1]
+    double t = -std::cos(M_PI * (4.0 * k + 3.0) / (4.0 * n + 2.0));
+    double dp = 1.0;
+    for (int iter = 0; iter < 64; ++iter) {
+      double pm1 = 1.0, p = t;  // P_0, P_1
+      for (int m = 2; m <= n; ++m) {
+        double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm1) / m;
+        pm1 = p;
+        p = pn;
+      }
+      if (n == 1) { p = t; pm1 = 1.0; }
+      dp = n * (pm1 - t * p) / (1.0 - t * t);
+      double step = p / dp;
+      t -= step;
+      if (std::fabs(step) <= 1e-17) break;
+    }
+    // recompute the derivative at the converged root
+    double pm1 = 1.0, p = t;
+    for (int m = 2; m <= n; ++m) {
+      double pn = ((2.0 * m - 1.0) * t * p - (m - 1.0) * pm1) / m;
+      pm1 = p;
+      p = pn;
+    }
+    if (n == 1) pm1 = 1.0;
+    dp = n * (pm1 - t * p) / (1.0 - t * t);
+    x[k] = 0.5 * (1.0 + t);
+    w[k] = 1.0 / ((1.0 - t * t) * dp * dp);  // (2 / ((1-t^2) P_n'^2)) / 2
+  }
+}
+
+// Lagrange polynomials of order p on the nodes 0, 1/p, ..., 1 (Eq. lagbas):
+// values and first derivatives at x, via barycentric weights.
+static void lagrange_01(int p, double x, double* val, double* der) {
+  double nodes[kMaxOrder + 1], bw[kMaxOrder + 1];
+  for (int m = 0; m <= p; ++m) nodes[m] = double(m) / p;
+  for (int m = 0; m <= p; ++m) {
+    double d = 1.0;
+    for (int s = 0; s <= p; ++s)
+      if (s != m) d *= nodes[m] - nodes[s];
+    bw[m] = 1.0 / d;
+  }
+  for (int m = 0; m <= p; ++m) {
+    double prod = 1.0, dsum = 0.0;
+    for (int s = 0; s <= p; ++s) {
+      if (s == m) continue;
+      // derivative of the running product: d(prod * (x - x_s)) = dsum*(x-x_s) + prod
+      dsum = dsum * (x - nodes[s]) + prod;
+      prod *= x - nodes[s];
+    }
+    val[m] = bw[m] * prod;
+    der[m] = bw[m] * dsum;
+  }
+}
+
+void build_ref_tables(int p, int nq1d, RefTables* t) {
+  t->p = p;
+  t->nq1d = nq1d;
+  const int n1 = p + 1;
+  t->nb = n1 * n1 * n1;
+  t->nq = nq1d * nq1d * nq1d;
+  double g[kMaxQ1d], gw[kMaxQ1d];
+  gauss_rule_01(nq1d, g, gw);
+  t->w.assign(t->nq, 0.0);
+  t->xq.assign(3 * t->nq, 0.0);
+  t->phi.assign(size_t(t->nq) * t->nb, 0.0);
+  t->dphi.assign(size_t(t->nq) * t->nb * 3, 0.0);
+  for (int q = 0; q < t->nq; ++q) {
+    const int qi[3] = {q % nq1d, (q / nq1d) % nq1d, q / (nq1d * nq1d)};
+    double lv[3][kMaxOrder + 1], ld[3][kMaxOrder + 1];
+    t->w[q] = gw[qi[0]] * gw[qi[1]] * gw[qi[2]];
+    for (int d = 0; d < 3; ++d) {
+      t->xq[3 * q + d] = g[qi[d]];
+      lagrange_01(p, g[qi[d]], lv[d], ld[d]);
+    }
+    for (int a = 0; a < t->nb; ++a) {
+      const int ai[3] = {a % n1, (a / n1) % n1, a / (n1 * n1)};
+      const double v0 = lv[0][ai[0]], v1 = lv[1][ai[1]], v2 = lv[2][ai[2]];
+      t->phi[size_t(q) * t->nb + a] = v0 * v1 * v2;
+      double* dp = &t->dphi[(size_t(q) * t->nb + a) * 3];
+      dp[0] = ld[0][ai[0]] * v1 * v2;
+      dp[1] = v0 * ld[1][ai[1]] * v2;
+      dp[2] = v0 * v1 * ld[2][ai[2]];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Global DOF numbering (paper, Sect. "Global DOF numbering generation",
+// list_dofs): cells in order; in each cell first the DOFs of nodes interior to
+// the cell, then the vefs (vertices, edges, faces; within a dimension by
+// extrusion bits then anchor bits), each vef's nodes in lexicographic order.
+// A node met before keeps the ids it got in its owner cell. Shared nodes are
+// identified by the vef's corner vertices and the node's integer bilinear
+// weights on them, which does not depend on how a cell orients the vef.
+
+namespace {
+
+struct NodeId {
+  int32_t corner[4];
+  int32_t weight[4];
+  int8_t dim;
+  bool operator==(const NodeId& o) const {
+    return dim == o.dim && std::memcmp(corner, o.corner, sizeof(corner)) == 0 &&
+           std::memcmp(weight, o.weight, sizeof(weight)) == 0;
+  }
+};
+
+struct NodeIdHash {
+  size_t operator()(const NodeId& k) const {
+    uint64_t h = 1469598103934665603ull ^ uint64_t(k.dim);
+    for (int i = 0; i < 4; ++i) {
+      h = (h ^ uint64_t(uint32_t(k.corner[i]))) * 1099511628211ull;
+      h = (h ^ uint64_t(uint32_t(k.weight[i]))) * 1099511628211ull;
+    }
+    return size_t(h ^ (h >> 29));
+  }
+};
+
+struct LocalNode {
+  int a;          // lexicographic index
+  int dim;        // dimension of the owning vef (3 = cell interior)
+  int ext, anc;   // extrusion and anchor bits of the owning vef
+  int alpha[3];
+};
+
+std::vector<LocalNode> local_nodes_in_visit_order(int p) {
+  const int n1 = p + 1;
+  std::vector<LocalNode> v;
+  for (int a = 0; a < n1 * n1 * n1; ++a) {
+    LocalNode ln{};
+    ln.a = a;
+    ln.alpha[0] = a % n1;
+    ln.alpha[1] = (a / n1) % n1;
+    ln.alpha[2] = a / (n1 * n1);
+    for (int d = 0; d < 3; ++d) {
+      const int al = ln.alpha[d];
+      if (al != 0 && al != p) { ln.ext |= 1 << d; ++ln.dim; }
+      if (al == p) ln.anc |= 1 << d;
+    }
+    v.push_back(ln);
+  }
+  auto rank = [](const LocalNode& n) { return n.dim == 3 ? -1 : n.dim; };
+  std::stable_sort(v.begin(), v.end(), [&](const LocalNode& x, const LocalNode& y) {
+    if (rank(x) != rank(y)) return rank(x) < rank(y);
+    if (x.ext != y.ext) return x.ext < y.ext;
+    if (x.anc != y.anc) return x.anc < y.anc;
+    return x.a < y.a;
+  });
+  return v;
+}
+
+NodeId node_identity(int p, const LocalNode& ln, const int32_t* cv) {
+  NodeId id;
+  std::memset(&id, 0, sizeof(id));
+  for (int i = 0; i < 4; ++i) id.corner[i] = -1;
+  id.dim = int8_t(ln.dim);
+  int n = 0;
+  // enumerate the 2^dim corners: free bits in the extruded directions
+  for (int c = 0; c < 8; ++c) {
+    if ((c & ~ln.ext & 7) != (ln.anc & ~ln.ext & 7)) continue;
+    int wgt = 1;
+    for (int d = 0; d < 3; ++d)
+      if (ln.ext >> d & 1) wgt *= (c >> d & 1) ? ln.alpha[d] : p - ln.alpha[d];
+    id.corner[n] = cv[c];
+    id.weight[n] = wgt;
+    ++n;
+  }
+  // canonical order: ascending vertex id
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (id.corner[j] < id.corner[i]) {
+        std::swap(id.corner[i], id.corner[j]);
+        std::swap(id.weight[i], id.weight[j]);
+      }
+  return id;
+}
+
+}  // namespace
+
+static int number_dofs(int p, int ncomp, int64_t n_cells, const int32_t* cv, std::vector<int32_t>* cell_dofs,
+                       int64_t* n_dofs, std::string* err) {
+  const int n1 = p + 1, nb = n1 * n1 * n1, nl = ncomp * nb;
+  const std::vector<LocalNode> visit = local_nodes_in_visit_order(p);
+  std::unordered_map<NodeId, int64_t, NodeIdHash> first_id;
+  first_id.reserve(size_t(n_cells) * (p == 1 ? 1 : 8) + 16);
+  cell_dofs->assign(size_t(n_cells) * nl, -1);
+  int64_t next = 0;
+  for (int64_t e = 0; e < n_cells; ++e) {
+    const int32_t* c = cv + 8 * e;
+    int32_t* out = cell_dofs->data() + size_t(e) * nl;
+    for (const LocalNode& ln : visit) {
+      int64_t base;
+      if (ln.dim == 3) {
+        base = next;
+        next += ncomp;
+      } else {
+        auto ins = first_id.emplace(node_identity(p, ln, c), next);
+        if (ins.second) next += ncomp;
+        base = ins.first->second;
+      }
+      for (int k = 0; k < ncomp; ++k) out[k * nb + ln.a] = int32_t(base + k);
+    }
+    if (next > INT32_MAX) {
+      *err = "more than 2^31-1 DOFs";
+      return FE_ERR_UNSUPPORTED;
+    }
+  }
+  *n_dofs = next;
+  return FE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Sparsity pattern and assembly permutation. Row r collects the cells around
+// DOF r ("slots", ascending cell id). Every pair (slot s, local column m) is a
+// contribution to nonzero (r, cell_dofs[e_s][m]); contributions are sorted by
+// column and, within one nonzero, by slot, i.e. by ascending cell. The code of
+// a contribution is (s << 8) | m; the scatter kernel reads
+// K^{e_s}[local row of r in e_s][m].
+static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body);
+
+int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
+                     HostSetup* hs, std::string* err) {
+  const int nb = (p + 1) * (p + 1) * (p + 1), nl = ncomp * nb;
+  for (int64_t i = 0; i < 8 * n_cells; ++i)
+    if (cell_vertices[i] < 0 || cell_vertices[i] >= n_vertices) {
+      *err = "cell_vertices entry out of range";
+      return FE_ERR_INVALID_ARG;
+    }
+  if (n_cells * nl > INT32_MAX) {
+    *err = "n_cells * n_loc exceeds int32";
+    return FE_ERR_UNSUPPORTED;
+  }
+  int rc = number_dofs(p, ncomp, n_cells, cell_vertices, &hs->cell_dofs, &hs->n_dofs, err);
+  if (rc) return rc;
+  const int64_t nd = hs->n_dofs;
+  const int64_t ninc = n_cells * nl;
+  // slots by counting sort (cell-major scan keeps cells ascending per row)
+  hs->slot_ptr.assign(nd + 1, 0);
+  for (int64_t i = 0; i < ninc; ++i) hs->slot_ptr[hs->cell_dofs[i] + 1]++;
+  int max_slots = 0;
+  for (int64_t r = 0; r < nd; ++r) max_slots = std::max<int64_t>(max_slots, hs->slot_ptr[r + 1]);
+  if (max_slots > kMaxSlots) {
+    *err = "more than 255 cells around one DOF";
+    return FE_ERR_UNSUPPORTED;
+  }
+  hs->max_slots = max_slots;
+  for (int64_t r = 0; r < nd; ++r) hs->slot_ptr[r + 1] += hs->slot_ptr[r];
+  hs->slots.assign(ninc, 0);
+  {
+    std::vector<int64_t> fill(hs->slot_ptr.begin(), hs->slot_ptr.end() - 1);
+    for (int64_t i = 0; i < ninc; ++i) hs->slots[fill[hs->cell_dofs[i]]++] = int32_t(i);
+  }
+  const int nthreads = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+  // pass 1: nonzeros per row (stamp arrays per thread)
+  std::vector<int64_t> row_nnz(nd, 0);
+  parallel_for(nd, nthreads, [&](int, int64_t r0, int64_t r1) {
+    std::vector<int32_t> stamp(nd, -1);
+    for (int64_t r = r0; r < r1; ++r) {
+      int64_t k = 0;
+      for (int64_t s = hs->slot_ptr[r]; s < hs->slot_ptr[r + 1]; ++s) {
+        const int64_t e = hs->slots[s] / nl;
+        const int32_t* dofs = hs->cell_dofs.data() + e * nl;
+        for (int m = 0; m < nl; ++m)
+          if (stamp[dofs[m]] != int32_t(r)) { stamp[dofs[m]] = int32_t(r); ++k; }
+      }
+      row_nnz[r] = k;
+    }
+  });
+  hs->row_ptr.assign(nd + 1, 0);
+  hs->code_ptr.assign(nd + 1, 0);
+  for (int64_t r = 0; r < nd; ++r) {
+    hs->row_ptr[r + 1] = hs->row_ptr[r] + row_nnz[r];
+    hs->code_ptr[r + 1] = hs->code_ptr[r] + (hs->slot_ptr[r + 1] - hs->slot_ptr[r]) * nl;
+  }
+  hs->nnz = hs->row_ptr[nd];
+  hs->n_contrib = hs->code_ptr[nd];
+  if (hs->nnz > (int64_t(1) << 40)) {
+    *err = "too many nonzeros";
+    return FE_ERR_UNSUPPORTED;
+  }
+  hs->col.assign(hs->nnz, 0);
+  hs->cnt.assign(hs->nnz, 0);
+  hs->codes.assign(hs->n_contrib, 0);
+  // pass 2: sorted contributions per row
+  parallel_for(nd, nthreads, [&](int, int64_t r0, int64_t r1) {
+    std::vector<uint64_t> keys;
+    keys.reserve(size_t(max_slots) * nl);
+    for (int64_t r = r0; r < r1; ++r) {
+      keys.clear();
+      const int64_t s0 = hs->slot_ptr[r], ns = hs->slot_ptr[r + 1] - s0;
+      for (int64_t s = 0; s < ns; ++s) {
+        const int64_t e = hs->slots[s0 + s] / nl;
+        const int32_t* dofs = hs->cell_dofs.data() + e * nl;
+        for (int m = 0; m < nl; ++m)
+          keys.push_back((uint64_t(uint32_t(dofs[m])) << 16) | (uint64_t(s) << 8) | uint64_t(m));
+      }
+      std::sort(keys.begin(), keys.end());
+      int64_t k = hs->row_ptr[r] - 1;
+      int64_t c = hs->code_ptr[r];
+      int64_t prev = -1;
+      for (uint64_t key : keys) {
+        const int64_t col = int64_t(key >> 16);
+        if (col != prev) {
+          ++k;
+          hs->col[k] = int32_t(col);
+          prev = col;
+        }
+        hs->cnt[k]++;
+        hs->codes[c++] = uint16_t(key & 0xffff);
+      }
+    }
+  });
+  return FE_OK;
+}
+
+static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body) {
+  if (n <= 0) return;
+  nthreads = int(std::max<int64_t>(1, std::min<int64_t>(nthreads, n / 1024 + 1)));
+  std::vector<std::thread> th;
+  const int64_t chunk = (n + nthreads - 1) / nthreads;
+  for (int t = 0; t < nthreads; ++t) {
+    const int64_t a = t * chunk, b = std::min(n, a + chunk);
+    if (a >= b) break;
+    th.emplace_back(body, t, a, b);
+  }
+  for (auto& x : th) x.join();
+}
+
+}  // namespace feasm

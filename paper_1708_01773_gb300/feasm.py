@@ -1,0 +1,274 @@
+"""Thin ctypes binding of libfeasm.so (the C ABI declared in include/feasm.h).
+
+Argument marshalling only: every step of integration and assembly runs in the
+library's CUDA kernels. Device buffers are torch tensors (their data_ptr() is
+passed through); the library never falls back to the CPU, and loading fails
+loudly when the shared library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libfeasm.so")
+
+FE_POISSON, FE_ELASTICITY = 0, 1
+FE_PREC_FP64, FE_PREC_FP32, FE_PREC_BF16 = 0, 1, 2
+PRECISIONS = {"fp64": FE_PREC_FP64, "fp32": FE_PREC_FP32, "bf16": FE_PREC_BF16}
+
+ERRORS = {
+    -1: "FE_ERR_INVALID_ARG", -2: "FE_ERR_CUDA", -3: "FE_ERR_OOM", -4: "FE_ERR_NEG_JACOBIAN",
+    -5: "FE_ERR_TIMEOUT", -6: "FE_ERR_UNSUPPORTED",
+}
+
+# every entry point declared in include/feasm.h
+EXPORTS = [
+    "fe_space_create", "fe_space_create_host", "fe_space_sizes", "fe_space_cell_dofs_host",
+    "fe_space_csr_pattern_host", "fe_space_permutation_host", "fe_space_csr_pattern", "fe_assemble", "fe_assemble_ex", "fe_assemble_host",
+    "fe_assemble_adjoint", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
+    "fe_batch_assemble", "fe_batch_destroy",
+]
+
+
+class FEError(RuntimeError):
+    def __init__(self, code: int, fn: str, msg: str):
+        super().__init__(f"{fn} failed: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class MeshDesc(ctypes.Structure):
+    _fields_ = [("n_vertices", ctypes.c_int64), ("coords", ctypes.c_void_p),
+                ("n_cells", ctypes.c_int64), ("cell_vertices", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Loads libfeasm.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1708_01773_gb300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, I64, D, V = ctypes.POINTER, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+        L.fe_space_create.argtypes = [P(MeshDesc), I, I, I, D, P(V)]
+        L.fe_space_create_host.argtypes = [P(MeshDesc), I, I, I, D, P(V)]
+        L.fe_space_sizes.argtypes = [V, P(I64), P(I64), P(I64), P(I64)]
+        L.fe_space_cell_dofs_host.argtypes = [V, V]
+        L.fe_space_csr_pattern_host.argtypes = [V, V, V]
+        L.fe_space_csr_pattern.argtypes = [V, V, V, V]
+        L.fe_space_permutation_host.argtypes = [V, V, V, V, V, V]
+        L.fe_assemble.argtypes = [V, V, V, V, V, I, V]
+        L.fe_assemble_host.argtypes = [V, V, V, V, V, I, V]
+        L.fe_assemble_ex.argtypes = [V, V, V, V, V, I, V, V]
+        L.fe_assemble_adjoint.argtypes = [V, V, V, D, V, V, I, V]
+        L.fe_status.argtypes = [V, V]
+        L.fe_space_destroy.argtypes = [V]
+        L.fe_space_destroy.restype = None
+        L.fe_last_error.argtypes = []
+        L.fe_last_error.restype = ctypes.c_char_p
+        L.fe_batch_create.argtypes = [V, I, I, P(V)]
+        L.fe_batch_assemble.argtypes = [V, V, V, V, V, I, V]
+        L.fe_batch_destroy.argtypes = [V]
+        L.fe_batch_destroy.restype = None
+        for n in EXPORTS:
+            if n not in ("fe_space_destroy", "fe_last_error", "fe_batch_destroy"):
+                getattr(L, n).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, fn: str):
+    if rc != 0:
+        raise FEError(rc, fn, lib().fe_last_error().decode())
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return 0
+    if hasattr(t, "data_ptr"):
+        return int(t.data_ptr())
+    return int(t.ctypes.data)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return stream
+    return int(stream.cuda_stream)
+
+
+def _mesh_desc(coords: np.ndarray, cell_vertices: np.ndarray):
+    coords = np.ascontiguousarray(coords, dtype=np.float64)
+    cv = np.ascontiguousarray(cell_vertices, dtype=np.int32)
+    d = MeshDesc(coords.shape[0], coords.ctypes.data, cv.shape[0], cv.ctypes.data)
+    return d, (coords, cv)
+
+
+def fe_space_create(coords, cell_vertices, order: int, quad_points_1d: int, problem: int, nu: float,
+                    host_only: bool = False) -> int:
+    d, keep = _mesh_desc(coords, cell_vertices)
+    out = ctypes.c_void_p()
+    fn = lib().fe_space_create_host if host_only else lib().fe_space_create
+    _check(fn(ctypes.byref(d), order, quad_points_1d, problem, float(nu), ctypes.byref(out)),
+           "fe_space_create")
+    del keep
+    return out.value
+
+
+def fe_space_sizes(space: int):
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(lib().fe_space_sizes(space, *[ctypes.byref(x) for x in v]), "fe_space_sizes")
+    return tuple(x.value for x in v)   # n_dofs, nnz, n_cells, n_contrib
+
+
+def fe_space_cell_dofs_host(space: int, n_cells: int, nl: int) -> np.ndarray:
+    out = np.zeros((n_cells, nl), dtype=np.int32)
+    _check(lib().fe_space_cell_dofs_host(space, out.ctypes.data), "fe_space_cell_dofs_host")
+    return out
+
+
+def fe_space_csr_pattern_host(space: int):
+    n_dofs, nnz, _, _ = fe_space_sizes(space)
+    rp = np.zeros(n_dofs + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    _check(lib().fe_space_csr_pattern_host(space, rp.ctypes.data, col.ctypes.data), "fe_space_csr_pattern_host")
+    return rp, col
+
+
+def fe_space_permutation_host(space: int):
+    n_dofs, nnz, n_cells, n_contrib = fe_space_sizes(space)
+    cnt = np.zeros(nnz, dtype=np.uint8)
+    code_ptr = np.zeros(n_dofs + 1, dtype=np.int64)
+    codes = np.zeros(n_contrib, dtype=np.uint16)
+    slot_ptr = np.zeros(n_dofs + 1, dtype=np.int64)
+    slots = np.zeros(int(slot_count(space)), dtype=np.int32)
+    _check(lib().fe_space_permutation_host(space, cnt.ctypes.data, code_ptr.ctypes.data, codes.ctypes.data,
+                                           slot_ptr.ctypes.data, slots.ctypes.data), "fe_space_permutation_host")
+    return cnt, code_ptr, codes, slot_ptr, slots
+
+
+def slot_count(space: int) -> int:
+    """Number of (cell, local DOF) incidences: n_contrib / n_loc."""
+    n_dofs, nnz, n_cells, n_contrib = fe_space_sizes(space)
+    nl = int(round((n_contrib / max(n_cells, 1)) ** 0.5))
+    return n_cells * nl
+
+
+def fe_space_csr_pattern(space: int, row_ptr, col_idx, stream=None):
+    _check(lib().fe_space_csr_pattern(space, _ptr(row_ptr), _ptr(col_idx), _stream(stream)), "fe_space_csr_pattern")
+
+
+def fe_assemble(space: int, coefficients, body_force, csr_values, rhs, prec: int, stream=None):
+    f = np.ascontiguousarray(np.resize(np.asarray(body_force, dtype=np.float64), 3))
+    _check(lib().fe_assemble(space, _ptr(coefficients), f.ctypes.data, _ptr(csr_values), _ptr(rhs), prec,
+                             _stream(stream)), "fe_assemble")
+
+
+def fe_assemble_ex(space: int, coefficients, body_force, csr_values, rhs, prec: int, stream, event_mid):
+    """fe_assemble that records the CUDA event handle `event_mid` between its two kernels."""
+    f = np.ascontiguousarray(np.resize(np.asarray(body_force, dtype=np.float64), 3))
+    _check(lib().fe_assemble_ex(space, _ptr(coefficients), f.ctypes.data, _ptr(csr_values), _ptr(rhs), prec,
+                                _stream(stream), int(event_mid)), "fe_assemble_ex")
+
+
+def fe_assemble_host(space: int, coefficients, body_force, csr_values, rhs, prec: int, stream=None):
+    f = np.ascontiguousarray(np.resize(np.asarray(body_force, dtype=np.float64), 3))
+    _check(lib().fe_assemble_host(space, _ptr(coefficients), f.ctypes.data, _ptr(csr_values), _ptr(rhs), prec,
+                                  _stream(stream)), "fe_assemble_host")
+
+
+def fe_assemble_adjoint(space: int, u, coefficients, grad_scale: float, dc_dcoef, compliance, prec: int,
+                        stream=None):
+    _check(lib().fe_assemble_adjoint(space, _ptr(u), _ptr(coefficients), float(grad_scale), _ptr(dc_dcoef),
+                                     _ptr(compliance), prec, _stream(stream)), "fe_assemble_adjoint")
+
+
+def fe_status(space: int, stream=None) -> int:
+    return int(lib().fe_status(space, _stream(stream)))
+
+
+def fe_space_destroy(space: int):
+    lib().fe_space_destroy(space)
+
+
+def fe_batch_create(spaces, cells_per_item: int = 0) -> int:
+    arr = (ctypes.c_void_p * len(spaces))(*spaces)
+    out = ctypes.c_void_p()
+    _check(lib().fe_batch_create(arr, len(spaces), cells_per_item, ctypes.byref(out)), "fe_batch_create")
+    return out.value
+
+
+def fe_batch_assemble(batch: int, coefficients, body_forces, csr_values, rhs, prec: int, stream=None):
+    n = len(coefficients)
+    cp = (ctypes.c_void_p * n)(*[_ptr(c) for c in coefficients])
+    vp = (ctypes.c_void_p * n)(*[_ptr(v) for v in csr_values])
+    rp = (ctypes.c_void_p * n)(*[_ptr(r) for r in rhs])
+    f = np.ascontiguousarray(np.concatenate([np.resize(np.asarray(b, dtype=np.float64), 3) for b in body_forces]))
+    _check(lib().fe_batch_assemble(batch, cp, f.ctypes.data, vp, rp, prec, _stream(stream)), "fe_batch_assemble")
+
+
+def fe_batch_destroy(batch: int):
+    lib().fe_batch_destroy(batch)
+
+
+class FESpace:
+    """Owns one fe_space handle built from a seeded workload (inputs.Problem)."""
+
+    def __init__(self, prob, host_only: bool = False):
+        self.prob = prob
+        self.handle = fe_space_create(prob.mesh.coords, prob.mesh.cell_vertices, prob.order, prob.quad_1d,
+                                      prob.problem, prob.nu, host_only=host_only)
+        self.n_dofs, self.nnz, self.n_cells, self.n_contrib = fe_space_sizes(self.handle)
+        self.nl = prob.ncomp * (prob.order + 1) ** 3
+
+    def cell_dofs(self) -> np.ndarray:
+        return fe_space_cell_dofs_host(self.handle, self.n_cells, self.nl)
+
+    def pattern_host(self):
+        return fe_space_csr_pattern_host(self.handle)
+
+    def pattern(self, device="cuda"):
+        import torch
+        rp = torch.empty(self.n_dofs + 1, dtype=torch.int64, device=device)
+        col = torch.empty(self.nnz, dtype=torch.int32, device=device)
+        fe_space_csr_pattern(self.handle, rp, col)
+        return rp, col
+
+    def assemble(self, coef, values=None, rhs=None, prec: str = "fp32", force=None, stream=None):
+        import torch
+        if values is None:
+            values = torch.empty(self.nnz, dtype=torch.float64, device=coef.device)
+        if rhs is None:
+            rhs = torch.empty(self.n_dofs, dtype=torch.float64, device=coef.device)
+        fe_assemble(self.handle, coef, self.prob.force if force is None else force, values, rhs,
+                    PRECISIONS[prec], stream)
+        return values, rhs
+
+    def adjoint(self, u, coef=None, grad_scale: float = 1.0, out=None, compliance=None, prec: str = "fp64",
+                stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.n_cells, dtype=torch.float64, device=u.device)
+        fe_assemble_adjoint(self.handle, u, coef, grad_scale, out, compliance, PRECISIONS[prec], stream)
+        return out
+
+    def status(self, stream=None) -> int:
+        return fe_status(self.handle, stream)
+
+    def close(self):
+        if self.handle:
+            fe_space_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

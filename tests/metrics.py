@@ -1,0 +1,53 @@
+"""Error metrics of the parity tests and the tolerances they use.
+
+Entry error (row scaled): max_ij |A_ij - A*_ij| / max_j |A*_ij|, so that entries
+that cancel to (near) zero do not blow up a relative measure. Energy error:
+max over seeded unit-RMS vectors (and, when positions are given, the linear
+fields) of |v^T (A - A*) v| / (v^T A* v). RHS and gradients: ||x - x*||_inf /
+||x*||_inf.
+
+Tolerances: the mixed FP32 form must stay within 1e-6 and the BF16 form within
+1e-2 of the FP64 oracle (the targets the method's precision plan states). The
+FP64 GPU path differs from the oracle only by summation order and by writing
+J^{-T} as cof(J)/det J: with at most a few hundred terms per entry, 1e-12 leaves
+ample room over FP64 rounding (~1e-16 per operation).
+"""
+import numpy as np
+
+TOL = {"fp64": 1e-12, "fp32": 1e-6, "bf16": 1e-2}
+
+
+def row_scaled_error(rp, col, val, val_ref):
+    """Both matrices share the CSR pattern (rp, col)."""
+    n = rp.size - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    rowmax = np.zeros(n)
+    np.maximum.at(rowmax, rows, np.abs(val_ref))
+    d = np.abs(val - val_ref) / np.maximum(rowmax[rows], 1e-300)
+    return float(d.max()) if d.size else 0.0
+
+
+def csr_matvec(rp, col, val, v):
+    n = rp.size - 1
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    out = np.zeros(n)
+    np.add.at(out, rows, val * v[col])
+    return out
+
+
+def energy_error(rp, col, val, val_ref, n_vec=8, seed=0, extra=()):
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    n = rp.size - 1
+    vs = [rng.standard_normal(n) for _ in range(n_vec)] + list(extra)
+    for v in vs:
+        num = abs(v @ csr_matvec(rp, col, val - val_ref, v))
+        den = abs(v @ csr_matvec(rp, col, val_ref, v))
+        if den > 0:
+            worst = max(worst, num / den)
+    return worst
+
+
+def vec_error(x, ref):
+    s = np.abs(ref).max()
+    return float(np.abs(x - ref).max() / s) if s > 0 else float(np.abs(x).max())

@@ -1,0 +1,239 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Small meshes are compared entry by entry (several tiles and a ragged tail per
+kernel); the paper-shaped full-size workloads are compared on sampled rows the
+oracle computes one by one, plus invariants that hold at any size.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from metrics import TOL, energy_error, row_scaled_error, vec_error
+from paper_1708_01773_gb300 import build, feasm, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    feasm.lib()
+
+
+def run(sp, prob, prec):
+    coef = torch.tensor(prob.coef, device="cuda")
+    vals, rhs = sp.assemble(coef, prec=prec)
+    torch.cuda.synchronize()
+    assert sp.status() == 0
+    return vals.cpu().numpy(), rhs.cpu().numpy()
+
+
+SMALL = [((3, 3, 3), 1, 0), ((3, 3, 3), 1, 1), ((3, 2, 3), 2, 0), ((3, 2, 2), 2, 1), ((2, 3, 2), 3, 0),
+         ((2, 2, 2), 3, 1), ((5, 1, 1), 2, 1)]
+
+
+@pytest.mark.parametrize("shape,p,problem", SMALL)
+def test_small_meshes_all_precisions(shape, p, problem):
+    prob = inputs.small_problem(shape, p, problem, seed=10 * p + problem)
+    cd, n = oracle.dof_numbering(prob.mesh, p, prob.ncomp)
+    rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob, cd, n)
+    sp = feasm.FESpace(prob)
+    rp, col = sp.pattern()
+    np.testing.assert_array_equal(rp.cpu().numpy(), rp_o)
+    np.testing.assert_array_equal(col.cpu().numpy(), col_o)
+    for prec in ("fp64", "fp32", "bf16"):
+        vals, rhs = run(sp, prob, prec)
+        e_inf = row_scaled_error(rp_o, col_o, vals, val_o)
+        e_en = energy_error(rp_o, col_o, vals, val_o)
+        assert e_inf <= TOL[prec], (prec, e_inf)
+        assert e_en <= TOL[prec], (prec, e_en)
+        assert vec_error(rhs, rhs_o) <= 1e-12
+    sp.close()
+
+
+def test_poisson_q1_8_full():
+    prob = inputs.poisson_q1_8()
+    rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob)
+    sp = feasm.FESpace(prob)
+    for prec in ("fp64", "fp32", "bf16"):
+        vals, rhs = run(sp, prob, prec)
+        assert row_scaled_error(rp_o, col_o, vals, val_o) <= TOL[prec]
+        assert energy_error(rp_o, col_o, vals, val_o) <= TOL[prec]
+        assert vec_error(rhs, rhs_o) <= 1e-12
+    sp.close()
+
+
+def test_bitwise_deterministic():
+    prob = inputs.small_problem((4, 3, 3), 2, 1, seed=3)
+    sp = feasm.FESpace(prob)
+    coef = torch.tensor(prob.coef, device="cuda")
+    for prec in ("fp64", "fp32", "bf16"):
+        a, ra = sp.assemble(coef, prec=prec)
+        b, rb = sp.assemble(coef, prec=prec)
+        assert torch.equal(a, b) and torch.equal(ra, rb)
+    sp.close()
+
+
+def sampled_rows(n, k=48, seed=0):
+    rng = np.random.default_rng(seed)
+    rows = np.unique(np.concatenate([[0, 1, 2, n // 3, n // 2, n - 2, n - 1], rng.integers(0, n, k)]))
+    return rows.astype(np.int64)
+
+
+def check_rows(prob, sp, vals, rhs, prec, rows):
+    cd = sp.cell_dofs()
+    ptr, col_o, val_o, rhs_o = oracle.assemble_rows(prob, rows, cd, sp.n_dofs)
+    rp, col = sp.pattern_host()
+    worst = 0.0
+    for q, r in enumerate(rows):
+        np.testing.assert_array_equal(col[rp[r]:rp[r + 1]], col_o[ptr[q]:ptr[q + 1]])
+        ref = val_o[ptr[q]:ptr[q + 1]]
+        got = vals[rp[r]:rp[r + 1]]
+        worst = max(worst, np.abs(got - ref).max() / np.abs(ref).max())
+    assert worst <= TOL[prec], (prec, worst)
+    assert np.abs(rhs[rows] - rhs_o).max() <= 1e-12 * max(np.abs(rhs_o).max(), 1e-300)
+    return worst
+
+
+def translation_residual(sp, vals, comp):
+    """||A t|| / (||A||_max ||t||) for the rigid translation t along `comp` (GPU matvec)."""
+    rp, col = sp.pattern()
+    A = torch.sparse_csr_tensor(rp, col.to(torch.int64), vals, size=(sp.n_dofs, sp.n_dofs))
+    t = torch.zeros(sp.n_dofs, dtype=torch.float64, device="cuda")
+    t[comp::3] = 1.0
+    r = torch.mv(A, t)
+    return float(r.abs().max() / vals.abs().max())
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16", "fp64"])
+def test_elasticity_q2_beam_full_size(prec):
+    """32x32x32 Q2 beam (the benchmark workload): sampled rows vs the oracle, rigid
+    translations in the kernel, RHS sums -vol = -4 on z rows."""
+    prob = inputs.elasticity_q2_beam()
+    sp = feasm.FESpace(prob)
+    coef = torch.tensor(prob.coef, device="cuda")
+    vals, rhs = sp.assemble(coef, prec=prec)
+    torch.cuda.synchronize()
+    assert sp.status() == 0
+    check_rows(prob, sp, vals.cpu().numpy(), rhs.cpu().numpy(), prec, sampled_rows(sp.n_dofs))
+    for c in range(3):
+        assert translation_residual(sp, vals, c) <= 8 * TOL[prec]
+    assert abs(float(rhs[2::3].sum()) + 4.0) < 1e-11 and abs(float(rhs[0::3].sum())) < 1e-11
+    sp.close()
+
+
+def test_elasticity_q1_128_full_size():
+    """128^3 Q1 elasticity (2.1M cells, 514M nonzeros), mixed FP32 form."""
+    prob = inputs.elasticity_q1_128()
+    sp = feasm.FESpace(prob)
+    coef = torch.tensor(prob.coef, device="cuda")
+    vals, rhs = sp.assemble(coef, prec="fp32")
+    torch.cuda.synchronize()
+    assert sp.status() == 0
+    check_rows(prob, sp, vals.cpu().numpy(), rhs.cpu().numpy(), "fp32", sampled_rows(sp.n_dofs, k=24))
+    assert translation_residual(sp, vals, 1) <= 8 * TOL["fp32"]
+    assert abs(float(rhs[2::3].sum()) + 1.0) < 1e-10
+    sp.close()
+
+
+def test_host_buffer_entry_matches_device_entry():
+    prob = inputs.small_problem((3, 3, 2), 2, 1, seed=5)
+    sp = feasm.FESpace(prob)
+    coef = torch.tensor(prob.coef, device="cuda")
+    vals, rhs = sp.assemble(coef, prec="fp32")
+    hv = torch.empty(sp.nnz, dtype=torch.float64).pin_memory()
+    hr = torch.empty(sp.n_dofs, dtype=torch.float64).pin_memory()
+    hc = torch.tensor(prob.coef).pin_memory()
+    feasm.fe_assemble_host(sp.handle, hc, prob.force, hv, hr, feasm.FE_PREC_FP32)
+    assert torch.equal(hv, vals.cpu()) and torch.equal(hr, rhs.cpu())
+    sp.close()
+
+
+def test_negative_jacobian_reported_without_fault():
+    prob = inputs.small_problem((2, 2, 2), 1, 0, seed=1)
+    coords = prob.mesh.coords.copy()
+    centre = 13  # the interior vertex of a 2x2x2 brick
+    coords[centre] = [1.2, 1.2, 1.2]  # pushed through the far corner: inverted cells
+    m = inputs.Mesh(coords, prob.mesh.cell_vertices, prob.mesh.shape, prob.mesh.extent)
+    bad = inputs.Problem("bad", m, 1, 2, 0, prob.coef, prob.force)
+    sp = feasm.FESpace(bad)
+    coef = torch.tensor(bad.coef, device="cuda")
+    sp.assemble(coef, prec="fp64")
+    assert sp.status() == -4
+    assert sp.status() == 0          # the word is cleared; the context is still usable
+    good = feasm.FESpace(prob)
+    vals, _ = good.assemble(torch.tensor(prob.coef, device="cuda"), prec="fp64")
+    assert good.status() == 0 and torch.isfinite(vals).all()
+    sp.close()
+    good.close()
+
+
+def test_empty_mesh():
+    mesh = inputs.Mesh(np.zeros((0, 3)), np.zeros((0, 8), dtype=np.int32), (0, 0, 0), (1, 1, 1))
+    prob = inputs.Problem("empty", mesh, 2, 3, 1, np.zeros(0), np.array([0.0, 0.0, -1.0]))
+    sp = feasm.FESpace(prob)
+    assert (sp.n_dofs, sp.nnz) == (0, 0)
+    sp.assemble(torch.zeros(0, dtype=torch.float64, device="cuda"), prec="fp32")
+    assert sp.status() == 0
+    sp.close()
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("shape,p,problem", [((3, 3, 3), 1, 1), ((2, 2, 3), 2, 1), ((2, 2, 2), 3, 0), ((3, 2, 2), 2, 0)])
+def test_adjoint_small_vs_oracle(shape, p, problem):
+    prob = inputs.small_problem(shape, p, problem, seed=70 + p)
+    sp = feasm.FESpace(prob)
+    cd = sp.cell_dofs()
+    u = inputs.unit_rms_field(sp.n_dofs, 9)
+    g_o = oracle.cell_energies(prob, u, cd)
+    ut = torch.tensor(u, device="cuda")
+    coef = torch.tensor(prob.coef, device="cuda")
+    c = torch.zeros(1, dtype=torch.float64, device="cuda")
+    g64 = sp.adjoint(ut, coef, 1.0, compliance=c, prec="fp64").cpu().numpy()
+    assert vec_error(g64, g_o) <= 1e-12
+    assert abs(float(c) - np.dot(prob.coef, g_o)) <= 1e-12 * abs(np.dot(prob.coef, g_o))
+    g32 = sp.adjoint(ut, None, 2.5, prec="fp32").cpu().numpy()
+    assert vec_error(g32, 2.5 * g_o) <= 1e-5
+    assert sp.status() == 0
+    sp.close()
+
+
+def test_adjoint_cantilever_full_size_fd_and_oracle():
+    """64^3 Q1 cantilever: adjoint vs the oracle gradient on sampled cells and vs central
+    finite differences (step 1e-6 relative) of the GPU compliance on 32 random cells."""
+    from paper_1708_01773_gb300.autograd import compliance
+    prob = inputs.cantilever_q1_64()
+    sp = feasm.FESpace(prob)
+    cd = sp.cell_dofs()
+    u = inputs.unit_rms_field(sp.n_dofs, 20171773 + 5)
+    ut = torch.tensor(u, device="cuda")
+    E = torch.tensor(prob.coef, device="cuda", requires_grad=True)
+    c = compliance(E, ut, sp)
+    c.backward()
+    g = E.grad.detach().cpu().numpy()
+    rng = np.random.default_rng(32)
+    cells = np.unique(np.concatenate([[0, prob.mesh.n_cells - 1], rng.integers(0, prob.mesh.n_cells, 32)]))
+    sub = inputs.Problem("sub", inputs.Mesh(prob.mesh.coords, prob.mesh.cell_vertices[cells]), 1, 2, 1,
+                         prob.coef[cells], prob.force)
+    g_o = oracle.cell_energies(sub, u, cd[cells])
+    assert vec_error(g[cells], g_o) <= 1e-12
+    # Euler identity for a functional linear in E
+    assert abs(float(c) - float((E.detach() * E.grad).sum())) <= 1e-12 * abs(float(c))
+    # central differences of the compliance computed on the GPU
+    terms = np.abs(prob.coef * g).sum()
+    cbuf = torch.zeros(1, dtype=torch.float64, device="cuda")
+    gbuf = torch.empty(sp.n_cells, dtype=torch.float64, device="cuda")
+    for e in rng.choice(prob.mesh.n_cells, 32, replace=False):
+        h = 1e-6 * prob.coef[e]
+        vals = []
+        for sgn in (1, -1):
+            Ep = E.detach().clone()
+            Ep[e] += sgn * h
+            sp.adjoint(ut, Ep, 1.0, out=gbuf, compliance=cbuf, prec="fp64")
+            vals.append(float(cbuf))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        noise = 64 * 2.2e-16 * terms / (2 * h)   # rounding of the reduction, no truncation (c is linear in E)
+        assert abs(fd - g[e]) <= noise + 1e-9 * abs(g[e]), (e, fd, g[e], noise)
+    sp.close()

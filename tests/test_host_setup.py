@@ -1,0 +1,136 @@
+"""CPU tests of the C-ABI library: it loads, exports every declared symbol, and its
+host-side setup (DOF numbering, CSR pattern, assembly permutation) agrees with the
+oracle. No compute call is made (no GPU here)."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1708_01773_gb300 import feasm, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1708_01773_gb300 import build
+    build.build()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "feasm.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(fe_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    names = declared_functions()
+    assert len(names) >= 15
+    assert set(names) == set(feasm.EXPORTS)
+    L = feasm.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    out = os.popen(f"nm -D --defined-only {feasm.LIB_PATH}").read()
+    for n in names:
+        assert re.search(rf"\bT {n}\b", out), n
+
+
+CASES = [
+    ((3, 2, 2), 1, 0), ((2, 2, 3), 1, 1), ((2, 3, 2), 2, 0), ((3, 2, 2), 2, 1), ((2, 2, 2), 3, 0), ((2, 1, 2), 3, 1),
+]
+
+
+@pytest.mark.parametrize("shape,p,problem", CASES)
+def test_numbering_pattern_permutation_match_oracle(shape, p, problem):
+    prob = inputs.small_problem(shape, p, problem, seed=3 * p + problem)
+    sp = feasm.FESpace(prob, host_only=True)
+    cd_o, n_o = oracle.dof_numbering(prob.mesh, p, prob.ncomp)
+    cd = sp.cell_dofs()
+    assert sp.n_dofs == n_o
+    np.testing.assert_array_equal(cd, cd_o)                      # list_dofs, bit-exact
+    rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob, cd_o, n_o)
+    rp, col = sp.pattern_host()
+    np.testing.assert_array_equal(rp, rp_o)
+    np.testing.assert_array_equal(col, col_o)
+    nl = prob.ncomp * (p + 1) ** 3
+    assert sp.n_contrib == prob.mesh.n_cells * nl * nl
+    # emulate the scatter on the CPU with the oracle's own FP64 cell matrices
+    cnt, code_ptr, codes, slot_ptr, slots = feasm.fe_space_permutation_host(sp.handle)
+    Ke = np.zeros((prob.mesh.n_cells, nl, nl))
+    fe = np.zeros((prob.mesh.n_cells, nl))
+    for e in range(prob.mesh.n_cells):
+        xv = prob.mesh.coords[prob.mesh.cell_vertices[e]]
+        Ke[e], fe[e] = oracle.cell_matrix(problem, p, p + 1, xv, prob.coef[e], prob.nu, prob.force)
+    Kflat = Ke.reshape(-1)
+    vals = np.zeros(sp.nnz)
+    rhs = np.zeros(sp.n_dofs)
+    seen = np.zeros(Kflat.size, dtype=np.int64)
+    for r in range(sp.n_dofs):
+        sl = slots[slot_ptr[r]:slot_ptr[r + 1]]
+        assert np.all(np.diff(sl // nl) > 0)                     # cells ascending
+        assert np.all(cd.reshape(-1)[sl] == r)
+        rhs[r] = fe.reshape(-1)[sl].sum()
+        c = code_ptr[r]
+        for k in range(rp[r], rp[r + 1]):
+            seg = codes[c:c + cnt[k]].astype(np.int64)
+            c += cnt[k]
+            s, m = seg >> 8, seg & 255
+            assert np.all(np.diff(s) > 0)                        # ascending cell within a nonzero
+            src = sl[s].astype(np.int64) * nl + m
+            assert np.all(cd.reshape(-1)[(sl[s] // nl) * nl + m] == col[k])
+            seen[src] += 1
+            vals[k] = Kflat[src].sum()
+        assert c == code_ptr[r + 1]
+    assert np.all(seen == 1)                                     # a permutation of all contributions
+    np.testing.assert_allclose(vals, val_o, rtol=0, atol=1e-13 * np.abs(val_o).max())
+    np.testing.assert_allclose(rhs, rhs_o, rtol=0, atol=1e-14)
+    sp.close()
+
+
+def test_structured_pattern_sizes():
+    """(3n+1)^3 nonzeros per component pair for Q1 and (8n+1)^3 for Q2 on n^3 bricks."""
+    for p, per in ((1, lambda n: 3 * n + 1), (2, lambda n: 8 * n + 1)):
+        prob = inputs.small_problem((4, 3, 2), p, 1, seed=1)
+        sp = feasm.FESpace(prob, host_only=True)
+        assert sp.nnz == 9 * per(4) * per(3) * per(2)
+        sp.close()
+
+
+def test_rotated_cell_orientation_matches_oracle():
+    prob = inputs.small_problem((2, 2, 1), 3, 1, seed=11)
+    cv = prob.mesh.cell_vertices.copy()
+    perm = [(1 - (v & 1)) + 2 * (1 - ((v >> 1) & 1)) + 4 * ((v >> 2) & 1) for v in range(8)]
+    cv[1] = cv[1][perm]
+    m2 = inputs.Mesh(prob.mesh.coords, cv, prob.mesh.shape, prob.mesh.extent)
+    p2 = inputs.Problem("rot", m2, 3, 4, 1, prob.coef, prob.force)
+    sp = feasm.FESpace(p2, host_only=True)
+    cd_o, n_o = oracle.dof_numbering(m2, 3, 3)
+    np.testing.assert_array_equal(sp.cell_dofs(), cd_o)
+    sp.close()
+
+
+def test_invalid_arguments_are_reported():
+    prob = inputs.small_problem((2, 2, 2), 1, 0)
+    with pytest.raises(feasm.FEError) as ei:
+        feasm.fe_space_create(prob.mesh.coords, prob.mesh.cell_vertices, 4, 0, 0, 0.3, host_only=True)
+    assert ei.value.code == -1 and "order" in str(ei.value)
+    bad = prob.mesh.cell_vertices.copy()
+    bad[0, 0] = prob.mesh.n_vertices + 5
+    with pytest.raises(feasm.FEError) as ei:
+        feasm.fe_space_create(prob.mesh.coords, bad, 1, 0, 0, 0.3, host_only=True)
+    assert ei.value.code == -1 and "range" in str(ei.value)
+    with pytest.raises(feasm.FEError) as ei:
+        feasm.fe_space_create(prob.mesh.coords, prob.mesh.cell_vertices, 1, 0, 1, 0.5, host_only=True)
+    assert ei.value.code == -1
+    with pytest.raises(feasm.FEError) as ei:
+        feasm.fe_space_create(prob.mesh.coords, prob.mesh.cell_vertices, 2, 9, 0, 0.3, host_only=True)
+    assert ei.value.code == -1
+
+
+def test_empty_mesh_host_setup():
+    mesh = inputs.Mesh(np.zeros((0, 3)), np.zeros((0, 8), dtype=np.int32), (0, 0, 0), (1, 1, 1))
+    h = feasm.fe_space_create(mesh.coords, mesh.cell_vertices, 2, 0, 1, 0.3, host_only=True)
+    assert feasm.fe_space_sizes(h) == (0, 0, 0, 0)
+    feasm.fe_space_destroy(h)
