@@ -76,7 +76,7 @@ typedef struct {
  *   out             receives the new space; destroy with fe_space_destroy.
  * Uses the current CUDA device. Host work is multi-threaded. Errors:
  * FE_ERR_INVALID_ARG (bad sizes, vertex ids out of range), FE_ERR_UNSUPPORTED
- * (index widths exceeded, more than 255 cells around one DOF), FE_ERR_OOM,
+ * (index widths exceeded, more than 127 cells around one DOF), FE_ERR_OOM,
  * FE_ERR_CUDA. */
 int fe_space_create(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem,
                     double nu, fe_space** out);
@@ -105,13 +105,16 @@ int fe_space_csr_pattern(const fe_space* s, int64_t* row_ptr, int32_t* col_idx, 
 
 /* Copies the assembly permutation of a host-only space into caller memory
  * (host): cnt [nnz] uint8 contributions per nonzero; code_ptr [n_dofs+1] int64
- * first code of each row; codes [n_contrib] uint16; slot_ptr [n_dofs+1] int64;
- * slots [n_cells * n_loc] int32. Row r has the cells ("slots", ascending) given
- * by slots[slot_ptr[r] .. slot_ptr[r+1]), each entry e * n_loc + (local index
- * of DOF r in cell e). Nonzero k of row r sums, in code order, the cell-matrix
- * entries K^{e_s}[local row][m] for the codes (s << 8) | m of its segment; the
- * segments of a row are consecutive from code_ptr[r], nonzeros in column order.
- * This is the deterministic gather form of Eq. assembly. Only spaces made by
+ * first code of each row; codes [code_ptr[n_dofs]] uint16 (may be NULL: call
+ * once without it to learn the length); slot_ptr [n_dofs+1] int64; slots
+ * [n_cells * n_loc] int32. Row r has the cells ("slots", ascending) given by
+ * slots[slot_ptr[r] .. slot_ptr[r+1]), each entry e * n_loc + (local index of
+ * DOF r in cell e). The row's ns * n_loc codes start at code_ptr[r] (a
+ * multiple of 8; the block is padded to a multiple of 8 codes); code bits are
+ * head << 15 | s << 8 | m. Nonzero k of the row (columns ascending) sums, in
+ * code order, the cell-matrix entries K^{e_s}[local row][m] of one run of codes
+ * that starts with head = 1, i.e. its cells in ascending order. This is the
+ * deterministic gather form of Eq. assembly. Only spaces made by
  * fe_space_create_host keep these arrays on the host (FE_ERR_INVALID_ARG
  * otherwise). */
 int fe_space_permutation_host(const fe_space* s, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
@@ -164,6 +167,15 @@ int fe_assemble_host(fe_space* s, const double* coefficients, const double* body
  *                 geometry and FP64 sums). */
 int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients, double grad_scale,
                         double* dc_dcoef, double* compliance, fe_precision prec, void* stream);
+
+/* Selects the cell-integration kernel of later fe_assemble calls:
+ * FE_KERNEL_AUTO (default: the tensor-core kernel where one exists for the
+ * order, problem, rule and precision, else the CUDA-core kernel),
+ * FE_KERNEL_CUDA_CORE, or FE_KERNEL_TENSOR_CORE (fe_assemble then fails with
+ * FE_ERR_UNSUPPORTED where none exists: Q2 elasticity with 3^3 points, FP32
+ * or BF16). Both kernels give results within the stated tolerances. */
+enum { FE_KERNEL_AUTO = 0, FE_KERNEL_CUDA_CORE = 1, FE_KERNEL_TENSOR_CORE = 2 };
+int fe_space_set_kernel(fe_space* s, int cell_kernel);
 
 /* Synchronises `stream`, returns and clears the device error word:
  * FE_OK, FE_ERR_NEG_JACOBIAN (some det J <= 0 at a quadrature point) or

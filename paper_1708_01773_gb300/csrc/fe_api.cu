@@ -74,6 +74,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
   s->nb = s->tab.nb;
   s->nq = s->tab.nq;
   s->nl = s->ncomp * s->nb;
+  s->nlp = (s->nl + 3) & ~3;
   std::string err;
   int rc;
   try {
@@ -117,7 +118,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     if (e == cudaSuccess) e = upload(&s->d_codes, hs.codes.data(), hs.codes.size());
     if (e == cudaSuccess) e = upload(&s->d_slot_ptr, hs.slot_ptr.data(), hs.slot_ptr.size());
     if (e == cudaSuccess) e = upload(&s->d_slots, hs.slots.data(), hs.slots.size());
-    const size_t nke = size_t(s->n_cells) * s->nl * s->nl;
+    const size_t nke = size_t(s->n_cells) * s->nl * s->nlp;
     if (e == cudaSuccess && nke) e = cudaMalloc(&s->d_ke, nke * sizeof(double));
     if (e == cudaSuccess && s->n_cells) e = cudaMalloc(&s->d_fe, size_t(s->n_cells) * s->nl * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
@@ -180,12 +181,12 @@ int fe_space_csr_pattern_host(const fe_space* s, int64_t* row_ptr, int32_t* col_
 
 int fe_space_permutation_host(const fe_space* s, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
                               int64_t* slot_ptr, int32_t* slots) {
-  if (!s || !cnt || !code_ptr || !codes || !slot_ptr || !slots) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+  if (!s || !cnt || !code_ptr || !slot_ptr || !slots) return fail(FE_ERR_INVALID_ARG, "NULL argument");
   if (!s->host_only) return fail(FE_ERR_INVALID_ARG, "the permutation is kept on the host only for host-only spaces");
   const auto& hs = s->hs;
   std::memcpy(cnt, hs.cnt.data(), hs.cnt.size());
   std::memcpy(code_ptr, hs.code_ptr.data(), hs.code_ptr.size() * sizeof(int64_t));
-  std::memcpy(codes, hs.codes.data(), hs.codes.size() * sizeof(uint16_t));
+  if (codes) std::memcpy(codes, hs.codes.data(), hs.codes.size() * sizeof(uint16_t));
   std::memcpy(slot_ptr, hs.slot_ptr.data(), hs.slot_ptr.size() * sizeof(int64_t));
   std::memcpy(slots, hs.slots.data(), hs.slots.size() * sizeof(int32_t));
   return FE_OK;
@@ -224,7 +225,13 @@ int fe_assemble_ex(fe_space* s, const double* coefficients, const double* body_f
   if (body_force)
     for (int k = 0; k < s->ncomp; ++k) f[k] = body_force[k];
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  FE_CUDA(feasm::launch_cell_integration(s, coefficients, f, prec, st));
+  const bool tc = feasm::cell_tc_applicable(s, prec) && s->cell_kernel != FE_KERNEL_CUDA_CORE;
+  if (s->cell_kernel == FE_KERNEL_TENSOR_CORE && !tc)
+    return fail(FE_ERR_UNSUPPORTED, "no tensor-core cell kernel for this order / problem / precision");
+  if (tc)
+    FE_CUDA(feasm::launch_cell_tc(s, coefficients, f, prec, st));
+  else
+    FE_CUDA(feasm::launch_cell_integration(s, coefficients, f, prec, st));
   if (event_mid) FE_CUDA(cudaEventRecord(static_cast<cudaEvent_t>(event_mid), st));
   FE_CUDA(feasm::launch_scatter(s, prec, csr_values, rhs, st));
   return FE_OK;
@@ -262,6 +269,14 @@ int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients
     return FE_OK;
   }
   FE_CUDA(feasm::launch_adjoint(s, u, coefficients, grad_scale, dc_dcoef, compliance, prec, st));
+  return FE_OK;
+}
+
+int fe_space_set_kernel(fe_space* s, int cell_kernel) {
+  if (!s) return fail(FE_ERR_INVALID_ARG, "space is NULL");
+  if (cell_kernel < FE_KERNEL_AUTO || cell_kernel > FE_KERNEL_TENSOR_CORE)
+    return fail(FE_ERR_INVALID_ARG, "unknown cell kernel");
+  s->cell_kernel = cell_kernel;
   return FE_OK;
 }
 

@@ -12,7 +12,7 @@ namespace feasm {
 
 constexpr int kMaxOrder = 3;
 constexpr int kMaxQ1d = 6;
-constexpr int kMaxSlots = 255;  // cells around one DOF (8 bits of a code)
+constexpr int kMaxSlots = 127;  // cells around one DOF (7 bits of a code)
 
 // Reference tables of the Q_p element at a tensor Gauss-Legendre rule on
 // [0,1]^3. Point q = q0 + n q1 + n^2 q2, node a = a0 + (p+1) a1 + (p+1)^2 a2.
@@ -26,14 +26,15 @@ struct RefTables {
 
 // Products of the host setup of one space.
 struct HostSetup {
-  int64_t n_dofs = 0, nnz = 0, n_contrib = 0;
+  int64_t n_dofs = 0, nnz = 0, n_contrib = 0, n_codes = 0;
   int max_slots = 0;
+  int64_t max_row_nnz = 0;
   std::vector<int32_t> cell_dofs;   // [n_cells][nl]
   std::vector<int64_t> row_ptr;     // [n_dofs+1]
   std::vector<int32_t> col;         // [nnz]
   std::vector<uint8_t> cnt;         // [nnz] contributions per nonzero
   std::vector<int64_t> code_ptr;    // [n_dofs+1] first code of each row
-  std::vector<uint16_t> codes;      // [n_contrib] (slot << 8) | local column
+  std::vector<uint16_t> codes;      // (head << 15) | (slot << 8) | local column, rows padded to 8 codes
   std::vector<int64_t> slot_ptr;    // [n_dofs+1]
   std::vector<int32_t> slots;       // [n_cells*nl] e*nl + local row, cells ascending
 };
@@ -47,13 +48,14 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
 
 struct fe_space {
   int order = 0, nq1d = 0, problem = 0, ncomp = 1, nb = 0, nq = 0, nl = 0;
+  int nlp = 0;  // row stride of a cell matrix: nl rounded up to a multiple of 4 (16-byte rows)
   double nu = 0.0;
   int64_t n_cells = 0, n_vertices = 0;
   bool host_only = false;
   int device = 0;
   feasm::RefTables tab;
   feasm::HostSetup hs;  // host arrays (pattern arrays are released after upload)
-  bool host_pattern_kept = true;
+  int cell_kernel = 0;  // FE_KERNEL_AUTO / _CUDA_CORE / _TENSOR_CORE
   // device data
   double* d_xv = nullptr;        // [n_cells][8][3] cell vertex coordinates
   double* d_w = nullptr;         // [nq]
@@ -69,7 +71,7 @@ struct fe_space {
   uint16_t* d_codes = nullptr;
   int64_t* d_slot_ptr = nullptr;
   int32_t* d_slots = nullptr;
-  void* d_ke = nullptr;          // cell matrices, [n_cells][nl][nl] FP64 or FP32
+  void* d_ke = nullptr;          // cell matrices, [n_cells][nl][nlp] FP64 or FP32
   double* d_fe = nullptr;        // cell vectors [n_cells][nl]
   int* d_err = nullptr;          // device error word
   double* d_partials = nullptr;  // reduction scratch for the compliance

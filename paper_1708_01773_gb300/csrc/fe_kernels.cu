@@ -19,22 +19,25 @@ int cells_per_block(int nb) {
 
 // Shared memory of k_cell: vertex coordinates [cpb][24], trilinear
 // coefficients [cpb][21], per-point geometry [cpb][nq][11] (cofactor matrix,
-// w/det, w*det) in FP64, and the cofactor-scaled reference gradients
+// w/det, w*det) in FP64, for the FP32/BF16 forms an FP32 copy [cpb][nq][12]
+// of the cofactors and w/det, and the cofactor-scaled reference gradients
 // [cpb][nq][3][nb] in the operand type.
 long cell_smem_bytes(int nb, int nq, fe_precision prec, int cpb) {
   const long tsz = prec == FE_PREC_FP64 ? 8 : 4;
-  const long bytes = long(cpb) * (24 + 21) * 8 + long(cpb) * nq * 11 * 8 + long(cpb) * nq * 3 * nb * tsz;
+  long bytes = long(cpb) * (24 + 21) * 8 + long(cpb) * nq * 11 * 8 + long(cpb) * nq * 3 * nb * tsz;
+  if (prec != FE_PREC_FP64) bytes += long(cpb) * nq * 12 * 4;
   return bytes <= 227 * 1024 ? bytes : -1;
 }
 
 struct CellParams {
   int64_t n_cells;
-  int nq, cpb;
+  int nq, cpb, qblock;
   const double* xv;
   const double* w;
   const double* xq;
   const double* phi;
   const double* dphi;
+  const float* dphi32;
   const double* coef;
   double f[3];
   double lam_hat, mu_hat;
@@ -88,6 +91,15 @@ __device__ __forceinline__ void trilinear_coefficients(const double* x, int k, d
   a[18 + k] = (d76 - d54) - (d32 - d10);
 }
 
+// Compensated (Kahan) addition of a block partial into (sum, carry).
+template <typename T>
+__device__ __forceinline__ void kahan_add(T& sum, T& carry, T part) {
+  const T y = part - carry;
+  const T t = sum + y;
+  carry = (t - sum) - y;
+  sum = t;
+}
+
 // One block integrates `cpb` cells. Steps (paper: Eq. fematrix, Eq.
 // shape_grad, the element loop of the Listing
 // "element_matrix_entries_computation"):
@@ -98,19 +110,24 @@ __device__ __forceinline__ void trilinear_coefficients(const double* x, int k, d
 //      Poisson   K_ab = kappa sum_i G^{ii}_{ab},
 //      elasticity K_(a,i),(b,j) = E (lam^ G^{ij}_ab + mu^ G^{ji}_ab + mu^ d_ij sum_k G^{kk}_ab),
 //   4. cell vector f_(a,i) = f_i sum_q w_q det J_q phihat_a(x_q).
-// PREC 0: FP64 throughout. PREC 1: FP32 gradients and contraction. PREC 2:
-// BF16-rounded operands with FP32 products and sums.
+// PREC 0: FP64 throughout. PREC 1: FP32 gradients and products; the sum over
+// quadrature points runs in blocks of `qblock` points (one z-slab of the
+// tensor rule) whose FP32 partials are added with Kahan compensation. PREC 2:
+// BF16-rounded operands, FP32 products and sums. Cell matrices are stored
+// row-major with row stride NLP (16-byte aligned rows).
 template <int P, int NC, int PREC>
 __global__ void __launch_bounds__(kCellThreads) k_cell(CellParams prm) {
   constexpr int NB = (P + 1) * (P + 1) * (P + 1);
   constexpr int NL = NC * NB;
+  constexpr int NLP = (NL + 3) & ~3;
   using T = typename std::conditional<PREC == 0, double, float>::type;
   extern __shared__ __align__(16) double smem[];
   const int cpb = prm.cpb, nq = prm.nq;
   double* sx = smem;
   double* sa = sx + cpb * 24;
   double* geo = sa + cpb * 21;
-  T* g = reinterpret_cast<T*>(geo + cpb * nq * 11);
+  float* geo32 = reinterpret_cast<float*>(geo + cpb * nq * 11);
+  T* g = reinterpret_cast<T*>(PREC == 0 ? reinterpret_cast<float*>(geo + cpb * nq * 11) : geo32 + cpb * nq * 12);
   const int64_t e0 = int64_t(blockIdx.x) * cpb;
   const int tid = threadIdx.x;
   const int ncell = int(prm.n_cells - e0 < cpb ? prm.n_cells - e0 : cpb);
@@ -130,77 +147,102 @@ __global__ void __launch_bounds__(kCellThreads) k_cell(CellParams prm) {
     for (int t = 0; t < 9; ++t) gm[t] = cof[t];
     gm[9] = wq / det;
     gm[10] = wq * det;
+    if (PREC != 0) {
+      float* g32 = geo32 + size_t(i) * 12;
+#pragma unroll
+      for (int t = 0; t < 9; ++t) g32[t] = float(cof[t]);
+      g32[9] = float(wq / det);
+    }
   }
   __syncthreads();
   for (int i = tid; i < ncell * nq * NB; i += blockDim.x) {
     const int a = i % NB, cq = i / NB, q = cq % nq;
-    const double* gm = geo + size_t(cq) * 11;
-    const double* dp = prm.dphi + (size_t(q) * NB + a) * 3;
     T* gg = g + size_t(cq) * 3 * NB;
+    if (PREC == 0) {
+      const double* gm = geo + size_t(cq) * 11;
+      const double* dp = prm.dphi + (size_t(q) * NB + a) * 3;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (PREC == 0) {
-        gg[k * NB + a] = gm[3 * k] * dp[0] + gm[3 * k + 1] * dp[1] + gm[3 * k + 2] * dp[2];
-      } else {
-        float v = float(gm[3 * k]) * float(dp[0]);
-        v = fmaf(float(gm[3 * k + 1]), float(dp[1]), v);
-        v = fmaf(float(gm[3 * k + 2]), float(dp[2]), v);
-        gg[k * NB + a] = T(v);
-      }
+      for (int k = 0; k < 3; ++k) gg[k * NB + a] = gm[3 * k] * dp[0] + gm[3 * k + 1] * dp[1] + gm[3 * k + 2] * dp[2];
+    } else {
+      const float* gm = geo32 + size_t(cq) * 12;
+      const float* dp = prm.dphi32 + (size_t(q) * NB + a) * 3;
+      const float d0 = dp[0], d1 = dp[1], d2 = dp[2];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) gg[k * NB + a] = T(fmaf(gm[3 * k + 2], d2, fmaf(gm[3 * k + 1], d1, gm[3 * k] * d0)));
     }
   }
   __syncthreads();
+  const int qb = PREC == 1 ? prm.qblock : nq;
   for (int i = tid; i < ncell * NB * NB; i += blockDim.x) {
     const int c = i / (NB * NB), ab = i % (NB * NB), a = ab / NB, b = ab % NB;
     const T* gc = g + size_t(c) * nq * 3 * NB;
     const double* gm = geo + size_t(c) * nq * 11;
+    const float* gm32 = geo32 + size_t(c) * nq * 12;
     const int64_t e = e0 + c;
     const double coef = prm.coef[e];
+    T* K = reinterpret_cast<T*>(prm.ke) + e * NL * NLP;
     if (NC == 1) {
-      T acc = T(0);
-      for (int q = 0; q < nq; ++q) {
-        const T* gq = gc + size_t(q) * 3 * NB;
-        const T s = T(gm[q * 11 + 9]);
+      T sum = T(0), carry = T(0);
+      for (int q0 = 0; q0 < nq; q0 += qb) {
+        T part = T(0);
+        const int q1 = q0 + qb < nq ? q0 + qb : nq;
+        for (int q = q0; q < q1; ++q) {
+          const T* gq = gc + size_t(q) * 3 * NB;
+          const T s = PREC == 0 ? T(gm[q * 11 + 9]) : T(gm32[q * 12 + 9]);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          T ga = s * gq[k * NB + a], gb = gq[k * NB + b];
-          if (PREC == 2) { ga = round_bf16(ga); gb = round_bf16(gb); }
-          acc += ga * gb;
+          for (int k = 0; k < 3; ++k) {
+            T ga = s * gq[k * NB + a], gb = gq[k * NB + b];
+            if (PREC == 2) { ga = round_bf16(ga); gb = round_bf16(gb); }
+            part += ga * gb;
+          }
         }
+        if (PREC == 1) kahan_add(sum, carry, part); else sum += part;
       }
-      T* K = reinterpret_cast<T*>(prm.ke) + e * NL * NL;
-      K[a * NB + b] = T(coef) * acc;
+      K[a * NLP + b] = T(coef) * sum;
     } else {
-      T G[3][3];
+      T S[3][3], C[3][3];
 #pragma unroll
       for (int i2 = 0; i2 < 3; ++i2)
 #pragma unroll
-        for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] = T(0);
-      for (int q = 0; q < nq; ++q) {
-        const T* gq = gc + size_t(q) * 3 * NB;
-        const T s = T(gm[q * 11 + 9]);
-        T ga[3], gb[3];
+        for (int j2 = 0; j2 < 3; ++j2) S[i2][j2] = C[i2][j2] = T(0);
+      for (int q0 = 0; q0 < nq; q0 += qb) {
+        T G[3][3];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          ga[k] = s * gq[k * NB + a];
-          gb[k] = gq[k * NB + b];
-          if (PREC == 2) { ga[k] = round_bf16(ga[k]); gb[k] = round_bf16(gb[k]); }
+        for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+          for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] = T(0);
+        const int q1 = q0 + qb < nq ? q0 + qb : nq;
+        for (int q = q0; q < q1; ++q) {
+          const T* gq = gc + size_t(q) * 3 * NB;
+          const T s = PREC == 0 ? T(gm[q * 11 + 9]) : T(gm32[q * 12 + 9]);
+          T ga[3], gb[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            ga[k] = s * gq[k * NB + a];
+            gb[k] = gq[k * NB + b];
+            if (PREC == 2) { ga[k] = round_bf16(ga[k]); gb[k] = round_bf16(gb[k]); }
+          }
+#pragma unroll
+          for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+            for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] += ga[i2] * gb[j2];
         }
 #pragma unroll
         for (int i2 = 0; i2 < 3; ++i2)
 #pragma unroll
-          for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] += ga[i2] * gb[j2];
+          for (int j2 = 0; j2 < 3; ++j2) {
+            if (PREC == 1) kahan_add(S[i2][j2], C[i2][j2], G[i2][j2]); else S[i2][j2] += G[i2][j2];
+          }
       }
       const T lh = T(prm.lam_hat), mh = T(prm.mu_hat), E = T(coef);
-      const T tr = G[0][0] + G[1][1] + G[2][2];
-      T* K = reinterpret_cast<T*>(prm.ke) + e * NL * NL;
+      const T tr = S[0][0] + S[1][1] + S[2][2];
 #pragma unroll
       for (int i2 = 0; i2 < 3; ++i2)
 #pragma unroll
         for (int j2 = 0; j2 < 3; ++j2) {
-          T v = lh * G[i2][j2] + mh * G[j2][i2];
+          T v = lh * S[i2][j2] + mh * S[j2][i2];
           if (i2 == j2) v += mh * tr;
-          K[size_t(i2 * NB + a) * NL + j2 * NB + b] = E * v;
+          K[size_t(i2 * NB + a) * NLP + j2 * NB + b] = E * v;
         }
     }
   }
@@ -242,11 +284,13 @@ cudaError_t launch_cell_integration(const fe_space* s, const double* coef, const
   prm.n_cells = s->n_cells;
   prm.nq = s->nq;
   prm.cpb = cells_per_block(s->nb);
+  prm.qblock = s->nq1d * s->nq1d;
   prm.xv = s->d_xv;
   prm.w = s->d_w;
   prm.xq = s->d_xq;
   prm.phi = s->d_phi;
   prm.dphi = s->d_dphi;
+  prm.dphi32 = s->d_dphi32;
   prm.coef = coef;
   for (int k = 0; k < 3; ++k) prm.f[k] = force[k];
   prm.lam_hat = s->nu / ((1.0 + s->nu) * (1.0 - 2.0 * s->nu));
@@ -269,15 +313,135 @@ cudaError_t launch_cell_integration(const fe_space* s, const double* coef, const
 }
 
 // ---------------------------------------------------------------------------
-// Deterministic scatter (Eq. assembly): one warp per CSR row. The row's cells
-// ("slots", ascending) are staged in shared memory as offsets of their cell
-// matrix rows. Lane l owns nonzero k = k0 + l of a 32-wide chunk; a warp
-// inclusive scan of the contribution counts gives each lane the start of its
-// contiguous segment of codes, and the lane sums its segment in FP64 in code
-// order (= ascending cell), then stores values[k] (coalesced across lanes).
+// Deterministic scatter (Eq. assembly). One warp assembles one CSR row r at a
+// time. The row's contributions are its codes, sorted by destination nonzero
+// (columns ascending) and, within a nonzero, by ascending cell; a code
+// (head << 15 | s << 8 | m) names entry m of the cell-matrix row of DOF r in
+// the row's s-th cell ("slot"), head marking the first contribution of a
+// nonzero.
+//
+// Exact FP64 accumulation without FP64 arithmetic. The FP64 pipe of this GPU
+// is a small fraction of its FP32/INT32 rate, so each nonzero is summed in
+// 64-bit integer fixed point: every term is split into sign, exponent and
+// integer mantissa, the mantissas are aligned to the largest exponent of the
+// nonzero (the largest term's leading bit at bit 57, so that up to 32 terms
+// cannot overflow) and added as int64, and the integer sum is rounded once to
+// the nearest double. Bits lost in the alignment are below 2^-57 of the
+// largest term, so the result is at least as accurate as sequential FP64
+// additions, is independent of the order of the terms, and is bitwise
+// reproducible. A nonzero with a single FP32 term takes the exact FP32->FP64
+// conversion, done on the integer bits.
+template <typename TK>
+struct FxTraits;
+template <>
+struct FxTraits<float> {
+  // value = mant * 2^(ex - 150), mant < 2^24; aligned mantissa MSB at bit 57
+  static constexpr int kShift0 = 34, kScale = 184;
+  __device__ static __forceinline__ void split(float x, uint64_t& m, int& ex, bool& neg) {
+    const uint32_t u = __float_as_uint(x);
+    neg = (u >> 31) != 0;
+    int e = int((u >> 23) & 0xffu);
+    uint32_t mm = u & 0x7fffffu;
+    if (e) mm |= 0x800000u; else e = 1;
+    m = mm;
+    ex = e;
+  }
+};
+template <>
+struct FxTraits<double> {
+  // value = mant * 2^(ex - 1075), mant < 2^53; aligned mantissa MSB at bit 57
+  static constexpr int kShift0 = 5, kScale = 1080;
+  __device__ static __forceinline__ void split(double x, uint64_t& m, int& ex, bool& neg) {
+    const uint64_t u = uint64_t(__double_as_longlong(x));
+    neg = (u >> 63) != 0;
+    int e = int((u >> 52) & 0x7ffu);
+    uint64_t mm = u & 0xfffffffffffffull;
+    if (e) mm |= 1ull << 52; else e = 1;
+    m = mm;
+    ex = e;
+  }
+};
+
+// Rounds the integer S * 2^scale to the nearest double (ties to even).
+__device__ __forceinline__ double fx_to_double(int64_t S, int scale) {
+  if (S == 0) return 0.0;
+  const bool neg = S < 0;
+  const uint64_t mag = neg ? uint64_t(-S) : uint64_t(S);
+  int lz = __clzll(static_cast<long long>(mag));
+  const uint64_t norm = mag << lz;
+  uint64_t mant = norm >> 11;
+  const uint32_t rem = uint32_t(norm & 0x7ffu);
+  if (rem > 0x400u || (rem == 0x400u && (mant & 1u))) ++mant;
+  if (mant >> 53) {
+    mant >>= 1;
+    --lz;
+  }
+  const int biased = 63 - lz + scale + 1023;
+  if (biased <= 0) return neg ? -0.0 : 0.0;
+  if (biased >= 2047) return neg ? -__longlong_as_double(0x7ff0000000000000ll) : __longlong_as_double(0x7ff0000000000000ll);
+  const uint64_t bits = (uint64_t(neg) << 63) | (uint64_t(biased) << 52) | (mant & 0xfffffffffffffull);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// Exact FP32 -> FP64 conversion on the integer bits (normal numbers and zero).
+__device__ __forceinline__ bool f32_to_f64_bits(float x, double& out) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t e = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) {
+    out = (u >> 31) ? -0.0 : 0.0;
+    return true;
+  }
+  if (e == 0 || e == 0xffu) return false;
+  const uint64_t bits = (uint64_t(u >> 31) << 63) | (uint64_t(e + 896u) << 52) | (uint64_t(u & 0x7fffffu) << 29);
+  out = __longlong_as_double(static_cast<long long>(bits));
+  return true;
+}
+
+// Sum of n terms produced by get(t), t = 0..n-1, accumulated exactly as above.
+template <typename TK, typename Get>
+__device__ __forceinline__ double fx_sum(int n, Get get) {
+  using Tr = FxTraits<TK>;
+  if (n == 1) {
+    const TK x = get(0);
+    if (sizeof(TK) == 8) return double(x);
+    double d;
+    if (f32_to_f64_bits(float(x), d)) return d;
+  }
+  int emax = 1;
+  for (int t = 0; t < n; ++t) {
+    uint64_t m;
+    int ex;
+    bool ng;
+    Tr::split(get(t), m, ex, ng);
+    if (m != 0 && ex > emax) emax = ex;
+  }
+  int64_t S = 0;
+  for (int t = 0; t < n; ++t) {
+    uint64_t m;
+    int ex;
+    bool ng;
+    Tr::split(get(t), m, ex, ng);
+    const int sh = Tr::kShift0 - (emax - ex);
+    const uint64_t a = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+    S += ng ? -int64_t(a) : int64_t(a);
+  }
+  return fx_to_double(S, emax - Tr::kScale);
+}
+
+// k_scatter_rows copies the row's cell-matrix rows (padded to NLP entries,
+// 16-byte vector loads) and its codes (16-byte aligned blocks) into a
+// per-warp region of shared memory, finds the segment starts from the head
+// flags with one ballot per 32 codes, then gives each lane one nonzero: the
+// lane sums its segment from shared memory and stores values[k] (consecutive
+// k across the lanes: coalesced). The RHS entry of the row is the exact sum of
+// its cells' FP64 cell-vector entries.
+//
+// k_scatter (one lane per nonzero, direct gathers from global memory, using
+// the per-nonzero counts, same arithmetic) serves meshes whose largest row does
+// not fit the shared-memory region or that have more than 32 cells around a DOF.
 struct ScatterParams {
   int64_t n_rows;
-  int nl;
+  int nl, nlp;
   const int64_t* row_ptr;
   const uint8_t* cnt;
   const int64_t* code_ptr;
@@ -288,7 +452,10 @@ struct ScatterParams {
   const double* fe;
   double* values;
   double* rhs;
+  int ke_bytes, code_bytes, warp_bytes;
 };
+
+constexpr unsigned kFull = 0xffffffffu;
 
 template <typename TK>
 __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter(ScatterParams p) {
@@ -299,13 +466,10 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter(ScatterParams p)
        r += int64_t(gridDim.x) * kScatterWarps) {
     const int64_t s0 = p.slot_ptr[r];
     const int ns = int(p.slot_ptr[r + 1] - s0);
-    for (int s = lane; s < ns; s += 32) sbase[warp][s] = int64_t(p.slots[s0 + s]) * p.nl;
+    for (int s = lane; s < ns; s += 32) sbase[warp][s] = int64_t(p.slots[s0 + s]) * p.nlp;
     __syncwarp();
-    if (p.rhs != nullptr && lane == 0) {
-      double f = 0.0;
-      for (int s = 0; s < ns; ++s) f += p.fe[p.slots[s0 + s]];
-      p.rhs[r] = f;
-    }
+    if (p.rhs != nullptr && lane == 0)
+      p.rhs[r] = fx_sum<double>(ns, [&](int t) { return p.fe[p.slots[s0 + t]]; });
     const int64_t k0 = p.row_ptr[r], k1 = p.row_ptr[r + 1];
     int64_t c = p.code_ptr[r];
     for (int64_t kb = k0; kb < k1; kb += 32) {
@@ -314,28 +478,96 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter(ScatterParams p)
       int incl = n;
 #pragma unroll
       for (int off = 1; off < 32; off <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, off);
+        const int t = __shfl_up_sync(kFull, incl, off);
         if (lane >= off) incl += t;
       }
-      const int total = __shfl_sync(0xffffffffu, incl, 31);
+      const int total = __shfl_sync(kFull, incl, 31);
       const uint16_t* cp = p.codes + c + (incl - n);
-      double v = 0.0;
-      for (int t = 0; t < n; ++t) {
-        const unsigned code = cp[t];
-        v += double(ke[sbase[warp][code >> 8] + (code & 255u)]);
+      if (k < k1) {
+        p.values[k] = fx_sum<TK>(n, [&](int t) {
+          const unsigned code = cp[t];
+          return ke[sbase[warp][(code >> 8) & 127u] + (code & 255u)];
+        });
       }
-      if (k < k1) p.values[k] = v;
       c += total;
     }
     __syncwarp();
   }
 }
 
+template <typename TK>
+__global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterParams p) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char* region = sm + size_t(warp) * p.warp_bytes;
+  TK* ske = reinterpret_cast<TK*>(region);
+  uint16_t* scode = reinterpret_cast<uint16_t*>(region + p.ke_bytes);
+  uint16_t* sseg = reinterpret_cast<uint16_t*>(region + p.ke_bytes + p.code_bytes);
+  const int vper = p.nlp * int(sizeof(TK)) / 16;  // 16-byte vectors per cell-matrix row
+  const uint4* ke4 = reinterpret_cast<const uint4*>(p.ke);
+  const unsigned lt_mask = (1u << lane) - 1u;
+  for (int64_t r = int64_t(blockIdx.x) * kScatterWarps + warp; r < p.n_rows;
+       r += int64_t(gridDim.x) * kScatterWarps) {
+    const int64_t s0 = p.slot_ptr[r];
+    const int ns = int(p.slot_ptr[r + 1] - s0);
+    const int64_t k0 = p.row_ptr[r];
+    const int64_t c0 = p.code_ptr[r];
+    const int nc = ns * p.nl;
+    const int my_slot = lane < ns ? p.slots[s0 + lane] : 0;
+    const uint4* c4 = reinterpret_cast<const uint4*>(p.codes + c0);
+    const int nc8 = (nc + 7) >> 3;
+    for (int i = lane; i < nc8; i += 32) reinterpret_cast<uint4*>(scode)[i] = __ldg(c4 + i);
+    const int nv = ns * vper;
+    for (int base = 0; base < nv; base += 32) {
+      const int i = base + lane;
+      const int s = min(i / vper, ns - 1);
+      const int sid = __shfl_sync(kFull, my_slot, s);
+      if (i < nv) reinterpret_cast<uint4*>(ske)[i] = __ldg(ke4 + int64_t(sid) * vper + (i - s * vper));
+    }
+    if (p.rhs != nullptr) {
+      // the same exact fixed-point sum, the terms spread over the lanes
+      uint64_t m = 0;
+      int ex = 1;
+      bool ng = false;
+      if (lane < ns) FxTraits<double>::split(p.fe[my_slot], m, ex, ng);
+      const int emax = __reduce_max_sync(kFull, m != 0 ? ex : 1);
+      const int sh = FxTraits<double>::kShift0 - (emax - ex);
+      const uint64_t a = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+      int64_t S = ng ? -int64_t(a) : int64_t(a);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) S += __shfl_xor_sync(kFull, S, off);
+      if (lane == 0) p.rhs[r] = fx_to_double(S, emax - FxTraits<double>::kScale);
+    }
+    __syncwarp();
+    int heads = 0;
+    for (int cb = 0; cb < nc; cb += 32) {
+      const int i = cb + lane;
+      const bool h = i < nc && (scode[i] & 0x8000u) != 0;
+      const unsigned m = __ballot_sync(kFull, h);
+      if (h) sseg[heads + __popc(m & lt_mask)] = uint16_t(i);
+      heads += __popc(m);
+    }
+    if (lane == 0) sseg[heads] = uint16_t(nc);
+    __syncwarp();
+    for (int k = lane; k < heads; k += 32) {
+      const int a = sseg[k], b = sseg[k + 1];
+      p.values[k0 + k] = fx_sum<TK>(b - a, [&](int t) {
+        const unsigned code = scode[a + t];
+        return ske[((code >> 8) & 127u) * p.nlp + (code & 255u)];
+      });
+    }
+    __syncwarp();
+  }
+}
+
+static int align16(long x) { return int((x + 15) & ~15L); }
+
 cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st) {
   if (s->hs.n_dofs == 0) return cudaSuccess;
   ScatterParams p;
   p.n_rows = s->hs.n_dofs;
   p.nl = s->nl;
+  p.nlp = s->nlp;
   p.row_ptr = s->d_row_ptr;
   p.cnt = s->d_cnt;
   p.code_ptr = s->d_code_ptr;
@@ -346,9 +578,27 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
   p.fe = s->d_fe;
   p.values = values;
   p.rhs = rhs;
+  const int tk = prec == FE_PREC_FP64 ? 8 : 4;
+  p.ke_bytes = align16(long(s->hs.max_slots) * s->nlp * tk);
+  p.code_bytes = align16(((long(s->hs.max_slots) * s->nl + 7) & ~7L) * 2);
+  p.warp_bytes = p.ke_bytes + p.code_bytes + align16((s->hs.max_row_nnz + 1) * 2);
+  const long smem = long(p.warp_bytes) * kScatterWarps;
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
   const int64_t need = (p.n_rows + kScatterWarps - 1) / kScatterWarps;
+  if (smem <= 200 * 1024 && s->hs.max_slots <= 32 && long(s->hs.max_slots) * s->nl < 65536) {
+    auto launch = [&](auto kern) -> cudaError_t {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScatterWarps * 32, size_t(smem));
+      if (e != cudaSuccess) return e;
+      const int blocks = int(std::min<int64_t>(need, int64_t(nsm) * std::max(1, per_sm)));
+      kern<<<blocks, kScatterWarps * 32, size_t(smem), st>>>(p);
+      return cudaGetLastError();
+    };
+    return prec == FE_PREC_FP64 ? launch(k_scatter_rows<double>) : launch(k_scatter_rows<float>);
+  }
   const int blocks = int(std::min<int64_t>(need, int64_t(nsm) * 8));
   if (prec == FE_PREC_FP64)
     k_scatter<double><<<blocks, kScatterWarps * 32, 0, st>>>(p);

@@ -17,6 +17,12 @@ constexpr int kErrTimeout = 2;
 cudaError_t launch_cell_integration(const fe_space* s, const double* coef, const double force[3],
                                     fe_precision prec, cudaStream_t st);
 
+// Tensor-core (tcgen05) cell integration for Q2 elasticity with the 3^3 rule,
+// FP32 (3xTF32) and BF16 forms; same outputs as launch_cell_integration.
+bool cell_tc_applicable(const fe_space* s, fe_precision prec);
+cudaError_t launch_cell_tc(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
+                           cudaStream_t st);
+
 // Deterministic scatter of the cell matrices/vectors into CSR values / RHS.
 cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st);
 

@@ -234,8 +234,10 @@ static int number_dofs(int p, int ncomp, int64_t n_cells, const int32_t* cv, std
 // DOF r ("slots", ascending cell id). Every pair (slot s, local column m) is a
 // contribution to nonzero (r, cell_dofs[e_s][m]); contributions are sorted by
 // column and, within one nonzero, by slot, i.e. by ascending cell. The code of
-// a contribution is (s << 8) | m; the scatter kernel reads
-// K^{e_s}[local row of r in e_s][m].
+// a contribution is (head << 15) | (s << 8) | m, where head marks the first
+// contribution of each nonzero; the scatter kernel reads
+// K^{e_s}[local row of r in e_s][m]. The codes of a row start on a 16-byte
+// boundary (each row's block is padded to a multiple of 8 codes).
 static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body);
 
 int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
@@ -260,7 +262,7 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
   int max_slots = 0;
   for (int64_t r = 0; r < nd; ++r) max_slots = std::max<int64_t>(max_slots, hs->slot_ptr[r + 1]);
   if (max_slots > kMaxSlots) {
-    *err = "more than 255 cells around one DOF";
+    *err = "more than 127 cells around one DOF";
     return FE_ERR_UNSUPPORTED;
   }
   hs->max_slots = max_slots;
@@ -290,17 +292,19 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
   hs->code_ptr.assign(nd + 1, 0);
   for (int64_t r = 0; r < nd; ++r) {
     hs->row_ptr[r + 1] = hs->row_ptr[r] + row_nnz[r];
-    hs->code_ptr[r + 1] = hs->code_ptr[r] + (hs->slot_ptr[r + 1] - hs->slot_ptr[r]) * nl;
+    hs->code_ptr[r + 1] = hs->code_ptr[r] + (((hs->slot_ptr[r + 1] - hs->slot_ptr[r]) * nl + 7) & ~int64_t(7));
   }
   hs->nnz = hs->row_ptr[nd];
-  hs->n_contrib = hs->code_ptr[nd];
+  for (int64_t r = 0; r < nd; ++r) hs->max_row_nnz = std::max(hs->max_row_nnz, row_nnz[r]);
+  hs->n_codes = hs->code_ptr[nd];
+  hs->n_contrib = ninc * nl;
   if (hs->nnz > (int64_t(1) << 40)) {
     *err = "too many nonzeros";
     return FE_ERR_UNSUPPORTED;
   }
   hs->col.assign(hs->nnz, 0);
   hs->cnt.assign(hs->nnz, 0);
-  hs->codes.assign(hs->n_contrib, 0);
+  hs->codes.assign(hs->n_codes, 0);
   // pass 2: sorted contributions per row
   parallel_for(nd, nthreads, [&](int, int64_t r0, int64_t r1) {
     std::vector<uint64_t> keys;
@@ -320,13 +324,15 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
       int64_t prev = -1;
       for (uint64_t key : keys) {
         const int64_t col = int64_t(key >> 16);
+        uint16_t head = 0;
         if (col != prev) {
           ++k;
           hs->col[k] = int32_t(col);
           prev = col;
+          head = 0x8000;
         }
         hs->cnt[k]++;
-        hs->codes[c++] = uint16_t(key & 0xffff);
+        hs->codes[c++] = uint16_t((key & 0xffff) | head);
       }
     }
   });

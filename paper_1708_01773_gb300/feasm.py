@@ -28,7 +28,7 @@ ERRORS = {
 EXPORTS = [
     "fe_space_create", "fe_space_create_host", "fe_space_sizes", "fe_space_cell_dofs_host",
     "fe_space_csr_pattern_host", "fe_space_permutation_host", "fe_space_csr_pattern", "fe_assemble", "fe_assemble_ex", "fe_assemble_host",
-    "fe_assemble_adjoint", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
+    "fe_assemble_adjoint", "fe_space_set_kernel", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
     "fe_batch_assemble", "fe_batch_destroy",
 ]
 
@@ -67,6 +67,7 @@ def lib() -> ctypes.CDLL:
         L.fe_assemble_ex.argtypes = [V, V, V, V, V, I, V, V]
         L.fe_assemble_adjoint.argtypes = [V, V, V, D, V, V, I, V]
         L.fe_status.argtypes = [V, V]
+        L.fe_space_set_kernel.argtypes = [V, I]
         L.fe_space_destroy.argtypes = [V]
         L.fe_space_destroy.restype = None
         L.fe_last_error.argtypes = []
@@ -146,9 +147,11 @@ def fe_space_permutation_host(space: int):
     n_dofs, nnz, n_cells, n_contrib = fe_space_sizes(space)
     cnt = np.zeros(nnz, dtype=np.uint8)
     code_ptr = np.zeros(n_dofs + 1, dtype=np.int64)
-    codes = np.zeros(n_contrib, dtype=np.uint16)
     slot_ptr = np.zeros(n_dofs + 1, dtype=np.int64)
     slots = np.zeros(int(slot_count(space)), dtype=np.int32)
+    _check(lib().fe_space_permutation_host(space, cnt.ctypes.data, code_ptr.ctypes.data, None,
+                                           slot_ptr.ctypes.data, slots.ctypes.data), "fe_space_permutation_host")
+    codes = np.zeros(int(code_ptr[-1]), dtype=np.uint16)
     _check(lib().fe_space_permutation_host(space, cnt.ctypes.data, code_ptr.ctypes.data, codes.ctypes.data,
                                            slot_ptr.ctypes.data, slots.ctypes.data), "fe_space_permutation_host")
     return cnt, code_ptr, codes, slot_ptr, slots
@@ -188,6 +191,14 @@ def fe_assemble_adjoint(space: int, u, coefficients, grad_scale: float, dc_dcoef
                         stream=None):
     _check(lib().fe_assemble_adjoint(space, _ptr(u), _ptr(coefficients), float(grad_scale), _ptr(dc_dcoef),
                                      _ptr(compliance), prec, _stream(stream)), "fe_assemble_adjoint")
+
+
+FE_KERNEL_AUTO, FE_KERNEL_CUDA_CORE, FE_KERNEL_TENSOR_CORE = 0, 1, 2
+KERNELS = {"auto": FE_KERNEL_AUTO, "cuda_core": FE_KERNEL_CUDA_CORE, "tensor_core": FE_KERNEL_TENSOR_CORE}
+
+
+def fe_space_set_kernel(space: int, kernel: str):
+    _check(lib().fe_space_set_kernel(space, KERNELS[kernel]), "fe_space_set_kernel")
 
 
 def fe_status(space: int, stream=None) -> int:
@@ -258,6 +269,9 @@ class FESpace:
             out = torch.empty(self.n_cells, dtype=torch.float64, device=u.device)
         fe_assemble_adjoint(self.handle, u, coef, grad_scale, out, compliance, PRECISIONS[prec], stream)
         return out
+
+    def set_kernel(self, kernel: str):
+        fe_space_set_kernel(self.handle, kernel)
 
     def status(self, stream=None) -> int:
         return fe_status(self.handle, stream)

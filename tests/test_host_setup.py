@@ -73,16 +73,18 @@ def test_numbering_pattern_permutation_match_oracle(shape, p, problem):
         assert np.all(cd.reshape(-1)[sl] == r)
         rhs[r] = fe.reshape(-1)[sl].sum()
         c = code_ptr[r]
+        assert c % 8 == 0 and code_ptr[r + 1] - c == (len(sl) * nl + 7) // 8 * 8
         for k in range(rp[r], rp[r + 1]):
             seg = codes[c:c + cnt[k]].astype(np.int64)
             c += cnt[k]
-            s, m = seg >> 8, seg & 255
+            head, s, m = seg >> 15, (seg >> 8) & 127, seg & 255
+            assert head[0] == 1 and np.all(head[1:] == 0)        # a run per nonzero
             assert np.all(np.diff(s) > 0)                        # ascending cell within a nonzero
             src = sl[s].astype(np.int64) * nl + m
             assert np.all(cd.reshape(-1)[(sl[s] // nl) * nl + m] == col[k])
             seen[src] += 1
             vals[k] = Kflat[src].sum()
-        assert c == code_ptr[r + 1]
+        assert c == code_ptr[r] + len(sl) * nl
     assert np.all(seen == 1)                                     # a permutation of all contributions
     np.testing.assert_allclose(vals, val_o, rtol=0, atol=1e-13 * np.abs(val_o).max())
     np.testing.assert_allclose(rhs, rhs_o, rtol=0, atol=1e-14)
