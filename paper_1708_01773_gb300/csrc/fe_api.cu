@@ -41,7 +41,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 
 void free_device(fe_space* s) {
   void* ptrs[] = {s->d_xv, s->d_w, s->d_xq, s->d_phi, s->d_dphi, s->d_dphi32, s->d_cell_dofs, s->d_row_ptr,
-                  s->d_col, s->d_cnt, s->d_code_ptr, s->d_codes, s->d_slot_ptr, s->d_slots, s->d_ke, s->d_fe,
+                  s->d_col, s->d_cnt, s->d_code_ptr, s->d_codes, s->d_pos, s->d_slot_ptr, s->d_slots, s->d_ke, s->d_fe,
                   s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -116,6 +116,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     if (e == cudaSuccess) e = upload(&s->d_cnt, hs.cnt.data(), hs.cnt.size());
     if (e == cudaSuccess) e = upload(&s->d_code_ptr, hs.code_ptr.data(), hs.code_ptr.size());
     if (e == cudaSuccess) e = upload(&s->d_codes, hs.codes.data(), hs.codes.size());
+    if (e == cudaSuccess) e = upload(&s->d_pos, hs.pos.data(), hs.pos.size());
     if (e == cudaSuccess) e = upload(&s->d_slot_ptr, hs.slot_ptr.data(), hs.slot_ptr.size());
     if (e == cudaSuccess) e = upload(&s->d_slots, hs.slots.data(), hs.slots.size());
     const size_t nke = size_t(s->n_cells) * s->nl * s->nlp;
@@ -134,6 +135,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     // the large host arrays are no longer needed (cell_dofs, row_ptr and col are kept for inspection)
     std::vector<uint8_t>().swap(s->hs.cnt);
     std::vector<uint16_t>().swap(s->hs.codes);
+    std::vector<uint16_t>().swap(s->hs.pos);
     std::vector<int64_t>().swap(s->hs.code_ptr);
     std::vector<int32_t>().swap(s->hs.slots);
   }

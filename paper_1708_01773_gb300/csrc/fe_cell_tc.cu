@@ -30,9 +30,9 @@ constexpr int GS = 85;  // row stride of the G staging area (odd: conflict-free 
 constexpr int OFF_AHI = 0, OFF_ALO = 16384, OFF_BHI = 32768, OFF_BLO = 45056;
 constexpr int OPER_BYTES = 57344;
 constexpr int OFF_G = 57344;
-constexpr int OFF_GEO32 = (OFF_G + NL * GS * 4 + 15) & ~15;  // [27][12] float: cof (9), w/det
-constexpr int OFF_DJW = OFF_GEO32 + NQ * 12 * 4;     // [27] double: w*det
-constexpr int OFF_X = OFF_DJW + NQ * 8;              // [24] double
+constexpr int OFF_GEO32 = (OFF_G + NL * GS * 4 + 15) & ~15;  // [2][27][12] float: cof (9), w/det
+constexpr int OFF_DJW = OFF_GEO32 + 2 * NQ * 12 * 4;  // [2][27] double: w*det
+constexpr int OFF_X = OFF_DJW + 2 * NQ * 8;          // [24] double
 constexpr int OFF_A = OFF_X + 24 * 8;                // [21] double
 constexpr int OFF_BAR = (OFF_A + 21 * 8 + 7) & ~7;   // mbarrier (8 bytes)
 constexpr int OFF_TMEM = OFF_BAR + 8;                // tensor-memory base address
@@ -182,15 +182,41 @@ struct Params {
   int* err;
 };
 
+// Geometry of cell e by one warp (FP64): vertex coordinates, monomial
+// coefficients, then one lane per quadrature point writes the FP32 cofactors,
+// w/det J (geo32) and w det J (djw). Returns false (and sets the error word) if
+// some det J <= 0.
+__device__ __forceinline__ void warp_geometry(const Params& p, int64_t e, int lane, double* X, double* A,
+                                              float* geo32, double* djw) {
+  if (lane < 24) X[lane] = p.xv[e * 24 + lane];
+  __syncwarp();
+  if (lane < 3) tri_coef(X, lane, A);
+  __syncwarp();
+  if (lane < NQ) {
+    double cof[9], det;
+    cof_det(A, p.xq[3 * lane], p.xq[3 * lane + 1], p.xq[3 * lane + 2], cof, &det);
+    if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
+    const double wq = p.w[lane];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) geo32[lane * 12 + t] = float(cof[t]);
+    geo32[lane * 12 + 9] = float(wq / det);
+    djw[lane] = wq * det;
+  }
+  __syncwarp();
+}
+
 // Persistent: each CTA loops over cells blockIdx.x, blockIdx.x + gridDim.x, ...
+// Warp 0 also carries the FP64 work: the geometry of the next cell while the
+// MMAs of the current one run, and the current cell vector while warps 1-7
+// form the cell matrix; the geometry is double-buffered.
 template <bool BF16>
 __global__ void __launch_bounds__(THREADS) k_cell_tc(Params p) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   float* G = reinterpret_cast<float*>(sm + OFF_G);
-  float* geo32 = reinterpret_cast<float*>(sm + OFF_GEO32);
-  double* djw = reinterpret_cast<double*>(sm + OFF_DJW);
+  float* geo32_0 = reinterpret_cast<float*>(sm + OFF_GEO32);
+  double* djw_0 = reinterpret_cast<double*>(sm + OFF_DJW);
   double* X = reinterpret_cast<double*>(sm + OFF_X);
   double* A = reinterpret_cast<double*>(sm + OFF_A);
   const uint32_t sbase = smem_u32(sm);
@@ -209,6 +235,7 @@ __global__ void __launch_bounds__(THREADS) k_cell_tc(Params p) {
   }
   // zero the operand area once: padding rows/columns are never written again
   for (int i = tid; i < OPER_BYTES / 16; i += THREADS) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  if (warp == 0 && int64_t(blockIdx.x) < p.n_cells) warp_geometry(p, blockIdx.x, lane, X, A, geo32_0, djw_0);
   fence_before();
   __syncthreads();
   fence_after();
@@ -216,48 +243,40 @@ __global__ void __launch_bounds__(THREADS) k_cell_tc(Params p) {
   constexpr uint32_t IDESC = instr_desc(M, N, BF16 ? 1u : 2u);
   uint32_t phase = 0;
   bool abort = false;
+  int buf = 0;
 
-  for (int64_t e = blockIdx.x; e < p.n_cells; e += gridDim.x) {
-    // 1. geometry (FP64)
-    if (tid < 24) X[tid] = p.xv[e * 24 + tid];
-    __syncthreads();
-    if (tid < 3) tri_coef(X, tid, A);
-    __syncthreads();
-    if (tid < NQ) {
-      double cof[9], det;
-      cof_det(A, p.xq[3 * tid], p.xq[3 * tid + 1], p.xq[3 * tid + 2], cof, &det);
-      if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
-      const double wq = p.w[tid];
-#pragma unroll
-      for (int t = 0; t < 9; ++t) geo32[tid * 12 + t] = float(cof[t]);
-      geo32[tid * 12 + 9] = float(wq / det);
-      djw[tid] = wq * det;
-    }
-    __syncthreads();
-    // 2. operands: A[(i,a)][q] = (w/det) gh_{a,i}(q), B[(j,b)][q] = gh_{b,j}(q)
-    for (int idx = tid; idx < NL * NQ; idx += THREADS) {
-      const int m = idx / NQ, q = idx - m * NQ;
-      const int i = m / NB, a = m - i * NB;
+  for (int64_t e = blockIdx.x; e < p.n_cells; e += gridDim.x, buf ^= 1) {
+    const float* geo32 = geo32_0 + buf * (NQ * 12);
+    const double* djw = djw_0 + buf * NQ;
+    // 1. operands: A[(i,a)][q] = (w/det) gh_{a,i}(q), B[(j,b)][q] = gh_{b,j}(q);
+    //    one thread per (node a, point q) forms the three components i.
+    for (int idx = tid; idx < NB * NQ; idx += THREADS) {
+      const int a = idx / NQ, q = idx - a * NQ;
       const float* gq = geo32 + q * 12;
       const float* dp = p.dphi32 + (q * NB + a) * 3;
-      const float g = fmaf(gq[3 * i + 2], dp[2], fmaf(gq[3 * i + 1], dp[1], gq[3 * i] * dp[0]));
-      const float av = gq[9] * g;
-      if (BF16) {
-        const uint32_t o = swz(m, q * 2);
-        *reinterpret_cast<__nv_bfloat16*>(sm + OFF_AHI + o) = __float2bfloat16_rn(av);
-        *reinterpret_cast<__nv_bfloat16*>(sm + OFF_BHI + o) = __float2bfloat16_rn(g);
-      } else {
-        const uint32_t o = swz(m, q * 4);
-        const float ah = to_tf32(av), bh = to_tf32(g);
-        *reinterpret_cast<float*>(sm + OFF_AHI + o) = ah;
-        *reinterpret_cast<float*>(sm + OFF_ALO + o) = to_tf32(av - ah);
-        *reinterpret_cast<float*>(sm + OFF_BHI + o) = bh;
-        *reinterpret_cast<float*>(sm + OFF_BLO + o) = to_tf32(g - bh);
+      const float d0 = dp[0], d1 = dp[1], d2 = dp[2], sq = gq[9];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float g = fmaf(gq[3 * i + 2], d2, fmaf(gq[3 * i + 1], d1, gq[3 * i] * d0));
+        const float av = sq * g;
+        const int m = i * NB + a;
+        if (BF16) {
+          const uint32_t o = swz(m, q * 2);
+          *reinterpret_cast<__nv_bfloat16*>(sm + OFF_AHI + o) = __float2bfloat16_rn(av);
+          *reinterpret_cast<__nv_bfloat16*>(sm + OFF_BHI + o) = __float2bfloat16_rn(g);
+        } else {
+          const uint32_t o = swz(m, q * 4);
+          const float ah = to_tf32(av), bh = to_tf32(g);
+          *reinterpret_cast<float*>(sm + OFF_AHI + o) = ah;
+          *reinterpret_cast<float*>(sm + OFF_ALO + o) = to_tf32(av - ah);
+          *reinterpret_cast<float*>(sm + OFF_BHI + o) = bh;
+          *reinterpret_cast<float*>(sm + OFF_BLO + o) = to_tf32(g - bh);
+        }
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    // 3. one thread issues the MMAs; completion is signalled on the mbarrier
+    // 2. one thread issues the MMAs; completion is signalled on the mbarrier
     if (tid == 0) {
       fence_after();
       const uint64_t ahi = sw128_desc(sbase + OFF_AHI), alo = sw128_desc(sbase + OFF_ALO);
@@ -279,6 +298,10 @@ __global__ void __launch_bounds__(THREADS) k_cell_tc(Params p) {
       }
       mma_commit(bar);
     }
+    __syncwarp();
+    // 3. warp 0: geometry of the next cell (FP64) while the MMAs run
+    if (warp == 0 && e + gridDim.x < p.n_cells)
+      warp_geometry(p, e + gridDim.x, lane, X, A, geo32_0 + (buf ^ 1) * (NQ * 12), djw_0 + (buf ^ 1) * NQ);
     // 4. bounded wait for the MMAs (about one second of clock cycles at most)
     {
       const long long t0 = clock64();
@@ -320,36 +343,38 @@ __global__ void __launch_bounds__(THREADS) k_cell_tc(Params p) {
     }
     fence_before();
     __syncthreads();
-    // 6. K^e from the Gram blocks, 16-byte stores; cell vector in FP64
-    {
+    // 6. warps 1-7: K^e from the Gram blocks, one thread per node pair (a, b)
+    //    (the nine G^{ij}_ab give the nine entries K_(a,i),(b,j): the
+    //    transposed block and the trace come from the same values);
+    //    consecutive threads take consecutive b (conflict-free reads,
+    //    coalesced stores). Warp 0: the FP64 cell vector.
+    if (warp > 0) {
       const float E = float(p.coef[e]);
-      const float lh = p.lam_hat, mh = p.mu_hat;
+      const float lh = p.lam_hat * E, mh = p.mu_hat * E;
       float* K = p.ke + e * (NL * NLP);
-      for (int idx = tid; idx < NL * (NLP / 4); idx += THREADS) {
-        const int l = idx / (NLP / 4), c4 = idx - l * (NLP / 4);
-        const int i = l / NB, a = l - i * NB;
-        float out[4];
+      for (int idx = tid - 32; idx < NB * NB; idx += THREADS - 32) {
+        const int a = idx / NB, b = idx - a * NB;
+        float g[3][3];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int m = 4 * c4 + t;
-          float v = 0.f;
-          if (m < NL) {
-            const int j = m / NB, b = m - j * NB;
-            v = lh * G[l * GS + m] + mh * G[(j * NB + a) * GS + i * NB + b];
-            if (i == j) v += mh * (G[a * GS + b] + G[(NB + a) * GS + NB + b] + G[(2 * NB + a) * GS + 2 * NB + b]);
-            v *= E;
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) g[i][j] = G[(i * NB + a) * GS + j * NB + b];
+        const float tr = g[0][0] + g[1][1] + g[2][2];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            float v = lh * g[i][j] + mh * g[j][i];
+            if (i == j) v += mh * tr;
+            K[(i * NB + a) * NLP + j * NB + b] = v;
           }
-          out[t] = v;
-        }
-        *reinterpret_cast<float4*>(K + l * NLP + 4 * c4) = make_float4(out[0], out[1], out[2], out[3]);
       }
-      if (tid < NB) {
-        double f = 0.0;
-        for (int q = 0; q < NQ; ++q) f += djw[q] * p.phi[q * NB + tid];
-        double* fe = p.fe + e * NL;
+    } else if (lane < NB) {
+      double f = 0.0;
+      for (int q = 0; q < NQ; ++q) f += djw[q] * p.phi[q * NB + lane];
+      double* fe = p.fe + e * NL;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) fe[k * NB + tid] = p.f[k] * f;
-      }
+      for (int k = 0; k < 3; ++k) fe[k * NB + lane] = p.f[k] * f;
     }
     __syncthreads();
   }

@@ -35,6 +35,7 @@ struct HostSetup {
   std::vector<uint8_t> cnt;         // [nnz] contributions per nonzero
   std::vector<int64_t> code_ptr;    // [n_dofs+1] first code of each row
   std::vector<uint16_t> codes;      // (head << 15) | (slot << 8) | local column, rows padded to 8 codes
+  std::vector<uint16_t> pos;        // same blocks, slot-major: nonzero index within the row of (slot, column)
   std::vector<int64_t> slot_ptr;    // [n_dofs+1]
   std::vector<int32_t> slots;       // [n_cells*nl] e*nl + local row, cells ascending
 };
@@ -69,6 +70,7 @@ struct fe_space {
   uint8_t* d_cnt = nullptr;
   int64_t* d_code_ptr = nullptr;
   uint16_t* d_codes = nullptr;
+  uint16_t* d_pos = nullptr;
   int64_t* d_slot_ptr = nullptr;
   int32_t* d_slots = nullptr;
   void* d_ke = nullptr;          // cell matrices, [n_cells][nl][nlp] FP64 or FP32

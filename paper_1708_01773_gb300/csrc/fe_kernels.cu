@@ -446,13 +446,14 @@ struct ScatterParams {
   const uint8_t* cnt;
   const int64_t* code_ptr;
   const uint16_t* codes;
+  const uint16_t* pos;
   const int64_t* slot_ptr;
   const int32_t* slots;
   const void* ke;
   const double* fe;
   double* values;
   double* rhs;
-  int ke_bytes, code_bytes, warp_bytes;
+  int ke_bytes, code_bytes, warp_bytes, acc_stride;
 };
 
 constexpr unsigned kFull = 0xffffffffu;
@@ -560,6 +561,118 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
   }
 }
 
+// Exact RHS entry of row r: the cells' FP64 cell-vector entries, one per lane
+// (lanes < ns), summed in integer fixed point across the warp.
+__device__ __forceinline__ void rhs_row(const ScatterParams& p, int64_t r, int ns, int my_slot, int lane) {
+  uint64_t m = 0;
+  int ex = 1;
+  bool ng = false;
+  if (lane < ns) FxTraits<double>::split(p.fe[my_slot], m, ex, ng);
+  const int emax = __reduce_max_sync(kFull, m != 0 ? ex : 1);
+  const int sh = FxTraits<double>::kShift0 - (emax - ex);
+  const uint64_t a = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+  int64_t S = ng ? -int64_t(a) : int64_t(a);
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) S += __shfl_xor_sync(kFull, S, off);
+  if (lane == 0) p.rhs[r] = fx_to_double(S, emax - FxTraits<double>::kScale);
+}
+
+// Exact FP32 -> FP64 conversion of any finite float on the integer bits
+// (denormals included), without the FP64 pipe.
+__device__ __forceinline__ double f32_to_f64_exact(float x) {
+  double d;
+  if (f32_to_f64_bits(x, d)) return d;
+  uint64_t m;
+  int ex;
+  bool ng;
+  FxTraits<float>::split(x, m, ex, ng);
+  return fx_to_double(ng ? -int64_t(m) : int64_t(m), ex - 150);
+}
+
+// hi + lo of a double-float accumulator, rounded once to the nearest double:
+// both parts convert exactly, and one FP64 addition rounds their exact sum.
+__device__ __forceinline__ double df_to_double(float hi, float lo) {
+  double dh, dl;
+  if (!f32_to_f64_bits(hi, dh)) dh = f32_to_f64_exact(hi);
+  if (lo == 0.f) return dh;
+  if (!f32_to_f64_bits(lo, dl)) dl = f32_to_f64_exact(lo);
+  return __dadd_rn(dh, dl);
+}
+
+// Slot-wise scatter for FP32 cell matrices (the FP32 and BF16 forms). One warp
+// per CSR row r: for each cell around DOF r in ascending order ("slot"), the
+// lanes read that cell's matrix row (coalesced) and the slot-major positions
+// pos[s][m] of its entries among the row's nonzeros, and add each entry into
+// a per-row double-float accumulator (hi, lo) in shared memory with Knuth's
+// TwoSum (the rounding error of every addition is kept exactly in lo). The
+// entries of one cell row go to distinct nonzeros, so the lanes never collide;
+// a __syncwarp between slots orders the additions, so every nonzero sums its
+// terms in ascending cell order. The accumulator is rounded once to FP64
+// (df_to_double) and stored coalesced. Global loads of up to SB slots are
+// issued before their additions to keep several in flight per lane.
+template <int NL>
+__global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_slots(ScatterParams p) {
+  constexpr int CH = (NL + 31) / 32;
+  constexpr int SB = CH >= 3 ? 4 : 8;
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float* acc_hi = reinterpret_cast<float*>(sm + size_t(warp) * p.warp_bytes);
+  float* acc_lo = acc_hi + p.acc_stride;
+  const float* ke = reinterpret_cast<const float*>(p.ke) + lane;
+  for (int64_t r = int64_t(blockIdx.x) * kScatterWarps + warp; r < p.n_rows;
+       r += int64_t(gridDim.x) * kScatterWarps) {
+    const int64_t s0 = p.slot_ptr[r];
+    const int ns = int(p.slot_ptr[r + 1] - s0);
+    const int64_t k0 = p.row_ptr[r];
+    const int nnz = int(p.row_ptr[r + 1] - k0);
+    const uint16_t* pos = p.pos + p.code_ptr[r] + lane;
+    const int my_slot = lane < ns ? p.slots[s0 + lane] : 0;
+    for (int k = lane; k < nnz; k += 32) {
+      acc_hi[k] = 0.f;
+      acc_lo[k] = 0.f;
+    }
+    if (p.rhs != nullptr) rhs_row(p, r, ns, my_slot, lane);
+    __syncwarp();
+    for (int sb0 = 0; sb0 < ns; sb0 += SB) {
+      float x[SB][CH];
+      int kk[SB][CH];
+#pragma unroll
+      for (int t = 0; t < SB; ++t) {
+        const int s = sb0 + t;
+        const int sid = __shfl_sync(kFull, my_slot, s < ns ? s : ns - 1);
+        const float* krow = ke + int64_t(sid) * p.nlp;
+        const uint16_t* prow = pos + s * NL;
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+          const bool ok = s < ns && (c < CH - 1 || c * 32 + lane < NL);
+          x[t][c] = ok ? __ldg(krow + c * 32) : 0.f;
+          kk[t][c] = ok ? int(__ldg(prow + c * 32)) : 0;
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < SB; ++t) {
+        if (sb0 + t < ns) {
+#pragma unroll
+          for (int c = 0; c < CH; ++c) {
+            if (c < CH - 1 || c * 32 + lane < NL) {
+              const int k = kk[t][c];
+              const float h = acc_hi[k], v = x[t][c];
+              const float sum = h + v;
+              const float bp = sum - h;
+              const float err = (h - (sum - bp)) + (v - bp);
+              acc_hi[k] = sum;
+              acc_lo[k] += err;
+            }
+          }
+          __syncwarp();
+        }
+      }
+    }
+    for (int k = lane; k < nnz; k += 32) p.values[k0 + k] = df_to_double(acc_hi[k], acc_lo[k]);
+    __syncwarp();
+  }
+}
+
 static int align16(long x) { return int((x + 15) & ~15L); }
 
 cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st) {
@@ -572,6 +685,7 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
   p.cnt = s->d_cnt;
   p.code_ptr = s->d_code_ptr;
   p.codes = s->d_codes;
+  p.pos = s->d_pos;
   p.slot_ptr = s->d_slot_ptr;
   p.slots = s->d_slots;
   p.ke = s->d_ke;
@@ -581,23 +695,40 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
   const int tk = prec == FE_PREC_FP64 ? 8 : 4;
   p.ke_bytes = align16(long(s->hs.max_slots) * s->nlp * tk);
   p.code_bytes = align16(((long(s->hs.max_slots) * s->nl + 7) & ~7L) * 2);
-  p.warp_bytes = p.ke_bytes + p.code_bytes + align16((s->hs.max_row_nnz + 1) * 2);
-  const long smem = long(p.warp_bytes) * kScatterWarps;
+  const int rows_warp_bytes = p.ke_bytes + p.code_bytes + align16((s->hs.max_row_nnz + 1) * 2);
+  const long smem = long(rows_warp_bytes) * kScatterWarps;
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
   const int64_t need = (p.n_rows + kScatterWarps - 1) / kScatterWarps;
-  if (smem <= 200 * 1024 && s->hs.max_slots <= 32 && long(s->hs.max_slots) * s->nl < 65536) {
-    auto launch = [&](auto kern) -> cudaError_t {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      if (e != cudaSuccess) return e;
-      int per_sm = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScatterWarps * 32, size_t(smem));
-      if (e != cudaSuccess) return e;
-      const int blocks = int(std::min<int64_t>(need, int64_t(nsm) * std::max(1, per_sm)));
-      kern<<<blocks, kScatterWarps * 32, size_t(smem), st>>>(p);
-      return cudaGetLastError();
-    };
-    return prec == FE_PREC_FP64 ? launch(k_scatter_rows<double>) : launch(k_scatter_rows<float>);
+  auto launch = [&](auto kern, long bytes) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(bytes));
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kScatterWarps * 32, size_t(bytes));
+    if (e != cudaSuccess) return e;
+    const int blocks = int(std::min<int64_t>(need, int64_t(nsm) * std::max(1, per_sm)));
+    kern<<<blocks, kScatterWarps * 32, size_t(bytes), st>>>(p);
+    return cudaGetLastError();
+  };
+  if (prec != FE_PREC_FP64 && s->hs.max_slots <= 32) {
+    p.acc_stride = int((s->hs.max_row_nnz + 3) & ~int64_t(3));
+    p.warp_bytes = p.acc_stride * 8;
+    const long bytes = long(p.warp_bytes) * kScatterWarps;
+    if (bytes <= 200 * 1024) {
+      switch (s->nl) {
+        case 8: return launch(k_scatter_slots<8>, bytes);
+        case 24: return launch(k_scatter_slots<24>, bytes);
+        case 27: return launch(k_scatter_slots<27>, bytes);
+        case 64: return launch(k_scatter_slots<64>, bytes);
+        case 81: return launch(k_scatter_slots<81>, bytes);
+        case 192: return launch(k_scatter_slots<192>, bytes);
+        default: break;
+      }
+    }
+  }
+  p.warp_bytes = rows_warp_bytes;
+  if (smem <= 200 * 1024 && s->hs.max_slots <= 32) {
+    return prec == FE_PREC_FP64 ? launch(k_scatter_rows<double>, smem) : launch(k_scatter_rows<float>, smem);
   }
   const int blocks = int(std::min<int64_t>(need, int64_t(nsm) * 8));
   if (prec == FE_PREC_FP64)

@@ -237,7 +237,9 @@ static int number_dofs(int p, int ncomp, int64_t n_cells, const int32_t* cv, std
 // a contribution is (head << 15) | (s << 8) | m, where head marks the first
 // contribution of each nonzero; the scatter kernel reads
 // K^{e_s}[local row of r in e_s][m]. The codes of a row start on a 16-byte
-// boundary (each row's block is padded to a multiple of 8 codes).
+// boundary (each row's block is padded to a multiple of 8 codes). The same
+// blocks also hold, slot-major, the index within the row of the nonzero that
+// each (slot, local column) contributes to ("pos"), for the slot-wise scatter.
 static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body);
 
 int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
@@ -261,6 +263,10 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
   for (int64_t i = 0; i < ninc; ++i) hs->slot_ptr[hs->cell_dofs[i] + 1]++;
   int max_slots = 0;
   for (int64_t r = 0; r < nd; ++r) max_slots = std::max<int64_t>(max_slots, hs->slot_ptr[r + 1]);
+  if (max_slots * nl > 65535) {
+    *err = "a row's contributions exceed 16-bit positions";
+    return FE_ERR_UNSUPPORTED;
+  }
   if (max_slots > kMaxSlots) {
     *err = "more than 127 cells around one DOF";
     return FE_ERR_UNSUPPORTED;
@@ -305,6 +311,7 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
   hs->col.assign(hs->nnz, 0);
   hs->cnt.assign(hs->nnz, 0);
   hs->codes.assign(hs->n_codes, 0);
+  hs->pos.assign(hs->n_codes, 0);
   // pass 2: sorted contributions per row
   parallel_for(nd, nthreads, [&](int, int64_t r0, int64_t r1) {
     std::vector<uint64_t> keys;
@@ -333,6 +340,8 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
         }
         hs->cnt[k]++;
         hs->codes[c++] = uint16_t((key & 0xffff) | head);
+        const int64_t s_m = int64_t((key >> 8) & 0xff) * nl + int64_t(key & 0xff);
+        hs->pos[hs->code_ptr[r] + s_m] = uint16_t(k - hs->row_ptr[r]);
       }
     }
   });
