@@ -177,6 +177,29 @@ int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients
 enum { FE_KERNEL_AUTO = 0, FE_KERNEL_CUDA_CORE = 1, FE_KERNEL_TENSOR_CORE = 2 };
 int fe_space_set_kernel(fe_space* s, int cell_kernel);
 
+/* fe_assemble_adjoint without any memory allocation (the paper has no
+ * counterpart; this is a service for callers that cannot allocate). Same
+ * arguments, results and determinism as fe_assemble_adjoint.
+ *
+ * For applications that own all device memory through their own pool and do
+ * not allow a library to call cudaMalloc, and for loops that must not enter
+ * the CUDA allocator while they run (cudaMalloc / cudaFree can synchronise the
+ * device). The call itself allocates nothing: the reduction scratch of the
+ * compliance is a fixed 512 KB array in the library's device image (held by
+ * every GPU that loads the library until the process exits).
+ * Limits and rules:
+ *   - with `compliance` non-NULL the space may have at most 8,388,608 cells
+ *     (FE_ERR_UNSUPPORTED with a message otherwise); without it, any size;
+ *   - the current device must be the space's device;
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - all calls share the one array, so calls that overlap on the GPU (on
+ *     different streams, or from different threads) race and may return a
+ *     wrong compliance: serialise them. Nothing in the array needs clearing:
+ *     each call writes every entry it reads. */
+int fe_assemble_adjoint_noalloc(fe_space* s, const double* u, const double* coefficients, double grad_scale,
+                                double* dc_dcoef, double* compliance, fe_precision prec, void* stream);
+
 /* Synchronises `stream`, returns and clears the device error word:
  * FE_OK, FE_ERR_NEG_JACOBIAN (some det J <= 0 at a quadrature point) or
  * FE_ERR_TIMEOUT (a bounded persistent-kernel wait gave up). */

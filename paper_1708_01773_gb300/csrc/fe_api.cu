@@ -145,6 +145,10 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
 
 }  // namespace
 
+namespace feasm {
+int set_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace feasm
+
 extern "C" {
 
 const char* fe_last_error(void) { return g_last_error.c_str(); }

@@ -26,6 +26,19 @@ cudaError_t launch_cell_tc(const fe_space* s, const double* coef, const double f
 // Deterministic scatter of the cell matrices/vectors into CSR values / RHS.
 cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st);
 
+// Threads per block of the adjoint kernel (one cell per thread); its per-block
+// partial sums of the compliance are what the reduction scratch holds.
+constexpr int kAdjointBlock = 128;
+
+// Records a message for fe_last_error() and returns `code`.
+int set_error(int code, const char* msg);
+
+// The adjoint with caller-provided reduction scratch `partials` of capacity
+// `max_partials` doubles (one per block of kAdjointBlock cells).
+cudaError_t launch_adjoint_with_scratch(const fe_space* s, const double* u, const double* coef, double grad_scale,
+                                        double* g, double* compliance, fe_precision prec, double* partials,
+                                        int max_partials, cudaStream_t st);
+
 // Compliance sensitivities and (optionally) the compliance.
 cudaError_t launch_adjoint(const fe_space* s, const double* u, const double* coef, double grad_scale,
                            double* g, double* compliance, fe_precision prec, cudaStream_t st);

@@ -28,7 +28,7 @@ ERRORS = {
 EXPORTS = [
     "fe_space_create", "fe_space_create_host", "fe_space_sizes", "fe_space_cell_dofs_host",
     "fe_space_csr_pattern_host", "fe_space_permutation_host", "fe_space_csr_pattern", "fe_assemble", "fe_assemble_ex", "fe_assemble_host",
-    "fe_assemble_adjoint", "fe_space_set_kernel", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
+    "fe_assemble_adjoint", "fe_assemble_adjoint_noalloc", "fe_space_set_kernel", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
     "fe_batch_assemble", "fe_batch_destroy",
 ]
 
@@ -66,6 +66,7 @@ def lib() -> ctypes.CDLL:
         L.fe_assemble_host.argtypes = [V, V, V, V, V, I, V]
         L.fe_assemble_ex.argtypes = [V, V, V, V, V, I, V, V]
         L.fe_assemble_adjoint.argtypes = [V, V, V, D, V, V, I, V]
+        L.fe_assemble_adjoint_noalloc.argtypes = [V, V, V, D, V, V, I, V]
         L.fe_status.argtypes = [V, V]
         L.fe_space_set_kernel.argtypes = [V, I]
         L.fe_space_destroy.argtypes = [V]
@@ -199,6 +200,14 @@ KERNELS = {"auto": FE_KERNEL_AUTO, "cuda_core": FE_KERNEL_CUDA_CORE, "tensor_cor
 
 def fe_space_set_kernel(space: int, kernel: str):
     _check(lib().fe_space_set_kernel(space, KERNELS[kernel]), "fe_space_set_kernel")
+
+
+def fe_assemble_adjoint_noalloc(space: int, u, coefficients, grad_scale: float, dc_dcoef, compliance, prec: int,
+                                stream=None):
+    """fe_assemble_adjoint with its reduction scratch in a static device array (no allocation)."""
+    _check(lib().fe_assemble_adjoint_noalloc(space, _ptr(u), _ptr(coefficients), float(grad_scale),
+                                             _ptr(dc_dcoef), _ptr(compliance), prec, _stream(stream)),
+           "fe_assemble_adjoint_noalloc")
 
 
 def fe_status(space: int, stream=None) -> int:
