@@ -119,8 +119,10 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     if (e == cudaSuccess) e = upload(&s->d_pos, hs.pos.data(), hs.pos.size());
     if (e == cudaSuccess) e = upload(&s->d_slot_ptr, hs.slot_ptr.data(), hs.slot_ptr.size());
     if (e == cudaSuccess) e = upload(&s->d_slots, hs.slots.data(), hs.slots.size());
+    // FP64-sized (the FP32 forms use the first half); 256 bytes of padding for the
+    // scatter's whole-chunk reads past the end of the last cell row
     const size_t nke = size_t(s->n_cells) * s->nl * s->nlp;
-    if (e == cudaSuccess && nke) e = cudaMalloc(&s->d_ke, nke * sizeof(double));
+    if (e == cudaSuccess && nke) e = cudaMalloc(&s->d_ke, nke * sizeof(double) + 256);
     if (e == cudaSuccess && s->n_cells) e = cudaMalloc(&s->d_fe, size_t(s->n_cells) * s->nl * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->d_err, 0, sizeof(int));

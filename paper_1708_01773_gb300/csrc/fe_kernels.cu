@@ -115,22 +115,22 @@ __device__ __forceinline__ void kahan_add(T& sum, T& carry, T part) {
 // tensor rule) whose FP32 partials are added with Kahan compensation. PREC 2:
 // BF16-rounded operands, FP32 products and sums. Cell matrices are stored
 // row-major with row stride NLP (16-byte aligned rows).
+// cell_block integrates cells e0 .. e0 + ncell - 1 (ncell <= prm.cpb) with the
+// whole thread block, using `smem` (cell_smem_bytes) as scratch; k_cell runs
+// one such block per thread block, the batched driver any number of them.
 template <int P, int NC, int PREC>
-__global__ void __launch_bounds__(kCellThreads) k_cell(CellParams prm) {
+__device__ __forceinline__ void cell_block(const CellParams& prm, int64_t e0, int ncell, double* smem) {
   constexpr int NB = (P + 1) * (P + 1) * (P + 1);
   constexpr int NL = NC * NB;
   constexpr int NLP = (NL + 3) & ~3;
   using T = typename std::conditional<PREC == 0, double, float>::type;
-  extern __shared__ __align__(16) double smem[];
   const int cpb = prm.cpb, nq = prm.nq;
   double* sx = smem;
   double* sa = sx + cpb * 24;
   double* geo = sa + cpb * 21;
   float* geo32 = reinterpret_cast<float*>(geo + cpb * nq * 11);
   T* g = reinterpret_cast<T*>(PREC == 0 ? reinterpret_cast<float*>(geo + cpb * nq * 11) : geo32 + cpb * nq * 12);
-  const int64_t e0 = int64_t(blockIdx.x) * cpb;
   const int tid = threadIdx.x;
-  const int ncell = int(prm.n_cells - e0 < cpb ? prm.n_cells - e0 : cpb);
 
   for (int i = tid; i < ncell * 24; i += blockDim.x) sx[i] = prm.xv[e0 * 24 + i];
   __syncthreads();
@@ -255,6 +255,14 @@ __global__ void __launch_bounds__(kCellThreads) k_cell(CellParams prm) {
 #pragma unroll
     for (int k = 0; k < NC; ++k) fe[k * NB + a] = prm.f[k] * f;
   }
+}
+
+template <int P, int NC, int PREC>
+__global__ void __launch_bounds__(kCellThreads) k_cell(CellParams prm) {
+  extern __shared__ __align__(16) double smem[];
+  const int64_t e0 = int64_t(blockIdx.x) * prm.cpb;
+  const int ncell = int(prm.n_cells - e0 < prm.cpb ? prm.n_cells - e0 : prm.cpb);
+  cell_block<P, NC, PREC>(prm, e0, ncell, smem);
 }
 
 template <int P, int NC, int PREC>
@@ -589,13 +597,39 @@ __device__ __forceinline__ double f32_to_f64_exact(float x) {
   return fx_to_double(ng ? -int64_t(m) : int64_t(m), ex - 150);
 }
 
+// FP32 -> FP64 bits for zero and normal numbers (exponent rebias by 1023 - 127
+// = 896 on the shifted exponent/mantissa field); `ok` is cleared for
+// denormals, infinities and NaNs, which take the general path.
+__device__ __forceinline__ double f32_to_f64_fast(float x, bool& ok) {
+  const uint32_t u = __float_as_uint(x);
+  const uint32_t mag = u & 0x7fffffffu;
+  const uint32_t e = mag >> 23;
+  ok = ok && (mag == 0 || (e != 0 && e != 0xffu));
+  const uint64_t body = mag == 0 ? 0ull : ((uint64_t(mag) << 29) + (uint64_t(896) << 52));
+  return __longlong_as_double(static_cast<long long>((uint64_t(u >> 31) << 63) | body));
+}
+
+// Aligned integer mantissa for the two-term sum below: m * 2^sh, with the bits
+// shifted out (sh < 0) folded into a sticky lowest bit.
+__device__ __forceinline__ uint64_t fx_align_sticky(uint64_t m, int sh) {
+  if (sh >= 0) return m << sh;
+  if (sh <= -64) return m != 0 ? 1ull : 0ull;
+  const uint64_t kept = m >> (-sh);
+  return kept | ((m & ((1ull << (-sh)) - 1ull)) != 0 ? 1ull : 0ull);
+}
+
 // hi + lo of a double-float accumulator, rounded once to the nearest double:
-// both parts convert exactly, and one FP64 addition rounds their exact sum.
+// both parts convert exactly on the integer bits, and one FP64 addition
+// (only where lo is non-zero) rounds their exact sum.
 __device__ __forceinline__ double df_to_double(float hi, float lo) {
-  double dh, dl;
-  if (!f32_to_f64_bits(hi, dh)) dh = f32_to_f64_exact(hi);
-  if (lo == 0.f) return dh;
-  if (!f32_to_f64_bits(lo, dl)) dl = f32_to_f64_exact(lo);
+  bool ok = true;
+  double dh = f32_to_f64_fast(hi, ok);
+  if (lo == 0.f && ok) return dh;
+  double dl = f32_to_f64_fast(lo, ok);
+  if (!ok) {
+    dh = f32_to_f64_exact(hi);
+    dl = f32_to_f64_exact(lo);
+  }
   return __dadd_rn(dh, dl);
 }
 
@@ -608,29 +642,47 @@ __device__ __forceinline__ double df_to_double(float hi, float lo) {
 // entries of one cell row go to distinct nonzeros, so the lanes never collide;
 // a __syncwarp between slots orders the additions, so every nonzero sums its
 // terms in ascending cell order. The accumulator is rounded once to FP64
-// (df_to_double) and stored coalesced. Global loads of up to SB slots are
-// issued before their additions to keep several in flight per lane.
-template <int NL>
-__global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_slots(ScatterParams p) {
+// (df_to_double) and stored coalesced. Lanes past the end of a cell row
+// (m >= NL) read padding and add zero into a private dummy accumulator, so the
+// inner loop has no divergent branches (the position array and the
+// cell-matrix scratch are allocated with enough padding for those reads).
+// Global loads of up to SB slots are issued before their additions, and the
+// row descriptors (pointers, slot ids) of the warp's next row are fetched
+// while the current row is reduced.
+template <int NL, bool IDX32>
+__global__ void __launch_bounds__(kScatterWarps * 32, 5) k_scatter_slots(ScatterParams p) {
   constexpr int CH = (NL + 31) / 32;
   constexpr int SB = CH >= 3 ? 4 : 8;
   extern __shared__ __align__(16) unsigned char sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float* acc_hi = reinterpret_cast<float*>(sm + size_t(warp) * p.warp_bytes);
-  float* acc_lo = acc_hi + p.acc_stride;
+  float2* acc = reinterpret_cast<float2*>(sm + size_t(warp) * p.warp_bytes);
+  const int dummy = p.acc_stride + lane;
   const float* ke = reinterpret_cast<const float*>(p.ke) + lane;
-  for (int64_t r = int64_t(blockIdx.x) * kScatterWarps + warp; r < p.n_rows;
-       r += int64_t(gridDim.x) * kScatterWarps) {
-    const int64_t s0 = p.slot_ptr[r];
-    const int ns = int(p.slot_ptr[r + 1] - s0);
-    const int64_t k0 = p.row_ptr[r];
-    const int nnz = int(p.row_ptr[r + 1] - k0);
-    const uint16_t* pos = p.pos + p.code_ptr[r] + lane;
-    const int my_slot = lane < ns ? p.slots[s0 + lane] : 0;
-    for (int k = lane; k < nnz; k += 32) {
-      acc_hi[k] = 0.f;
-      acc_lo[k] = 0.f;
+  const int64_t stride = int64_t(gridDim.x) * kScatterWarps;
+  int64_t r = int64_t(blockIdx.x) * kScatterWarps + warp;
+  int64_t s0 = 0, k0 = 0, c0 = 0;
+  int ns = 0, nnz = 0, my_slot = 0;
+  if (r < p.n_rows) {
+    s0 = p.slot_ptr[r];
+    ns = int(p.slot_ptr[r + 1] - s0);
+    k0 = p.row_ptr[r];
+    nnz = int(p.row_ptr[r + 1] - k0);
+    c0 = p.code_ptr[r];
+    my_slot = lane < ns ? p.slots[s0 + lane] : 0;
+  }
+  for (; r < p.n_rows; r += stride) {
+    // first-level descriptors of the next row (independent loads)
+    const int64_t rn = r + stride;
+    int64_t s0n = 0, s1n = 0, k0n = 0, k1n = 0, c0n = 0;
+    if (rn < p.n_rows) {
+      s0n = p.slot_ptr[rn];
+      s1n = p.slot_ptr[rn + 1];
+      k0n = p.row_ptr[rn];
+      k1n = p.row_ptr[rn + 1];
+      c0n = p.code_ptr[rn];
     }
+    const uint16_t* pos = p.pos + c0 + lane;
+    for (int k = lane; k < nnz; k += 32) acc[k] = make_float2(0.f, 0.f);
     if (p.rhs != nullptr) rhs_row(p, r, ns, my_slot, lane);
     __syncwarp();
     for (int sb0 = 0; sb0 < ns; sb0 += SB) {
@@ -638,15 +690,15 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_slots(ScatterPar
       int kk[SB][CH];
 #pragma unroll
       for (int t = 0; t < SB; ++t) {
-        const int s = sb0 + t;
-        const int sid = __shfl_sync(kFull, my_slot, s < ns ? s : ns - 1);
-        const float* krow = ke + int64_t(sid) * p.nlp;
+        const int s = sb0 + t < ns ? sb0 + t : ns - 1;
+        const int sid = __shfl_sync(kFull, my_slot, s);
+        const float* krow = IDX32 ? ke + uint32_t(sid) * uint32_t(p.nlp) : ke + int64_t(sid) * p.nlp;
         const uint16_t* prow = pos + s * NL;
 #pragma unroll
         for (int c = 0; c < CH; ++c) {
-          const bool ok = s < ns && (c < CH - 1 || c * 32 + lane < NL);
-          x[t][c] = ok ? __ldg(krow + c * 32) : 0.f;
-          kk[t][c] = ok ? int(__ldg(prow + c * 32)) : 0;
+          x[t][c] = __ldg(krow + c * 32);
+          const int k = int(__ldg(prow + c * 32));
+          kk[t][c] = (c < CH - 1 || c * 32 + lane < NL) ? k : dummy;
         }
       }
 #pragma unroll
@@ -654,22 +706,32 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_slots(ScatterPar
         if (sb0 + t < ns) {
 #pragma unroll
           for (int c = 0; c < CH; ++c) {
-            if (c < CH - 1 || c * 32 + lane < NL) {
-              const int k = kk[t][c];
-              const float h = acc_hi[k], v = x[t][c];
-              const float sum = h + v;
-              const float bp = sum - h;
-              const float err = (h - (sum - bp)) + (v - bp);
-              acc_hi[k] = sum;
-              acc_lo[k] += err;
-            }
+            const int k = kk[t][c];
+            const float v = (c < CH - 1 || c * 32 + lane < NL) ? x[t][c] : 0.f;
+            const float2 a = acc[k];
+            const float sum = a.x + v;
+            const float bp = sum - a.x;
+            const float err = (a.x - (sum - bp)) + (v - bp);
+            acc[k] = make_float2(sum, a.y + err);
           }
           __syncwarp();
         }
       }
     }
-    for (int k = lane; k < nnz; k += 32) p.values[k0 + k] = df_to_double(acc_hi[k], acc_lo[k]);
+    // second-level descriptor of the next row (its slot ids)
+    const int nsn = int(s1n - s0n);
+    const int my_slot_n = (rn < p.n_rows && lane < nsn) ? p.slots[s0n + lane] : 0;
+    for (int k = lane; k < nnz; k += 32) {
+      const float2 a = acc[k];
+      p.values[k0 + k] = df_to_double(a.x, a.y);
+    }
     __syncwarp();
+    s0 = s0n;
+    ns = nsn;
+    k0 = k0n;
+    nnz = int(k1n - k0n);
+    c0 = c0n;
+    my_slot = my_slot_n;
   }
 }
 
@@ -712,16 +774,23 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
   };
   if (prec != FE_PREC_FP64 && s->hs.max_slots <= 32) {
     p.acc_stride = int((s->hs.max_row_nnz + 3) & ~int64_t(3));
-    p.warp_bytes = p.acc_stride * 8;
+    p.warp_bytes = (p.acc_stride + 32) * 8;  // accumulators + one dummy per lane
     const long bytes = long(p.warp_bytes) * kScatterWarps;
     if (bytes <= 200 * 1024) {
-      switch (s->nl) {
-        case 8: return launch(k_scatter_slots<8>, bytes);
-        case 24: return launch(k_scatter_slots<24>, bytes);
-        case 27: return launch(k_scatter_slots<27>, bytes);
-        case 64: return launch(k_scatter_slots<64>, bytes);
-        case 81: return launch(k_scatter_slots<81>, bytes);
-        case 192: return launch(k_scatter_slots<192>, bytes);
+      const bool idx32 = int64_t(s->n_cells) * s->nl * s->nlp < (int64_t(1) << 32);
+      switch (s->nl * 2 + (idx32 ? 1 : 0)) {
+        case 16: return launch(k_scatter_slots<8, false>, bytes);
+        case 17: return launch(k_scatter_slots<8, true>, bytes);
+        case 48: return launch(k_scatter_slots<24, false>, bytes);
+        case 49: return launch(k_scatter_slots<24, true>, bytes);
+        case 54: return launch(k_scatter_slots<27, false>, bytes);
+        case 55: return launch(k_scatter_slots<27, true>, bytes);
+        case 128: return launch(k_scatter_slots<64, false>, bytes);
+        case 129: return launch(k_scatter_slots<64, true>, bytes);
+        case 162: return launch(k_scatter_slots<81, false>, bytes);
+        case 163: return launch(k_scatter_slots<81, true>, bytes);
+        case 384: return launch(k_scatter_slots<192, false>, bytes);
+        case 385: return launch(k_scatter_slots<192, true>, bytes);
         default: break;
       }
     }

@@ -311,7 +311,9 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
   hs->col.assign(hs->nnz, 0);
   hs->cnt.assign(hs->nnz, 0);
   hs->codes.assign(hs->n_codes, 0);
-  hs->pos.assign(hs->n_codes, 0);
+  // 64 entries of padding: the scatter's lanes read whole 32-wide chunks of a
+  // cell row's positions, past the end of the last row's block
+  hs->pos.assign(hs->n_codes + 64, 0);
   // pass 2: sorted contributions per row
   parallel_for(nd, nthreads, [&](int, int64_t r0, int64_t r1) {
     std::vector<uint64_t> keys;
