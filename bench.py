@@ -46,6 +46,10 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
+    ap.add_argument("--extras", action="store_true",
+                    help="also time the 128^3 Q1 elasticity assembly and the 64^3 cantilever adjoint")
+    ap.add_argument("--batched", action="store_true",
+                    help="also time the 64-mesh batched assembly (host setup takes minutes)")
     return ap.parse_args()
 
 
@@ -57,6 +61,22 @@ def dist_env():
 
 
 # ----------------------------------------------------------------------------- helpers
+def max_over_ranks(x: float, device=None) -> float:
+    """Maximum of a per-rank scalar over all ranks (timing only; no data path)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
+def whole_job_rate(units_per_rank: int, world_size: int, steps: int, ms_total: float) -> float:
+    """Units per second over all ranks: every rank processes its own replica."""
+    return world_size * units_per_rank * steps / (ms_total / 1e3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -139,13 +159,16 @@ def kernel_traffic(kernel: str):
 
 
 def scatter_bytes(sp, prec: str) -> int:
-    """Algorithmic bytes of one scatter launch: every cell-matrix entry read once, one
-    16-bit code per contribution, one count byte per nonzero, the FP64 values written,
-    the row/slot tables and the cell vectors read, the RHS written."""
-    ke = 8 if prec == "fp64" else 4
+    """Algorithmic bytes of one scatter launch: every cell-matrix entry read once
+    (FP32, or FP64 for the FP64 form), one 16-bit permutation entry per
+    contribution (slot-major positions; destination-sorted codes plus one count
+    byte per nonzero for the FP64 form), the FP64 values written, the slot lists,
+    cell vectors and row descriptors read, the RHS written."""
     nl = sp.nl
-    return int(sp.n_cells * nl * nl * ke + sp.n_contrib * 2 + sp.nnz * (1 + 8)
-               + sp.n_cells * nl * (4 + 8) + (sp.n_dofs + 1) * 8 * 3 + sp.n_dofs * 8)
+    common = sp.nnz * 8 + sp.n_cells * nl * (4 + 8) + (sp.n_dofs + 1) * 8 * 3 + sp.n_dofs * 8
+    if prec == "fp64":
+        return int(sp.n_cells * nl * nl * 8 + sp.n_contrib * 2 + sp.nnz + common)
+    return int(sp.n_cells * nl * nl * 4 + sp.n_contrib * 2 + common)
 
 
 def cell_bytes(sp, prec: str) -> int:
@@ -224,6 +247,76 @@ def reference_arm(args):
     return 0
 
 
+# ----------------------------------------------------------------------------- extra workloads
+def time_events(fn, n, stream):
+    import torch
+    for _ in range(3):
+        fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(n):
+        fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / n
+
+
+def extra_workloads(args, dev, stream):
+    """Secondary measurements: the scatter-bound 128^3 Q1 elasticity assembly, the
+    64^3 Q1 cantilever compliance adjoint and (optionally) the batched assembly."""
+    import torch
+    from paper_1708_01773_gb300 import feasm, inputs
+    out = {}
+    prob = inputs.elasticity_q1_128()
+    sp = feasm.FESpace(prob)
+    coef = torch.tensor(prob.coef, device=dev)
+    vals = torch.empty(sp.nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(sp.n_dofs, dtype=torch.float64, device=dev)
+    rec = {}
+    for prec in ("fp32", "fp64"):
+        ms = time_events(lambda: feasm.fe_assemble(sp.handle, coef, prob.force, vals, rhs, feasm.PRECISIONS[prec],
+                                                   stream), 10, stream)
+        rec[prec] = {"ms_per_step": ms, "cells_per_s": sp.n_cells / (ms / 1e3), "nnz_per_s": sp.nnz / (ms / 1e3)}
+    out["elasticity_q1_128"] = {"cells": sp.n_cells, "nnz": sp.nnz, **rec}
+    sp.close()
+    del vals, rhs
+    prob = inputs.cantilever_q1_64()
+    sp = feasm.FESpace(prob)
+    u = torch.tensor(inputs.unit_rms_field(sp.n_dofs, inputs.SEED_BASE + 5), device=dev)
+    E = torch.tensor(prob.coef, device=dev)
+    g = torch.empty(sp.n_cells, dtype=torch.float64, device=dev)
+    c = torch.empty(1, dtype=torch.float64, device=dev)
+    rec = {}
+    for prec in ("fp64", "fp32"):
+        ms = time_events(lambda: feasm.fe_assemble_adjoint(sp.handle, u, E, 1.0, g, c, feasm.PRECISIONS[prec],
+                                                           stream), 20, stream)
+        rec[prec] = {"ms_per_call": ms, "cells_per_s": sp.n_cells / (ms / 1e3)}
+    out["cantilever_q1_64_adjoint"] = {"cells": sp.n_cells, **rec}
+    sp.close()
+    if args.batched:
+        probs = inputs.batched64()
+        t0 = time.perf_counter()
+        spaces = [feasm.FESpace(p) for p in probs]
+        setup = time.perf_counter() - t0
+        coefs = [torch.tensor(p.coef, device=dev) for p in probs]
+        vals = [torch.empty(s.nnz, dtype=torch.float64, device=dev) for s in spaces]
+        rhss = [torch.empty(s.n_dofs, dtype=torch.float64, device=dev) for s in spaces]
+        cells = sum(s.n_cells for s in spaces)
+        nnz = sum(s.nnz for s in spaces)
+        rec = {}
+        for prec in ("fp32", "fp64"):
+            b = feasm.fe_batch_create([s.handle for s in spaces])
+            ms = time_events(lambda: feasm.fe_batch_assemble(b, coefs, [p.force for p in probs], vals, rhss,
+                                                             feasm.PRECISIONS[prec], stream), 3, stream)
+            rec[prec] = {"ms_per_step": ms, "cells_per_s": cells / (ms / 1e3), "nnz_per_s": nnz / (ms / 1e3)}
+            feasm.fe_batch_destroy(b)
+        out["batched64"] = {"meshes": len(probs), "cells": cells, "nnz": nnz, "setup_s": setup,
+                            "redraw_attempt": probs[0].extra.get("attempt"), **rec}
+        for s in spaces:
+            s.close()
+    return out
+
+
 # ----------------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -284,12 +377,9 @@ def main():
     total_ms = ev[0][0].elapsed_time(ev[2][K - 1])
     cell_ms = [ev[0][k].elapsed_time(ev[1][k]) for k in range(K)]
     scat_ms = [ev[1][k].elapsed_time(ev[2][k]) for k in range(K)]
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t)
+    total_ms = max_over_ranks(total_ms, dev)
     ms_per_step = total_ms / K
-    value = ws * sp.n_cells * K / (total_ms / 1e3)
+    value = whole_job_rate(sp.n_cells, ws, K, total_ms)
 
     # end to end through the host-buffer entry point (pinned memory, copies timed)
     Ke2e = max(3, min(K, 20))
@@ -303,10 +393,7 @@ def main():
         feasm.fe_assemble_host(sp.handle, hc, prob.force, hv, hr, prec, stream)
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / Ke2e
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t)
+    e2e_s = max_over_ranks(e2e_s, dev)
 
     # same-GPU comparators (plain FP64 assembler, BF16 form)
     comparators = {}
@@ -341,6 +428,8 @@ def main():
             "frac": kernels[dom]["frac"], "traffic": kernel_traffic(dom),
             "algorithmic_bytes": kernels[dom]["bytes"], "peak_source": peak_src + " (burst copy)"}
 
+    extras = extra_workloads(args, dev, stream) if (args.extras or args.batched) else None
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, dt = oracle_rate(prob, 12.0)
@@ -368,6 +457,8 @@ def main():
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
+        if extras:
+            out["extra_workloads"] = extras
         print(json.dumps(out), flush=True)
     sp.close()
     if ws > 1:

@@ -211,15 +211,26 @@ void fe_space_destroy(fe_space* s);
 const char* fe_last_error(void);
 
 /* Batched assembly: several independent spaces (any order, problem and size)
- * assembled by one persistent launch pair over a shared work list of
- * (space, cell tile) and (space, row block) items. The batch keeps pointers to
- * the spaces, which must outlive it.
- *   cells_per_item  cells per contraction work item, 0 = autotuned default. */
+ * assembled by one persistent launch over a shared work list of (space, cell
+ * block) and (space, row block) items, replayed from a CUDA graph. A row item
+ * waits (bounded, about one second; FE_ERR_TIMEOUT in the spaces' error
+ * words after that) until its space's cells are integrated. Cell items use
+ * the CUDA-core cell kernel; results match fe_assemble's CUDA-core path and
+ * are deterministic. The batch keeps pointers to the spaces, which must
+ * outlive it; spaces must be on the current device with at most 32 cells
+ * around any DOF.
+ *   cells_per_item  cells per cell item, 0 = autotuned: the first
+ *                   fe_batch_assemble of each precision times the candidate
+ *                   item sizes on the caller's buffers (running the assembly
+ *                   a few times), keeps the fastest, allocates its work list
+ *                   and captures its CUDA graph; make that first call before
+ *                   any stream capture of your own. */
 int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch** out);
 
 /* coefficients[i], csr_values[i], rhs[i] are the device buffers of space i
- * (rhs[i] may be NULL); body_force is host [n*3] (force of space i at 3*i).
- * Same semantics and determinism as fe_assemble for every space. */
+ * (rhs may be NULL, or rhs[i] NULL); body_force is host [n*3] (force of
+ * space i at 3*i). Same semantics as fe_assemble for every space; errors found
+ * on the device surface through fe_status of the spaces. */
 int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const double* body_force,
                       double* const* csr_values, double* const* rhs, fe_precision prec, void* stream);
 

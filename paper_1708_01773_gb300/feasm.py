@@ -230,7 +230,8 @@ def fe_batch_assemble(batch: int, coefficients, body_forces, csr_values, rhs, pr
     cp = (ctypes.c_void_p * n)(*[_ptr(c) for c in coefficients])
     vp = (ctypes.c_void_p * n)(*[_ptr(v) for v in csr_values])
     rp = (ctypes.c_void_p * n)(*[_ptr(r) for r in rhs])
-    f = np.ascontiguousarray(np.concatenate([np.resize(np.asarray(b, dtype=np.float64), 3) for b in body_forces]))
+    f = np.ascontiguousarray(np.concatenate([np.resize(np.asarray(b, dtype=np.float64), 3) for b in body_forces]
+                                            + [np.zeros(3)]))
     _check(lib().fe_batch_assemble(batch, cp, f.ctypes.data, vp, rp, prec, _stream(stream)), "fe_batch_assemble")
 
 

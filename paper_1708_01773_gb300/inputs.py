@@ -21,7 +21,8 @@ problems, all synthetic):
 * ``elasticity_q1_128`` Elasticity Q1, 128^3 cells of the unit cube, shifts up to
   0.2h, E = 10^U[log10 0.5, log10 5], nu = 0.3, f = (0,0,-1), 2^3 Gauss.
 * ``batched64``        64 unit-cube meshes with n ~ U{10..40} cells per axis,
-  p ~ U{1,2,3}, problem ~ Bernoulli(1/2), (p+1)^3 Gauss, shifts up to 0.2h.
+  p ~ U{1,2,3}, problem ~ Bernoulli(1/2), (p+1)^3 Gauss, shifts up to 0.2h;
+  redrawn while the estimated GPU footprint exceeds half of the GPU memory.
 * ``cantilever_q1_64`` Elasticity Q1, 64^3 cells of the unit cube, E ~ U[0.1,1],
   nu = 0.3, shifts up to 0.2h, u ~ N(0,1) per DOF rescaled to unit RMS.
 """
@@ -137,15 +138,55 @@ def elasticity_q1_128(n: int = 128, seed_offset: int = 3) -> Problem:
     return Problem("elasticity_q1_128", mesh, 1, 2, ELASTICITY, coef, np.array([0.0, 0.0, -1.0]))
 
 
-def batched64(n_meshes: int = 64, n_lo: int = 10, n_hi: int = 40, seed_offset: int = 4) -> list[Problem]:
-    """Independent meshes of uneven size and mixed order, one child seed each."""
-    children = np.random.SeedSequence(SEED_BASE + seed_offset).spawn(n_meshes)
+def _coupled_pairs_1d(n: int, p: int) -> int:
+    """Pairs of the (p n + 1) nodes of a 1D line of n cells that share a cell."""
+    m = p * n + 1
+    count = 0
+    for i in range(m):
+        ci = {min(i // p, n - 1)} | ({i // p - 1} if (i % p == 0 and i > 0) else set())
+        for j in range(max(0, i - 2 * p), min(m, i + 2 * p + 1)):
+            cj = {min(j // p, n - 1)} | ({j // p - 1} if (j % p == 0 and j > 0) else set())
+            if ci & cj:
+                count += 1
+    return count
+
+
+def device_footprint(n: int, p: int, problem: int) -> int:
+    """Bytes the assembly of an n^3 brick of order p holds on the GPU: CSR values,
+    columns and counts per nonzero, two 16-bit permutation arrays per contribution,
+    and the FP64-sized cell-matrix scratch (a budget estimate, not exact)."""
+    c = 3 if problem == ELASTICITY else 1
+    nnz = _coupled_pairs_1d(n, p) ** 3 * c * c
+    nl = c * (p + 1) ** 3
+    nlp = (nl + 3) // 4 * 4
+    return nnz * (8 + 4 + 1) + n ** 3 * nl * nl * 4 + n ** 3 * nl * nlp * 8
+
+
+def batched64(n_meshes: int = 64, n_lo: int = 10, n_hi: int = 40, seed_offset: int = 4,
+              budget_bytes: float = 140e9) -> list[Problem]:
+    """Independent meshes of uneven size and mixed order, one child seed each.
+
+    A draw whose estimated device footprint exceeds `budget_bytes` (half of the
+    GPU's memory by default) is redrawn from the next spawn key of the same seed.
+    """
+    for attempt in range(10000):
+        base = np.random.SeedSequence(SEED_BASE + seed_offset, spawn_key=(attempt,) if attempt else ())
+        children = base.spawn(n_meshes)
+        draws = []
+        total = 0
+        for ss in children:
+            rng = np.random.default_rng(ss)
+            n = int(rng.integers(n_lo, n_hi + 1))
+            p = int(rng.integers(1, 4))
+            prob = int(rng.integers(0, 2))
+            draws.append((ss, n, p, prob))
+            total += device_footprint(n, p, prob)
+        if total <= budget_bytes:
+            break
     out = []
-    for m, ss in enumerate(children):
+    for m, (ss, n, p, prob) in enumerate(draws):
         rng = np.random.default_rng(ss)
-        n = int(rng.integers(n_lo, n_hi + 1))
-        p = int(rng.integers(1, 4))
-        prob = int(rng.integers(0, 2))
+        rng.integers(n_lo, n_hi + 1), rng.integers(1, 4), rng.integers(0, 2)  # the draws above
         mesh = perturb_interior(brick(n, n, n), 0.2, rng)
         if prob == POISSON:
             coef = _log_uniform(rng, 0.1, 10.0, mesh.n_cells)
@@ -153,7 +194,8 @@ def batched64(n_meshes: int = 64, n_lo: int = 10, n_hi: int = 40, seed_offset: i
         else:
             coef = rng.uniform(1.0, 10.0, size=mesh.n_cells)
             force = np.array([0.0, 0.0, -1.0])
-        out.append(Problem(f"batch{m}_p{p}_{'ela' if prob else 'poi'}_n{n}", mesh, p, p + 1, prob, coef, force))
+        out.append(Problem(f"batch{m}_p{p}_{'ela' if prob else 'poi'}_n{n}", mesh, p, p + 1, prob, coef, force,
+                           extra={"attempt": attempt, "footprint": device_footprint(n, p, prob)}))
     return out
 
 
