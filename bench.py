@@ -144,8 +144,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def source_sha(files) -> str:
+    """Short hash of the kernel's source files (csrc/), to tell stale counters."""
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1708_01773_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(kernel: str):
-    """DRAM traffic per launch from a committed ncu summary, if the kernel source is unchanged."""
+    """DRAM traffic per launch from a committed ncu summary, if the kernel sources
+    are unchanged since the counters were taken (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
@@ -153,9 +162,7 @@ def kernel_traffic(kernel: str):
         d = json.load(f).get(kernel)
     if not d:
         return None
-    src = os.path.join(ROOT, "paper_1708_01773_gb300", "csrc", d["source"])
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return d["bytes_per_launch"] if sha == d["source_sha"] else None
+    return d["bytes_per_launch"] if source_sha(d["sources"]) == d["sources_sha"] else None
 
 
 def scatter_bytes(sp, prec: str) -> int:
