@@ -268,6 +268,24 @@ def time_events(fn, n, stream):
     return a.elapsed_time(b) / n
 
 
+def split_kernels(sp, coef, force, vals, rhs, prec, stream, n=5):
+    """Cell-kernel and scatter times (ms) of one assembly, from an event recorded between them."""
+    import torch
+    from paper_1708_01773_gb300 import feasm
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(n)] for _ in range(3)]
+    for e in evs[1]:
+        e.record(stream)
+    torch.cuda.synchronize()
+    for k in range(n):
+        evs[0][k].record(stream)
+        feasm.fe_assemble_ex(sp.handle, coef, force, vals, rhs, feasm.PRECISIONS[prec], stream, evs[1][k].cuda_event)
+        evs[2][k].record(stream)
+    torch.cuda.synchronize()
+    cell = float(np.mean([evs[0][k].elapsed_time(evs[1][k]) for k in range(n)]))
+    scat = float(np.mean([evs[1][k].elapsed_time(evs[2][k]) for k in range(n)]))
+    return {"cell_ms": cell, "scatter_ms": scat}
+
+
 def extra_workloads(args, dev, stream):
     """Secondary measurements: the scatter-bound 128^3 Q1 elasticity assembly, the
     64^3 Q1 cantilever compliance adjoint and (optionally) the batched assembly."""
@@ -283,7 +301,8 @@ def extra_workloads(args, dev, stream):
     for prec in ("fp32", "fp64"):
         ms = time_events(lambda: feasm.fe_assemble(sp.handle, coef, prob.force, vals, rhs, feasm.PRECISIONS[prec],
                                                    stream), 10, stream)
-        rec[prec] = {"ms_per_step": ms, "cells_per_s": sp.n_cells / (ms / 1e3), "nnz_per_s": sp.nnz / (ms / 1e3)}
+        rec[prec] = {"ms_per_step": ms, "cells_per_s": sp.n_cells / (ms / 1e3), "nnz_per_s": sp.nnz / (ms / 1e3),
+                     **split_kernels(sp, coef, prob.force, vals, rhs, prec, stream)}
     out["elasticity_q1_128"] = {"cells": sp.n_cells, "nnz": sp.nnz, **rec}
     sp.close()
     del vals, rhs

@@ -40,7 +40,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 }
 
 void free_device(fe_space* s) {
-  void* ptrs[] = {s->d_xv, s->d_w, s->d_xq, s->d_phi, s->d_dphi, s->d_dphi32, s->d_cell_dofs, s->d_row_ptr,
+  void* ptrs[] = {s->d_xv, s->d_w, s->d_xq, s->d_phi, s->d_dphi, s->d_dphi32, s->d_phi2, s->d_cell_dofs, s->d_row_ptr,
                   s->d_col, s->d_cnt, s->d_code_ptr, s->d_codes, s->d_pos, s->d_slot_ptr, s->d_slots, s->d_ke, s->d_fe,
                   s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs};
   for (void* p : ptrs)
@@ -88,8 +88,9 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     return fail(rc, err);
   }
   if (!host_only) {
-    const long smem = feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP64, feasm::cells_per_block(s->nb));
-    if (smem < 0) {
+    const int cpb = feasm::cells_per_block(s->nb);
+    if (feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP64, cpb) < 0 ||
+        feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP32, cpb) < 0) {
       delete s;
       return fail(FE_ERR_UNSUPPORTED, "quadrature too large for one block at this order");
     }
@@ -103,6 +104,12 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
             xv[size_t(c) * 24 + v * 3 + k] = mesh->coords[3 * int64_t(mesh->cell_vertices[8 * c + v]) + k];
     }
     std::vector<float> dphi32(s->tab.dphi.begin(), s->tab.dphi.end());
+    std::vector<float> phi2(2 * s->tab.phi.size());
+    for (size_t i = 0; i < s->tab.phi.size(); ++i) {
+      const float hi = float(s->tab.phi[i]);
+      phi2[2 * i] = hi;
+      phi2[2 * i + 1] = float(s->tab.phi[i] - double(hi));
+    }
     const auto& hs = s->hs;
     if (e == cudaSuccess) e = upload(&s->d_xv, xv.data(), xv.size());
     if (e == cudaSuccess) e = upload(&s->d_w, s->tab.w.data(), s->tab.w.size());
@@ -110,6 +117,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     if (e == cudaSuccess) e = upload(&s->d_phi, s->tab.phi.data(), s->tab.phi.size());
     if (e == cudaSuccess) e = upload(&s->d_dphi, s->tab.dphi.data(), s->tab.dphi.size());
     if (e == cudaSuccess) e = upload(&s->d_dphi32, dphi32.data(), dphi32.size());
+    if (e == cudaSuccess) e = upload(&s->d_phi2, phi2.data(), phi2.size());
     if (e == cudaSuccess) e = upload(&s->d_cell_dofs, hs.cell_dofs.data(), hs.cell_dofs.size());
     if (e == cudaSuccess) e = upload(&s->d_row_ptr, hs.row_ptr.data(), hs.row_ptr.size());
     if (e == cudaSuccess) e = upload(&s->d_col, hs.col.data(), hs.col.size());

@@ -74,7 +74,7 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
     for (int c = 0; c < CH; ++c) {
       const bool ok = c < CH - 1 || c * 32 + lane < NL;
       x[c] = ok ? __ldcg(krow + c * 32) : 0.f;
-      kk[c] = ok ? int(prow[c * 32]) : dummy;
+      kk[c] = ok ? (int(prow[c * 32]) & 0x7fff) : dummy;
     }
 #pragma unroll
     for (int c = 0; c < CH; ++c) {
@@ -88,9 +88,11 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
     }
     __syncwarp();
   }
-  for (int k = lane; k < nnz; k += 32) {
-    const float2 a = acc[k];
-    p.values[k0 + k] = df_to_double(a.x, a.y);
+  for (int kb = 0; kb < nnz; kb += 32) {
+    const int k = kb + lane;
+    const float2 a = acc[k < nnz ? k : dummy];
+    const double v = df_to_double(a.x, a.y);
+    if (k < nnz) p.values[k0 + k] = v;
   }
   __syncwarp();
 }
@@ -434,10 +436,12 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
     c.nq = s->nq;
     c.cpb = feasm::cells_per_block(s->nb);
     c.qblock = s->nq1d * s->nq1d;
+    c.nq1d = s->nq1d;
     c.xv = s->d_xv;
     c.w = s->d_w;
     c.xq = s->d_xq;
     c.phi = s->d_phi;
+    c.phi2 = reinterpret_cast<const float2*>(s->d_phi2);
     c.dphi = s->d_dphi;
     c.dphi32 = s->d_dphi32;
     c.coef = nullptr;

@@ -2,19 +2,33 @@
 // (tcgen05, sm_103a): the per-cell Gram contraction
 //     G[(i,a),(j,b)] = sum_q (w_q / det J_q) gh_{a,i}(q) gh_{b,j}(q),
 // gh_a = cof(J) gradhat(phihat_a) (Eq. shape_grad with J^{-T} = cof(J)/det J,
-// Eq. fematrix), is one 128x96x32 MMA per cell (81 rows/columns used, 27
-// quadrature points along K), operands staged in shared memory in the 128-byte
-// swizzled K-major layout, the accumulator in tensor memory.
+// Eq. fematrix), is one 128x96x32 MMA group per cell (81 rows/columns used,
+// 27 quadrature points along K), operands staged in shared memory in the
+// 128-byte swizzled K-major layout, the accumulator in tensor memory.
 //
 // FP32 form: 3xTF32 split (hi = tf32(x), lo = tf32(x - hi); products
-// hi*hi + hi*lo + lo*hi) accumulated in FP32, with the 27 quadrature points
-// split into two accumulators (points 0-15 and 16-31) that the epilogue adds.
-// BF16 form: BF16 operands, one product, FP32 accumulation.
-// The epilogue reads G from tensor memory into shared memory and forms
+// hi*hi + hi*lo + lo*hi) accumulated in FP32, the 27 points split into two
+// accumulators (points 0-15 and 16-31) that the epilogue adds. BF16 form: BF16
+// operands, one product, FP32 accumulation. The epilogue forms
 //     K_(a,i),(b,j) = E (lam^ G^{ij}_ab + mu^ G^{ji}_ab + mu^ d_ij sum_k G^{kk}_ab)
-// (the isotropic Hooke law written on the Gram blocks), stored with 16-byte
-// vector stores; the cell vector is formed in FP64. Geometry (Jacobian,
-// cofactors, determinant) is FP64, as in the CUDA-core kernel.
+// (the isotropic Hooke law written on the Gram blocks). Geometry (Jacobian,
+// cofactors, determinant) is FP64; the cell vector is a double-float sum
+// rounded once to FP64.
+//
+// One persistent CTA per SM runs a warp-specialised pipeline over its cells:
+//   warp 0      allocates tensor memory; lane 0 issues the MMAs of cell n
+//               into accumulator stage n % 2 once its operands are staged;
+//   warps 1-4   FP64 geometry of cell n into geometry slot n % 4, warp
+//               1 + n % 4 (four cells at a time, one per SM sub-partition:
+//               each sub-partition has its own small share of the FP64 pipe,
+//               and an FP64 warp instruction costs the same with 27 active
+//               lanes as with 7, so a whole cell's points fill one warp);
+//   warps 5-8   operands of cell n into operand stage n % 2, and the cell
+//               vector of cell n;
+//   warps 9-16  accumulators of cell n -> shared staging -> cell matrix.
+// Hand-offs use mbarriers (full/empty per slot or stage); every wait is
+// bounded (about one second of clock cycles), after which the role sets
+// FE_ERR_TIMEOUT, leaves its loop, and the CTA frees tensor memory and exits.
 #include <cuda_bf16.h>
 
 #include "fe_launch.h"
@@ -26,24 +40,39 @@ namespace tc {
 constexpr int NB = 27, NL = 81, NLP = 84, NQ = 27;
 constexpr int M = 128, N = 96;
 constexpr int GS = 85;  // row stride of the G staging area (odd: conflict-free column writes)
+// warp roles
+constexpr int W_MMA = 0, W_GEO0 = 1, N_GEO = 4, W_OP0 = 5, N_OP = 4, W_EPI0 = 9, N_EPI = 8;
+constexpr int THREADS = 32 * (W_EPI0 + N_EPI);
+constexpr int OP_THREADS = 32 * N_OP, EPI_THREADS = 32 * N_EPI;
+constexpr int GEO_SLOTS = 4;
+// shared memory (offsets from a 1024-byte aligned base)
+constexpr int STAGE_BYTES = 57344;  // Ahi 16 KB, Alo 16 KB, Bhi 12 KB, Blo 12 KB
 constexpr int OFF_AHI = 0, OFF_ALO = 16384, OFF_BHI = 32768, OFF_BLO = 45056;
-constexpr int OPER_BYTES = 57344;
-constexpr int OFF_G = 57344;
-constexpr int OFF_GEO32 = (OFF_G + NL * GS * 4 + 15) & ~15;  // [2][27][12] float: cof (9), w/det
-constexpr int OFF_DJW = OFF_GEO32 + 2 * NQ * 12 * 4;  // [2][27][2] float: w*det as hi + lo
-constexpr int OFF_X = OFF_DJW + 2 * NQ * 8;          // [24] double
-constexpr int OFF_A = OFF_X + 24 * 8;                // [21] double
-constexpr int OFF_DPHI = (OFF_A + 21 * 8 + 15) & ~15;  // [27][27][3] float reference gradients
-constexpr int OFF_PHI = (OFF_DPHI + NQ * NB * 3 * 4 + 15) & ~15;  // [27][27][2] float reference values, hi + lo
-constexpr int OFF_BAR = (OFF_PHI + NQ * NB * 8 + 7) & ~7;  // mbarrier (8 bytes)
-constexpr int OFF_TMEM = OFF_BAR + 8;                // tensor-memory base address, then the abort flag
+constexpr int OFF_G = 2 * STAGE_BYTES;
+// geo32 [27][12] float, djw [27][2] float; a multiple of 16 bytes, since the
+// operand warps read geo32 rows as float4
+constexpr int GEO_SLOT_BYTES = (NQ * 12 * 4 + NQ * 2 * 4 + 15) & ~15;
+constexpr int OFF_GEO = (OFF_G + NL * GS * 4 + 15) & ~15;
+// per geometry warp: edge differences [3][4][3] and Jacobian columns [3][9][3] (double)
+constexpr int GEO_WARP_DOUBLES = 36 + 81;
+constexpr int OFF_EJ = (OFF_GEO + GEO_SLOTS * GEO_SLOT_BYTES + 15) & ~15;
+constexpr int OFF_WT = OFF_EJ + N_GEO * GEO_WARP_DOUBLES * 8;              // [9][4] double bilinear weights
+constexpr int OFF_DPHI = (OFF_WT + 36 * 8 + 15) & ~15;                     // [27][27][3] float
+constexpr int OFF_PHI = (OFF_DPHI + NQ * NB * 3 * 4 + 15) & ~15;           // [27][27][2] float hi + lo
+constexpr int OFF_BAR = (OFF_PHI + NQ * NB * 8 + 7) & ~7;
+// mbarriers: geo_full[4], geo_empty[4], op_full[2], op_empty[2], acc_full[2], acc_empty[2]
+constexpr int BAR_GEO_FULL = 0, BAR_GEO_EMPTY = 4, BAR_OP_FULL = 8, BAR_OP_EMPTY = 10, BAR_ACC_FULL = 12,
+              BAR_ACC_EMPTY = 14, N_BARS = 16;
+constexpr int OFF_TMEM = OFF_BAR + N_BARS * 8;  // tensor-memory base address, then the abort flag
 constexpr int SMEM_USED = OFF_TMEM + 8;
-// 1 KB of slack to align the base to the 1024-byte swizzle atom; the request is
-// also kept above a third of the SM's shared memory so that at most two CTAs
-// (2 x 256 tensor-memory columns) share an SM.
-constexpr int SMEM_BYTES = (SMEM_USED + 1024) > 80 * 1024 ? (SMEM_USED + 1024) : 80 * 1024;
-constexpr uint32_t TMEM_COLS = 256;
-static_assert(OFF_GEO32 % 16 == 0 && OFF_DJW % 8 == 0 && SMEM_BYTES <= 227 * 1024, "layout");
+constexpr int SMEM_BYTES = SMEM_USED + 1024;  // + alignment slack; > half of the SM: one CTA per SM
+constexpr uint32_t TMEM_COLS = 512;            // two accumulator stages of 2 x 96 columns, at 0 and 256
+static_assert(OFF_GEO % 16 == 0 && GEO_SLOT_BYTES % 16 == 0 && OFF_DPHI % 16 == 0 && OFF_BAR % 8 == 0 &&
+                  SMEM_BYTES <= 227 * 1024,
+              "layout");
+static_assert(SMEM_BYTES > 114 * 1024, "one CTA per SM (512 tensor-memory columns)");
+static_assert(GEO_SLOTS == N_GEO, "geometry warp w owns geometry slot w");
+constexpr long long WAIT_CYCLES = 1ll << 31;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -128,50 +157,49 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+// Two groups of 16 columns with one wait.
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&va)[16], float (&vb)[16]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%33];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    va[j] = __uint_as_float(r[j]);
+    vb[j] = __uint_as_float(r[16 + j]);
+  }
+}
+
 __device__ __forceinline__ float to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return __uint_as_float(r);
 }
 
+// FP32 -> FP64, exact, on the integer bits for zero and normal numbers (the
+// exponent is rebiased by 1023 - 127 = 896); other values take the hardware
+// conversion.
+__device__ __noinline__ double f2d_slow(float x);
+__device__ __forceinline__ double f2d(float x) {
+  const uint32_t u = __float_as_uint(x), mag = u & 0x7fffffffu, e = mag >> 23;
+  if (mag == 0) return __longlong_as_double(static_cast<long long>(uint64_t(u >> 31) << 63));
+  if (e == 0 || e == 0xffu) return f2d_slow(x);
+  return __longlong_as_double(
+      static_cast<long long>((uint64_t(u >> 31) << 63) | ((uint64_t(mag) << 29) + (uint64_t(896) << 52))));
+}
+
 // hi + lo (FP32 pair) rounded once to FP64: both parts convert exactly, one
 // FP64 addition rounds their sum.
 __device__ __forceinline__ double feasm_df_to_double(float hi, float lo) {
-  return __dadd_rn(double(hi), double(lo));
-}
-
-// Same FP64 geometry as the CUDA-core kernel (trilinear map in monomials).
-__device__ __forceinline__ void tri_coef(const double* x, int k, double* a) {
-  const double x0 = x[k], x1 = x[3 + k], x2 = x[6 + k], x3 = x[9 + k], x4 = x[12 + k], x5 = x[15 + k],
-               x6 = x[18 + k], x7 = x[21 + k];
-  const double d10 = x1 - x0, d32 = x3 - x2, d54 = x5 - x4, d76 = x7 - x6, d20 = x2 - x0, d64 = x6 - x4;
-  a[0 + k] = d10;
-  a[3 + k] = d20;
-  a[6 + k] = x4 - x0;
-  a[9 + k] = d32 - d10;
-  a[12 + k] = d54 - d10;
-  a[15 + k] = d64 - d20;
-  a[18 + k] = (d76 - d54) - (d32 - d10);
-}
-
-__device__ __forceinline__ void cof_det(const double* a, double x, double y, double z, double cof[9], double* det) {
-  double J[3][3];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    J[k][0] = a[0 + k] + a[9 + k] * y + a[12 + k] * z + a[18 + k] * (y * z);
-    J[k][1] = a[3 + k] + a[9 + k] * x + a[15 + k] * z + a[18 + k] * (x * z);
-    J[k][2] = a[6 + k] + a[12 + k] * x + a[15 + k] * y + a[18 + k] * (x * y);
-  }
-  cof[0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
-  cof[1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
-  cof[2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
-  cof[3] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
-  cof[4] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
-  cof[5] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
-  cof[6] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
-  cof[7] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
-  cof[8] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
-  *det = J[0][0] * cof[0] + J[0][1] * cof[1] + J[0][2] * cof[2];
+  return __dadd_rn(f2d(hi), f2d(lo));
 }
 
 struct Params {
@@ -189,13 +217,22 @@ struct Params {
   int* err;
 };
 
-// FP64 -> FP32 round to nearest even on the integer bits (normal results;
-// values that would under- or overflow FP32 take the hardware conversion).
-// Keeps the conversions of the FP64 geometry off the FP64 pipe.
+// Out-of-line hardware conversions for the rare operands of the integer
+// conversions below (a real branch: FP64-pipe instructions on a predicated
+// path would still occupy the pipe).
+__device__ __noinline__ float d2f_slow(double x) { return __double2float_rn(x); }
+__device__ __noinline__ double f2d_slow(float x) { return double(x); }
+
+// FP64 -> FP32 round to nearest even on the integer bits (zero and results in
+// the FP32 normal range; other values take the hardware conversion). Keeps
+// the conversions of the FP64 geometry off the FP64 pipe.
 __device__ __forceinline__ float d2f_rn(double x) {
   const uint64_t u = uint64_t(__double_as_longlong(x));
   const int e = int((u >> 52) & 0x7ffu) - 896;
-  if (e <= 0 || e >= 255) return __double2float_rn(x);
+  if (e <= 0 || e >= 255) {
+    if ((u << 1) == 0) return __uint_as_float(uint32_t(u >> 63) << 31);
+    return d2f_slow(x);
+  }
   const uint64_t mant = u & 0xfffffffffffffull;
   uint32_t body = (uint32_t(e) << 23) | uint32_t(mant >> 29);
   const uint32_t rem = uint32_t(mant & 0x1fffffffu);
@@ -203,262 +240,439 @@ __device__ __forceinline__ float d2f_rn(double x) {
   return __uint_as_float((uint32_t(u >> 63) << 31) | body);
 }
 
-// Geometry of one cell by warps 0-1 (`t` = thread index 0..63, `xreg` this
-// thread's vertex coordinate, t < 24): FP64 monomial coefficients, Jacobian,
-// cofactors and determinant; one thread per quadrature point writes the FP32
-// cofactors, w/det J in FP32 (geo32), and w det J split into FP32 hi + lo
-// (djw). A non-positive det J sets the error word. Warps 0-1 synchronise on
-// named barrier 1.
-__device__ __forceinline__ void pair_geometry(const Params& p, int t, double xreg, double* X, double* A,
-                                              float* geo32, float* djw) {
-  if (t < 24) X[t] = xreg;
-  asm volatile("bar.sync 1, 64;" ::: "memory");  // geometry role only (64 threads)
-  if (t < 3) tri_coef(X, t, A);
-  asm volatile("bar.sync 1, 64;" ::: "memory");
-  if (t < NQ) {
-    double cof[9], det;
-    cof_det(A, p.xq[3 * t], p.xq[3 * t + 1], p.xq[3 * t + 2], cof, &det);
-    if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
-    const double wq = p.w[t];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) geo32[t * 12 + k] = d2f_rn(cof[k]);
-    geo32[t * 12 + 9] = float(wq) / d2f_rn(det);
-    const double wd = wq * det;
-    const float hi = d2f_rn(wd);
-    djw[2 * t] = hi;
-    djw[2 * t + 1] = d2f_rn(wd - double(hi));
+// Bounded wait on an mbarrier phase; false after about one second.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > WAIT_CYCLES) return false;
   }
-  asm volatile("bar.sync 1, 64;" ::: "memory");
+  return true;
 }
 
-// Persistent: each CTA loops over cells blockIdx.x, blockIdx.x + gridDim.x, ...
-// Warp roles: warps 0-7 ("math") build the operands, issue the MMAs (thread 0),
-// move the accumulators to shared memory and form the cell matrix and cell
-// vector of cell n; warps 8-9 ("geometry") compute the FP64 geometry of cell
-// n+1 meanwhile, into the other half of a double buffer. The two roles meet
-// once per cell at a block barrier; inside the math role, named barrier 2
-// (256 threads) orders its phases.
-constexpr int MATH_THREADS = 256;
-constexpr int ALL_THREADS = MATH_THREADS + 64;
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
 
-__device__ __forceinline__ void math_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Named-barrier OR-reduction over the `count` threads of barrier `id`.
+template <int ID, int COUNT>
+__device__ __forceinline__ bool bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.or.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(uint32_t(v)), "n"(ID), "n"(COUNT)
+      : "memory");
+  return r != 0;
+}
+
+template <int ID, int COUNT>
+__device__ __forceinline__ void bar_sync() {
+  asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(COUNT) : "memory");
+}
+
+// Per-lane constants of a geometry warp. The Jacobian of the trilinear map
+// is built from the 36 edge differences of the cell (direction d, edge c of
+// the four parallel ones, component k): column d at reference point xi is
+// the bilinear interpolation of the four edge differences of direction d in
+// the other two coordinates (u, v) (in axis order), with weights
+// (1-u)(1-v), u(1-v), (1-u)v, uv for edges c = 0..3 (bit 0 of c: u side,
+// bit 1: v side). Column d depends on (u, v) only, so the 27 points need 9
+// pairs per column: 81 entries (d, pair, k), 3 per lane. Lanes 0-26 then
+// take one quadrature point each.
+struct GeoLane {
+  int src0[2], src1[2];  // edge-difference items: lanes holding the two vertex values
+  int jw[3], je[3];      // Jacobian items: weight row and edge-difference base
+  int q, j0, j1, j2;
+  double wq;
+  float wq32;
+};
+
+__device__ __forceinline__ GeoLane geo_lane(const Params& p, int lane) {
+  GeoLane g;
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const int L = (32 * r + lane) < 36 ? 32 * r + lane : 0;
+    const int d = L / 12, c = (L / 3) % 4, k = L % 3, bu = c & 1, bv = c >> 1;
+    const int v0 = d == 0 ? 2 * bu + 4 * bv : d == 1 ? bu + 4 * bv : bu + 2 * bv;
+    const int v1 = v0 + (d == 0 ? 1 : d == 1 ? 2 : 4);
+    g.src0[r] = 3 * v0 + k;
+    g.src1[r] = 3 * v1 + k;
+  }
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const int t = (32 * r + lane) < 81 ? 32 * r + lane : 0;
+    const int d = t / 27, pr = (t % 27) / 3, k = t % 3;
+    g.jw[r] = 4 * pr;
+    g.je[r] = 12 * d + k;
+  }
+  g.q = lane < NQ ? lane : -1;
+  const int q = lane < NQ ? lane : 0;
+  const int ix = q % 3, iy = (q / 3) % 3, iz = q / 9;
+  g.j0 = (0 + iy + 3 * iz) * 3;
+  g.j1 = (9 + ix + 3 * iz) * 3;
+  g.j2 = (18 + ix + 3 * iy) * 3;
+  g.wq = p.w[q];
+  g.wq32 = d2f_rn(g.wq);
+  return g;
+}
+
+// FP64 geometry of one cell by one geometry warp (xreg = this lane's vertex
+// coordinate for lanes < 24, vertex v component k at lane 3 v + k): edge
+// differences (ED), Jacobian columns per point pair (JC), then per quadrature
+// point the FP32 cofactors and w/det J (geo32) and w det J as FP32 hi + lo
+// (djw). A non-positive det J sets the error word.
+__device__ __forceinline__ void cell_geometry(const Params& p, const GeoLane& g, int lane, double xreg, double* ED,
+                                              double* JC, const double* WT, float* geo32, float* djw) {
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const double x1 = __shfl_sync(0xffffffffu, xreg, g.src1[r]);
+    const double x0 = __shfl_sync(0xffffffffu, xreg, g.src0[r]);
+    if (32 * r + lane < 36) ED[32 * r + lane] = x1 - x0;
+  }
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    if (32 * r + lane < 81) {
+      const double* w = WT + g.jw[r];
+      const double* ed = ED + g.je[r];
+      JC[32 * r + lane] = fma(w[3], ed[9], fma(w[2], ed[6], fma(w[1], ed[3], w[0] * ed[0])));
+    }
+  }
+  __syncwarp();
+  if (g.q >= 0) {
+    const int q = g.q;
+    double J[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      J[k][0] = JC[g.j0 + k];
+      J[k][1] = JC[g.j1 + k];
+      J[k][2] = JC[g.j2 + k];
+    }
+    double cof[9];
+    cof[0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    cof[1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    cof[2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    cof[3] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    cof[4] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    cof[5] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    cof[6] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    cof[7] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    cof[8] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * cof[0] + J[0][1] * cof[1] + J[0][2] * cof[2];
+    if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) geo32[q * 12 + k] = d2f_rn(cof[k]);
+    geo32[q * 12 + 9] = g.wq32 / d2f_rn(det);
+    const double wd = g.wq * det;
+    const float hi = d2f_rn(wd);
+    djw[2 * q] = hi;
+    djw[2 * q + 1] = d2f_rn(wd - f2d(hi));
+  }
+}
+
+// Cell vector of one cell, entry a: f_a = sum_q (w det J)_q phihat_a(x_q),
+// both factors as FP32 hi + lo, products and sums in double-float arithmetic
+// (three interleaved partial sums over q = 0, 1, 2 mod 3, then combined),
+// rounded once to FP64 and scaled by the body force.
+__device__ __forceinline__ void cell_vector(const Params& p, int64_t e, int a, const float* djw, const float* sphi) {
+  float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    const int r = q % 3;
+    const float ah = djw[2 * q], al = djw[2 * q + 1];
+    const float bh = sphi[2 * (q * NB + a)], bl = sphi[2 * (q * NB + a) + 1];
+    const float ph = ah * bh;
+    const float pe = fmaf(ah, bh, -ph) + (ah * bl + al * bh);
+    const float sum = sh[r] + ph;
+    const float bp = sum - sh[r];
+    const float err = (sh[r] - (sum - bp)) + (ph - bp);
+    sh[r] = sum;
+    sl[r] += err + pe;
+  }
+  float h = sh[0], l = sl[0];
+#pragma unroll
+  for (int r = 1; r < 3; ++r) {
+    const float sum = h + sh[r];
+    const float bp = sum - h;
+    const float err = (h - (sum - bp)) + (sh[r] - bp);
+    h = sum;
+    l += err + sl[r];
+  }
+  const double f = feasm_df_to_double(h, l);
+  double* fe = p.fe + e * NL;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) fe[k * NB + a] = p.f[k] * f;
+}
+
+// Operands of one cell from its geometry slot: A[(i,a)][q] = (w/det) gh_{a,i}(q),
+// B[(j,b)][q] = gh_{b,j}(q); one thread per (node a, 4 points q0..q0+3) forms
+// the three components and stores each 16-byte K-chunk of the four arrays
+// with one vector store (points q >= 27 are the zero padding of K).
+template <bool BF16>
+__device__ __forceinline__ void build_operands(unsigned char* st, const float* geo32, const float* sdphi, int t) {
+  for (int idx = t; idx < NB * 7; idx += OP_THREADS) {
+    const int a = idx / 7, qc = idx - a * 7, q0 = 4 * qc;
+    float g[3][4], sq[4];
+#pragma unroll
+    for (int dq = 0; dq < 4; ++dq) {
+      const int q = q0 + dq;
+      if (q < NQ) {
+        const float4* gq4 = reinterpret_cast<const float4*>(geo32 + q * 12);
+        const float4 c0 = gq4[0], c1 = gq4[1], c2 = gq4[2];
+        const float* dp = sdphi + (q * NB + a) * 3;
+        const float d0 = dp[0], d1 = dp[1], d2 = dp[2];
+        g[0][dq] = fmaf(c0.z, d2, fmaf(c0.y, d1, c0.x * d0));
+        g[1][dq] = fmaf(c1.y, d2, fmaf(c1.x, d1, c0.w * d0));
+        g[2][dq] = fmaf(c2.x, d2, fmaf(c1.w, d1, c1.z * d0));
+        sq[dq] = c2.y;
+      } else {
+        g[0][dq] = g[1][dq] = g[2][dq] = 0.f;
+        sq[dq] = 0.f;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int m = i * NB + a;
+      if (BF16) {
+        const uint32_t o = swz(m, q0 * 2);
+        __nv_bfloat162 ah0 = __floats2bfloat162_rn(sq[0] * g[i][0], sq[1] * g[i][1]);
+        __nv_bfloat162 ah1 = __floats2bfloat162_rn(sq[2] * g[i][2], sq[3] * g[i][3]);
+        __nv_bfloat162 bh0 = __floats2bfloat162_rn(g[i][0], g[i][1]);
+        __nv_bfloat162 bh1 = __floats2bfloat162_rn(g[i][2], g[i][3]);
+        *reinterpret_cast<uint2*>(st + OFF_AHI + o) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&ah0), *reinterpret_cast<uint32_t*>(&ah1));
+        *reinterpret_cast<uint2*>(st + OFF_BHI + o) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&bh0), *reinterpret_cast<uint32_t*>(&bh1));
+      } else {
+        const uint32_t o = swz(m, q0 * 4);
+        float ah[4], al[4], bh[4], bl[4];
+#pragma unroll
+        for (int dq = 0; dq < 4; ++dq) {
+          const float av = sq[dq] * g[i][dq];
+          ah[dq] = to_tf32(av);
+          al[dq] = to_tf32(av - ah[dq]);
+          bh[dq] = to_tf32(g[i][dq]);
+          bl[dq] = to_tf32(g[i][dq] - bh[dq]);
+        }
+        *reinterpret_cast<float4*>(st + OFF_AHI + o) = make_float4(ah[0], ah[1], ah[2], ah[3]);
+        *reinterpret_cast<float4*>(st + OFF_ALO + o) = make_float4(al[0], al[1], al[2], al[3]);
+        *reinterpret_cast<float4*>(st + OFF_BHI + o) = make_float4(bh[0], bh[1], bh[2], bh[3]);
+        *reinterpret_cast<float4*>(st + OFF_BLO + o) = make_float4(bl[0], bl[1], bl[2], bl[3]);
+      }
+    }
+  }
+}
 
 template <bool BF16>
-__global__ void __launch_bounds__(ALL_THREADS) k_cell_tc(Params p) {
+__global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* sm = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const bool geo_role = tid >= MATH_THREADS;
-  const int gt = tid - MATH_THREADS;  // thread index inside the geometry role
   float* G = reinterpret_cast<float*>(sm + OFF_G);
-  float* geo32_0 = reinterpret_cast<float*>(sm + OFF_GEO32);
-  float* djw_0 = reinterpret_cast<float*>(sm + OFF_DJW);
-  double* X = reinterpret_cast<double*>(sm + OFF_X);
-  double* A = reinterpret_cast<double*>(sm + OFF_A);
+  float* sdphi = reinterpret_cast<float*>(sm + OFF_DPHI);
+  float* sphi = reinterpret_cast<float*>(sm + OFF_PHI);
   const uint32_t sbase = smem_u32(sm);
-  const uint32_t bar = sbase + OFF_BAR;
+  auto bar = [&](int i) { return sbase + OFF_BAR + 8u * uint32_t(i); };
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + OFF_TMEM);
-  int* abort_flag = reinterpret_cast<int*>(sm + OFF_TMEM + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + OFF_TMEM + 4);
+  const int64_t n_mine = p.n_cells > blockIdx.x ? (p.n_cells - 1 - blockIdx.x) / gridDim.x + 1 : 0;
 
-  if (warp == 0) {
+  if (warp == W_MMA) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sbase + OFF_TMEM),
                  "r"(TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(1u) : "memory");
+    for (int i = 0; i < GEO_SLOTS; ++i) {
+      mbar_init(bar(BAR_GEO_FULL + i), 32);
+      mbar_init(bar(BAR_GEO_EMPTY + i), OP_THREADS);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(bar(BAR_OP_FULL + i), OP_THREADS);
+      mbar_init(bar(BAR_OP_EMPTY + i), 1);
+      mbar_init(bar(BAR_ACC_FULL + i), 1);
+      mbar_init(bar(BAR_ACC_EMPTY + i), EPI_THREADS);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
-  float* sdphi = reinterpret_cast<float*>(sm + OFF_DPHI);
-  float* sphi = reinterpret_cast<float*>(sm + OFF_PHI);
-  double xnext = 0.0;
-  if (!geo_role) {
-    // zero the operand area once: padding rows/columns are never written again
-    for (int i = tid; i < OPER_BYTES / 16; i += MATH_THREADS) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
-    for (int i = tid; i < NQ * NB * 3; i += MATH_THREADS) sdphi[i] = p.dphi32[i];
-    for (int i = tid; i < NQ * NB; i += MATH_THREADS) {
-      const double v = p.phi[i];
-      const float hi = __double2float_rn(v);
-      sphi[2 * i] = hi;
-      sphi[2 * i + 1] = __double2float_rn(v - double(hi));
-    }
-  } else {
-    if (int64_t(blockIdx.x) < p.n_cells) {
-      const double x0 = gt < 24 ? p.xv[int64_t(blockIdx.x) * 24 + gt] : 0.0;
-      pair_geometry(p, gt, x0, X, A, geo32_0, djw_0);
-    }
-    if (gt < 24 && int64_t(blockIdx.x) + gridDim.x < p.n_cells)
-      xnext = p.xv[(int64_t(blockIdx.x) + gridDim.x) * 24 + gt];
+  // zero both operand stages once (padding rows and columns are never written
+  // again), load the reference tables
+  for (int i = tid; i < 2 * STAGE_BYTES / 16; i += THREADS) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < NQ * NB * 3; i += THREADS) sdphi[i] = p.dphi32[i];
+  if (tid < 36) {
+    const int pr = tid / 4, c = tid % 4;
+    const double u = p.xq[3 * (pr % 3)], v = p.xq[3 * (pr / 3)];
+    reinterpret_cast<double*>(sm + OFF_WT)[tid] = ((c & 1) ? u : 1.0 - u) * ((c >> 1) ? v : 1.0 - v);
+  }
+  for (int i = tid; i < NQ * NB; i += THREADS) {
+    const double v = p.phi[i];
+    const float hi = __double2float_rn(v);
+    sphi[2 * i] = hi;
+    sphi[2 * i + 1] = __double2float_rn(v - double(hi));
   }
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = *tmem_slot;
-  constexpr uint32_t IDESC = instr_desc(M, N, BF16 ? 1u : 2u);
-  uint32_t phase = 0;
-  int buf = 0;
+  bool failed = false;
 
-  for (int64_t e = blockIdx.x; e < p.n_cells; e += gridDim.x, buf ^= 1) {
-    if (geo_role) {
-      // geometry of the next cell (FP64), then fetch the coordinates of the one after
-      if (e + gridDim.x < p.n_cells) {
-        pair_geometry(p, gt, xnext, X, A, geo32_0 + (buf ^ 1) * (NQ * 12), djw_0 + (buf ^ 1) * (2 * NQ));
-        if (gt < 24 && e + 2 * int64_t(gridDim.x) < p.n_cells) xnext = p.xv[(e + 2 * int64_t(gridDim.x)) * 24 + gt];
-      }
-    } else {
-      const float* geo32 = geo32_0 + buf * (NQ * 12);
-      const float* djw = djw_0 + buf * (2 * NQ);
-      // 1. operands: A[(i,a)][q] = (w/det) gh_{a,i}(q), B[(j,b)][q] = gh_{b,j}(q);
-      //    one thread per (node a, point q) forms the three components i.
-      for (int idx = tid; idx < NB * NQ; idx += MATH_THREADS) {
-        const int a = idx / NQ, q = idx - a * NQ;
-        const float* gq = geo32 + q * 12;
-        const float* dp = sdphi + (q * NB + a) * 3;
-        const float d0 = dp[0], d1 = dp[1], d2 = dp[2], sq = gq[9];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const float g = fmaf(gq[3 * i + 2], d2, fmaf(gq[3 * i + 1], d1, gq[3 * i] * d0));
-          const float av = sq * g;
-          const int m = i * NB + a;
-          if (BF16) {
-            const uint32_t o = swz(m, q * 2);
-            *reinterpret_cast<__nv_bfloat16*>(sm + OFF_AHI + o) = __float2bfloat16_rn(av);
-            *reinterpret_cast<__nv_bfloat16*>(sm + OFF_BHI + o) = __float2bfloat16_rn(g);
-          } else {
-            const uint32_t o = swz(m, q * 4);
-            const float ah = to_tf32(av), bh = to_tf32(g);
-            *reinterpret_cast<float*>(sm + OFF_AHI + o) = ah;
-            *reinterpret_cast<float*>(sm + OFF_ALO + o) = to_tf32(av - ah);
-            *reinterpret_cast<float*>(sm + OFF_BHI + o) = bh;
-            *reinterpret_cast<float*>(sm + OFF_BLO + o) = to_tf32(g - bh);
-          }
+  if (warp == W_MMA) {
+    // ---------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      constexpr uint32_t IDESC = instr_desc(M, N, BF16 ? 1u : 2u);
+      for (int64_t n = 0; n < n_mine && !failed; ++n) {
+        const int st = int(n & 1);
+        const uint32_t use = uint32_t((n >> 1) & 1);
+        if (!mbar_wait(bar(BAR_OP_FULL + st), use) || !mbar_wait(bar(BAR_ACC_EMPTY + st), use ^ 1u)) {
+          failed = true;
+          break;
         }
-      }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      math_sync();
-      // 2. one thread issues the MMAs; completion is signalled on the mbarrier
-      if (tid == 0) {
         fence_after();
-        const uint64_t ahi = sw128_desc(sbase + OFF_AHI), alo = sw128_desc(sbase + OFF_ALO);
-        const uint64_t bhi = sw128_desc(sbase + OFF_BHI), blo = sw128_desc(sbase + OFF_BLO);
+        const uint32_t sb = sbase + uint32_t(st * STAGE_BYTES);
+        const uint64_t ahi = sw128_desc(sb + OFF_AHI), alo = sw128_desc(sb + OFF_ALO);
+        const uint64_t bhi = sw128_desc(sb + OFF_BHI), blo = sw128_desc(sb + OFF_BLO);
+        const uint32_t dst = tmem + uint32_t(st * 256);
         if (BF16) {
 #pragma unroll
-          for (int ks = 0; ks < 2; ++ks) mma_bf16(tmem, ahi + 2 * ks, bhi + 2 * ks, IDESC, ks > 0);
+          for (int ks = 0; ks < 2; ++ks) mma_bf16(dst, ahi + 2 * ks, bhi + 2 * ks, IDESC, ks > 0);
         } else {
 #pragma unroll
           for (int g = 0; g < 2; ++g)
 #pragma unroll
             for (int k2 = 0; k2 < 2; ++k2) {
               const int ks = 2 * g + k2;
-              const uint32_t d = tmem + uint32_t(g * N);
+              const uint32_t d = dst + uint32_t(g * N);
               mma_tf32(d, alo + 2 * ks, bhi + 2 * ks, IDESC, k2 > 0);
               mma_tf32(d, ahi + 2 * ks, blo + 2 * ks, IDESC, 1);
               mma_tf32(d, ahi + 2 * ks, bhi + 2 * ks, IDESC, 1);
             }
         }
-        mma_commit(bar);
+        mma_commit(bar(BAR_OP_EMPTY + st));   // operands may be overwritten
+        mma_commit(bar(BAR_ACC_FULL + st));   // accumulators ready for the epilogue
       }
-      __syncwarp();
-      // 3. bounded wait for the MMAs (about one second of clock cycles at most)
-      bool done = false;
-      {
-        const long long t0 = clock64();
-        while (!done) {
-          done = mbar_try_wait(bar, phase);
-          if (!done && clock64() - t0 > (1ll << 31)) break;
-        }
+    }
+    __syncwarp();
+  } else if (warp >= W_GEO0 && warp < W_GEO0 + N_GEO) {
+    // ---------------------------------------------------------------- geometry
+    const int gw = warp - W_GEO0;  // cells n = gw, gw + 4, ... into slot gw
+    double* ED = reinterpret_cast<double*>(sm + OFF_EJ) + gw * GEO_WARP_DOUBLES;
+    double* JC = ED + 36;
+    const double* WT = reinterpret_cast<const double*>(sm + OFF_WT);
+    const GeoLane g = geo_lane(p, lane);
+    float* geo32 = reinterpret_cast<float*>(sm + OFF_GEO + gw * GEO_SLOT_BYTES);
+    float* djw = geo32 + NQ * 12;
+    double xnext = (lane < 24 && gw < n_mine) ? p.xv[(int64_t(blockIdx.x) + int64_t(gw) * gridDim.x) * 24 + lane] : 0.0;
+    for (int64_t n = gw; n < n_mine; n += N_GEO) {
+      const int64_t e = blockIdx.x + n * int64_t(gridDim.x);
+      const uint32_t use = uint32_t((n / GEO_SLOTS) & 1);
+      const bool ok = __all_sync(0xffffffffu, mbar_wait(bar(BAR_GEO_EMPTY + gw), use ^ 1u));
+      if (!ok) {
+        failed = true;
+        break;
       }
-      done = __all_sync(0xffffffffu, done);  // tcgen05.ld below is warp-collective
-      phase ^= 1u;
-      if (!done) *abort_flag = 1;
+      const double xcur = xnext;
+      if (lane < 24 && n + N_GEO < n_mine) xnext = p.xv[(e + int64_t(N_GEO) * gridDim.x) * 24 + lane];
+      cell_geometry(p, g, lane, xcur, ED, JC, WT, geo32, djw);
+      mbar_arrive(bar(BAR_GEO_FULL + gw));
+    }
+  } else if (warp >= W_OP0 && warp < W_OP0 + N_OP) {
+    // ---------------------------------------------------------------- operands
+    const int t = tid - 32 * W_OP0;
+    for (int64_t n = 0; n < n_mine; ++n) {
+      const int slot = int(n % GEO_SLOTS), st = int(n & 1);
+      const uint32_t guse = uint32_t((n / GEO_SLOTS) & 1), use = uint32_t((n >> 1) & 1);
+      if (!mbar_wait(bar(BAR_GEO_FULL + slot), guse) || !mbar_wait(bar(BAR_OP_EMPTY + st), use ^ 1u)) {
+        failed = true;
+        break;
+      }
+      const float* geo32 = reinterpret_cast<const float*>(sm + OFF_GEO + slot * GEO_SLOT_BYTES);
+      build_operands<BF16>(sm + st * STAGE_BYTES, geo32, sdphi, t);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(bar(BAR_OP_FULL + st));
+      // threads 64-90 have no second operand item: they form the cell vector
+      if (t >= 64 && t < 64 + NB) cell_vector(p, blockIdx.x + n * int64_t(gridDim.x), t - 64, geo32 + NQ * 12, sphi);
+      mbar_arrive(bar(BAR_GEO_EMPTY + slot));
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int t = tid - 32 * W_EPI0;
+    const int ew = warp - W_EPI0;  // 0..7: lane quadrant warp % 4, column half ew / 4
+    const int row = 32 * (warp & 3) + lane;
+    double coef_next = n_mine > 0 ? p.coef[blockIdx.x] : 0.0;
+    for (int64_t n = 0; n < n_mine; ++n) {
+      const int64_t e = blockIdx.x + n * int64_t(gridDim.x);
+      const int st = int(n & 1);
+      const uint32_t use = uint32_t((n >> 1) & 1);
+      const float E = d2f_rn(coef_next);
+      if (n + 1 < n_mine) coef_next = p.coef[e + gridDim.x];  // in flight during this cell
+      bool ok = mbar_wait(bar(BAR_ACC_FULL + st), use);
+      ok = __all_sync(0xffffffffu, ok);
+      if (bar_or<3, EPI_THREADS>(!ok)) {
+        failed = true;
+        break;
+      }
       fence_after();
-      // 4. accumulators -> shared staging of G (FP32): warp w reads lanes
-      //    32 (w % 4) .. +31 (rows), column half w / 4
-      if (done) {
-        const int row = 32 * (warp & 3) + lane;
-        const uint32_t lane_addr = tmem + (uint32_t(32 * (warp & 3)) << 16);
+      const uint32_t lane_addr = tmem + uint32_t(st * 256) + (uint32_t(32 * (warp & 3)) << 16);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          const int col0 = ((warp >> 2) * 3 + c) * 16;
-          float v[16];
+      for (int c = 0; c < 3; ++c) {
+        const int col0 = ((ew >> 2) * 3 + c) * 16;
+        float v[16];
+        if (BF16) {
           tmem_ld16(lane_addr + uint32_t(col0), v);
-          if (!BF16) {
-            float v2[16];
-            tmem_ld16(lane_addr + uint32_t(N + col0), v2);
+        } else {
+          float v2[16];
+          tmem_ld16x2(lane_addr + uint32_t(col0), lane_addr + uint32_t(N + col0), v, v2);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) v[j] += v2[j];
-          }
-          if (row < NL) {
+          for (int j = 0; j < 16; ++j) v[j] += v2[j];
+        }
+        if (row < NL) {
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-              if (col0 + j < NL) G[row * GS + col0 + j] = v[j];
-          }
+          for (int j = 0; j < 16; ++j)
+            if (col0 + j < NL) G[row * GS + col0 + j] = v[j];
         }
       }
       fence_before();
-      math_sync();
-      // 5. warps 1-7: K^e from the Gram blocks, one thread per node pair (a, b)
-      //    (the nine G^{ij}_ab give the nine entries K_(a,i),(b,j): the
-      //    transposed block and the trace come from the same values);
-      //    consecutive threads take consecutive b (conflict-free reads,
-      //    coalesced stores). Warp 0: the cell vector.
-      if (*abort_flag == 0) {
-        if (warp > 0) {
-          const float E = float(p.coef[e]);
-          const float lh = p.lam_hat * E, mh = p.mu_hat * E;
-          float* K = p.ke + e * (NL * NLP);
-          for (int idx = tid - 32; idx < NB * NB; idx += MATH_THREADS - 32) {
-            const int a = idx / NB, b = idx - a * NB;
-            float g[3][3];
+      mbar_arrive(bar(BAR_ACC_EMPTY + st));
+      bar_sync<3, EPI_THREADS>();
+      // K^e from the Gram blocks: one thread per node pair (a, b) reads the nine
+      // G^{ij}_ab and forms the nine entries K_(a,i),(b,j) (the transposed block
+      // and the trace come from the same values); consecutive threads take
+      // consecutive b (conflict-free reads, coalesced stores).
+      const float lh = p.lam_hat * E, mh = p.mu_hat * E;
+      float* K = p.ke + e * (NL * NLP);
+      for (int idx = t; idx < NB * NB; idx += EPI_THREADS) {
+        const int a = idx / NB, b = idx - a * NB;
+        float g[3][3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-              for (int j = 0; j < 3; ++j) g[i][j] = G[(i * NB + a) * GS + j * NB + b];
-            const float tr = g[0][0] + g[1][1] + g[2][2];
+          for (int j = 0; j < 3; ++j) g[i][j] = G[(i * NB + a) * GS + j * NB + b];
+        const float tr = g[0][0] + g[1][1] + g[2][2];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i)
 #pragma unroll
-              for (int j = 0; j < 3; ++j) {
-                float v = lh * g[i][j] + mh * g[j][i];
-                if (i == j) v += mh * tr;
-                K[(i * NB + a) * NLP + j * NB + b] = v;
-              }
+          for (int j = 0; j < 3; ++j) {
+            float v = lh * g[i][j] + mh * g[j][i];
+            if (i == j) v += mh * tr;
+            K[(i * NB + a) * NLP + j * NB + b] = v;
           }
-        } else if (lane < NB) {
-          // f_a = sum_q (w det J)_q phihat_a(x_q), both factors as FP32 hi + lo,
-          // products and sum in double-float arithmetic (error ~2^-46
-          // relative), rounded once to FP64.
-          float sh = 0.f, sl = 0.f;
-          for (int q = 0; q < NQ; ++q) {
-            const float ah = djw[2 * q], al = djw[2 * q + 1];
-            const float bh = sphi[2 * (q * NB + lane)], bl = sphi[2 * (q * NB + lane) + 1];
-            const float ph = ah * bh;
-            const float pe = fmaf(ah, bh, -ph) + (ah * bl + al * bh);
-            const float sum = sh + ph;
-            const float bp = sum - sh;
-            const float err = (sh - (sum - bp)) + (ph - bp);
-            sh = sum;
-            sl += err + pe;
-          }
-          const double f = feasm_df_to_double(sh, sl);
-          double* fe = p.fe + e * NL;
-#pragma unroll
-          for (int k = 0; k < 3; ++k) fe[k * NB + lane] = p.f[k] * f;
-        }
       }
+      bar_sync<3, EPI_THREADS>();
     }
-    // cell boundary: the next geometry is ready and the staging area is free
-    __syncthreads();
-    if (*abort_flag) {
-      if (tid == 0) atomicOr(p.err, kErrTimeout);
-      break;
-    }
+  }
+  if (failed) {
+    *abort_flag = 1;
+    atomicOr(p.err, kErrTimeout);
   }
   fence_before();
   __syncthreads();
-  if (warp == 0) {
+  if (warp == W_MMA) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
@@ -492,8 +706,8 @@ cudaError_t launch_cell_tc(const fe_space* s, const double* coef, const double f
   auto run = [&](auto kern) -> cudaError_t {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tc::SMEM_BYTES);
     if (e != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>(s->n_cells, int64_t(nsm) * 2);
-    kern<<<unsigned(grid), tc::ALL_THREADS, tc::SMEM_BYTES, st>>>(p);
+    const int64_t grid = std::min<int64_t>(s->n_cells, int64_t(nsm));
+    kern<<<unsigned(grid), tc::THREADS, tc::SMEM_BYTES, st>>>(p);
     return cudaGetLastError();
   };
   return prec == FE_PREC_BF16 ? run(tc::k_cell_tc<true>) : run(tc::k_cell_tc<false>);

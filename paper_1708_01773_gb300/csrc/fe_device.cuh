@@ -18,11 +18,12 @@ constexpr int kScatterWarps = 8;
 
 struct CellParams {
   int64_t n_cells;
-  int nq, cpb, qblock;
+  int nq, cpb, qblock, nq1d;
   const double* xv;
   const double* w;
   const double* xq;
   const double* phi;
+  const float2* phi2;  // [nq][nb] phihat as FP32 hi + lo (hi + lo == phihat to ~2^-48)
   const double* dphi;
   const float* dphi32;
   const double* coef;
@@ -87,36 +88,29 @@ __device__ __forceinline__ void kahan_add(T& sum, T& carry, T part) {
   sum = t;
 }
 
-// One block integrates `cpb` cells. Steps (paper: Eq. fematrix, Eq.
-// shape_grad, the element loop of the Listing
-// "element_matrix_entries_computation"):
-//   1. geometry at every quadrature point (FP64),
+// One block integrates `cpb` cells in FP64 (paper: Eq. fematrix, Eq.
+// shape_grad, the element loop of the element-matrix computation):
+//   1. geometry at every quadrature point,
 //   2. cofactor gradients gh_a = cof(J) gradhat(phihat_a), so that
 //      grad(phi_a) = gh_a / det J,
 //   3. G^{ij}_{ab} = sum_q (w_q / det J_q) gh_{a,i} gh_{b,j}, and
 //      Poisson   K_ab = kappa sum_i G^{ii}_{ab},
 //      elasticity K_(a,i),(b,j) = E (lam^ G^{ij}_ab + mu^ G^{ji}_ab + mu^ d_ij sum_k G^{kk}_ab),
 //   4. cell vector f_(a,i) = f_i sum_q w_q det J_q phihat_a(x_q).
-// PREC 0: FP64 throughout. PREC 1: FP32 gradients and products; the sum over
-// quadrature points runs in blocks of `qblock` points (one z-slab of the
-// tensor rule) whose FP32 partials are added with Kahan compensation. PREC 2:
-// BF16-rounded operands, FP32 products and sums. Cell matrices are stored
-// row-major with row stride NLP (16-byte aligned rows).
-// cell_block integrates cells e0 .. e0 + ncell - 1 (ncell <= prm.cpb) with the
-// whole thread block, using `smem` (cell_smem_bytes) as scratch; k_cell runs
-// one such block per thread block, the batched driver any number of them.
-template <int P, int NC, int PREC>
-__device__ __forceinline__ void cell_block(const CellParams& prm, int64_t e0, int ncell, double* smem) {
+// Cell matrices are stored row-major with row stride NLP (16-byte aligned
+// rows). Shared memory: vertex coordinates [cpb][24], trilinear coefficients
+// [cpb][21], per-point geometry [cpb][nq][11] (cofactors, w/det, w*det), the
+// cofactor gradients [cpb][nq][3][nb].
+template <int P, int NC>
+__device__ __forceinline__ void cell_block_fp64(const CellParams& prm, int64_t e0, int ncell, double* smem) {
   constexpr int NB = (P + 1) * (P + 1) * (P + 1);
   constexpr int NL = NC * NB;
   constexpr int NLP = (NL + 3) & ~3;
-  using T = typename std::conditional<PREC == 0, double, float>::type;
   const int cpb = prm.cpb, nq = prm.nq;
   double* sx = smem;
   double* sa = sx + cpb * 24;
   double* geo = sa + cpb * 21;
-  float* geo32 = reinterpret_cast<float*>(geo + cpb * nq * 11);
-  T* g = reinterpret_cast<T*>(PREC == 0 ? reinterpret_cast<float*>(geo + cpb * nq * 11) : geo32 + cpb * nq * 12);
+  double* g = geo + cpb * nq * 11;
   const int tid = threadIdx.x;
 
   for (int i = tid; i < ncell * 24; i += blockDim.x) sx[i] = prm.xv[e0 * 24 + i];
@@ -134,102 +128,62 @@ __device__ __forceinline__ void cell_block(const CellParams& prm, int64_t e0, in
     for (int t = 0; t < 9; ++t) gm[t] = cof[t];
     gm[9] = wq / det;
     gm[10] = wq * det;
-    if (PREC != 0) {
-      float* g32 = geo32 + size_t(i) * 12;
-#pragma unroll
-      for (int t = 0; t < 9; ++t) g32[t] = float(cof[t]);
-      g32[9] = float(wq / det);
-    }
   }
   __syncthreads();
   for (int i = tid; i < ncell * nq * NB; i += blockDim.x) {
     const int a = i % NB, cq = i / NB, q = cq % nq;
-    T* gg = g + size_t(cq) * 3 * NB;
-    if (PREC == 0) {
-      const double* gm = geo + size_t(cq) * 11;
-      const double* dp = prm.dphi + (size_t(q) * NB + a) * 3;
+    double* gg = g + size_t(cq) * 3 * NB;
+    const double* gm = geo + size_t(cq) * 11;
+    const double* dp = prm.dphi + (size_t(q) * NB + a) * 3;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) gg[k * NB + a] = gm[3 * k] * dp[0] + gm[3 * k + 1] * dp[1] + gm[3 * k + 2] * dp[2];
-    } else {
-      const float* gm = geo32 + size_t(cq) * 12;
-      const float* dp = prm.dphi32 + (size_t(q) * NB + a) * 3;
-      const float d0 = dp[0], d1 = dp[1], d2 = dp[2];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) gg[k * NB + a] = T(fmaf(gm[3 * k + 2], d2, fmaf(gm[3 * k + 1], d1, gm[3 * k] * d0)));
-    }
+    for (int k = 0; k < 3; ++k) gg[k * NB + a] = gm[3 * k] * dp[0] + gm[3 * k + 1] * dp[1] + gm[3 * k + 2] * dp[2];
   }
   __syncthreads();
-  const int qb = PREC == 1 ? prm.qblock : nq;
   for (int i = tid; i < ncell * NB * NB; i += blockDim.x) {
     const int c = i / (NB * NB), ab = i % (NB * NB), a = ab / NB, b = ab % NB;
-    const T* gc = g + size_t(c) * nq * 3 * NB;
+    const double* gc = g + size_t(c) * nq * 3 * NB;
     const double* gm = geo + size_t(c) * nq * 11;
-    const float* gm32 = geo32 + size_t(c) * nq * 12;
     const int64_t e = e0 + c;
     const double coef = prm.coef[e];
-    T* K = reinterpret_cast<T*>(prm.ke) + e * NL * NLP;
+    double* K = reinterpret_cast<double*>(prm.ke) + e * NL * NLP;
     if (NC == 1) {
-      T sum = T(0), carry = T(0);
-      for (int q0 = 0; q0 < nq; q0 += qb) {
-        T part = T(0);
-        const int q1 = q0 + qb < nq ? q0 + qb : nq;
-        for (int q = q0; q < q1; ++q) {
-          const T* gq = gc + size_t(q) * 3 * NB;
-          const T s = PREC == 0 ? T(gm[q * 11 + 9]) : T(gm32[q * 12 + 9]);
+      double sum = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        const double* gq = gc + size_t(q) * 3 * NB;
+        const double s = gm[q * 11 + 9];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            T ga = s * gq[k * NB + a], gb = gq[k * NB + b];
-            if (PREC == 2) { ga = round_bf16(ga); gb = round_bf16(gb); }
-            part += ga * gb;
-          }
-        }
-        if (PREC == 1) kahan_add(sum, carry, part); else sum += part;
+        for (int k = 0; k < 3; ++k) sum += (s * gq[k * NB + a]) * gq[k * NB + b];
       }
-      K[a * NLP + b] = T(coef) * sum;
+      K[a * NLP + b] = coef * sum;
     } else {
-      T S[3][3], C[3][3];
+      double S[3][3];
 #pragma unroll
       for (int i2 = 0; i2 < 3; ++i2)
 #pragma unroll
-        for (int j2 = 0; j2 < 3; ++j2) S[i2][j2] = C[i2][j2] = T(0);
-      for (int q0 = 0; q0 < nq; q0 += qb) {
-        T G[3][3];
+        for (int j2 = 0; j2 < 3; ++j2) S[i2][j2] = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        const double* gq = gc + size_t(q) * 3 * NB;
+        const double s = gm[q * 11 + 9];
+        double ga[3], gb[3];
 #pragma unroll
-        for (int i2 = 0; i2 < 3; ++i2)
-#pragma unroll
-          for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] = T(0);
-        const int q1 = q0 + qb < nq ? q0 + qb : nq;
-        for (int q = q0; q < q1; ++q) {
-          const T* gq = gc + size_t(q) * 3 * NB;
-          const T s = PREC == 0 ? T(gm[q * 11 + 9]) : T(gm32[q * 12 + 9]);
-          T ga[3], gb[3];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) {
-            ga[k] = s * gq[k * NB + a];
-            gb[k] = gq[k * NB + b];
-            if (PREC == 2) { ga[k] = round_bf16(ga[k]); gb[k] = round_bf16(gb[k]); }
-          }
-#pragma unroll
-          for (int i2 = 0; i2 < 3; ++i2)
-#pragma unroll
-            for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] += ga[i2] * gb[j2];
+        for (int k = 0; k < 3; ++k) {
+          ga[k] = s * gq[k * NB + a];
+          gb[k] = gq[k * NB + b];
         }
 #pragma unroll
         for (int i2 = 0; i2 < 3; ++i2)
 #pragma unroll
-          for (int j2 = 0; j2 < 3; ++j2) {
-            if (PREC == 1) kahan_add(S[i2][j2], C[i2][j2], G[i2][j2]); else S[i2][j2] += G[i2][j2];
-          }
+          for (int j2 = 0; j2 < 3; ++j2) S[i2][j2] += ga[i2] * gb[j2];
       }
-      const T lh = T(prm.lam_hat), mh = T(prm.mu_hat), E = T(coef);
-      const T tr = S[0][0] + S[1][1] + S[2][2];
+      const double lh = prm.lam_hat, mh = prm.mu_hat;
+      const double tr = S[0][0] + S[1][1] + S[2][2];
 #pragma unroll
       for (int i2 = 0; i2 < 3; ++i2)
 #pragma unroll
         for (int j2 = 0; j2 < 3; ++j2) {
-          T v = lh * S[i2][j2] + mh * S[j2][i2];
+          double v = lh * S[i2][j2] + mh * S[j2][i2];
           if (i2 == j2) v += mh * tr;
-          K[size_t(i2 * NB + a) * NLP + j2 * NB + b] = E * v;
+          K[size_t(i2 * NB + a) * NLP + j2 * NB + b] = coef * v;
         }
     }
   }
@@ -419,19 +373,301 @@ __device__ __forceinline__ double f32_to_f64_fast(float x, bool& ok) {
 }
 
 // hi + lo of a double-float accumulator, rounded once to the nearest double:
-// both parts convert exactly on the integer bits, and one FP64 addition
-// (only where lo is non-zero) rounds their exact sum.
+// both parts convert exactly on the integer bits and one FP64 addition rounds
+// their exact sum (lo == 0 keeps hi, sign of zero included). Branch-free; a
+// warp vote sends the whole warp to the general conversion in the rare case of
+// a denormal part. All 32 lanes of the warp must call it.
 __device__ __forceinline__ double df_to_double(float hi, float lo) {
   bool ok = true;
   double dh = f32_to_f64_fast(hi, ok);
-  if (lo == 0.f && ok) return dh;
   double dl = f32_to_f64_fast(lo, ok);
-  if (!ok) {
-    dh = f32_to_f64_exact(hi);
-    dl = f32_to_f64_exact(lo);
+  if (!__all_sync(kFull, ok)) {
+    if (!ok) {
+      dh = f32_to_f64_exact(hi);
+      dl = f32_to_f64_exact(lo);
+    }
   }
-  return __dadd_rn(dh, dl);
+  const double sum = __dadd_rn(dh, dl);
+  return lo == 0.f ? dh : sum;
 }
 
+
+// FP64 -> FP32 round to nearest even on the integer bits (zero and
+// FP32-normal results; values that would under- or overflow FP32 take the
+// hardware conversion, out of line). Keeps the conversions of the FP64 geometry off the FP64 pipe.
+static __device__ __noinline__ float d2f_slow(double x) { return __double2float_rn(x); }
+__device__ __forceinline__ float d2f_rn(double x) {
+  const uint64_t u = uint64_t(__double_as_longlong(x));
+  const int e = int((u >> 52) & 0x7ffu) - 896;
+  if (e <= 0 || e >= 255) {
+    if ((u << 1) == 0) return __uint_as_float(uint32_t(u >> 63) << 31);
+    return d2f_slow(x);  // out of line: FP64-pipe instructions on a predicated path still occupy the pipe
+  }
+  const uint64_t mant = u & 0xfffffffffffffull;
+  uint32_t body = (uint32_t(e) << 23) | uint32_t(mant >> 29);
+  const uint32_t rem = uint32_t(mant & 0x1fffffffu);
+  if (rem > 0x10000000u || (rem == 0x10000000u && (body & 1u))) ++body;  // carries into the exponent
+  return __uint_as_float((uint32_t(u >> 63) << 31) | body);
+}
+
+// Shared-memory layout of the FP32/BF16 cell block (byte offsets; host and
+// device agree on it through this one function). Regions: vertex coordinates
+// [cpb][24] and trilinear coefficients [cpb][21] (FP64), the Jacobian columns
+// [cpb][3][n1d^2][3] (FP64), the products u v of the 1D points [n1d^2] (FP64),
+// w det J as hi + lo [cpb][nq] (float2), FP32 cofactors and w/det J
+// [cpb][nq][12], then the operands: for nb <= 27 the scaled and plain
+// cofactor gradients as float4 [cpb][nq][nb] each, else the plain gradients
+// [cpb][nq][3][nb] (float).
+struct MixedLayout {
+  long x, a, jc, uv, djw, geo32, ga, gb, bytes;
+};
+__host__ __device__ inline MixedLayout mixed_layout(int cpb, int nq, int n1d, int nb) {
+  MixedLayout L;
+  const long p2 = long(n1d) * n1d;
+  L.x = 0;
+  L.a = L.x + long(cpb) * 24 * 8;
+  L.jc = L.a + long(cpb) * 21 * 8;
+  L.uv = L.jc + long(cpb) * 9 * p2 * 8;
+  L.djw = (L.uv + p2 * 8 + 15) & ~15l;
+  L.geo32 = (L.djw + long(cpb) * nq * 8 + 15) & ~15l;
+  L.ga = L.geo32 + long(cpb) * nq * 48;
+  if (nb <= 27) {
+    L.gb = L.ga + long(cpb) * nq * nb * 16;
+    L.bytes = L.gb + long(cpb) * nq * nb * 16;
+  } else {
+    L.gb = L.ga;
+    L.bytes = L.ga + long(cpb) * nq * 3 * nb * 4;
+  }
+  return L;
+}
+
+// One block integrates `cpb` cells for the FP32 (PREC 1) and BF16 (PREC 2)
+// forms; same steps as cell_block_fp64, with the geometry FP64 and everything
+// after it FP32:
+//   * each Jacobian column of the trilinear map depends on two of the three
+//     reference coordinates only (column d is linear in the other two and
+//     bilinear in their product), so it is evaluated once per pair of 1D
+//     points of the tensor rule, n1d^2 instead of n1d^3 times (FP64);
+//   * per quadrature point: cofactors and det J (FP64), rounded once to FP32
+//     on the integer bits; w/det J as the FP32 quotient of the rounded values;
+//     w det J as an FP32 hi + lo pair;
+//   * gradients gh_a = cof gradhat(phihat_a) in FP32, stored as (w/det) gh_a
+//     and gh_a (rounded to BF16 for PREC 2), so that a product of one point
+//     costs one load per side;
+//   * PREC 1 sums the points in blocks of `qblock` (one z-slab of the rule)
+//     with Kahan compensation between blocks; PREC 2 sums plainly;
+//   * the cell vector sum_q (w det J)_q phihat_a(x_q) in double-float
+//     arithmetic (products with fmaf error terms, TwoSum accumulation),
+//     rounded once to FP64.
+template <int P, int NC, int PREC>
+__device__ __forceinline__ void cell_block_mixed(const CellParams& prm, int64_t e0, int ncell, double* smem) {
+  constexpr int NB = (P + 1) * (P + 1) * (P + 1);
+  constexpr int NL = NC * NB;
+  constexpr int NLP = (NL + 3) & ~3;
+  constexpr bool VEC = NB <= 27;
+  const int cpb = prm.cpb, nq = prm.nq, n1d = prm.nq1d, p2 = n1d * n1d;
+  const MixedLayout L = mixed_layout(cpb, nq, n1d, NB);
+  unsigned char* base = reinterpret_cast<unsigned char*>(smem);
+  double* sx = reinterpret_cast<double*>(base + L.x);
+  double* sa = reinterpret_cast<double*>(base + L.a);
+  double* sj = reinterpret_cast<double*>(base + L.jc);
+  double* suv = reinterpret_cast<double*>(base + L.uv);
+  float2* djw = reinterpret_cast<float2*>(base + L.djw);
+  float* geo32 = reinterpret_cast<float*>(base + L.geo32);
+  float4* gA = reinterpret_cast<float4*>(base + L.ga);
+  float4* gB = reinterpret_cast<float4*>(base + L.gb);
+  float* g = reinterpret_cast<float*>(base + L.ga);
+  const int tid = threadIdx.x;
+
+  for (int i = tid; i < ncell * 24; i += blockDim.x) sx[i] = prm.xv[e0 * 24 + i];
+  __syncthreads();
+  // trilinear coefficients; u v of the 1D point pairs (the 1D rule is the x
+  // coordinates of the first n1d points)
+  for (int i = tid; i < ncell * 3 + p2; i += blockDim.x) {
+    if (i < ncell * 3) {
+      trilinear_coefficients(sx + (i / 3) * 24, i % 3, sa + (i / 3) * 21);
+    } else {
+      const int pr = i - ncell * 3;
+      suv[pr] = prm.xq[3 * (pr % n1d)] * prm.xq[3 * (pr / n1d)];
+    }
+  }
+  __syncthreads();
+  // Jacobian columns: J[k][d] at the pair (u, v) of the other two coordinates
+  // (in axis order): d = 0: a1 + a4 y + a5 z + a7 yz; d = 1: a2 + a4 x + a6 z +
+  // a7 xz; d = 2: a3 + a5 x + a6 y + a7 xy (coefficients a1..a7 at offsets
+  // 0, 3, .., 18 of the component).
+  for (int i = tid; i < ncell * 9 * p2; i += blockDim.x) {
+    const int c = i / (9 * p2), r = i % (9 * p2), d = r / (3 * p2), rem = r % (3 * p2), pr = rem / 3, k = rem % 3;
+    const double* a = sa + c * 21;
+    const double u = prm.xq[3 * (pr % n1d)], v = prm.xq[3 * (pr / n1d)];
+    const int o0 = 3 * d, ou = d == 2 ? 12 : 9, ov = d == 0 ? 12 : 15;
+    sj[i] = fma(a[18 + k], suv[pr], fma(a[ov + k], v, fma(a[ou + k], u, a[o0 + k])));
+  }
+  __syncthreads();
+  for (int i = tid; i < ncell * nq; i += blockDim.x) {
+    const int c = i / nq, q = i % nq;
+    const int ix = q % n1d, iy = (q / n1d) % n1d, iz = q / p2;
+    const double* jc = sj + c * 9 * p2;
+    double J[3][3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      J[k][0] = jc[(0 * p2 + iy + n1d * iz) * 3 + k];
+      J[k][1] = jc[(1 * p2 + ix + n1d * iz) * 3 + k];
+      J[k][2] = jc[(2 * p2 + ix + n1d * iy) * 3 + k];
+    }
+    double cof[9];
+    cof[0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    cof[1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    cof[2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    cof[3] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    cof[4] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    cof[5] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    cof[6] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    cof[7] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    cof[8] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * cof[0] + J[0][1] * cof[1] + J[0][2] * cof[2];
+    if (!(det > 0.0)) atomicOr(prm.err, kErrNegJacobian);
+    const double wq = prm.w[q];
+    float* g32 = geo32 + size_t(i) * 12;
+#pragma unroll
+    for (int t = 0; t < 9; ++t) g32[t] = d2f_rn(cof[t]);
+    g32[9] = d2f_rn(wq) / d2f_rn(det);
+    const double wd = wq * det;
+    const float hi = d2f_rn(wd);
+    djw[i] = make_float2(hi, d2f_rn(wd - f32_to_f64_exact(hi)));
+  }
+  __syncthreads();
+  for (int i = tid; i < ncell * nq * NB; i += blockDim.x) {
+    const int a = i % NB, cq = i / NB, q = cq % nq;
+    const float4* gq4 = reinterpret_cast<const float4*>(geo32 + size_t(cq) * 12);
+    const float4 c0 = gq4[0], c1 = gq4[1], c2 = gq4[2];
+    const float* dp = prm.dphi32 + (size_t(q) * NB + a) * 3;
+    const float d0 = dp[0], d1 = dp[1], d2 = dp[2];
+    float g0 = fmaf(c0.z, d2, fmaf(c0.y, d1, c0.x * d0));
+    float g1 = fmaf(c1.y, d2, fmaf(c1.x, d1, c0.w * d0));
+    float g2 = fmaf(c2.x, d2, fmaf(c1.w, d1, c1.z * d0));
+    if (VEC) {
+      const float s = c2.y;
+      float a0 = s * g0, a1 = s * g1, a2 = s * g2;
+      if (PREC == 2) {
+        a0 = round_bf16(a0), a1 = round_bf16(a1), a2 = round_bf16(a2);
+        g0 = round_bf16(g0), g1 = round_bf16(g1), g2 = round_bf16(g2);
+      }
+      gA[i] = make_float4(a0, a1, a2, 0.f);
+      gB[i] = make_float4(g0, g1, g2, 0.f);
+    } else {
+      float* gg = g + size_t(cq) * 3 * NB;
+      gg[a] = g0;
+      gg[NB + a] = g1;
+      gg[2 * NB + a] = g2;
+    }
+  }
+  __syncthreads();
+  const int qb = PREC == 1 ? prm.qblock : nq;
+  for (int i = tid; i < ncell * NB * NB; i += blockDim.x) {
+    const int c = i / (NB * NB), ab = i % (NB * NB), a = ab / NB, b = ab % NB;
+    const int64_t e = e0 + c;
+    const float coef = d2f_rn(prm.coef[e]);
+    float* K = reinterpret_cast<float*>(prm.ke) + e * NL * NLP;
+    // (w/det) gh_a and gh_b of point q as float3
+    auto load = [&](int q, float (&ga)[3], float (&gb)[3]) {
+      if (VEC) {
+        const float4 A = gA[(size_t(c) * nq + q) * NB + a], B = gB[(size_t(c) * nq + q) * NB + b];
+        ga[0] = A.x, ga[1] = A.y, ga[2] = A.z;
+        gb[0] = B.x, gb[1] = B.y, gb[2] = B.z;
+      } else {
+        const float* gq = g + (size_t(c) * nq + q) * 3 * NB;
+        const float s = geo32[(size_t(c) * nq + q) * 12 + 9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          ga[k] = s * gq[k * NB + a];
+          gb[k] = gq[k * NB + b];
+          if (PREC == 2) ga[k] = round_bf16(ga[k]), gb[k] = round_bf16(gb[k]);
+        }
+      }
+    };
+    if (NC == 1) {
+      float sum = 0.f, carry = 0.f;
+      for (int q0 = 0; q0 < nq; q0 += qb) {
+        float part = 0.f;
+        const int q1 = q0 + qb < nq ? q0 + qb : nq;
+        for (int q = q0; q < q1; ++q) {
+          float ga[3], gb[3];
+          load(q, ga, gb);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) part = fmaf(ga[k], gb[k], part);
+        }
+        if (PREC == 1) kahan_add(sum, carry, part); else sum += part;
+      }
+      K[a * NLP + b] = coef * sum;
+    } else {
+      float S[3][3], C[3][3];
+#pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2) S[i2][j2] = C[i2][j2] = 0.f;
+      for (int q0 = 0; q0 < nq; q0 += qb) {
+        float G[3][3];
+#pragma unroll
+        for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+          for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] = 0.f;
+        const int q1 = q0 + qb < nq ? q0 + qb : nq;
+        for (int q = q0; q < q1; ++q) {
+          float ga[3], gb[3];
+          load(q, ga, gb);
+#pragma unroll
+          for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+            for (int j2 = 0; j2 < 3; ++j2) G[i2][j2] = fmaf(ga[i2], gb[j2], G[i2][j2]);
+        }
+#pragma unroll
+        for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+          for (int j2 = 0; j2 < 3; ++j2) {
+            if (PREC == 1) kahan_add(S[i2][j2], C[i2][j2], G[i2][j2]); else S[i2][j2] += G[i2][j2];
+          }
+      }
+      const float lh = d2f_rn(prm.lam_hat), mh = d2f_rn(prm.mu_hat);
+      const float tr = S[0][0] + S[1][1] + S[2][2];
+#pragma unroll
+      for (int i2 = 0; i2 < 3; ++i2)
+#pragma unroll
+        for (int j2 = 0; j2 < 3; ++j2) {
+          float v = lh * S[i2][j2] + mh * S[j2][i2];
+          if (i2 == j2) v += mh * tr;
+          K[size_t(i2 * NB + a) * NLP + j2 * NB + b] = coef * v;
+        }
+    }
+  }
+  for (int i = tid; i < ncell * NB; i += blockDim.x) {
+    const int c = i / NB, a = i % NB;
+    float sh = 0.f, sl = 0.f;
+    for (int q = 0; q < nq; ++q) {
+      const float2 w2 = djw[c * nq + q], p2v = prm.phi2[size_t(q) * NB + a];
+      const float ph = w2.x * p2v.x;
+      const float pe = fmaf(w2.x, p2v.x, -ph) + (w2.x * p2v.y + w2.y * p2v.x);
+      const float sum = sh + ph;
+      const float bp = sum - sh;
+      const float err = (sh - (sum - bp)) + (ph - bp);
+      sh = sum;
+      sl += err + pe;
+    }
+    const double f = sl == 0.f ? f32_to_f64_exact(sh) : __dadd_rn(f32_to_f64_exact(sh), f32_to_f64_exact(sl));
+    double* fe = prm.fe + (e0 + c) * NL;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) fe[k * NB + a] = prm.f[k] * f;
+  }
+}
+
+// Cell integration of one block of cells in the given precision.
+template <int P, int NC, int PREC>
+__device__ __forceinline__ void cell_block(const CellParams& prm, int64_t e0, int ncell, double* smem) {
+  if constexpr (PREC == 0) {
+    cell_block_fp64<P, NC>(prm, e0, ncell, smem);
+  } else {
+    cell_block_mixed<P, NC, PREC>(prm, e0, ncell, smem);
+  }
+}
 
 }  // namespace feasm

@@ -29,13 +29,15 @@ struct HostSetup {
   int64_t n_dofs = 0, nnz = 0, n_contrib = 0, n_codes = 0;
   int max_slots = 0;
   int64_t max_row_nnz = 0;
+  bool node_rows = false;           // the ncomp rows of each node share cells and positions
   std::vector<int32_t> cell_dofs;   // [n_cells][nl]
   std::vector<int64_t> row_ptr;     // [n_dofs+1]
   std::vector<int32_t> col;         // [nnz]
   std::vector<uint8_t> cnt;         // [nnz] contributions per nonzero
   std::vector<int64_t> code_ptr;    // [n_dofs+1] first code of each row
   std::vector<uint16_t> codes;      // (head << 15) | (slot << 8) | local column, rows padded to 8 codes
-  std::vector<uint16_t> pos;        // same blocks, slot-major: nonzero index within the row of (slot, column)
+  std::vector<uint16_t> pos;        // same blocks, slot-major: nonzero index within the row of (slot, column),
+                                    // bit 15 set on the first contribution of each nonzero
   std::vector<int64_t> slot_ptr;    // [n_dofs+1]
   std::vector<int32_t> slots;       // [n_cells*nl] e*nl + local row, cells ascending
 };
@@ -64,6 +66,7 @@ struct fe_space {
   double* d_phi = nullptr;       // [nq][nb]
   double* d_dphi = nullptr;      // [nq][nb][3]
   float* d_dphi32 = nullptr;     // [nq][nb][3]
+  float* d_phi2 = nullptr;       // [nq][nb][2] phihat as FP32 hi + lo
   int32_t* d_cell_dofs = nullptr;
   int64_t* d_row_ptr = nullptr;
   int32_t* d_col = nullptr;

@@ -10,15 +10,19 @@ int cells_per_block(int nb) {
   return pairs >= kCellThreads ? 1 : kCellThreads / pairs;
 }
 
-// Shared memory of k_cell: vertex coordinates [cpb][24], trilinear
-// coefficients [cpb][21], per-point geometry [cpb][nq][11] (cofactor matrix,
-// w/det, w*det) in FP64, for the FP32/BF16 forms an FP32 copy [cpb][nq][12]
-// of the cofactors and w/det, and the cofactor-scaled reference gradients
-// [cpb][nq][3][nb] in the operand type.
+// Shared memory of k_cell: for FP64, vertex coordinates [cpb][24],
+// trilinear coefficients [cpb][21], per-point geometry [cpb][nq][11]
+// (cofactors, w/det, w*det) and the cofactor gradients [cpb][nq][3][nb]; for
+// the FP32/BF16 forms the layout of mixed_layout. -1 if it exceeds an SM.
 long cell_smem_bytes(int nb, int nq, fe_precision prec, int cpb) {
-  const long tsz = prec == FE_PREC_FP64 ? 8 : 4;
-  long bytes = long(cpb) * (24 + 21) * 8 + long(cpb) * nq * 11 * 8 + long(cpb) * nq * 3 * nb * tsz;
-  if (prec != FE_PREC_FP64) bytes += long(cpb) * nq * 12 * 4;
+  long bytes;
+  if (prec == FE_PREC_FP64) {
+    bytes = long(cpb) * (24 + 21) * 8 + long(cpb) * nq * 11 * 8 + long(cpb) * nq * 3 * nb * 8;
+  } else {
+    int n1d = 1;
+    while (n1d * n1d * n1d < nq) ++n1d;
+    bytes = mixed_layout(cpb, nq, n1d, nb).bytes;
+  }
   return bytes <= 227 * 1024 ? bytes : -1;
 }
 
@@ -58,10 +62,12 @@ cudaError_t launch_cell_integration(const fe_space* s, const double* coef, const
   prm.nq = s->nq;
   prm.cpb = cells_per_block(s->nb);
   prm.qblock = s->nq1d * s->nq1d;
+  prm.nq1d = s->nq1d;
   prm.xv = s->d_xv;
   prm.w = s->d_w;
   prm.xq = s->d_xq;
   prm.phi = s->d_phi;
+  prm.phi2 = reinterpret_cast<const float2*>(s->d_phi2);
   prm.dphi = s->d_dphi;
   prm.dphi32 = s->d_dphi32;
   prm.coef = coef;
@@ -208,50 +214,114 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 }
 
 // Slot-wise scatter for FP32 cell matrices (the FP32 and BF16 forms). One warp
-// per CSR row r: for each cell around DOF r in ascending order ("slot"), the
-// lanes read that cell's matrix row (coalesced) and the slot-major positions
-// pos[s][m] of its entries among the row's nonzeros, and add each entry into
-// a per-row double-float accumulator (hi, lo) in shared memory with Knuth's
-// TwoSum (the rounding error of every addition is kept exactly in lo). The
-// entries of one cell row go to distinct nonzeros, so the lanes never collide;
-// a __syncwarp between slots orders the additions, so every nonzero sums its
-// terms in ascending cell order. The accumulator is rounded once to FP64
-// (df_to_double) and stored coalesced. Lanes past the end of a cell row
-// (m >= NL) read padding and add zero into a private dummy accumulator, so the
-// inner loop has no divergent branches (the position array and the
-// cell-matrix scratch are allocated with enough padding for those reads).
-// Global loads of up to SB slots are issued before their additions, and the
-// row descriptors (pointers, slot ids) of the warp's next row are fetched
-// while the current row is reduced.
-template <int NL, bool IDX32>
-__global__ void __launch_bounds__(kScatterWarps * 32, 5) k_scatter_slots(ScatterParams p) {
-  constexpr int CH = (NL + 31) / 32;
-  constexpr int SB = CH >= 3 ? 4 : 8;
+// per work item: a CSR row r (R = 1), or the R = ncomp rows of one node, which
+// lie in the same cells at local rows i * nb + a and share their column
+// pattern (R = 3). For each cell around the DOF in ascending order ("slot"),
+// the lanes read that cell's matrix row(s) (coalesced) and the slot-major
+// positions pos[s][m] of the entries among the row's nonzeros (one position
+// block serves all R rows). The first contribution of each nonzero (flag bit
+// 15 of pos; every entry of slot 0) stores (v, 0) into the row's double-float
+// accumulator in shared memory; later ones add with Knuth's TwoSum, whose
+// rounding error is kept exactly in the low part. The entries of one cell row
+// go to distinct nonzeros, so the lanes never collide; a __syncwarp between
+// slots orders the additions, so every nonzero sums its terms in ascending cell
+// order. Each accumulator is rounded once to FP64 (df_to_double) and stored
+// coalesced. Lanes past the end of a cell row (m >= NL) read padding and touch
+// a private dummy accumulator, so the inner loop has no divergent branches
+// (the position array and the cell-matrix scratch are allocated with padding
+// for those reads). Slots are processed in batches of 8, 4, 2 or 1 (the
+// largest that fits the slots left and the register budget), all loads of a
+// batch issued before its additions; the item descriptors (pointers, slot ids,
+// RHS terms) of the warp's next item are fetched while the current one is
+// reduced.
+template <int NL, int R>
+struct SlotScatter {
+  static constexpr int CH = (NL + 31) / 32;
+  static constexpr int NBR = NL / R;  // local-row offset between the rows of one node
+  static constexpr int LOADS = CH * (R + 1);
+  static constexpr int SB = (LOADS <= 4 && R > 1) ? 8 : LOADS <= 8 ? 4 : LOADS <= 16 ? 2 : 1;
+
+  // One batch of B slots starting at slot s_begin.
+  template <int B, bool IDX32>
+  __device__ __forceinline__ static void batch(const ScatterParams& p, const float* ke, const uint16_t* pos,
+                                               int my_slot, int s_begin, float2* acc, int rs, int dummy, int lane) {
+    float x[B][CH][R];
+    int kk[B][CH];
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+      const int s = s_begin + t;
+      const int sid = __shfl_sync(kFull, my_slot, s);
+      const float* krow = IDX32 ? ke + uint32_t(sid) * uint32_t(p.nlp) : ke + int64_t(sid) * p.nlp;
+      const uint16_t* prow = pos + s * NL;
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int k = int(__ldg(prow + c * 32));
+        kk[t][c] = (c < CH - 1 || c * 32 + lane < NL) ? k : dummy;
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[t][c][i] = __ldg(krow + i * NBR * p.nlp + c * 32);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int raw = kk[t][c];
+        const int k = raw & 0x7fff;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          float2* ai = acc + i * rs;
+          const float v = (c < CH - 1 || c * 32 + lane < NL) ? x[t][c][i] : 0.f;
+          if (s_begin + t == 0) {
+            ai[k] = make_float2(v, 0.f);
+          } else {
+            const float2 a = (raw & 0x8000) ? make_float2(0.f, 0.f) : ai[k];
+            const float sum = a.x + v;
+            const float bp = sum - a.x;
+            const float err = (a.x - (sum - bp)) + (v - bp);
+            ai[k] = make_float2(sum, a.y + err);
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+};
+
+template <int NL, int R, bool IDX32>
+__global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5) : 3) k_scatter_slots(ScatterParams p) {
+  using S = SlotScatter<NL, R>;
   extern __shared__ __align__(16) unsigned char sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* acc = reinterpret_cast<float2*>(sm + size_t(warp) * p.warp_bytes);
-  const int dummy = p.acc_stride + lane;
+  const int rs = p.acc_stride + 32;       // accumulator row: acc_stride nonzeros, then one dummy per lane
+  const int dummy = p.acc_stride + lane;  // within each accumulator row
   const float* ke = reinterpret_cast<const float*>(p.ke) + lane;
   const bool want_rhs = p.rhs != nullptr;
+  const int64_t n_items = p.n_rows / R;
   const int64_t stride = int64_t(gridDim.x) * kScatterWarps;
-  int64_t r = int64_t(blockIdx.x) * kScatterWarps + warp;
+  int64_t u = int64_t(blockIdx.x) * kScatterWarps + warp;
   int64_t s0 = 0, k0 = 0, c0 = 0;
   int ns = 0, nnz = 0, my_slot = 0;
-  double my_fe = 0.0;
-  if (r < p.n_rows) {
+  double my_fe[R];
+#pragma unroll
+  for (int i = 0; i < R; ++i) my_fe[i] = 0.0;
+  if (u < n_items) {
+    const int64_t r = u * R;
     s0 = p.slot_ptr[r];
     ns = int(p.slot_ptr[r + 1] - s0);
     k0 = p.row_ptr[r];
     nnz = int(p.row_ptr[r + 1] - k0);
     c0 = p.code_ptr[r];
     my_slot = lane < ns ? p.slots[s0 + lane] : 0;
-    my_fe = (want_rhs && lane < ns) ? p.fe[my_slot] : 0.0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) my_fe[i] = (want_rhs && lane < ns) ? p.fe[my_slot + i * S::NBR] : 0.0;
   }
-  for (; r < p.n_rows; r += stride) {
-    // first-level descriptors of the next row (independent loads)
-    const int64_t rn = r + stride;
+  for (; u < n_items; u += stride) {
+    const int64_t r = u * R;
+    // first-level descriptors of the next item (independent loads)
+    const int64_t un = u + stride, rn = un * R;
     int64_t s0n = 0, s1n = 0, k0n = 0, k1n = 0, c0n = 0;
-    if (rn < p.n_rows) {
+    if (un < n_items) {
       s0n = p.slot_ptr[rn];
       s1n = p.slot_ptr[rn + 1];
       k0n = p.row_ptr[rn];
@@ -259,56 +329,45 @@ __global__ void __launch_bounds__(kScatterWarps * 32, 5) k_scatter_slots(Scatter
       c0n = p.code_ptr[rn];
     }
     const uint16_t* pos = p.pos + c0 + lane;
-    bool first = true;
-    for (int sb0 = 0; sb0 < ns; sb0 += SB) {
-      float x[SB][CH];
-      int kk[SB][CH];
-#pragma unroll
-      for (int t = 0; t < SB; ++t) {
-        const int s = sb0 + t < ns ? sb0 + t : ns - 1;
-        const int sid = __shfl_sync(kFull, my_slot, s);
-        const float* krow = IDX32 ? ke + uint32_t(sid) * uint32_t(p.nlp) : ke + int64_t(sid) * p.nlp;
-        const uint16_t* prow = pos + s * NL;
-#pragma unroll
-        for (int c = 0; c < CH; ++c) {
-          x[t][c] = __ldg(krow + c * 32);
-          const int k = int(__ldg(prow + c * 32));
-          kk[t][c] = (c < CH - 1 || c * 32 + lane < NL) ? k : dummy;
-        }
-      }
-      if (first) {
-        // while the first batch is in flight: clear the accumulators and
-        // reduce the RHS entry (its terms were fetched with the descriptors)
-        for (int k = lane; k < nnz; k += 32) acc[k] = make_float2(0.f, 0.f);
-        if (want_rhs) rhs_row_value(p, r, my_fe, lane);
-        __syncwarp();
-        first = false;
-      }
-#pragma unroll
-      for (int t = 0; t < SB; ++t) {
-        if (sb0 + t < ns) {
-#pragma unroll
-          for (int c = 0; c < CH; ++c) {
-            const int k = kk[t][c];
-            const float v = (c < CH - 1 || c * 32 + lane < NL) ? x[t][c] : 0.f;
-            const float2 a = acc[k];
-            const float sum = a.x + v;
-            const float bp = sum - a.x;
-            const float err = (a.x - (sum - bp)) + (v - bp);
-            acc[k] = make_float2(sum, a.y + err);
-          }
-          __syncwarp();
-        }
+    int sb = 0;
+    while (sb < ns) {
+      const int left = ns - sb;
+      if (S::SB >= 8 && left >= 8) {
+        S::template batch<8, IDX32>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
+        sb += 8;
+      } else if (S::SB >= 4 && left >= 4) {
+        S::template batch<4, IDX32>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
+        sb += 4;
+      } else if (S::SB >= 2 && left >= 2) {
+        S::template batch<2, IDX32>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
+        sb += 2;
+      } else {
+        S::template batch<1, IDX32>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
+        sb += 1;
       }
     }
-    // second-level descriptors of the next row (its slot ids, then its RHS terms)
+    if (want_rhs) {
+#pragma unroll
+      for (int i = 0; i < R; ++i) rhs_row_value(p, r + i, my_fe[i], lane);
+    }
+    // second-level descriptors of the next item (its slot ids, then its RHS terms)
     const int nsn = int(s1n - s0n);
-    const int my_slot_n = (rn < p.n_rows && lane < nsn) ? p.slots[s0n + lane] : 0;
-    for (int k = lane; k < nnz; k += 32) {
-      const float2 a = acc[k];
-      p.values[k0 + k] = df_to_double(a.x, a.y);
+    const int my_slot_n = (un < n_items && lane < nsn) ? p.slots[s0n + lane] : 0;
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int64_t ki = k0 + int64_t(i) * nnz;  // the rows of one node are consecutive and equally long
+      const float2* ai = acc + i * rs;
+      for (int kb = 0; kb < nnz; kb += 32) {
+        const int k = kb + lane;
+        const float2 a = ai[k < nnz ? k : dummy];
+        const double v = df_to_double(a.x, a.y);
+        if (k < nnz) p.values[ki + k] = v;
+      }
     }
-    const double my_fe_n = (want_rhs && rn < p.n_rows && lane < nsn) ? p.fe[my_slot_n] : 0.0;
+    double my_fe_n[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i)
+      my_fe_n[i] = (want_rhs && un < n_items && lane < nsn) ? p.fe[my_slot_n + i * S::NBR] : 0.0;
     __syncwarp();
     s0 = s0n;
     ns = nsn;
@@ -316,7 +375,8 @@ __global__ void __launch_bounds__(kScatterWarps * 32, 5) k_scatter_slots(Scatter
     nnz = int(k1n - k0n);
     c0 = c0n;
     my_slot = my_slot_n;
-    my_fe = my_fe_n;
+#pragma unroll
+    for (int i = 0; i < R; ++i) my_fe[i] = my_fe_n[i];
   }
 }
 
@@ -358,24 +418,32 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
     return cudaGetLastError();
   };
   if (prec != FE_PREC_FP64 && s->hs.max_slots <= 32) {
+    const bool idx32 = int64_t(s->n_cells) * s->nl * s->nlp < (int64_t(1) << 32);
     p.acc_stride = int((s->hs.max_row_nnz + 3) & ~int64_t(3));
-    p.warp_bytes = (p.acc_stride + 32) * 8;  // accumulators + one dummy per lane
+    // rows of one node together (3-component problems), else one row per warp
+    const int R = (s->hs.node_rows && s->ncomp == 3) ? 3 : 1;
+    p.warp_bytes = R * (p.acc_stride + 32) * 8;  // R accumulator rows, each with one dummy per lane
     const long bytes = long(p.warp_bytes) * kScatterWarps;
     if (bytes <= 200 * 1024) {
-      const bool idx32 = int64_t(s->n_cells) * s->nl * s->nlp < (int64_t(1) << 32);
-      switch (s->nl * 2 + (idx32 ? 1 : 0)) {
-        case 16: return launch(k_scatter_slots<8, false>, bytes);
-        case 17: return launch(k_scatter_slots<8, true>, bytes);
-        case 48: return launch(k_scatter_slots<24, false>, bytes);
-        case 49: return launch(k_scatter_slots<24, true>, bytes);
-        case 54: return launch(k_scatter_slots<27, false>, bytes);
-        case 55: return launch(k_scatter_slots<27, true>, bytes);
-        case 128: return launch(k_scatter_slots<64, false>, bytes);
-        case 129: return launch(k_scatter_slots<64, true>, bytes);
-        case 162: return launch(k_scatter_slots<81, false>, bytes);
-        case 163: return launch(k_scatter_slots<81, true>, bytes);
-        case 384: return launch(k_scatter_slots<192, false>, bytes);
-        case 385: return launch(k_scatter_slots<192, true>, bytes);
+      switch (s->nl * 4 + (R == 3 ? 2 : 0) + (idx32 ? 1 : 0)) {
+        case 32: return launch(k_scatter_slots<8, 1, false>, bytes);
+        case 33: return launch(k_scatter_slots<8, 1, true>, bytes);
+        case 96: return launch(k_scatter_slots<24, 1, false>, bytes);
+        case 97: return launch(k_scatter_slots<24, 1, true>, bytes);
+        case 98: return launch(k_scatter_slots<24, 3, false>, bytes);
+        case 99: return launch(k_scatter_slots<24, 3, true>, bytes);
+        case 108: return launch(k_scatter_slots<27, 1, false>, bytes);
+        case 109: return launch(k_scatter_slots<27, 1, true>, bytes);
+        case 256: return launch(k_scatter_slots<64, 1, false>, bytes);
+        case 257: return launch(k_scatter_slots<64, 1, true>, bytes);
+        case 324: return launch(k_scatter_slots<81, 1, false>, bytes);
+        case 325: return launch(k_scatter_slots<81, 1, true>, bytes);
+        case 326: return launch(k_scatter_slots<81, 3, false>, bytes);
+        case 327: return launch(k_scatter_slots<81, 3, true>, bytes);
+        case 768: return launch(k_scatter_slots<192, 1, false>, bytes);
+        case 769: return launch(k_scatter_slots<192, 1, true>, bytes);
+        case 770: return launch(k_scatter_slots<192, 3, false>, bytes);
+        case 771: return launch(k_scatter_slots<192, 3, true>, bytes);
         default: break;
       }
     }

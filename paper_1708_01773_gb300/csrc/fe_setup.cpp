@@ -239,7 +239,8 @@ static int number_dofs(int p, int ncomp, int64_t n_cells, const int32_t* cv, std
 // K^{e_s}[local row of r in e_s][m]. The codes of a row start on a 16-byte
 // boundary (each row's block is padded to a multiple of 8 codes). The same
 // blocks also hold, slot-major, the index within the row of the nonzero that
-// each (slot, local column) contributes to ("pos"), for the slot-wise scatter.
+// each (slot, local column) contributes to ("pos", bit 15 set on the first
+// contribution of each nonzero in slot order), for the slot-wise scatter.
 static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body);
 
 int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
@@ -263,7 +264,7 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
   for (int64_t i = 0; i < ninc; ++i) hs->slot_ptr[hs->cell_dofs[i] + 1]++;
   int max_slots = 0;
   for (int64_t r = 0; r < nd; ++r) max_slots = std::max<int64_t>(max_slots, hs->slot_ptr[r + 1]);
-  if (max_slots * nl > 65535) {
+  if (max_slots * nl > 32767) {
     *err = "a row's contributions exceed 16-bit positions";
     return FE_ERR_UNSUPPORTED;
   }
@@ -343,10 +344,28 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
         hs->cnt[k]++;
         hs->codes[c++] = uint16_t((key & 0xffff) | head);
         const int64_t s_m = int64_t((key >> 8) & 0xff) * nl + int64_t(key & 0xff);
-        hs->pos[hs->code_ptr[r] + s_m] = uint16_t(k - hs->row_ptr[r]);
+        hs->pos[hs->code_ptr[r] + s_m] = uint16_t((k - hs->row_ptr[r]) | (head ? 0x8000 : 0));
       }
     }
   });
+  // The ncomp rows of one node (consecutive DOFs, components in order) lie in
+  // the same cells, at local rows i * nb + a, and so share their column
+  // pattern and positions; the scatter then treats them together.
+  hs->node_rows = false;
+  if (ncomp > 1 && nd % ncomp == 0) {
+    bool ok = true;
+    for (int64_t n = 0; n < nd / ncomp && ok; ++n) {
+      const int64_t r0 = n * ncomp, ns = hs->slot_ptr[r0 + 1] - hs->slot_ptr[r0];
+      const int64_t len = hs->row_ptr[r0 + 1] - hs->row_ptr[r0];
+      for (int i = 1; i < ncomp && ok; ++i) {
+        const int64_t r = r0 + i;
+        ok = hs->slot_ptr[r + 1] - hs->slot_ptr[r] == ns && hs->row_ptr[r + 1] - hs->row_ptr[r] == len;
+        for (int64_t t = 0; t < ns && ok; ++t)
+          ok = hs->slots[hs->slot_ptr[r] + t] == hs->slots[hs->slot_ptr[r0] + t] + i * nb;
+      }
+    }
+    hs->node_rows = ok;
+  }
   return FE_OK;
 }
 

@@ -58,6 +58,22 @@ def test_small_meshes_all_precisions(shape, p, problem):
     sp.close()
 
 
+def test_tensor_core_pipeline_wraps():
+    """Q2 elasticity on 768 cells: every persistent CTA of the tensor-core kernel takes
+    five or six cells, so the geometry slots (4) and operand/accumulator stages (2)
+    are all reused; every entry is compared with the oracle."""
+    prob = inputs.small_problem((12, 8, 8), 2, 1, seed=21)
+    rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob)
+    sp = feasm.FESpace(prob)
+    sp.set_kernel("tensor_core")
+    for prec in ("fp32", "bf16"):
+        vals, rhs = run(sp, prob, prec)
+        assert row_scaled_error(rp_o, col_o, vals, val_o) <= TOL[prec], prec
+        assert energy_error(rp_o, col_o, vals, val_o) <= TOL[prec], prec
+        assert vec_error(rhs, rhs_o) <= 1e-12
+    sp.close()
+
+
 def test_poisson_q1_8_full():
     prob = inputs.poisson_q1_8()
     rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob)

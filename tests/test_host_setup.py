@@ -86,6 +86,19 @@ def test_numbering_pattern_permutation_match_oracle(shape, p, problem):
             vals[k] = Kflat[src].sum()
         assert c == code_ptr[r] + len(sl) * nl
     assert np.all(seen == 1)                                     # a permutation of all contributions
+    if prob.ncomp == 3:
+        # the three rows of a node (consecutive DOFs) lie in the same cells at local rows
+        # i*nb + a and share columns and codes: the scatter reads one position block per node
+        nb = (p + 1) ** 3
+        for n in range(sp.n_dofs // 3):
+            r0 = 3 * n
+            for i in (1, 2):
+                r = r0 + i
+                np.testing.assert_array_equal(slots[slot_ptr[r]:slot_ptr[r + 1]],
+                                              slots[slot_ptr[r0]:slot_ptr[r0 + 1]] + i * nb)
+                np.testing.assert_array_equal(col[rp[r]:rp[r + 1]], col[rp[r0]:rp[r0 + 1]])
+                np.testing.assert_array_equal(codes[code_ptr[r]:code_ptr[r + 1]],
+                                              codes[code_ptr[r0]:code_ptr[r0 + 1]])
     np.testing.assert_allclose(vals, val_o, rtol=0, atol=1e-13 * np.abs(val_o).max())
     np.testing.assert_allclose(rhs, rhs_o, rtol=0, atol=1e-14)
     sp.close()
