@@ -88,7 +88,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     return fail(rc, err);
   }
   if (!host_only) {
-    const int cpb = feasm::cells_per_block(s->nb);
+    const int cpb = feasm::cells_per_block(s->nb, s->nq);
     if (feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP64, cpb) < 0 ||
         feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP32, cpb) < 0) {
       delete s;

@@ -262,8 +262,8 @@ int build_plan(fe_batch* b, fe_precision prec, int cell_mult, int rows_per_item,
   const int n = int(b->spaces.size());
   auto add_cells = [&](int i) {
     const fe_space* s = b->spaces[i];
-    const int64_t step = int64_t(feasm::cells_per_block(s->nb)) *
-                         (b->cells_per_item > 0 ? std::max(1, b->cells_per_item / feasm::cells_per_block(s->nb))
+    const int64_t step = int64_t(feasm::cells_per_block(s->nb, s->nq)) *
+                         (b->cells_per_item > 0 ? std::max(1, b->cells_per_item / feasm::cells_per_block(s->nb, s->nq))
                                                 : cell_mult);
     for (int64_t c = 0; c < s->n_cells; c += step) items.push_back(Item{i, 0, c, std::min(s->n_cells, c + step)});
   };
@@ -280,7 +280,7 @@ int build_plan(fe_batch* b, fe_precision prec, int cell_mult, int rows_per_item,
   size_t smem = 0;
   int rwb = 0;
   for (const fe_space* s : b->spaces) {
-    smem = std::max<size_t>(smem, size_t(feasm::cell_smem_bytes(s->nb, s->nq, prec, feasm::cells_per_block(s->nb))));
+    smem = std::max<size_t>(smem, size_t(feasm::cell_smem_bytes(s->nb, s->nq, prec, feasm::cells_per_block(s->nb, s->nq))));
     rwb = std::max(rwb, row_warp_bytes_for(s, prec));
   }
   smem = std::max<size_t>(smem, size_t(rwb) * feasm::batch::kWarps);
@@ -434,7 +434,7 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
     feasm::CellParams& c = S.cell;
     c.n_cells = s->n_cells;
     c.nq = s->nq;
-    c.cpb = feasm::cells_per_block(s->nb);
+    c.cpb = feasm::cells_per_block(s->nb, s->nq);
     c.qblock = s->nq1d * s->nq1d;
     c.nq1d = s->nq1d;
     c.xv = s->d_xv;

@@ -3,13 +3,15 @@
 //     G[(i,a),(j,b)] = sum_q (w_q / det J_q) gh_{a,i}(q) gh_{b,j}(q),
 // gh_a = cof(J) gradhat(phihat_a) (Eq. shape_grad with J^{-T} = cof(J)/det J,
 // Eq. fematrix), is one 128x96x32 MMA group per cell (81 rows/columns used,
-// 27 quadrature points along K), operands staged in shared memory in the
-// 128-byte swizzled K-major layout, the accumulator in tensor memory.
+// 27 quadrature points along K). Both operands are the one matrix
+// C[(i,a)][q] = sqrt(w_q / det J_q) gh_{a,i}(q), so that G = C C^T (B is the
+// first 96 rows of A); C is staged in shared memory in the 128-byte swizzled
+// K-major layout, the accumulator in tensor memory.
 //
 // FP32 form: 3xTF32 split (hi = tf32(x), lo = tf32(x - hi); products
 // hi*hi + hi*lo + lo*hi) accumulated in FP32, the 27 points split into two
 // accumulators (points 0-15 and 16-31) that the epilogue adds. BF16 form: BF16
-// operands, one product, FP32 accumulation. The epilogue forms
+// operand, one product, FP32 accumulation. The epilogue forms
 //     K_(a,i),(b,j) = E (lam^ G^{ij}_ab + mu^ G^{ji}_ab + mu^ d_ij sum_k G^{kk}_ab)
 // (the isotropic Hooke law written on the Gram blocks). Geometry (Jacobian,
 // cofactors, determinant) is FP64; the cell vector is a double-float sum
@@ -23,9 +25,9 @@
 //               each sub-partition has its own small share of the FP64 pipe,
 //               and an FP64 warp instruction costs the same with 27 active
 //               lanes as with 7, so a whole cell's points fill one warp);
-//   warps 5-8   operands of cell n into operand stage n % 2, and the cell
-//               vector of cell n;
-//   warps 9-16  accumulators of cell n -> shared staging -> cell matrix.
+//   warps 5-11  operands of cell n into operand stage n % 2 (one item per
+//               thread), and the cell vector of cell n (idle threads);
+//   warps 12-19 accumulators of cell n -> shared staging -> cell matrix.
 // Hand-offs use mbarriers (full/empty per slot or stage); every wait is
 // bounded (about one second of clock cycles), after which the role sets
 // FE_ERR_TIMEOUT, leaves its loop, and the CTA frees tensor memory and exits.
@@ -39,15 +41,15 @@ namespace tc {
 
 constexpr int NB = 27, NL = 81, NLP = 84, NQ = 27;
 constexpr int M = 128, N = 96;
-constexpr int GS = 85;  // row stride of the G staging area (odd: conflict-free column writes)
+constexpr int GS = 100;  // row stride of the G staging area (GS % 32 == 4: conflict-free 16-byte column writes)
 // warp roles
-constexpr int W_MMA = 0, W_GEO0 = 1, N_GEO = 4, W_OP0 = 5, N_OP = 4, W_EPI0 = 9, N_EPI = 8;
+constexpr int W_MMA = 0, W_GEO0 = 1, N_GEO = 4, W_OP0 = 5, N_OP = 7, W_EPI0 = 12, N_EPI = 8;
 constexpr int THREADS = 32 * (W_EPI0 + N_EPI);
 constexpr int OP_THREADS = 32 * N_OP, EPI_THREADS = 32 * N_EPI;
 constexpr int GEO_SLOTS = 4;
 // shared memory (offsets from a 1024-byte aligned base)
-constexpr int STAGE_BYTES = 57344;  // Ahi 16 KB, Alo 16 KB, Bhi 12 KB, Blo 12 KB
-constexpr int OFF_AHI = 0, OFF_ALO = 16384, OFF_BHI = 32768, OFF_BLO = 45056;
+constexpr int STAGE_BYTES = 32768;  // C hi 16 KB, C lo 16 KB (128 rows of 128 bytes each)
+constexpr int OFF_CHI = 0, OFF_CLO = 16384;
 constexpr int OFF_G = 2 * STAGE_BYTES;
 // geo32 [27][12] float, djw [27][2] float; a multiple of 16 bytes, since the
 // operand warps read geo32 rows as float4
@@ -59,7 +61,11 @@ constexpr int OFF_EJ = (OFF_GEO + GEO_SLOTS * GEO_SLOT_BYTES + 15) & ~15;
 constexpr int OFF_WT = OFF_EJ + N_GEO * GEO_WARP_DOUBLES * 8;              // [9][4] double bilinear weights
 constexpr int OFF_DPHI = (OFF_WT + 36 * 8 + 15) & ~15;                     // [27][27][3] float
 constexpr int OFF_PHI = (OFF_DPHI + NQ * NB * 3 * 4 + 15) & ~15;           // [27][27][2] float hi + lo
-constexpr int OFF_BAR = (OFF_PHI + NQ * NB * 8 + 7) & ~7;
+constexpr int OFF_KS = (OFF_PHI + NQ * NB * 8 + 15) & ~15;                 // [81][84] float cell-matrix staging
+constexpr int KS_BYTES = NL * NLP * 4;                                      // 27,216: a multiple of 16
+constexpr int N_PAIRS = NB * (NB + 1) / 2;                                  // node pairs a <= b
+constexpr int OFF_PAIRS = OFF_KS + KS_BYTES;                                // [378] u16 (a << 8 | b)
+constexpr int OFF_BAR = (OFF_PAIRS + N_PAIRS * 2 + 7) & ~7;
 // mbarriers: geo_full[4], geo_empty[4], op_full[2], op_empty[2], acc_full[2], acc_empty[2]
 constexpr int BAR_GEO_FULL = 0, BAR_GEO_EMPTY = 4, BAR_OP_FULL = 8, BAR_OP_EMPTY = 10, BAR_ACC_FULL = 12,
               BAR_ACC_EMPTY = 14, N_BARS = 16;
@@ -67,7 +73,8 @@ constexpr int OFF_TMEM = OFF_BAR + N_BARS * 8;  // tensor-memory base address, t
 constexpr int SMEM_USED = OFF_TMEM + 8;
 constexpr int SMEM_BYTES = SMEM_USED + 1024;  // + alignment slack; > half of the SM: one CTA per SM
 constexpr uint32_t TMEM_COLS = 512;            // two accumulator stages of 2 x 96 columns, at 0 and 256
-static_assert(OFF_GEO % 16 == 0 && GEO_SLOT_BYTES % 16 == 0 && OFF_DPHI % 16 == 0 && OFF_BAR % 8 == 0 &&
+static_assert(OFF_GEO % 16 == 0 && GEO_SLOT_BYTES % 16 == 0 && OFF_DPHI % 16 == 0 && OFF_KS % 16 == 0 &&
+                  KS_BYTES % 16 == 0 && OFF_BAR % 8 == 0 &&
                   SMEM_BYTES <= 227 * 1024,
               "layout");
 static_assert(SMEM_BYTES > 114 * 1024, "one CTA per SM (512 tensor-memory columns)");
@@ -124,6 +131,22 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
+// Bulk copy (TMA engine) of `bytes` from shared to global memory, tracked by
+// this thread's bulk-async groups; both addresses 16-byte aligned, bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
+  asm volatile(
+      "{\n.reg .u64 g;\ncvta.to.global.u64 g, %0;\n"
+      "cp.async.bulk.global.shared::cta.bulk_group [g], [%1], %2;\n"
+      "cp.async.bulk.commit_group;\n}\n" ::"l"(gdst),
+      "r"(ssrc), "r"(bytes)
+      : "memory");
+}
+// Waits until the shared-memory source of every committed bulk copy has been read.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until every committed bulk copy has completed.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -155,6 +178,33 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
                : "memory");
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// Two groups of 16 columns, no wait (tmem_wait32 completes them).
+__device__ __forceinline__ void tmem_ld16x2_start(uint32_t ta, uint32_t tb, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, "
+      "[%33];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(ta), "r"(tb)
+      : "memory");
+}
+
+// Waits for this thread's outstanding tensor-memory loads; tied to the
+// registers of the last load so that no use is scheduled before it.
+__device__ __forceinline__ void tmem_wait32(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                 "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                 "+r"(r[15]), "+r"(r[16]), "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]),
+                 "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]),
+                 "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+               :
+               : "memory");
 }
 
 // Two groups of 16 columns with one wait.
@@ -366,7 +416,9 @@ __device__ __forceinline__ void cell_geometry(const Params& p, const GeoLane& g,
     if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
 #pragma unroll
     for (int k = 0; k < 9; ++k) geo32[q * 12 + k] = d2f_rn(cof[k]);
-    geo32[q * 12 + 9] = g.wq32 / d2f_rn(det);
+    const float s = g.wq32 / d2f_rn(det);
+    geo32[q * 12 + 9] = s;
+    geo32[q * 12 + 10] = sqrtf(s);
     const double wd = g.wq * det;
     const float hi = d2f_rn(wd);
     djw[2 * q] = hi;
@@ -408,10 +460,10 @@ __device__ __forceinline__ void cell_vector(const Params& p, int64_t e, int a, c
   for (int k = 0; k < 3; ++k) fe[k * NB + a] = p.f[k] * f;
 }
 
-// Operands of one cell from its geometry slot: A[(i,a)][q] = (w/det) gh_{a,i}(q),
-// B[(j,b)][q] = gh_{b,j}(q); one thread per (node a, 4 points q0..q0+3) forms
-// the three components and stores each 16-byte K-chunk of the four arrays
-// with one vector store (points q >= 27 are the zero padding of K).
+// Operand of one cell from its geometry slot: C[(i,a)][q] =
+// sqrt(w/det) gh_{a,i}(q); one thread per (node a, 4 points q0..q0+3) forms
+// the three components and stores each K-chunk of the hi and lo arrays with
+// one vector store (points q >= 27 are the zero padding of K).
 template <bool BF16>
 __device__ __forceinline__ void build_operands(unsigned char* st, const float* geo32, const float* sdphi, int t) {
   for (int idx = t; idx < NB * 7; idx += OP_THREADS) {
@@ -428,7 +480,7 @@ __device__ __forceinline__ void build_operands(unsigned char* st, const float* g
         g[0][dq] = fmaf(c0.z, d2, fmaf(c0.y, d1, c0.x * d0));
         g[1][dq] = fmaf(c1.y, d2, fmaf(c1.x, d1, c0.w * d0));
         g[2][dq] = fmaf(c2.x, d2, fmaf(c1.w, d1, c1.z * d0));
-        sq[dq] = c2.y;
+        sq[dq] = c2.z;  // sqrt(w/det)
       } else {
         g[0][dq] = g[1][dq] = g[2][dq] = 0.f;
         sq[dq] = 0.f;
@@ -439,29 +491,21 @@ __device__ __forceinline__ void build_operands(unsigned char* st, const float* g
       const int m = i * NB + a;
       if (BF16) {
         const uint32_t o = swz(m, q0 * 2);
-        __nv_bfloat162 ah0 = __floats2bfloat162_rn(sq[0] * g[i][0], sq[1] * g[i][1]);
-        __nv_bfloat162 ah1 = __floats2bfloat162_rn(sq[2] * g[i][2], sq[3] * g[i][3]);
-        __nv_bfloat162 bh0 = __floats2bfloat162_rn(g[i][0], g[i][1]);
-        __nv_bfloat162 bh1 = __floats2bfloat162_rn(g[i][2], g[i][3]);
-        *reinterpret_cast<uint2*>(st + OFF_AHI + o) =
-            make_uint2(*reinterpret_cast<uint32_t*>(&ah0), *reinterpret_cast<uint32_t*>(&ah1));
-        *reinterpret_cast<uint2*>(st + OFF_BHI + o) =
-            make_uint2(*reinterpret_cast<uint32_t*>(&bh0), *reinterpret_cast<uint32_t*>(&bh1));
+        __nv_bfloat162 c0 = __floats2bfloat162_rn(sq[0] * g[i][0], sq[1] * g[i][1]);
+        __nv_bfloat162 c1 = __floats2bfloat162_rn(sq[2] * g[i][2], sq[3] * g[i][3]);
+        *reinterpret_cast<uint2*>(st + OFF_CHI + o) =
+            make_uint2(*reinterpret_cast<uint32_t*>(&c0), *reinterpret_cast<uint32_t*>(&c1));
       } else {
         const uint32_t o = swz(m, q0 * 4);
-        float ah[4], al[4], bh[4], bl[4];
+        float ch[4], cl[4];
 #pragma unroll
         for (int dq = 0; dq < 4; ++dq) {
-          const float av = sq[dq] * g[i][dq];
-          ah[dq] = to_tf32(av);
-          al[dq] = to_tf32(av - ah[dq]);
-          bh[dq] = to_tf32(g[i][dq]);
-          bl[dq] = to_tf32(g[i][dq] - bh[dq]);
+          const float cv = sq[dq] * g[i][dq];
+          ch[dq] = to_tf32(cv);
+          cl[dq] = to_tf32(cv - ch[dq]);
         }
-        *reinterpret_cast<float4*>(st + OFF_AHI + o) = make_float4(ah[0], ah[1], ah[2], ah[3]);
-        *reinterpret_cast<float4*>(st + OFF_ALO + o) = make_float4(al[0], al[1], al[2], al[3]);
-        *reinterpret_cast<float4*>(st + OFF_BHI + o) = make_float4(bh[0], bh[1], bh[2], bh[3]);
-        *reinterpret_cast<float4*>(st + OFF_BLO + o) = make_float4(bl[0], bl[1], bl[2], bl[3]);
+        *reinterpret_cast<float4*>(st + OFF_CHI + o) = make_float4(ch[0], ch[1], ch[2], ch[3]);
+        *reinterpret_cast<float4*>(st + OFF_CLO + o) = make_float4(cl[0], cl[1], cl[2], cl[3]);
       }
     }
   }
@@ -505,6 +549,10 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
   // again), load the reference tables
   for (int i = tid; i < 2 * STAGE_BYTES / 16; i += THREADS) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
   for (int i = tid; i < NQ * NB * 3; i += THREADS) sdphi[i] = p.dphi32[i];
+  for (int i = tid; i < NB * NB; i += THREADS) {
+    const int a = i / NB, b = i % NB;
+    if (a <= b) reinterpret_cast<uint16_t*>(sm + OFF_PAIRS)[a * NB - a * (a - 1) / 2 + (b - a)] = uint16_t(a << 8 | b);
+  }
   if (tid < 36) {
     const int pr = tid / 4, c = tid % 4;
     const double u = p.xq[3 * (pr % 3)], v = p.xq[3 * (pr / 3)];
@@ -535,8 +583,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
         }
         fence_after();
         const uint32_t sb = sbase + uint32_t(st * STAGE_BYTES);
-        const uint64_t ahi = sw128_desc(sb + OFF_AHI), alo = sw128_desc(sb + OFF_ALO);
-        const uint64_t bhi = sw128_desc(sb + OFF_BHI), blo = sw128_desc(sb + OFF_BLO);
+        // A = C (128 rows), B = the first 96 rows of C: the same descriptors
+        const uint64_t ahi = sw128_desc(sb + OFF_CHI), alo = sw128_desc(sb + OFF_CLO);
+        const uint64_t bhi = ahi, blo = alo;
         const uint32_t dst = tmem + uint32_t(st * 256);
         if (BF16) {
 #pragma unroll
@@ -595,8 +644,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
       build_operands<BF16>(sm + st * STAGE_BYTES, geo32, sdphi, t);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       mbar_arrive(bar(BAR_OP_FULL + st));
-      // threads 64-90 have no second operand item: they form the cell vector
-      if (t >= 64 && t < 64 + NB) cell_vector(p, blockIdx.x + n * int64_t(gridDim.x), t - 64, geo32 + NQ * 12, sphi);
+      // threads 192-218 have no operand item: they form the cell vector
+      if (t >= 192 && t < 192 + NB) cell_vector(p, blockIdx.x + n * int64_t(gridDim.x), t - 192, geo32 + NQ * 12, sphi);
       mbar_arrive(bar(BAR_GEO_EMPTY + slot));
     }
   } else {
@@ -619,52 +668,90 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
       }
       fence_after();
       const uint32_t lane_addr = tmem + uint32_t(st * 256) + (uint32_t(32 * (warp & 3)) << 16);
+      const int cbase = (ew >> 2) * 48;  // this warp's 48 of the 96 accumulator columns
+      float* grow = G + (row < NL ? row : 0) * GS + cbase;
+      if (BF16) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const int col0 = ((ew >> 2) * 3 + c) * 16;
-        float v[16];
-        if (BF16) {
-          tmem_ld16(lane_addr + uint32_t(col0), v);
-        } else {
-          float v2[16];
-          tmem_ld16x2(lane_addr + uint32_t(col0), lane_addr + uint32_t(N + col0), v, v2);
+        for (int c = 0; c < 3; ++c) {
+          float v[16];
+          tmem_ld16(lane_addr + uint32_t(cbase + 16 * c), v);
+          if (row < NL) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) v[j] += v2[j];
+            for (int j = 0; j < 16; j += 4)
+              *reinterpret_cast<float4*>(grow + 16 * c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          }
         }
-        if (row < NL) {
+      } else {
+        // the two accumulators (points 0-15, 16-31) of 16 columns per load
+        // pair; the next pair is in flight while this one is stored
+        uint32_t ra[32], rb[32];
+        tmem_ld16x2_start(lane_addr + uint32_t(cbase), lane_addr + uint32_t(N + cbase), ra);
+        tmem_wait32(ra);
 #pragma unroll
-          for (int j = 0; j < 16; ++j)
-            if (col0 + j < NL) G[row * GS + col0 + j] = v[j];
+        for (int c = 0; c < 3; ++c) {
+          uint32_t(&cur)[32] = (c & 1) ? rb : ra;
+          uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
+          if (c < 2)
+            tmem_ld16x2_start(lane_addr + uint32_t(cbase + 16 * (c + 1)), lane_addr + uint32_t(N + cbase + 16 * (c + 1)),
+                              nxt);
+          if (row < NL) {
+#pragma unroll
+            for (int j = 0; j < 16; j += 4)
+              *reinterpret_cast<float4*>(grow + 16 * c + j) = make_float4(
+                  __uint_as_float(cur[j]) + __uint_as_float(cur[16 + j]),
+                  __uint_as_float(cur[j + 1]) + __uint_as_float(cur[17 + j]),
+                  __uint_as_float(cur[j + 2]) + __uint_as_float(cur[18 + j]),
+                  __uint_as_float(cur[j + 3]) + __uint_as_float(cur[19 + j]));
+          }
+          if (c < 2) tmem_wait32(nxt);
         }
       }
       fence_before();
       mbar_arrive(bar(BAR_ACC_EMPTY + st));
+      if (t == 0) bulk_wait_read();  // the previous cell's bulk store has read the staging area
       bar_sync<3, EPI_THREADS>();
-      // K^e from the Gram blocks: one thread per node pair (a, b) reads the nine
-      // G^{ij}_ab and forms the nine entries K_(a,i),(b,j) (the transposed block
-      // and the trace come from the same values); consecutive threads take
-      // consecutive b (conflict-free reads, coalesced stores).
+      // K^e from the Gram blocks: one thread per node pair a <= b reads the
+      // nine G^{ij}_ab and forms the nine entries K_(a,i),(b,j) (the
+      // transposed block and the trace come from the same values), written
+      // to block (a, b) and, K^e being symmetric, transposed to block (b, a).
+      // K^e is staged in shared memory in its global layout and leaves with
+      // one bulk copy.
       const float lh = p.lam_hat * E, mh = p.mu_hat * E;
-      float* K = p.ke + e * (NL * NLP);
-      for (int idx = t; idx < NB * NB; idx += EPI_THREADS) {
-        const int a = idx / NB, b = idx - a * NB;
-        float g[3][3];
+      float* K = reinterpret_cast<float*>(sm + OFF_KS);
+      const uint16_t* pairs = reinterpret_cast<const uint16_t*>(sm + OFF_PAIRS);
+      constexpr int ROUNDS = (N_PAIRS + EPI_THREADS - 1) / EPI_THREADS;
+      float g[ROUNDS][3][3];
+      int ab[ROUNDS];
+#pragma unroll
+      for (int r = 0; r < ROUNDS; ++r) {
+        ab[r] = pairs[t + r * EPI_THREADS < N_PAIRS ? t + r * EPI_THREADS : 0];
+        const int a = ab[r] >> 8, b = ab[r] & 255;
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int j = 0; j < 3; ++j) g[i][j] = G[(i * NB + a) * GS + j * NB + b];
-        const float tr = g[0][0] + g[1][1] + g[2][2];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) {
-            float v = lh * g[i][j] + mh * g[j][i];
-            if (i == j) v += mh * tr;
-            K[(i * NB + a) * NLP + j * NB + b] = v;
-          }
+          for (int j = 0; j < 3; ++j) g[r][i][j] = G[(i * NB + a) * GS + j * NB + b];
       }
+#pragma unroll
+      for (int r = 0; r < ROUNDS; ++r) {
+        if (t + r * EPI_THREADS < N_PAIRS) {
+          const int a = ab[r] >> 8, b = ab[r] & 255;
+          const float tr = g[r][0][0] + g[r][1][1] + g[r][2][2];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              float v = lh * g[r][i][j] + mh * g[r][j][i];
+              if (i == j) v += mh * tr;
+              K[(i * NB + a) * NLP + j * NB + b] = v;
+              if (a != b) K[(j * NB + b) * NLP + i * NB + a] = v;
+            }
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       bar_sync<3, EPI_THREADS>();
+      if (t == 0) bulk_store(p.ke + e * (NL * NLP), sbase + OFF_KS, KS_BYTES);
     }
+    if (t == 0) bulk_wait_all();
   }
   if (failed) {
     *abort_flag = 1;

@@ -5,10 +5,6 @@
 
 namespace feasm {
 
-int cells_per_block(int nb) {
-  const int pairs = nb * nb;
-  return pairs >= kCellThreads ? 1 : kCellThreads / pairs;
-}
 
 // Shared memory of k_cell: for FP64, vertex coordinates [cpb][24],
 // trilinear coefficients [cpb][21], per-point geometry [cpb][nq][11]
@@ -24,6 +20,22 @@ long cell_smem_bytes(int nb, int nq, fe_precision prec, int cpb) {
     bytes = mixed_layout(cpb, nq, n1d, nb).bytes;
   }
   return bytes <= 227 * 1024 ? bytes : -1;
+}
+
+// Cells per block of k_cell: at least one node pair per thread, then doubled
+// while the block has fewer than 128 quadrature points (the FP64 geometry
+// runs one thread per point: 128 points fill four warps, one per SM
+// sub-partition, each with its own share of the FP64 pipe) and the shared
+// memory of every precision stays within 64 KB.
+int cells_per_block(int nb, int nq) {
+  const int pairs = nb * nb;
+  int cpb = pairs >= kCellThreads ? 1 : kCellThreads / pairs;
+  auto fits = [&](int c) {
+    const long a = cell_smem_bytes(nb, nq, FE_PREC_FP64, c), b = cell_smem_bytes(nb, nq, FE_PREC_FP32, c);
+    return a >= 0 && b >= 0 && a <= 64 * 1024 && b <= 64 * 1024;
+  };
+  while (cpb * nq < 128 && fits(2 * cpb)) cpb *= 2;
+  return cpb;
 }
 
 template <int P, int NC, int PREC>
@@ -60,7 +72,7 @@ cudaError_t launch_cell_integration(const fe_space* s, const double* coef, const
   CellParams prm;
   prm.n_cells = s->n_cells;
   prm.nq = s->nq;
-  prm.cpb = cells_per_block(s->nb);
+  prm.cpb = cells_per_block(s->nb, s->nq);
   prm.qblock = s->nq1d * s->nq1d;
   prm.nq1d = s->nq1d;
   prm.xv = s->d_xv;
@@ -231,9 +243,11 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 // (the position array and the cell-matrix scratch are allocated with padding
 // for those reads). Slots are processed in batches of 8, 4, 2 or 1 (the
 // largest that fits the slots left and the register budget), all loads of a
-// batch issued before its additions; the item descriptors (pointers, slot ids,
-// RHS terms) of the warp's next item are fetched while the current one is
-// reduced.
+// batch issued before its additions; the item descriptors (pointers, slot ids)
+// of the warp's next item are fetched while the current one is reduced. The
+// RHS entries are formed every 32 items for the warp's next 32 items, one
+// item per lane (exact fixed-point sum of its cells' FP64 cell-vector
+// entries).
 template <int NL, int R>
 struct SlotScatter {
   static constexpr int CH = (NL + 31) / 32;
@@ -302,9 +316,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
   int64_t u = int64_t(blockIdx.x) * kScatterWarps + warp;
   int64_t s0 = 0, k0 = 0, c0 = 0;
   int ns = 0, nnz = 0, my_slot = 0;
-  double my_fe[R];
-#pragma unroll
-  for (int i = 0; i < R; ++i) my_fe[i] = 0.0;
+  int64_t rhs_u = u;  // first item of this warp whose RHS entries are not formed yet
   if (u < n_items) {
     const int64_t r = u * R;
     s0 = p.slot_ptr[r];
@@ -313,11 +325,19 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
     nnz = int(p.row_ptr[r + 1] - k0);
     c0 = p.code_ptr[r];
     my_slot = lane < ns ? p.slots[s0 + lane] : 0;
-#pragma unroll
-    for (int i = 0; i < R; ++i) my_fe[i] = (want_rhs && lane < ns) ? p.fe[my_slot + i * S::NBR] : 0.0;
   }
   for (; u < n_items; u += stride) {
-    const int64_t r = u * R;
+    if (want_rhs && u == rhs_u) {
+      const int64_t uu = u + int64_t(lane) * stride;
+      if (uu < n_items) {
+        const int64_t ss = p.slot_ptr[uu * R];
+        const int nss = int(p.slot_ptr[uu * R + 1] - ss);
+#pragma unroll
+        for (int i = 0; i < R; ++i)
+          p.rhs[uu * R + i] = fx_sum<double>(nss, [&](int t) { return p.fe[p.slots[ss + t] + i * S::NBR]; });
+      }
+      rhs_u += 32 * stride;
+    }
     // first-level descriptors of the next item (independent loads)
     const int64_t un = u + stride, rn = un * R;
     int64_t s0n = 0, s1n = 0, k0n = 0, k1n = 0, c0n = 0;
@@ -346,11 +366,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
         sb += 1;
       }
     }
-    if (want_rhs) {
-#pragma unroll
-      for (int i = 0; i < R; ++i) rhs_row_value(p, r + i, my_fe[i], lane);
-    }
-    // second-level descriptors of the next item (its slot ids, then its RHS terms)
+    // second-level descriptors of the next item (its slot ids)
     const int nsn = int(s1n - s0n);
     const int my_slot_n = (un < n_items && lane < nsn) ? p.slots[s0n + lane] : 0;
 #pragma unroll
@@ -364,10 +380,6 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
         if (k < nnz) p.values[ki + k] = v;
       }
     }
-    double my_fe_n[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i)
-      my_fe_n[i] = (want_rhs && un < n_items && lane < nsn) ? p.fe[my_slot_n + i * S::NBR] : 0.0;
     __syncwarp();
     s0 = s0n;
     ns = nsn;
@@ -375,8 +387,6 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
     nnz = int(k1n - k0n);
     c0 = c0n;
     my_slot = my_slot_n;
-#pragma unroll
-    for (int i = 0; i < R; ++i) my_fe[i] = my_fe_n[i];
   }
 }
 
@@ -421,7 +431,8 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
     const bool idx32 = int64_t(s->n_cells) * s->nl * s->nlp < (int64_t(1) << 32);
     p.acc_stride = int((s->hs.max_row_nnz + 3) & ~int64_t(3));
     // rows of one node together (3-component problems), else one row per warp
-    const int R = (s->hs.node_rows && s->ncomp == 3) ? 3 : 1;
+    // (measured: pays for Q1, 24-entry cell rows; for wider rows one row per warp is faster)
+    const int R = (s->hs.node_rows && s->ncomp == 3 && s->nl <= 32) ? 3 : 1;
     p.warp_bytes = R * (p.acc_stride + 32) * 8;  // R accumulator rows, each with one dummy per lane
     const long bytes = long(p.warp_bytes) * kScatterWarps;
     if (bytes <= 200 * 1024) {

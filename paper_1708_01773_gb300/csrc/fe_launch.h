@@ -46,6 +46,6 @@ cudaError_t launch_adjoint(const fe_space* s, const double* u, const double* coe
 // Dynamic shared memory needed by the cell-integration kernel (bytes), or -1
 // if the combination does not fit one block.
 long cell_smem_bytes(int nb, int nq, fe_precision prec, int cells_per_block);
-int cells_per_block(int nb);
+int cells_per_block(int nb, int nq);
 
 }  // namespace feasm
