@@ -48,11 +48,13 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
 // One CSR row by one warp for FP32 cell matrices: the slot-wise double-float
-// accumulation of k_scatter_slots; loads bypass L1 (the cell matrices were
-// written earlier in this launch by other blocks).
+// accumulation of k_scatter_slots (slot batches of 4, 2 or 1, first
+// contributions stored, later ones added with TwoSum); loads bypass L1 (the
+// cell matrices were written earlier in this launch by other blocks). The
+// RHS entries are formed separately (rhs_rows).
 template <int NL>
 __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* acc) {
-  constexpr int CH = (NL + 31) / 32;
+  using S = SlotScatter<NL, 1, true>;
   const int64_t s0 = p.slot_ptr[r];
   const int ns = int(p.slot_ptr[r + 1] - s0);
   const int64_t k0 = p.row_ptr[r];
@@ -60,33 +62,21 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
   const uint16_t* pos = p.pos + p.code_ptr[r] + lane;
   const int my_slot = lane < ns ? p.slots[s0 + lane] : 0;
   const float* ke = reinterpret_cast<const float*>(p.ke) + lane;
+  const int rs = p.acc_stride + 32;
   const int dummy = p.acc_stride + lane;
-  for (int k = lane; k < nnz; k += 32) acc[k] = make_float2(0.f, 0.f);
-  if (p.rhs != nullptr) rhs_row_value(p, r, lane < ns ? __ldcg(p.fe + my_slot) : 0.0, lane);
-  __syncwarp();
-  for (int s = 0; s < ns; ++s) {
-    const int sid = __shfl_sync(kFull, my_slot, s);
-    const float* krow = ke + int64_t(sid) * p.nlp;
-    const uint16_t* prow = pos + s * NL;
-    float x[CH];
-    int kk[CH];
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const bool ok = c < CH - 1 || c * 32 + lane < NL;
-      x[c] = ok ? __ldcg(krow + c * 32) : 0.f;
-      kk[c] = ok ? (int(prow[c * 32]) & 0x7fff) : dummy;
+  int sb = 0;
+  while (sb < ns) {
+    const int left = ns - sb;
+    if (S::SB >= 4 && left >= 4) {
+      S::template batch<4, false>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
+      sb += 4;
+    } else if (S::SB >= 2 && left >= 2) {
+      S::template batch<2, false>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
+      sb += 2;
+    } else {
+      S::template batch<1, false>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
+      sb += 1;
     }
-#pragma unroll
-    for (int c = 0; c < CH; ++c) {
-      const int k = kk[c];
-      const float v = x[c];
-      const float2 a = acc[k];
-      const float sum = a.x + v;
-      const float bp = sum - a.x;
-      const float err = (a.x - (sum - bp)) + (v - bp);
-      acc[k] = make_float2(sum, a.y + err);
-    }
-    __syncwarp();
   }
   for (int kb = 0; kb < nnz; kb += 32) {
     const int k = kb + lane;
@@ -95,6 +85,16 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
     if (k < nnz) p.values[k0 + k] = v;
   }
   __syncwarp();
+}
+
+// RHS entries of rows r0, r0 + step, ... (< r1), one row per lane: the exact
+// fixed-point sum of the row's cells' FP64 cell-vector entries.
+__device__ void rhs_rows(const ScatterParams& p, int64_t r0, int64_t r1, int64_t step, int lane) {
+  for (int64_t r = r0 + lane * step; r < r1; r += 32 * step) {
+    const int64_t s0 = p.slot_ptr[r];
+    const int ns = int(p.slot_ptr[r + 1] - s0);
+    p.rhs[r] = fx_sum<double>(ns, [&](int t) { return __ldcg(p.fe + p.slots[s0 + t]); });
+  }
 }
 
 // One CSR row by one warp for FP64 cell matrices: one lane per nonzero, each
@@ -208,6 +208,7 @@ __global__ void __launch_bounds__(kThreads) k_batch(const Space* sp, int n_space
       }
       __threadfence();
       unsigned char* wsm = reinterpret_cast<unsigned char*>(smem) + size_t(warp) * row_warp_bytes;
+      if (PREC != 0 && S.scat.rhs != nullptr) rhs_rows(S.scat, item.begin + warp, item.end, kWarps, lane);
       for (int64_t r = item.begin + warp; r < item.end; r += kWarps) run_row<PREC>(S, r, lane, wsm, sbase[warp]);
     }
     __syncthreads();

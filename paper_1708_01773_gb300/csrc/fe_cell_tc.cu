@@ -54,17 +54,18 @@ constexpr int OFF_G = 2 * STAGE_BYTES;
 // geo32 [27][12] float, djw [27][2] float; a multiple of 16 bytes, since the
 // operand warps read geo32 rows as float4
 constexpr int GEO_SLOT_BYTES = (NQ * 12 * 4 + NQ * 2 * 4 + 15) & ~15;
-constexpr int OFF_GEO = (OFF_G + NL * GS * 4 + 15) & ~15;
+constexpr int G_BYTES = NL * GS * 4;  // 32,400: a multiple of 16; two buffers
+constexpr int OFF_GEO = (OFF_G + 2 * G_BYTES + 15) & ~15;
 // per geometry warp: edge differences [3][4][3] and Jacobian columns [3][9][3] (double)
 constexpr int GEO_WARP_DOUBLES = 36 + 81;
 constexpr int OFF_EJ = (OFF_GEO + GEO_SLOTS * GEO_SLOT_BYTES + 15) & ~15;
 constexpr int OFF_WT = OFF_EJ + N_GEO * GEO_WARP_DOUBLES * 8;              // [9][4] double bilinear weights
 constexpr int OFF_DPHI = (OFF_WT + 36 * 8 + 15) & ~15;                     // [27][27][3] float
 constexpr int OFF_PHI = (OFF_DPHI + NQ * NB * 3 * 4 + 15) & ~15;           // [27][27][2] float hi + lo
-constexpr int OFF_KS = (OFF_PHI + NQ * NB * 8 + 15) & ~15;                 // [81][84] float cell-matrix staging
+constexpr int OFF_KS = (OFF_PHI + NQ * NB * 8 + 15) & ~15;                 // [2][81][84] float cell-matrix staging
 constexpr int KS_BYTES = NL * NLP * 4;                                      // 27,216: a multiple of 16
 constexpr int N_PAIRS = NB * (NB + 1) / 2;                                  // node pairs a <= b
-constexpr int OFF_PAIRS = OFF_KS + KS_BYTES;                                // [378] u16 (a << 8 | b)
+constexpr int OFF_PAIRS = OFF_KS + 2 * KS_BYTES;                            // [378] u16 (a << 8 | b)
 constexpr int OFF_BAR = (OFF_PAIRS + N_PAIRS * 2 + 7) & ~7;
 // mbarriers: geo_full[4], geo_empty[4], op_full[2], op_empty[2], acc_full[2], acc_empty[2]
 constexpr int BAR_GEO_FULL = 0, BAR_GEO_EMPTY = 4, BAR_OP_FULL = 8, BAR_OP_EMPTY = 10, BAR_ACC_FULL = 12,
@@ -73,7 +74,7 @@ constexpr int OFF_TMEM = OFF_BAR + N_BARS * 8;  // tensor-memory base address, t
 constexpr int SMEM_USED = OFF_TMEM + 8;
 constexpr int SMEM_BYTES = SMEM_USED + 1024;  // + alignment slack; > half of the SM: one CTA per SM
 constexpr uint32_t TMEM_COLS = 512;            // two accumulator stages of 2 x 96 columns, at 0 and 256
-static_assert(OFF_GEO % 16 == 0 && GEO_SLOT_BYTES % 16 == 0 && OFF_DPHI % 16 == 0 && OFF_KS % 16 == 0 &&
+static_assert(G_BYTES % 16 == 0 && OFF_GEO % 16 == 0 && GEO_SLOT_BYTES % 16 == 0 && OFF_DPHI % 16 == 0 && OFF_KS % 16 == 0 &&
                   KS_BYTES % 16 == 0 && OFF_BAR % 8 == 0 &&
                   SMEM_BYTES <= 227 * 1024,
               "layout");
@@ -192,6 +193,15 @@ __device__ __forceinline__ void tmem_ld16x2_start(uint32_t ta, uint32_t tb, uint
         "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(ta), "r"(tb)
       : "memory");
+}
+
+// One group of 16 columns into r[0..15], no wait.
+__device__ __forceinline__ void tmem_ld16_start(uint32_t ta, uint32_t (&r)[32]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                 "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(ta)
+               : "memory");
 }
 
 // Waits for this thread's outstanding tensor-memory loads; tied to the
@@ -650,106 +660,119 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
     }
   } else {
     // ---------------------------------------------------------------- epilogue
+    // Software-pipelined: iteration n starts the accumulator loads of cell n,
+    // forms K^e of cell n - 1 from G buffer (n - 1) % 2 while they are in
+    // flight, stores cell n's G into buffer n % 2 and releases its
+    // accumulators; one barrier per cell, then one thread sends K^e of cell
+    // n - 1 with a bulk copy from staging buffer (n - 1) % 2.
     const int t = tid - 32 * W_EPI0;
     const int ew = warp - W_EPI0;  // 0..7: lane quadrant warp % 4, column half ew / 4
     const int row = 32 * (warp & 3) + lane;
+    const int cbase = (ew >> 2) * 48;  // this warp's 48 of the 96 accumulator columns
+    const uint16_t* pairs = reinterpret_cast<const uint16_t*>(sm + OFF_PAIRS);
     double coef_next = n_mine > 0 ? p.coef[blockIdx.x] : 0.0;
-    for (int64_t n = 0; n < n_mine; ++n) {
-      const int64_t e = blockIdx.x + n * int64_t(gridDim.x);
+    float E_prev = 0.f;
+    uint32_t ra[32], rb[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) ra[j] = rb[j] = 0u;
+    for (int64_t n = 0; n <= n_mine; ++n) {
+      const bool drain = n < n_mine, form = n > 0;
       const int st = int(n & 1);
-      const uint32_t use = uint32_t((n >> 1) & 1);
-      const float E = d2f_rn(coef_next);
-      if (n + 1 < n_mine) coef_next = p.coef[e + gridDim.x];  // in flight during this cell
-      bool ok = mbar_wait(bar(BAR_ACC_FULL + st), use);
-      ok = __all_sync(0xffffffffu, ok);
-      if (bar_or<3, EPI_THREADS>(!ok)) {
-        failed = true;
-        break;
+      const float E_cur = d2f_rn(coef_next);
+      if (n + 1 < n_mine) coef_next = p.coef[blockIdx.x + (n + 1) * int64_t(gridDim.x)];
+      const uint32_t lane_addr = tmem + uint32_t(st * 256) + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(cbase);
+      float* grow = G + st * (G_BYTES / 4) + (row < NL ? row : 0) * GS + cbase;
+      if (drain) {
+        bool ok = mbar_wait(bar(BAR_ACC_FULL + st), uint32_t((n >> 1) & 1));
+        ok = __all_sync(0xffffffffu, ok);
+        if (bar_or<3, EPI_THREADS>(!ok)) {
+          failed = true;
+          break;
+        }
+        fence_after();
+        if (BF16) tmem_ld16_start(lane_addr, ra);
+        else tmem_ld16x2_start(lane_addr, lane_addr + uint32_t(N), ra);
       }
-      fence_after();
-      const uint32_t lane_addr = tmem + uint32_t(st * 256) + (uint32_t(32 * (warp & 3)) << 16);
-      const int cbase = (ew >> 2) * 48;  // this warp's 48 of the 96 accumulator columns
-      float* grow = G + (row < NL ? row : 0) * GS + cbase;
-      if (BF16) {
+      if (form) {
+        // K^e of cell n - 1: one thread per node pair a <= b reads the nine
+        // G^{ij}_ab and forms the nine entries K_(a,i),(b,j) (the transposed
+        // block and the trace come from the same values), written to block
+        // (a, b) and, K^e being symmetric, transposed to block (b, a), in a
+        // shared staging copy of K^e in its global layout.
+        const float* Gp = G + (st ^ 1) * (G_BYTES / 4);
+        float* K = reinterpret_cast<float*>(sm + OFF_KS + (st ^ 1) * KS_BYTES);
+        const float lh = p.lam_hat * E_prev, mh = p.mu_hat * E_prev;
+        constexpr int ROUNDS = (N_PAIRS + EPI_THREADS - 1) / EPI_THREADS;
+        float g[ROUNDS][3][3];
+        int ab[ROUNDS];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          float v[16];
-          tmem_ld16(lane_addr + uint32_t(cbase + 16 * c), v);
-          if (row < NL) {
+        for (int r = 0; r < ROUNDS; ++r) {
+          ab[r] = pairs[t + r * EPI_THREADS < N_PAIRS ? t + r * EPI_THREADS : 0];
+          const int a = ab[r] >> 8, b = ab[r] & 255;
 #pragma unroll
-            for (int j = 0; j < 16; j += 4)
-              *reinterpret_cast<float4*>(grow + 16 * c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) g[r][i][j] = Gp[(i * NB + a) * GS + j * NB + b];
+        }
+#pragma unroll
+        for (int r = 0; r < ROUNDS; ++r) {
+          if (t + r * EPI_THREADS < N_PAIRS) {
+            const int a = ab[r] >> 8, b = ab[r] & 255;
+            const float tr = g[r][0][0] + g[r][1][1] + g[r][2][2];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+              for (int j = 0; j < 3; ++j) {
+                float v = lh * g[r][i][j] + mh * g[r][j][i];
+                if (i == j) v += mh * tr;
+                K[(i * NB + a) * NLP + j * NB + b] = v;
+                if (a != b) K[(j * NB + b) * NLP + i * NB + a] = v;
+              }
           }
         }
-      } else {
-        // the two accumulators (points 0-15, 16-31) of 16 columns per load
-        // pair; the next pair is in flight while this one is stored
-        uint32_t ra[32], rb[32];
-        tmem_ld16x2_start(lane_addr + uint32_t(cbase), lane_addr + uint32_t(N + cbase), ra);
-        tmem_wait32(ra);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      }
+      if (drain) {
+        // cell n's accumulators -> G buffer n % 2 (FP32: the two 16-point
+        // partial sums of 16 columns per load pair, the next pair in flight
+        // while this one is stored)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           uint32_t(&cur)[32] = (c & 1) ? rb : ra;
           uint32_t(&nxt)[32] = (c & 1) ? ra : rb;
-          if (c < 2)
-            tmem_ld16x2_start(lane_addr + uint32_t(cbase + 16 * (c + 1)), lane_addr + uint32_t(N + cbase + 16 * (c + 1)),
-                              nxt);
+          tmem_wait32(cur);
+          if (c < 2) {
+            if (BF16) tmem_ld16_start(lane_addr + uint32_t(16 * (c + 1)), nxt);
+            else tmem_ld16x2_start(lane_addr + uint32_t(16 * (c + 1)), lane_addr + uint32_t(N + 16 * (c + 1)), nxt);
+          }
           if (row < NL) {
 #pragma unroll
-            for (int j = 0; j < 16; j += 4)
-              *reinterpret_cast<float4*>(grow + 16 * c + j) = make_float4(
-                  __uint_as_float(cur[j]) + __uint_as_float(cur[16 + j]),
-                  __uint_as_float(cur[j + 1]) + __uint_as_float(cur[17 + j]),
-                  __uint_as_float(cur[j + 2]) + __uint_as_float(cur[18 + j]),
-                  __uint_as_float(cur[j + 3]) + __uint_as_float(cur[19 + j]));
-          }
-          if (c < 2) tmem_wait32(nxt);
-        }
-      }
-      fence_before();
-      mbar_arrive(bar(BAR_ACC_EMPTY + st));
-      if (t == 0) bulk_wait_read();  // the previous cell's bulk store has read the staging area
-      bar_sync<3, EPI_THREADS>();
-      // K^e from the Gram blocks: one thread per node pair a <= b reads the
-      // nine G^{ij}_ab and forms the nine entries K_(a,i),(b,j) (the
-      // transposed block and the trace come from the same values), written
-      // to block (a, b) and, K^e being symmetric, transposed to block (b, a).
-      // K^e is staged in shared memory in its global layout and leaves with
-      // one bulk copy.
-      const float lh = p.lam_hat * E, mh = p.mu_hat * E;
-      float* K = reinterpret_cast<float*>(sm + OFF_KS);
-      const uint16_t* pairs = reinterpret_cast<const uint16_t*>(sm + OFF_PAIRS);
-      constexpr int ROUNDS = (N_PAIRS + EPI_THREADS - 1) / EPI_THREADS;
-      float g[ROUNDS][3][3];
-      int ab[ROUNDS];
-#pragma unroll
-      for (int r = 0; r < ROUNDS; ++r) {
-        ab[r] = pairs[t + r * EPI_THREADS < N_PAIRS ? t + r * EPI_THREADS : 0];
-        const int a = ab[r] >> 8, b = ab[r] & 255;
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-          for (int j = 0; j < 3; ++j) g[r][i][j] = G[(i * NB + a) * GS + j * NB + b];
-      }
-#pragma unroll
-      for (int r = 0; r < ROUNDS; ++r) {
-        if (t + r * EPI_THREADS < N_PAIRS) {
-          const int a = ab[r] >> 8, b = ab[r] & 255;
-          const float tr = g[r][0][0] + g[r][1][1] + g[r][2][2];
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              float v = lh * g[r][i][j] + mh * g[r][j][i];
-              if (i == j) v += mh * tr;
-              K[(i * NB + a) * NLP + j * NB + b] = v;
-              if (a != b) K[(j * NB + b) * NLP + i * NB + a] = v;
+            for (int j = 0; j < 16; j += 4) {
+              float4 v;
+              if (BF16) {
+                v = make_float4(__uint_as_float(cur[j]), __uint_as_float(cur[j + 1]), __uint_as_float(cur[j + 2]),
+                                __uint_as_float(cur[j + 3]));
+              } else {
+                v = make_float4(__uint_as_float(cur[j]) + __uint_as_float(cur[16 + j]),
+                                __uint_as_float(cur[j + 1]) + __uint_as_float(cur[17 + j]),
+                                __uint_as_float(cur[j + 2]) + __uint_as_float(cur[18 + j]),
+                                __uint_as_float(cur[j + 3]) + __uint_as_float(cur[19 + j]));
+              }
+              *reinterpret_cast<float4*>(grow + 16 * c + j) = v;
             }
+          }
         }
+        fence_before();
+        mbar_arrive(bar(BAR_ACC_EMPTY + st));
       }
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      // the bulk copy issued last iteration (cell n - 2) has read staging
+      // buffer n % 2, which the next iteration overwrites
+      if (t == 0) bulk_wait_read();
       bar_sync<3, EPI_THREADS>();
-      if (t == 0) bulk_store(p.ke + e * (NL * NLP), sbase + OFF_KS, KS_BYTES);
+      if (form && t == 0)
+        bulk_store(p.ke + (blockIdx.x + (n - 1) * int64_t(gridDim.x)) * (NL * NLP), sbase + OFF_KS + (st ^ 1) * KS_BYTES,
+                   KS_BYTES);
+      E_prev = E_cur;
     }
     if (t == 0) bulk_wait_all();
   }

@@ -328,26 +328,6 @@ struct ScatterParams {
 constexpr unsigned kFull = 0xffffffffu;
 
 
-// Exact RHS entry of row r: the cells' FP64 cell-vector entries, one per lane
-// (lanes < ns), summed in integer fixed point across the warp.
-__device__ __forceinline__ void rhs_row_value(const ScatterParams& p, int64_t r, double my_fe, int lane) {
-  uint64_t m = 0;
-  int ex = 1;
-  bool ng = false;
-  FxTraits<double>::split(my_fe, m, ex, ng);
-  const int emax = __reduce_max_sync(kFull, m != 0 ? ex : 1);
-  const int sh = FxTraits<double>::kShift0 - (emax - ex);
-  const uint64_t a = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
-  int64_t S = ng ? -int64_t(a) : int64_t(a);
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) S += __shfl_xor_sync(kFull, S, off);
-  if (lane == 0) p.rhs[r] = fx_to_double(S, emax - FxTraits<double>::kScale);
-}
-
-__device__ __forceinline__ void rhs_row(const ScatterParams& p, int64_t r, int ns, int my_slot, int lane) {
-  rhs_row_value(p, r, lane < ns ? p.fe[my_slot] : 0.0, lane);
-}
-
 // Exact FP32 -> FP64 conversion of any finite float on the integer bits
 // (denormals included), without the FP64 pipe.
 __device__ __forceinline__ double f32_to_f64_exact(float x) {
@@ -564,7 +544,82 @@ __device__ __forceinline__ void cell_block_mixed(const CellParams& prm, int64_t 
   }
   __syncthreads();
   const int qb = PREC == 1 ? prm.qblock : nq;
-  for (int i = tid; i < ncell * NB * NB; i += blockDim.x) {
+  if constexpr (NC == 1) {
+    // Poisson: each thread sums a TA x TB tile of node pairs, so that one
+    // point's loads (TA + TB gradients, w/det) serve TA TB products per
+    // component; per pair the same slab-blocked (Kahan) sum as one pair per
+    // thread.
+    constexpr int TA = NB == 64 ? 4 : NB == 27 ? 3 : 2, TB = NB == 64 ? 2 : TA;  // 4 x 2 for Q3: fewer registers
+    constexpr int NTA = NB / TA, NTB = NB / TB;
+    static_assert(NB % TA == 0 && NB % TB == 0, "tile");
+    for (int i = tid; i < ncell * NTA * NTB; i += blockDim.x) {
+      const int c = i / (NTA * NTB), tt = i % (NTA * NTB), a0 = (tt / NTB) * TA, b0 = (tt % NTB) * TB;
+      const int64_t e = e0 + c;
+      const float coef = d2f_rn(prm.coef[e]);
+      float sum[TA][TB], carry[TA][TB];
+#pragma unroll
+      for (int u = 0; u < TA; ++u)
+#pragma unroll
+        for (int v = 0; v < TB; ++v) sum[u][v] = carry[u][v] = 0.f;
+      for (int q0 = 0; q0 < nq; q0 += qb) {
+        float part[TA][TB];
+#pragma unroll
+        for (int u = 0; u < TA; ++u)
+#pragma unroll
+          for (int v = 0; v < TB; ++v) part[u][v] = 0.f;
+        const int q1 = q0 + qb < nq ? q0 + qb : nq;
+        for (int q = q0; q < q1; ++q) {
+          float ga[3][TA], gb[3][TB];
+          if (VEC) {
+#pragma unroll
+            for (int u = 0; u < TA; ++u) {
+              const float4 A = gA[(size_t(c) * nq + q) * NB + a0 + u];
+              ga[0][u] = A.x, ga[1][u] = A.y, ga[2][u] = A.z;
+            }
+#pragma unroll
+            for (int v = 0; v < TB; ++v) {
+              const float4 B = gB[(size_t(c) * nq + q) * NB + b0 + v];
+              gb[0][v] = B.x, gb[1][v] = B.y, gb[2][v] = B.z;
+            }
+          } else {
+            const float* gq = g + (size_t(c) * nq + q) * 3 * NB;
+            const float sq = geo32[(size_t(c) * nq + q) * 12 + 9];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+#pragma unroll
+              for (int u = 0; u < TA; ++u) {
+                ga[k][u] = sq * gq[k * NB + a0 + u];
+                if (PREC == 2) ga[k][u] = round_bf16(ga[k][u]);
+              }
+#pragma unroll
+              for (int v = 0; v < TB; ++v) {
+                gb[k][v] = gq[k * NB + b0 + v];
+                if (PREC == 2) gb[k][v] = round_bf16(gb[k][v]);
+              }
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int u = 0; u < TA; ++u)
+#pragma unroll
+              for (int v = 0; v < TB; ++v) part[u][v] = fmaf(ga[k][u], gb[k][v], part[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < TA; ++u)
+#pragma unroll
+          for (int v = 0; v < TB; ++v) {
+            if (PREC == 1) kahan_add(sum[u][v], carry[u][v], part[u][v]); else sum[u][v] += part[u][v];
+          }
+      }
+      float* K = reinterpret_cast<float*>(prm.ke) + e * NL * NLP;
+#pragma unroll
+      for (int u = 0; u < TA; ++u)
+#pragma unroll
+        for (int v = 0; v < TB; ++v) K[(a0 + u) * NLP + b0 + v] = coef * sum[u][v];
+    }
+  }
+  for (int i = tid; i < (NC == 1 ? 0 : ncell * NB * NB); i += blockDim.x) {
     const int c = i / (NB * NB), ab = i % (NB * NB), a = ab / NB, b = ab % NB;
     const int64_t e = e0 + c;
     const float coef = d2f_rn(prm.coef[e]);
@@ -669,5 +724,73 @@ __device__ __forceinline__ void cell_block(const CellParams& prm, int64_t e0, in
     cell_block_mixed<P, NC, PREC>(prm, e0, ncell, smem);
   }
 }
+
+// Read-only loads of the scatter: through the non-coherent read-only path,
+// or, for data written earlier in the same launch by other blocks (the
+// batched driver), bypassing L1 (ld.global.cg).
+template <bool CG, typename T>
+__device__ __forceinline__ T ld_ro(const T* p) {
+  if constexpr (CG) return __ldcg(p); else return __ldg(p);
+}
+
+// One batch of the slot-wise double-float scatter of k_scatter_slots (see
+// there): B slots from s_begin, R rows per item (R = 3: the rows of one node,
+// local rows i * NL / R + a of each cell), accumulator rows of stride rs with
+// a private dummy per lane at index `dummy`. The first contribution of a
+// nonzero (flag bit 15 of pos; every entry of slot 0) stores (v, 0); later
+// ones add with TwoSum.
+template <int NL, int R, bool CG = false>
+struct SlotScatter {
+  static constexpr int CH = (NL + 31) / 32;
+  static constexpr int NBR = NL / R;  // local-row offset between the rows of one node
+  static constexpr int LOADS = CH * (R + 1);
+  static constexpr int SB = (LOADS <= 4 && R > 1) ? 8 : LOADS <= 8 ? 4 : LOADS <= 16 ? 2 : 1;
+
+  // One batch of B slots starting at slot s_begin.
+  template <int B, bool IDX32>
+  __device__ __forceinline__ static void batch(const ScatterParams& p, const float* ke, const uint16_t* pos,
+                                               int my_slot, int s_begin, float2* acc, int rs, int dummy, int lane) {
+    float x[B][CH][R];
+    int kk[B][CH];
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+      const int s = s_begin + t;
+      const int sid = __shfl_sync(kFull, my_slot, s);
+      const float* krow = IDX32 ? ke + uint32_t(sid) * uint32_t(p.nlp) : ke + int64_t(sid) * p.nlp;
+      const uint16_t* prow = pos + s * NL;
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int k = int(ld_ro<CG>(prow + c * 32));
+        kk[t][c] = (c < CH - 1 || c * 32 + lane < NL) ? k : dummy;
+#pragma unroll
+        for (int i = 0; i < R; ++i) x[t][c][i] = ld_ro<CG>(krow + i * NBR * p.nlp + c * 32);
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < B; ++t) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) {
+        const int raw = kk[t][c];
+        const int k = raw & 0x7fff;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+          float2* ai = acc + i * rs;
+          const float v = (c < CH - 1 || c * 32 + lane < NL) ? x[t][c][i] : 0.f;
+          if (s_begin + t == 0) {
+            ai[k] = make_float2(v, 0.f);
+          } else {
+            const float2 a = (raw & 0x8000) ? make_float2(0.f, 0.f) : ai[k];
+            const float sum = a.x + v;
+            const float bp = sum - a.x;
+            const float err = (a.x - (sum - bp)) + (v - bp);
+            ai[k] = make_float2(sum, a.y + err);
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+};
+
 
 }  // namespace feasm

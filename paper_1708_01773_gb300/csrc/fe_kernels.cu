@@ -248,61 +248,8 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 // RHS entries are formed every 32 items for the warp's next 32 items, one
 // item per lane (exact fixed-point sum of its cells' FP64 cell-vector
 // entries).
-template <int NL, int R>
-struct SlotScatter {
-  static constexpr int CH = (NL + 31) / 32;
-  static constexpr int NBR = NL / R;  // local-row offset between the rows of one node
-  static constexpr int LOADS = CH * (R + 1);
-  static constexpr int SB = (LOADS <= 4 && R > 1) ? 8 : LOADS <= 8 ? 4 : LOADS <= 16 ? 2 : 1;
-
-  // One batch of B slots starting at slot s_begin.
-  template <int B, bool IDX32>
-  __device__ __forceinline__ static void batch(const ScatterParams& p, const float* ke, const uint16_t* pos,
-                                               int my_slot, int s_begin, float2* acc, int rs, int dummy, int lane) {
-    float x[B][CH][R];
-    int kk[B][CH];
-#pragma unroll
-    for (int t = 0; t < B; ++t) {
-      const int s = s_begin + t;
-      const int sid = __shfl_sync(kFull, my_slot, s);
-      const float* krow = IDX32 ? ke + uint32_t(sid) * uint32_t(p.nlp) : ke + int64_t(sid) * p.nlp;
-      const uint16_t* prow = pos + s * NL;
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int k = int(__ldg(prow + c * 32));
-        kk[t][c] = (c < CH - 1 || c * 32 + lane < NL) ? k : dummy;
-#pragma unroll
-        for (int i = 0; i < R; ++i) x[t][c][i] = __ldg(krow + i * NBR * p.nlp + c * 32);
-      }
-    }
-#pragma unroll
-    for (int t = 0; t < B; ++t) {
-#pragma unroll
-      for (int c = 0; c < CH; ++c) {
-        const int raw = kk[t][c];
-        const int k = raw & 0x7fff;
-#pragma unroll
-        for (int i = 0; i < R; ++i) {
-          float2* ai = acc + i * rs;
-          const float v = (c < CH - 1 || c * 32 + lane < NL) ? x[t][c][i] : 0.f;
-          if (s_begin + t == 0) {
-            ai[k] = make_float2(v, 0.f);
-          } else {
-            const float2 a = (raw & 0x8000) ? make_float2(0.f, 0.f) : ai[k];
-            const float sum = a.x + v;
-            const float bp = sum - a.x;
-            const float err = (a.x - (sum - bp)) + (v - bp);
-            ai[k] = make_float2(sum, a.y + err);
-          }
-        }
-      }
-      __syncwarp();
-    }
-  }
-};
-
 template <int NL, int R, bool IDX32>
-__global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5) : 3) k_scatter_slots(ScatterParams p) {
+__global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5) : 4) k_scatter_slots(ScatterParams p) {
   using S = SlotScatter<NL, R>;
   extern __shared__ __align__(16) unsigned char sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
