@@ -308,6 +308,35 @@ __device__ __forceinline__ double fx_sum(int n, Get get) {
 }
 
 
+// fx_sum of N terms held in registers (zeros pad a shorter list): the same
+// fixed-point sum and rounding, so the same result, without a second pass
+// over memory.
+template <int N>
+__device__ __forceinline__ double fx_sum_regs(const double (&v)[N]) {
+  using Tr = FxTraits<double>;
+  int emax = 1;
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    uint64_t m;
+    int ex;
+    bool ng;
+    Tr::split(v[t], m, ex, ng);
+    if (m != 0 && ex > emax) emax = ex;
+  }
+  int64_t S = 0;
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    uint64_t m;
+    int ex;
+    bool ng;
+    Tr::split(v[t], m, ex, ng);
+    const int sh = Tr::kShift0 - (emax - ex);
+    const uint64_t a = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+    S += ng ? -int64_t(a) : int64_t(a);
+  }
+  return fx_to_double(S, emax - Tr::kScale);
+}
+
 struct ScatterParams {
   int64_t n_rows;
   int nl, nlp;

@@ -279,9 +279,23 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
       if (uu < n_items) {
         const int64_t ss = p.slot_ptr[uu * R];
         const int nss = int(p.slot_ptr[uu * R + 1] - ss);
+        if (nss <= 8) {
+          // all gathers issued at once, the sum from registers
+          int sl[8];
 #pragma unroll
-        for (int i = 0; i < R; ++i)
-          p.rhs[uu * R + i] = fx_sum<double>(nss, [&](int t) { return p.fe[p.slots[ss + t] + i * S::NBR]; });
+          for (int t = 0; t < 8; ++t) sl[t] = t < nss ? p.slots[ss + t] : 0;
+#pragma unroll
+          for (int i = 0; i < R; ++i) {
+            double v[8];
+#pragma unroll
+            for (int t = 0; t < 8; ++t) v[t] = t < nss ? p.fe[sl[t] + i * S::NBR] : 0.0;
+            p.rhs[uu * R + i] = fx_sum_regs(v);
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < R; ++i)
+            p.rhs[uu * R + i] = fx_sum<double>(nss, [&](int t) { return p.fe[p.slots[ss + t] + i * S::NBR]; });
+        }
       }
       rhs_u += 32 * stride;
     }
