@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 
 #include "fe_launch.h"
+#include "fe_pair_table.h"
 
 namespace feasm {
 
@@ -64,9 +65,8 @@ constexpr int OFF_DPHI = (OFF_WT + 36 * 8 + 15) & ~15;                     // [2
 constexpr int OFF_PHI = (OFF_DPHI + NQ * NB * 3 * 4 + 15) & ~15;           // [27][27][2] float hi + lo
 constexpr int OFF_KS = (OFF_PHI + NQ * NB * 8 + 15) & ~15;                 // [2][81][84] float cell-matrix staging
 constexpr int KS_BYTES = NL * NLP * 4;                                      // 27,216: a multiple of 16
-constexpr int N_PAIRS = NB * (NB + 1) / 2;                                  // node pairs a <= b
-constexpr int OFF_PAIRS = OFF_KS + 2 * KS_BYTES;                            // [378] u16 (a << 8 | b)
-constexpr int OFF_BAR = (OFF_PAIRS + N_PAIRS * 2 + 7) & ~7;
+constexpr int OFF_PAIRS = OFF_KS + 2 * KS_BYTES;  // [PAIR_GROUPS][32] u16 node pairs (kPairTable)
+constexpr int OFF_BAR = (OFF_PAIRS + PAIR_GROUPS * 32 * 2 + 7) & ~7;
 // mbarriers: geo_full[4], geo_empty[4], op_full[2], op_empty[2], acc_full[2], acc_empty[2]
 constexpr int BAR_GEO_FULL = 0, BAR_GEO_EMPTY = 4, BAR_OP_FULL = 8, BAR_OP_EMPTY = 10, BAR_ACC_FULL = 12,
               BAR_ACC_EMPTY = 14, N_BARS = 16;
@@ -477,7 +477,11 @@ __device__ __forceinline__ void cell_vector(const Params& p, int64_t e, int a, c
 template <bool BF16>
 __device__ __forceinline__ void build_operands(unsigned char* st, const float* geo32, const float* sdphi, int t) {
   for (int idx = t; idx < NB * 7; idx += OP_THREADS) {
-    const int a = idx / 7, qc = idx - a * 7, q0 = 4 * qc;
+    // consecutive threads take consecutive nodes of one 4-point chunk: the
+    // geometry-row loads are broadcasts, the reference-gradient loads
+    // (stride 3 words) and the swizzled 16-byte stores (consecutive rows) are
+    // conflict-free
+    const int qc = idx / NB, a = idx - qc * NB, q0 = 4 * qc;
     float g[3][4], sq[4];
 #pragma unroll
     for (int dq = 0; dq < 4; ++dq) {
@@ -559,10 +563,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
   // again), load the reference tables
   for (int i = tid; i < 2 * STAGE_BYTES / 16; i += THREADS) reinterpret_cast<uint4*>(sm)[i] = make_uint4(0, 0, 0, 0);
   for (int i = tid; i < NQ * NB * 3; i += THREADS) sdphi[i] = p.dphi32[i];
-  for (int i = tid; i < NB * NB; i += THREADS) {
-    const int a = i / NB, b = i % NB;
-    if (a <= b) reinterpret_cast<uint16_t*>(sm + OFF_PAIRS)[a * NB - a * (a - 1) / 2 + (b - a)] = uint16_t(a << 8 | b);
-  }
+  for (int i = tid; i < PAIR_GROUPS * 32; i += THREADS)
+    reinterpret_cast<uint16_t*>(sm + OFF_PAIRS)[i] = kPairTable[i / 32][i % 32];
   if (tid < 36) {
     const int pr = tid / 4, c = tid % 4;
     const double u = p.xq[3 * (pr % 3)], v = p.xq[3 * (pr / 3)];
@@ -698,17 +700,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
         // G^{ij}_ab and forms the nine entries K_(a,i),(b,j) (the transposed
         // block and the trace come from the same values), written to block
         // (a, b) and, K^e being symmetric, transposed to block (b, a), in a
-        // shared staging copy of K^e in its global layout.
+        // shared staging copy of K^e in its global layout. Warp w takes the
+        // pair groups w and w + 8 of kPairTable, whose lanes hit distinct
+        // banks in the G loads and in both stores.
         const float* Gp = G + (st ^ 1) * (G_BYTES / 4);
         float* K = reinterpret_cast<float*>(sm + OFF_KS + (st ^ 1) * KS_BYTES);
         const float lh = p.lam_hat * E_prev, mh = p.mu_hat * E_prev;
-        constexpr int ROUNDS = (N_PAIRS + EPI_THREADS - 1) / EPI_THREADS;
+        constexpr int ROUNDS = (PAIR_GROUPS + N_EPI - 1) / N_EPI;
         float g[ROUNDS][3][3];
         int ab[ROUNDS];
 #pragma unroll
         for (int r = 0; r < ROUNDS; ++r) {
-          ab[r] = pairs[t + r * EPI_THREADS < N_PAIRS ? t + r * EPI_THREADS : 0];
-          const int a = ab[r] >> 8, b = ab[r] & 255;
+          const int grp = ew + N_EPI * r;
+          ab[r] = grp < PAIR_GROUPS ? pairs[grp * 32 + lane] : 0xffff;
+          const int a = ab[r] == 0xffff ? 0 : ab[r] >> 8, b = ab[r] == 0xffff ? 0 : ab[r] & 255;
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -716,7 +721,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
         }
 #pragma unroll
         for (int r = 0; r < ROUNDS; ++r) {
-          if (t + r * EPI_THREADS < N_PAIRS) {
+          if (ab[r] != 0xffff) {
             const int a = ab[r] >> 8, b = ab[r] & 255;
             const float tr = g[r][0][0] + g[r][1][1] + g[r][2][2];
 #pragma unroll
