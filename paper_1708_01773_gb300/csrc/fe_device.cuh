@@ -369,16 +369,20 @@ __device__ __forceinline__ double f32_to_f64_exact(float x) {
   return fx_to_double(ng ? -int64_t(m) : int64_t(m), ex - 150);
 }
 
-// FP32 -> FP64 bits for zero and normal numbers (exponent rebias by 1023 - 127
-// = 896 on the shifted exponent/mantissa field); `ok` is cleared for
-// denormals, infinities and NaNs, which take the general path.
-__device__ __forceinline__ double f32_to_f64_fast(float x, bool& ok) {
-  const uint32_t u = __float_as_uint(x);
-  const uint32_t mag = u & 0x7fffffffu;
-  const uint32_t e = mag >> 23;
-  ok = ok && (mag == 0 || (e != 0 && e != 0xffu));
-  const uint64_t body = mag == 0 ? 0ull : ((uint64_t(mag) << 29) + (uint64_t(896) << 52));
-  return __longlong_as_double(static_cast<long long>((uint64_t(u >> 31) << 63) | body));
+// FP32 -> FP64, exact, for zero and normal numbers, in 32-bit integer
+// operations: the high word is the sign, the exponent rebiased by
+// 1023 - 127 = 896 and the top 20 mantissa bits, i.e. sign | ((|x| >> 3) +
+// (896 << 20)); the low word holds the last 3 mantissa bits, |x| << 29.
+__device__ __forceinline__ double f32_to_f64_normal(float x) {
+  const uint32_t u = __float_as_uint(x), mag = u & 0x7fffffffu, sgn = u & 0x80000000u;
+  const uint32_t hw = mag == 0 ? sgn : (sgn | ((mag >> 3) + 0x38000000u));
+  return __hiloint2double(int(hw), int(mag << 29));
+}
+
+// True for zero and FP32-normal x (exponent field 1..254).
+__device__ __forceinline__ bool f32_zero_or_normal(float x) {
+  const uint32_t mag = __float_as_uint(x) & 0x7fffffffu;
+  return mag == 0 || mag - 0x00800000u < 0x7f000000u;
 }
 
 // hi + lo of a double-float accumulator, rounded once to the nearest double:
@@ -387,14 +391,13 @@ __device__ __forceinline__ double f32_to_f64_fast(float x, bool& ok) {
 // warp vote sends the whole warp to the general conversion in the rare case of
 // a denormal part. All 32 lanes of the warp must call it.
 __device__ __forceinline__ double df_to_double(float hi, float lo) {
-  bool ok = true;
-  double dh = f32_to_f64_fast(hi, ok);
-  double dl = f32_to_f64_fast(lo, ok);
-  if (!__all_sync(kFull, ok)) {
-    if (!ok) {
-      dh = f32_to_f64_exact(hi);
-      dl = f32_to_f64_exact(lo);
-    }
+  double dh, dl;
+  if (__all_sync(kFull, f32_zero_or_normal(hi) && f32_zero_or_normal(lo))) {
+    dh = f32_to_f64_normal(hi);
+    dl = f32_to_f64_normal(lo);
+  } else {
+    dh = f32_to_f64_exact(hi);
+    dl = f32_to_f64_exact(lo);
   }
   const double sum = __dadd_rn(dh, dl);
   return lo == 0.f ? dh : sum;

@@ -187,6 +187,19 @@ def test_host_buffer_entry_matches_device_entry():
     hc = torch.tensor(prob.coef).pin_memory()
     feasm.fe_assemble_host(sp.handle, hc, prob.force, hv, hr, feasm.FE_PREC_FP32)
     assert torch.equal(hv, vals.cpu()) and torch.equal(hr, rhs.cpu())
+    # pageable buffers take the staging path: same values
+    pv = torch.full((sp.nnz,), float("nan"), dtype=torch.float64)
+    pr = torch.full((sp.n_dofs,), float("nan"), dtype=torch.float64)
+    feasm.fe_assemble_host(sp.handle, torch.tensor(prob.coef), prob.force, pv, pr, feasm.FE_PREC_FP32)
+    assert torch.equal(pv, vals.cpu()) and torch.equal(pr, rhs.cpu())
+    # pinned values with a pageable RHS, and no RHS at all
+    hv.fill_(float("nan"))
+    pr.fill_(float("nan"))
+    feasm.fe_assemble_host(sp.handle, hc, prob.force, hv, pr, feasm.FE_PREC_FP32)
+    assert torch.equal(hv, vals.cpu()) and torch.equal(pr, rhs.cpu())
+    feasm.fe_assemble_host(sp.handle, hc, prob.force, hv, None, feasm.FE_PREC_FP64)
+    v64, _ = sp.assemble(coef, prec="fp64")
+    assert torch.equal(hv, v64.cpu())
     sp.close()
 
 
