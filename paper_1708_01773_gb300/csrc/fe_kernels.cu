@@ -448,6 +448,7 @@ struct AdjParams {
   const double* w;
   const double* xq;
   const double* dphi;
+  const float* dphi32;
   const int32_t* cell_dofs;
   const double* u;
   const double* coef;
@@ -472,6 +473,62 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjParams p) {
     for (int i = 0; i < 24; ++i) x[i] = p.xv[e * 24 + i];
 #pragma unroll
     for (int k = 0; k < 3; ++k) trilinear_coefficients(x, k, a);
+    if constexpr (std::is_same<T, float>::value) {
+      // FP32 strain, FP64 geometry and sums: the conversions run on the
+      // integer bits, w/det J and the physical gradients in FP32, one FP64
+      // multiply-add per point accumulates w det J times the energy density
+      // (GB300's FP64 pipe is the limit of this kernel).
+      float ue[NL];
+#pragma unroll
+      for (int l = 0; l < NL; ++l) ue[l] = d2f_rn(p.u[p.cell_dofs[e * NL + l]]);
+      const float lh = d2f_rn(p.lam_hat), mh2 = 2.f * d2f_rn(p.mu_hat);
+      for (int q = 0; q < p.nq; ++q) {
+        double cof[9], det;
+        geometry_at(a, p.xq[3 * q], p.xq[3 * q + 1], p.xq[3 * q + 2], cof, &det);
+        if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
+        float gr[NC][3];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) gr[c][0] = gr[c][1] = gr[c][2] = 0.f;
+        const float* dq = p.dphi32 + size_t(q) * NB * 3;
+#pragma unroll 4
+        for (int b = 0; b < NB; ++b) {
+          const float d0 = dq[3 * b], d1 = dq[3 * b + 1], d2 = dq[3 * b + 2];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const float uc = ue[c * NB + b];
+            gr[c][0] = fmaf(uc, d0, gr[c][0]);
+            gr[c][1] = fmaf(uc, d1, gr[c][1]);
+            gr[c][2] = fmaf(uc, d2, gr[c][2]);
+          }
+        }
+        const float rdet = 1.f / d2f_rn(det);
+        float cs[9];
+#pragma unroll
+        for (int t = 0; t < 9; ++t) cs[t] = d2f_rn(cof[t]) * rdet;
+        float gu[NC][3];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+          for (int k = 0; k < 3; ++k) gu[c][k] = gr[c][0] * cs[3 * k] + gr[c][1] * cs[3 * k + 1] + gr[c][2] * cs[3 * k + 2];
+        float dens;
+        if (NC == 1) {
+          dens = gu[0][0] * gu[0][0] + gu[0][1] * gu[0][1] + gu[0][2] * gu[0][2];
+        } else {
+          const float div = gu[0][0] + gu[1 % NC][1] + gu[2 % NC][2];
+          float ee = 0.f;
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+              const float eps = 0.5f * (gu[k % NC][l] + gu[l % NC][k]);
+              ee += eps * eps;
+            }
+          dens = lh * (div * div) + mh2 * ee;
+        }
+        energy = fma(p.w[q] * det, f32_to_f64_exact(dens), energy);
+      }
+      p.g[e] = p.grad_scale * energy;
+    } else {
     T ue[NL];
 #pragma unroll
     for (int l = 0; l < NL; ++l) ue[l] = T(p.u[p.cell_dofs[e * NL + l]]);
@@ -523,6 +580,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(AdjParams p) {
       energy += p.w[q] * det * dens;
     }
     p.g[e] = p.grad_scale * energy;
+    }
   }
   if (p.partials != nullptr) {
     red[threadIdx.x] = (e < p.n_cells) ? p.coef[e] * energy : 0.0;
@@ -568,6 +626,7 @@ cudaError_t launch_adjoint(const fe_space* s, const double* u, const double* coe
   prm.w = s->d_w;
   prm.xq = s->d_xq;
   prm.dphi = s->d_dphi;
+  prm.dphi32 = s->d_dphi32;
   prm.cell_dofs = s->d_cell_dofs;
   prm.u = u;
   prm.coef = coef;
@@ -607,6 +666,7 @@ cudaError_t launch_adjoint_with_scratch(const fe_space* s, const double* u, cons
   prm.w = s->d_w;
   prm.xq = s->d_xq;
   prm.dphi = s->d_dphi;
+  prm.dphi32 = s->d_dphi32;
   prm.cell_dofs = s->d_cell_dofs;
   prm.u = u;
   prm.coef = coef;
