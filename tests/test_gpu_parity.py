@@ -271,6 +271,8 @@ def test_adjoint_cantilever_full_size_fd_and_oracle():
                          prob.coef[cells], prob.force)
     g_o = oracle.cell_energies(sub, u, cd[cells])
     assert vec_error(g[cells], g_o) <= 1e-12
+    g32 = sp.adjoint(ut, None, 1.0, prec="fp32").cpu().numpy()   # FP32 strain, FP64 geometry and sums
+    assert vec_error(g32[cells], g_o) <= 1e-5
     # Euler identity for a functional linear in E
     assert abs(float(c) - float((E.detach() * E.grad).sum())) <= 1e-12 * abs(float(c))
     # central differences of the compliance computed on the GPU
