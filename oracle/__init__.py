@@ -6,7 +6,8 @@ the two share no code: the oracle is the plain C file ``fe_oracle.c`` compiled
 with gcc and reached through ctypes.
 
 Each wrapper names the passage of the FEMPAR paper it follows (see the header of
-``fe_oracle.c``).
+``fe_oracle.c``). The strong Dirichlet split (``dirichlet_labels``,
+``dirichlet_reduce``) is plain numpy on top of the assembled matrix.
 """
 from __future__ import annotations
 
@@ -178,3 +179,60 @@ def cell_energies(prob, u, cell_dofs):
     if rc:
         raise ValueError(f"or_cell_energies -> {rc}")
     return g
+
+
+# ----------------------------------------------------------------------------- strong Dirichlet conditions
+def dirichlet_labels(fixed):
+    """Free/fixed split of the DOFs (Sect. "Strong imposition of boundary
+    conditions"): free DOFs get the ids 0, 1, ... and fixed DOFs -1, -2, ...,
+    each set in ascending global id (the paper labels them 1..n_free and
+    -1..-n_fixed). Returns int64 labels [n_dofs]."""
+    fixed = np.asarray(fixed).astype(bool)
+    lab = np.empty(fixed.size, dtype=np.int64)
+    lab[~fixed] = np.arange(int((~fixed).sum()))
+    lab[fixed] = -1 - np.arange(int(fixed.sum()))
+    return lab
+
+
+def dirichlet_reduce(row_ptr, col, val, rhs, fixed, u_fixed, rows=None):
+    """The constrained system of Eq. dirichlet_bc_discrete_problem, from the
+    assembled matrix A and vector f of the whole space:
+        sum_{b free} A_ab u_b = f_a - sum_{c fixed} A_ac u^D_c   for every free a.
+    Rows and columns of fixed DOFs are dropped; the remaining ones are renumbered
+    by ``dirichlet_labels``; each fixed column moves to the right-hand side times
+    its prescribed value u_fixed[fixed id].
+
+    (row_ptr, col, val, rhs) hold the rows ``rows`` of A and f (default: every
+    row, in order); those rows must all be free. Returns the constrained rows as
+    (row_ptr, col, val, rhs), columns ascending."""
+    lab = dirichlet_labels(fixed)
+    row_ptr = np.asarray(row_ptr, dtype=np.int64)
+    col = np.asarray(col, dtype=np.int64)
+    val = np.asarray(val, dtype=np.float64)
+    n_rows = row_ptr.size - 1
+    if rows is None:                       # the whole matrix: drop the fixed rows
+        if n_rows != lab.size:
+            raise ValueError("dirichlet_reduce: matrix and mask sizes differ")
+        keep_rows = lab >= 0
+    else:                                  # a block of free rows: keep them all
+        rows = np.asarray(rows, dtype=np.int64)
+        if rows.size != n_rows or (rows.size and lab[rows].min() < 0):
+            raise ValueError("dirichlet_reduce: the block's rows must be free DOFs")
+        keep_rows = np.ones(n_rows, dtype=bool)
+    u_fixed = np.asarray(u_fixed, dtype=np.float64)
+    row_of = np.repeat(np.arange(n_rows), np.diff(row_ptr))
+    free_col = lab[col] >= 0
+    # matrix: the free x free block, renumbered
+    kept = free_col & keep_rows[row_of]
+    out_ptr = np.zeros(int(keep_rows.sum()) + 1, dtype=np.int64)
+    new_row = np.cumsum(keep_rows) - 1
+    np.add.at(out_ptr, new_row[row_of[kept]] + 1, 1)
+    out_ptr = np.cumsum(out_ptr)
+    out_col = lab[col[kept]]
+    out_val = val[kept]
+    # right-hand side: f_a minus the fixed columns times the prescribed values
+    lift = np.zeros(n_rows)
+    fx = ~free_col
+    np.add.at(lift, row_of[fx], val[fx] * u_fixed[-1 - lab[col[fx]]])
+    out_rhs = (np.asarray(rhs, dtype=np.float64) - lift)[keep_rows]
+    return out_ptr, out_col.astype(np.int32), out_val, out_rhs

@@ -486,3 +486,113 @@ def test_workload_meshes_valid_and_patterns():
     assert n == 3 * 17 ** 3
     pc = inputs.cantilever_q1_64(n=16)
     assert oracle.min_det_jacobian(pc.mesh, 2) > 0
+
+
+# ---------------------------------------------------------------- strong Dirichlet conditions
+def test_dirichlet_hand_example():
+    """Eq. dirichlet_bc_discrete_problem on a 3x3 system worked by hand: fixing DOF 1
+    at 2 leaves rows/columns {0, 2}, and each right-hand side loses A_a1 * 2."""
+    rp = np.array([0, 3, 6, 9])
+    col = np.array([0, 1, 2] * 3)
+    val = np.array([4.0, -1.0, 0.5, -1.0, 4.0, -1.0, 0.5, -1.0, 4.0])
+    f = np.array([1.0, 10.0, 3.0])
+    lab = oracle.dirichlet_labels([0, 1, 0])
+    assert lab.tolist() == [0, -1, 1]
+    ptr, c, v, b = oracle.dirichlet_reduce(rp, col, val, f, [0, 1, 0], [2.0])
+    assert ptr.tolist() == [0, 2, 4] and c.tolist() == [0, 1, 0, 1]
+    assert v.tolist() == [4.0, 0.5, 0.5, 4.0]
+    assert b.tolist() == [1.0 + 2.0, 3.0 + 2.0]
+    # two fixed DOFs, labelled -1, -2 in ascending global id
+    ptr, c, v, b = oracle.dirichlet_reduce(rp, col, val, f, [1, 0, 1], [3.0, -5.0])
+    assert oracle.dirichlet_labels([1, 0, 1]).tolist() == [-1, 0, -2]
+    assert ptr.tolist() == [0, 1] and c.tolist() == [0] and v.tolist() == [4.0]
+    assert b.tolist() == [10.0 - (-1.0 * 3.0) - (-1.0 * -5.0)]
+
+
+def test_dirichlet_nothing_fixed_is_identity():
+    prob = inputs.small_problem((2, 2, 1), 2, 1, seed=61)
+    cd, n, rp, col, val, rhs = assembled(prob)
+    ptr, c, v, b = oracle.dirichlet_reduce(rp, col, val, rhs, np.zeros(n, bool), np.zeros(0))
+    np.testing.assert_array_equal(ptr, rp)
+    np.testing.assert_array_equal(c, col)
+    np.testing.assert_array_equal(v, val)
+    np.testing.assert_array_equal(b, rhs)
+
+
+@pytest.mark.parametrize("p,problem", [(1, 0), (2, 1), (3, 0)])
+def test_dirichlet_single_cell_brute_force(p, problem):
+    """One distorted cell: the constrained system equals the cell matrix restricted to
+    the free local DOFs, with K_free,fixed u^D moved to the right-hand side (taken
+    directly from the oracle's cell matrix and the cell's DOF map with numpy)."""
+    rng = np.random.default_rng(70 + p)
+    xv = inputs.brick(1, 1, 1).coords + rng.uniform(-0.12, 0.12, size=(8, 3))
+    mesh = inputs.Mesh(xv, np.arange(8, dtype=np.int32)[None, :])
+    ncomp = 3 if problem == 1 else 1
+    force = np.array([0.3, -0.2, 1.0]) if problem == 1 else np.array([1.5])
+    prob = inputs.Problem("one", mesh, p, p + 1, problem, np.array([2.5]), force)
+    cd, n, rp, col, val, rhs = assembled(prob)
+    K, fe = oracle.cell_matrix(problem, p, p + 1, xv, 2.5, NU, force)
+    fixed = rng.uniform(size=n) < 0.6
+    fixed[0] = False
+    uD = rng.standard_normal(int(fixed.sum()))
+    ptr, c, v, b = oracle.dirichlet_reduce(rp, col, val, rhs, fixed, uD)
+    g = np.empty(n, dtype=np.int64)
+    g[cd[0]] = np.arange(n)                 # global DOF -> local index in the cell
+    fr, fx = np.flatnonzero(~fixed), np.flatnonzero(fixed)
+    A_ff = K[np.ix_(g[fr], g[fr])]
+    b_ref = fe[g[fr]] - K[np.ix_(g[fr], g[fx])] @ uD
+    A = csr_to_dense(ptr, c, v, fr.size)
+    np.testing.assert_allclose(A, A_ff, rtol=0, atol=1e-14 * np.abs(K).max())
+    np.testing.assert_allclose(b, b_ref, rtol=0, atol=1e-13 * (np.abs(K).max() * np.abs(uD).sum() + 1))
+    assert ncomp * (p + 1) ** 3 == n
+
+
+@pytest.mark.parametrize("p,shape", [(1, (3, 3, 3)), (2, (3, 2, 2)), (3, (2, 2, 2))])
+def test_dirichlet_poisson_patch_reproduces_linear_data(p, shape):
+    """Patch test through the constrained system: u^D = g linear on the whole boundary,
+    f = 0, constant conductivity. g lies in the trial space (trilinear map, Q_p with p >= 1) and the (p+1)^3
+    Gauss rule integrates a(g, v) exactly, so the free values solving Eq.
+    dirichlet_bc_discrete_problem are g at the free nodes."""
+    prob = inputs.small_problem(shape, p, 0, seed=80 + p)
+    prob.force[:] = 0.0
+    prob.coef[:] = 2.0                      # a linear field has zero flux jumps only for constant kappa
+    cd, n, rp, col, val, rhs = assembled(prob)
+    pos, comp = node_positions(prob, cd, n)
+    fixed = boundary_dofs(pos)
+    g = pos @ np.array([1.3, -0.4, 2.2]) - 0.7
+    ptr, c, v, b = oracle.dirichlet_reduce(rp, col, val, rhs, fixed, g[fixed])
+    u = np.linalg.solve(csr_to_dense(ptr, c, v, int((~fixed).sum())), b)
+    np.testing.assert_allclose(u, g[~fixed], rtol=0, atol=1e-11 * np.abs(g).max())
+
+
+@pytest.mark.parametrize("p,shape", [(1, (3, 2, 3)), (2, (2, 2, 2))])
+def test_dirichlet_elasticity_patch_reproduces_linear_field(p, shape):
+    """A linear displacement x -> B x + t prescribed on the boundary with zero body
+    force has constant stress, so it solves the constrained elasticity system."""
+    prob = inputs.small_problem(shape, p, 1, seed=90 + p)
+    prob.force[:] = 0.0
+    prob.coef[:] = 3.0                      # constant E: the stress is constant across cells
+    cd, n, rp, col, val, rhs = assembled(prob)
+    pos, comp = node_positions(prob, cd, n)
+    fixed = boundary_dofs(pos)
+    B = np.array([[0.2, -0.3, 0.1], [0.4, 0.05, -0.2], [-0.1, 0.3, 0.25]])
+    disp = pos @ B.T + np.array([0.1, -0.2, 0.3])
+    g = disp[np.arange(n), comp]
+    ptr, c, v, b = oracle.dirichlet_reduce(rp, col, val, rhs, fixed, g[fixed])
+    u = np.linalg.solve(csr_to_dense(ptr, c, v, int((~fixed).sum())), b)
+    np.testing.assert_allclose(u, g[~fixed], rtol=0, atol=1e-10 * np.abs(g).max())
+
+
+def test_dirichlet_clamped_beam_is_spd_and_homogeneous_keeps_f():
+    """Clamping the x = 0 face removes the six rigid modes: the constrained matrix is
+    symmetric positive definite; with u^D = 0 the right-hand side is f on the free rows."""
+    prob = inputs.small_problem((4, 1, 1), 2, 1, seed=95, extent=(4.0, 1.0, 1.0))
+    cd, n, rp, col, val, rhs = assembled(prob)
+    pos, comp = node_positions(prob, cd, n)
+    fixed = np.abs(pos[:, 0]) < 1e-12
+    assert fixed.sum() == 3 * 9
+    ptr, c, v, b = oracle.dirichlet_reduce(rp, col, val, rhs, fixed, np.zeros(int(fixed.sum())))
+    A = csr_to_dense(ptr, c, v, int((~fixed).sum()))
+    assert np.abs(A - A.T).max() < 1e-15 * np.abs(A).max()
+    assert np.linalg.eigvalsh(A).min() > 0
+    np.testing.assert_array_equal(b, rhs[~fixed])
