@@ -286,12 +286,55 @@ def split_kernels(sp, coef, force, vals, rhs, prec, stream, n=5):
     return {"cell_ms": cell, "scatter_ms": scat}
 
 
-def extra_workloads(args, dev, stream):
-    """Secondary measurements: the scatter-bound 128^3 Q1 elasticity assembly, the
-    64^3 Q1 cantilever compliance adjoint and (optionally) the batched assembly."""
+def clamped_beam(dev, stream):
+    """The Q2 beam with its x = 0 face clamped to a prescribed linear displacement
+    (strong Dirichlet conditions): fe_assemble_dirichlet against fe_assemble on the
+    same space, and the algorithmic bytes of the constrained scatter."""
     import torch
     from paper_1708_01773_gb300 import feasm, inputs
-    out = {}
+    prob = inputs.elasticity_q2_beam()
+    sp = feasm.FESpace(prob)
+    pos = sp.dof_points()
+    fixed = np.abs(pos[:, 0]) < 1e-12
+    comp = np.arange(sp.n_dofs) % 3
+    disp = np.stack([0.01 * pos[:, 1], -0.02 * pos[:, 2], 0.03 * (pos[:, 1] - 0.5)], axis=1)
+    dsys = sp.dirichlet(fixed)
+    coef = torch.tensor(prob.coef, device=dev)
+    uD = torch.tensor(disp[fixed, comp[fixed]], device=dev)
+    vals = torch.empty(dsys.nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(dsys.n_free, dtype=torch.float64, device=dev)
+    vals_u = torch.empty(sp.nnz, dtype=torch.float64, device=dev)
+    rhs_u = torch.empty(sp.n_dofs, dtype=torch.float64, device=dev)
+    cd = sp.cell_dofs()
+    free_inc = int((~fixed[cd]).sum())          # (cell, local DOF) incidences of free rows
+    rec = {}
+    for prec in ("fp32", "fp64"):
+        pr = feasm.PRECISIONS[prec]
+        ms = time_events(lambda: feasm.fe_assemble_dirichlet(dsys.handle, coef, prob.force, uD, vals, rhs, pr,
+                                                             stream), 20, stream)
+        ms_u = time_events(lambda: feasm.fe_assemble(sp.handle, coef, prob.force, vals_u, rhs_u, pr, stream),
+                           20, stream)
+        split = split_kernels(sp, coef, prob.force, vals_u, rhs_u, prec, stream)
+        tk = 8 if prec == "fp64" else 4
+        sbytes = (free_inc * sp.nl * (tk + 2) + dsys.nnz * 8 + free_inc * (4 + 8) + (dsys.n_free + 1) * 24
+                  + dsys.n_free * 8)
+        rec[prec] = {"ms_per_step": ms, "cells_per_s": sp.n_cells / (ms / 1e3), "nnz_per_s": dsys.nnz / (ms / 1e3),
+                     "unconstrained_ms_per_step": ms_u, "cell_ms": split["cell_ms"],
+                     "lift_and_scatter_ms": ms - split["cell_ms"], "scatter_algorithmic_bytes": int(sbytes)}
+    torch.cuda.synchronize()
+    out = {"cells": sp.n_cells, "n_free": dsys.n_free, "n_fixed": dsys.n_fixed, "nnz": dsys.nnz, **rec}
+    dsys.close()
+    sp.close()
+    return out
+
+
+def extra_workloads(args, dev, stream):
+    """Secondary measurements: the clamped Q2 beam (strong Dirichlet conditions), the
+    scatter-bound 128^3 Q1 elasticity assembly, the 64^3 Q1 cantilever compliance
+    adjoint and (optionally) the batched assembly."""
+    import torch
+    from paper_1708_01773_gb300 import feasm, inputs
+    out = {"elasticity_q2_beam_clamped": clamped_beam(dev, stream)}
     prob = inputs.elasticity_q1_128()
     sp = feasm.FESpace(prob)
     coef = torch.tensor(prob.coef, device=dev)

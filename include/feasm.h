@@ -15,6 +15,11 @@
  *     time and freed by the matching destroy.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream). Compute calls
  *     are asynchronous on it and allocate nothing.
+ *   - Compute calls on one space (fe_assemble*, and fe_assemble_dirichlet on
+ *     its constrained systems) must not overlap on the GPU: they share the
+ *     space's cell-matrix scratch and the scatter's work counters (which the
+ *     scatter leaves at zero when it completes). Issue them on one stream, or
+ *     order them with events.
  *   - Errors found on the device (a non-positive Jacobian determinant, a
  *     persistent-kernel wait that gave up) are recorded in a device error word
  *     and reported by fe_status(); kernels never trap.
@@ -235,6 +240,86 @@ int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const doub
                       double* const* csr_values, double* const* rhs, fe_precision prec, void* stream);
 
 void fe_batch_destroy(fe_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Strong Dirichlet conditions (paper, Sect. "Strong imposition of boundary
+ * conditions", Eq. dirichlet_bc_discrete_problem). The DOFs of a space split
+ * into free and fixed ones; the constrained system keeps the rows and columns
+ * of the free DOFs only,
+ *   sum_{b free} A_ab u_b = f_a - sum_{c fixed} A_ac u^D_c   (a free),
+ * and its right-hand side carries the prescribed values u^D of the fixed DOFs.
+ * Free DOFs are numbered 0 .. n_free-1 and fixed DOFs 0 .. n_fixed-1, each in
+ * ascending global DOF id (the paper's labels 1..n_free and -1..-n_fixed).
+ * ------------------------------------------------------------------------ */
+typedef struct fe_dirichlet fe_dirichlet; /* opaque, library-owned */
+
+/* Physical position of every DOF's node (host [n_dofs*3]): the node's
+ * reference point alpha/p mapped by the cell's trilinear map (the DOFs of the
+ * ncomp components of one node share it). `mesh` must be the mesh the space
+ * was created from (same sizes; host pointers). Serves the choice of fixed
+ * DOFs by position. Works on host-only spaces. Errors: FE_ERR_INVALID_ARG. */
+int fe_space_dof_points_host(const fe_space* s, const fe_mesh_desc* mesh, double* points);
+
+/* Builds the constrained system of space `s`: the free/fixed labels, the
+ * sparsity pattern of the free x free block (columns ascending) and its
+ * assembly permutation, and the list of cells that carry both fixed and free
+ * DOFs (where the right-hand side is lifted).
+ *   fixed  host [n_dofs] uint8 in the space's global numbering: nonzero marks a
+ *          fixed DOF; copied.
+ * Works on host-only spaces (inspection only). The space must outlive the
+ * object and is shared with it: fe_assemble and fe_assemble_dirichlet on one
+ * space must not overlap on the GPU. Errors: FE_ERR_INVALID_ARG,
+ * FE_ERR_UNSUPPORTED, FE_ERR_OOM, FE_ERR_CUDA. */
+int fe_dirichlet_create(fe_space* s, const uint8_t* fixed, fe_dirichlet** out);
+
+/* Numbers of free and fixed DOFs and nonzeros of the constrained matrix. Any
+ * pointer may be NULL. */
+int fe_dirichlet_sizes(const fe_dirichlet* d, int64_t* n_free, int64_t* n_fixed, int64_t* nnz);
+
+/* Host [n_dofs] int32 labels: the free id (>= 0) of a free DOF, or -1 - its
+ * fixed id for a fixed DOF. */
+int fe_dirichlet_labels_host(const fe_dirichlet* d, int32_t* labels);
+
+/* CSR pattern of the constrained matrix: row_ptr [n_free+1] int64, col_idx
+ * [nnz] int32 (free ids). _host: host pointers; plain: device pointers, copied
+ * asynchronously on `stream`. */
+int fe_dirichlet_csr_pattern_host(const fe_dirichlet* d, int64_t* row_ptr, int32_t* col_idx);
+int fe_dirichlet_csr_pattern(const fe_dirichlet* d, int64_t* row_ptr, int32_t* col_idx, void* stream);
+
+/* Assembly permutation of the constrained system of a host-only space (host
+ * pointers), in the layout of fe_space_permutation_host with rows = free DOFs:
+ * cnt [nnz]; code_ptr [n_free+1]; codes (may be NULL) hold ncode[r] codes per
+ * row, those of fixed columns left out; ncode [n_free] int32; pos (may be
+ * NULL) [code_ptr[n_free]] the slot-major positions, where an entry (s, m) of
+ * a fixed column holds the index of the reading lane's private dummy
+ * accumulator, acc_stride + (m mod 32), acc_stride being the largest row
+ * length rounded up to a multiple of 4; slot_ptr [n_free+1]; slots. */
+int fe_dirichlet_permutation_host(const fe_dirichlet* d, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
+                                  int32_t* ncode, uint16_t* pos, int64_t* slot_ptr, int32_t* slots);
+
+/* Lifting lists (host): n_cells cells carrying fixed and free DOFs, ascending
+ * (cells [n_cells]); the fixed local columns of cells[i] are m[ptr[i] ..
+ * ptr[i+1]) (ascending) with fixed ids fix[...]. Array pointers may be NULL
+ * (call once with them NULL to learn n_cells and n_entries). */
+int fe_dirichlet_lift_host(const fe_dirichlet* d, int64_t* n_cells, int64_t* n_entries, int32_t* cells,
+                           int32_t* ptr, uint8_t* m, int32_t* fix);
+
+/* Integrates every cell and assembles the constrained system (Eq.
+ * dirichlet_bc_discrete_problem): the cell matrices and vectors as in
+ * fe_assemble, then for each listed cell the lifting
+ *   f^K_a -= sum_{fixed local columns m} A^K_am u^D_m  (every local row a;
+ *   FP64 products of the stored cell-matrix entries, summed in a fixed order),
+ * then the scatter of the free rows and columns.
+ *   coefficients, body_force, prec  as for fe_assemble.
+ *   u_fixed     device [n_fixed] FP64 prescribed values, or NULL for u^D = 0.
+ *   csr_values  device [nnz] FP64, overwritten (fe_dirichlet_csr_pattern).
+ *   rhs         device [n_free] FP64, overwritten; may be NULL.
+ * Deterministic like fe_assemble. */
+int fe_assemble_dirichlet(fe_dirichlet* d, const double* coefficients, const double* body_force,
+                          const double* u_fixed, double* csr_values, double* rhs, fe_precision prec, void* stream);
+
+/* Frees the constrained system (before its space). */
+void fe_dirichlet_destroy(fe_dirichlet* d);
 
 #ifdef __cplusplus
 }

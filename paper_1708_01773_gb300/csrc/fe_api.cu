@@ -42,7 +42,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 void free_device(fe_space* s) {
   void* ptrs[] = {s->d_xv, s->d_w, s->d_xq, s->d_phi, s->d_dphi, s->d_dphi32, s->d_phi2, s->d_cell_dofs, s->d_row_ptr,
                   s->d_col, s->d_cnt, s->d_code_ptr, s->d_codes, s->d_pos, s->d_slot_ptr, s->d_slots, s->d_ke, s->d_fe,
-                  s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs};
+                  s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs, s->d_sched};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -134,6 +134,8 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     if (e == cudaSuccess && s->n_cells) e = cudaMalloc(&s->d_fe, size_t(s->n_cells) * s->nl * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&s->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(s->d_err, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_sched, 2 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s->d_sched, 0, 2 * sizeof(unsigned long long));
     s->n_partials = int((s->n_cells + 127) / 128) + 1;
     if (e == cudaSuccess) e = cudaMalloc(&s->d_partials, size_t(s->n_partials) * sizeof(double));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
@@ -157,6 +159,17 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
 
 namespace feasm {
 int set_error(int code, const char* msg) { return fail(code, msg); }
+
+int cell_stage(fe_space* s, const double* coef, const double force[3], fe_precision prec, cudaStream_t st) {
+  const bool tc = cell_tc_applicable(s, prec) && s->cell_kernel != FE_KERNEL_CUDA_CORE;
+  if (s->cell_kernel == FE_KERNEL_TENSOR_CORE && !tc)
+    return fail(FE_ERR_UNSUPPORTED, "no tensor-core cell kernel for this order / problem / precision");
+  if (tc)
+    FE_CUDA(launch_cell_tc(s, coef, force, prec, st));
+  else
+    FE_CUDA(launch_cell_integration(s, coef, force, prec, st));
+  return FE_OK;
+}
 }  // namespace feasm
 
 extern "C" {
@@ -241,13 +254,7 @@ int fe_assemble_ex(fe_space* s, const double* coefficients, const double* body_f
   if (body_force)
     for (int k = 0; k < s->ncomp; ++k) f[k] = body_force[k];
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const bool tc = feasm::cell_tc_applicable(s, prec) && s->cell_kernel != FE_KERNEL_CUDA_CORE;
-  if (s->cell_kernel == FE_KERNEL_TENSOR_CORE && !tc)
-    return fail(FE_ERR_UNSUPPORTED, "no tensor-core cell kernel for this order / problem / precision");
-  if (tc)
-    FE_CUDA(feasm::launch_cell_tc(s, coefficients, f, prec, st));
-  else
-    FE_CUDA(feasm::launch_cell_integration(s, coefficients, f, prec, st));
+  if (int rc = feasm::cell_stage(s, coefficients, f, prec, st)) return rc;
   if (event_mid) FE_CUDA(cudaEventRecord(static_cast<cudaEvent_t>(event_mid), st));
   FE_CUDA(feasm::launch_scatter(s, prec, csr_values, rhs, st));
   return FE_OK;

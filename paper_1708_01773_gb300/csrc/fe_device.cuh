@@ -16,6 +16,8 @@ constexpr int kCellThreads = 256;
 constexpr int kScatterWarps = 8;
 
 
+
+
 struct CellParams {
   int64_t n_cells;
   int nq, cpb, qblock, nq1d;
@@ -347,6 +349,8 @@ struct ScatterParams {
   const uint16_t* pos;
   const int64_t* slot_ptr;
   const int32_t* slots;
+  const int32_t* ncode;  // codes per row (constrained patterns), or nullptr: slots * nl
+  unsigned long long* sched;  // [2] item counters of the dynamic schedule, zero between launches
   const void* ke;
   const double* fe;
   double* values;
@@ -355,6 +359,55 @@ struct ScatterParams {
 };
 
 constexpr unsigned kFull = 0xffffffffu;
+
+// Dynamic assignment of work items (CSR rows, or the rows of one node) to the
+// warps of a scatter launch. A warp takes `grab` consecutive items at a time
+// from a counter in device memory (one atomicAdd by lane 0) and holds its next
+// grab in reserve, so that the atomic's latency hides behind the current
+// items. Rows differ in cost (a node lies in 1, 2, 4 or 8 cells, in a pattern
+// that repeats every few tens of rows and shifts wherever rows are dropped);
+// any static cyclic schedule lets that pattern line up with the warp index
+// for some meshes and warp counts, so that a few warps collect the expensive
+// rows. Taking items on demand balances the warps to within one grab, while
+// the items in flight still form one contiguous window of rows. Every warp
+// calls finish() once at the end; the last one resets both counters (next
+// item, finished warps) to zero for the next launch on the stream.
+struct ItemStream {
+  unsigned long long* ctr;
+  int64_t n, u, end, nxt;
+  int grab;
+  __device__ __forceinline__ int64_t take(int lane) const {
+    unsigned long long b = 0;
+    if (lane == 0) b = atomicAdd(ctr, static_cast<unsigned long long>(grab));
+    return static_cast<int64_t>(__shfl_sync(kFull, b, 0));
+  }
+  __device__ __forceinline__ ItemStream(unsigned long long* c, int64_t n_items, int grab_size, int lane)
+      : ctr(c), n(n_items), grab(grab_size) {
+    u = take(lane);
+    end = u + grab < n ? u + grab : n;
+    nxt = take(lane);
+  }
+  __device__ __forceinline__ bool valid() const { return u < n; }
+  // the item after the current one (>= n: no more); takes a new reserve grab when needed
+  __device__ __forceinline__ void advance(int lane) {
+    if (u + 1 < end) {
+      ++u;
+    } else {
+      u = nxt;
+      end = u + grab < n ? u + grab : n;
+      nxt = u < n ? take(lane) : u;
+    }
+  }
+  __device__ __forceinline__ void finish(int64_t n_warps, int lane) const {
+    if (lane == 0) {
+      __threadfence();
+      if (atomicAdd(ctr + 1, 1ull) == static_cast<unsigned long long>(n_warps - 1)) {
+        atomicExch(ctr, 0ull);
+        atomicExch(ctr + 1, 0ull);
+      }
+    }
+  }
+};
 
 
 // Exact FP32 -> FP64 conversion of any finite float on the integer bits

@@ -40,12 +40,21 @@ struct HostSetup {
                                     // bit 15 set on the first contribution of each nonzero
   std::vector<int64_t> slot_ptr;    // [n_dofs+1]
   std::vector<int32_t> slots;       // [n_cells*nl] e*nl + local row, cells ascending
+  std::vector<int32_t> ncode;       // [n_dofs] codes of each row (constrained patterns only; empty: ns * nl)
+  bool pos_ok = true;               // the positions of dropped columns fit the 15-bit dummy index
 };
 
 void build_ref_tables(int p, int nq1d, RefTables* t);
 // Returns 0 or an FE_ERR_* code (message in *err).
 int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
                      HostSetup* hs, std::string* err);
+// Sparsity pattern and assembly permutation from a cell-to-DOF map. With
+// label == nullptr the rows and columns are the DOFs themselves (n_rows =
+// n_dofs); otherwise DOF d is row/column label[d] if label[d] >= 0 and is
+// dropped if label[d] < 0 (a fixed DOF), n_rows being the number of kept DOFs.
+// Fills everything in *hs except cell_dofs.
+int build_pattern(int p, int ncomp, int64_t n_cells, const int32_t* cell_dofs, const int32_t* label,
+                  int64_t n_rows, HostSetup* hs, std::string* err);
 
 }  // namespace feasm
 
@@ -79,6 +88,7 @@ struct fe_space {
   void* d_ke = nullptr;          // cell matrices, [n_cells][nl][nlp] FP64 or FP32
   double* d_fe = nullptr;        // cell vectors [n_cells][nl]
   int* d_err = nullptr;          // device error word
+  unsigned long long* d_sched = nullptr;  // [2] scatter schedule counters (zero between launches)
   double* d_partials = nullptr;  // reduction scratch for the compliance
   int n_partials = 0;
   // staging buffers of fe_assemble_host

@@ -127,8 +127,9 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter(ScatterParams p)
   __shared__ int64_t sbase[kScatterWarps][kMaxSlots + 1];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const TK* ke = reinterpret_cast<const TK*>(p.ke);
-  for (int64_t r = int64_t(blockIdx.x) * kScatterWarps + warp; r < p.n_rows;
-       r += int64_t(gridDim.x) * kScatterWarps) {
+  ItemStream items(p.sched, p.n_rows, 1, lane);
+  for (; items.valid(); items.advance(lane)) {
+    const int64_t r = items.u;
     const int64_t s0 = p.slot_ptr[r];
     const int ns = int(p.slot_ptr[r + 1] - s0);
     for (int s = lane; s < ns; s += 32) sbase[warp][s] = int64_t(p.slots[s0 + s]) * p.nlp;
@@ -158,6 +159,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter(ScatterParams p)
     }
     __syncwarp();
   }
+  items.finish(int64_t(gridDim.x) * kScatterWarps, lane);
 }
 
 template <typename TK>
@@ -171,13 +173,14 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
   const int vper = p.nlp * int(sizeof(TK)) / 16;  // 16-byte vectors per cell-matrix row
   const uint4* ke4 = reinterpret_cast<const uint4*>(p.ke);
   const unsigned lt_mask = (1u << lane) - 1u;
-  for (int64_t r = int64_t(blockIdx.x) * kScatterWarps + warp; r < p.n_rows;
-       r += int64_t(gridDim.x) * kScatterWarps) {
+  ItemStream items(p.sched, p.n_rows, 1, lane);
+  for (; items.valid(); items.advance(lane)) {
+    const int64_t r = items.u;
     const int64_t s0 = p.slot_ptr[r];
     const int ns = int(p.slot_ptr[r + 1] - s0);
     const int64_t k0 = p.row_ptr[r];
     const int64_t c0 = p.code_ptr[r];
-    const int nc = ns * p.nl;
+    const int nc = p.ncode ? p.ncode[r] : ns * p.nl;
     const int my_slot = lane < ns ? p.slots[s0 + lane] : 0;
     const uint4* c4 = reinterpret_cast<const uint4*>(p.codes + c0);
     const int nc8 = (nc + 7) >> 3;
@@ -223,6 +226,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
     }
     __syncwarp();
   }
+  items.finish(int64_t(gridDim.x) * kScatterWarps, lane);
 }
 
 // Slot-wise scatter for FP32 cell matrices (the FP32 and BF16 forms). One warp
@@ -244,10 +248,12 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 // for those reads). Slots are processed in batches of 8, 4, 2 or 1 (the
 // largest that fits the slots left and the register budget), all loads of a
 // batch issued before its additions; the item descriptors (pointers, slot ids)
-// of the warp's next item are fetched while the current one is reduced. The
-// RHS entries are formed every 32 items for the warp's next 32 items, one
-// item per lane (exact fixed-point sum of its cells' FP64 cell-vector
-// entries).
+// of the warp's next item are fetched while the current one is reduced. Items
+// go to warps on demand, kSlotGrab at a time (ItemStream). The RHS entries are
+// formed first, in a static pass of 32 consecutive items per warp, one item per
+// lane (exact fixed-point sum of its cells' FP64 cell-vector entries).
+constexpr int kSlotGrab = 4;  // items per grab of k_scatter_slots
+
 template <int NL, int R, bool IDX32>
 __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5) : 4) k_scatter_slots(ScatterParams p) {
   using S = SlotScatter<NL, R>;
@@ -259,23 +265,12 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
   const float* ke = reinterpret_cast<const float*>(p.ke) + lane;
   const bool want_rhs = p.rhs != nullptr;
   const int64_t n_items = p.n_rows / R;
-  const int64_t stride = int64_t(gridDim.x) * kScatterWarps;
-  int64_t u = int64_t(blockIdx.x) * kScatterWarps + warp;
-  int64_t s0 = 0, k0 = 0, c0 = 0;
-  int ns = 0, nnz = 0, my_slot = 0;
-  int64_t rhs_u = u;  // first item of this warp whose RHS entries are not formed yet
-  if (u < n_items) {
-    const int64_t r = u * R;
-    s0 = p.slot_ptr[r];
-    ns = int(p.slot_ptr[r + 1] - s0);
-    k0 = p.row_ptr[r];
-    nnz = int(p.row_ptr[r + 1] - k0);
-    c0 = p.code_ptr[r];
-    my_slot = lane < ns ? p.slots[s0 + lane] : 0;
-  }
-  for (; u < n_items; u += stride) {
-    if (want_rhs && u == rhs_u) {
-      const int64_t uu = u + int64_t(lane) * stride;
+  const int64_t n_warps = int64_t(gridDim.x) * kScatterWarps;
+  ItemStream items(p.sched, n_items, kSlotGrab, lane);
+  if (want_rhs) {
+    // RHS entries first, statically: 32 consecutive items per warp pass, one per lane
+    for (int64_t ub = (int64_t(blockIdx.x) * kScatterWarps + warp) * 32; ub < n_items; ub += n_warps * 32) {
+      const int64_t uu = ub + lane;
       if (uu < n_items) {
         const int64_t ss = p.slot_ptr[uu * R];
         const int nss = int(p.slot_ptr[uu * R + 1] - ss);
@@ -297,10 +292,24 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
             p.rhs[uu * R + i] = fx_sum<double>(nss, [&](int t) { return p.fe[p.slots[ss + t] + i * S::NBR]; });
         }
       }
-      rhs_u += 32 * stride;
     }
+  }
+  int64_t u = items.u;
+  int64_t s0 = 0, k0 = 0, c0 = 0;
+  int ns = 0, nnz = 0, my_slot = 0;
+  if (u < n_items) {
+    const int64_t r = u * R;
+    s0 = p.slot_ptr[r];
+    ns = int(p.slot_ptr[r + 1] - s0);
+    k0 = p.row_ptr[r];
+    nnz = int(p.row_ptr[r + 1] - k0);
+    c0 = p.code_ptr[r];
+    my_slot = lane < ns ? p.slots[s0 + lane] : 0;
+  }
+  while (u < n_items) {
     // first-level descriptors of the next item (independent loads)
-    const int64_t un = u + stride, rn = un * R;
+    items.advance(lane);
+    const int64_t un = items.u, rn = un * R;
     int64_t s0n = 0, s1n = 0, k0n = 0, k1n = 0, c0n = 0;
     if (un < n_items) {
       s0n = p.slot_ptr[rn];
@@ -348,32 +357,61 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
     nnz = int(k1n - k0n);
     c0 = c0n;
     my_slot = my_slot_n;
+    u = un;
   }
+  items.finish(n_warps, lane);
 }
 
 static int align16(long x) { return int((x + 15) & ~15L); }
 
+ScatterPattern space_pattern(const fe_space* s) {
+  ScatterPattern pt;
+  pt.n_rows = s->hs.n_dofs;
+  pt.nnz = s->hs.nnz;
+  pt.max_row_nnz = s->hs.max_row_nnz;
+  pt.max_slots = s->hs.max_slots;
+  pt.node_rows = s->hs.node_rows;
+  pt.pos_ok = s->hs.pos_ok;
+  pt.row_ptr = s->d_row_ptr;
+  pt.cnt = s->d_cnt;
+  pt.code_ptr = s->d_code_ptr;
+  pt.codes = s->d_codes;
+  pt.pos = s->d_pos;
+  pt.slot_ptr = s->d_slot_ptr;
+  pt.slots = s->d_slots;
+  pt.ncode = nullptr;
+  pt.sched = s->d_sched;
+  return pt;
+}
+
 cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st) {
-  if (s->hs.n_dofs == 0) return cudaSuccess;
+  return launch_scatter_pattern(s, space_pattern(s), prec, values, rhs, st);
+}
+
+cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, fe_precision prec, double* values,
+                                   double* rhs, cudaStream_t st) {
+  if (pt.n_rows == 0) return cudaSuccess;
   ScatterParams p;
-  p.n_rows = s->hs.n_dofs;
+  p.n_rows = pt.n_rows;
   p.nl = s->nl;
   p.nlp = s->nlp;
-  p.row_ptr = s->d_row_ptr;
-  p.cnt = s->d_cnt;
-  p.code_ptr = s->d_code_ptr;
-  p.codes = s->d_codes;
-  p.pos = s->d_pos;
-  p.slot_ptr = s->d_slot_ptr;
-  p.slots = s->d_slots;
+  p.row_ptr = pt.row_ptr;
+  p.cnt = pt.cnt;
+  p.code_ptr = pt.code_ptr;
+  p.codes = pt.codes;
+  p.pos = pt.pos;
+  p.slot_ptr = pt.slot_ptr;
+  p.slots = pt.slots;
+  p.ncode = pt.ncode;
+  p.sched = pt.sched;
   p.ke = s->d_ke;
   p.fe = s->d_fe;
   p.values = values;
   p.rhs = rhs;
   const int tk = prec == FE_PREC_FP64 ? 8 : 4;
-  p.ke_bytes = align16(long(s->hs.max_slots) * s->nlp * tk);
-  p.code_bytes = align16(((long(s->hs.max_slots) * s->nl + 7) & ~7L) * 2);
-  const int rows_warp_bytes = p.ke_bytes + p.code_bytes + align16((s->hs.max_row_nnz + 1) * 2);
+  p.ke_bytes = align16(long(pt.max_slots) * s->nlp * tk);
+  p.code_bytes = align16(((long(pt.max_slots) * s->nl + 7) & ~7L) * 2);
+  const int rows_warp_bytes = p.ke_bytes + p.code_bytes + align16((pt.max_row_nnz + 1) * 2);
   const long smem = long(rows_warp_bytes) * kScatterWarps;
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
@@ -388,12 +426,12 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
     kern<<<blocks, kScatterWarps * 32, size_t(bytes), st>>>(p);
     return cudaGetLastError();
   };
-  if (prec != FE_PREC_FP64 && s->hs.max_slots <= 32) {
+  if (prec != FE_PREC_FP64 && pt.max_slots <= 32 && pt.pos_ok) {
     const bool idx32 = int64_t(s->n_cells) * s->nl * s->nlp < (int64_t(1) << 32);
-    p.acc_stride = int((s->hs.max_row_nnz + 3) & ~int64_t(3));
+    p.acc_stride = int((pt.max_row_nnz + 3) & ~int64_t(3));
     // rows of one node together (3-component problems), else one row per warp
     // (measured: pays for Q1, 24-entry cell rows; for wider rows one row per warp is faster)
-    const int R = (s->hs.node_rows && s->ncomp == 3 && s->nl <= 32) ? 3 : 1;
+    const int R = (pt.node_rows && s->ncomp == 3 && s->nl <= 32) ? 3 : 1;
     p.warp_bytes = R * (p.acc_stride + 32) * 8;  // R accumulator rows, each with one dummy per lane
     const long bytes = long(p.warp_bytes) * kScatterWarps;
     if (bytes <= 200 * 1024) {
@@ -421,7 +459,7 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
     }
   }
   p.warp_bytes = rows_warp_bytes;
-  if (smem <= 200 * 1024 && s->hs.max_slots <= 32) {
+  if (smem <= 200 * 1024 && pt.max_slots <= 32) {
     return prec == FE_PREC_FP64 ? launch(k_scatter_rows<double>, smem) : launch(k_scatter_rows<float>, smem);
   }
   const int blocks = int(std::min<int64_t>(need, int64_t(nsm) * 8));

@@ -23,8 +23,48 @@ bool cell_tc_applicable(const fe_space* s, fe_precision prec);
 cudaError_t launch_cell_tc(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
                            cudaStream_t st);
 
+// Device arrays and host-side sizes of one assembly permutation: the space's
+// own (every DOF a row) or a constrained one (free DOFs only).
+struct ScatterPattern {
+  int64_t n_rows = 0, nnz = 0, max_row_nnz = 0;
+  int max_slots = 0;
+  bool node_rows = false, pos_ok = true;
+  const int64_t* row_ptr = nullptr;
+  const uint8_t* cnt = nullptr;
+  const int64_t* code_ptr = nullptr;
+  const uint16_t* codes = nullptr;
+  const uint16_t* pos = nullptr;
+  const int64_t* slot_ptr = nullptr;
+  const int32_t* slots = nullptr;
+  const int32_t* ncode = nullptr;  // codes per row, or nullptr: slots * n_loc
+  unsigned long long* sched = nullptr;  // [2] counters of the dynamic row schedule (zero between launches)
+};
+ScatterPattern space_pattern(const fe_space* s);
+
 // Deterministic scatter of the cell matrices/vectors into CSR values / RHS.
 cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st);
+cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, fe_precision prec, double* values,
+                                   double* rhs, cudaStream_t st);
+
+// Integrates every cell of `s` into its cell-matrix and cell-vector scratch
+// with the kernel chosen by the space's kernel selection. Returns an FE code.
+int cell_stage(fe_space* s, const double* coef, const double force[3], fe_precision prec, cudaStream_t st);
+
+// Lifting of strong Dirichlet data into the cell vectors: for the cells
+// listed, fe[e][a] -= sum_j A^e[a][m_j] * u_fixed[fix_j] over the cell's fixed
+// local columns m_j (every local row a).
+struct LiftParams {
+  int64_t n_cells = 0;
+  int nl = 0, nlp = 0;
+  const int32_t* cell = nullptr;  // [n_cells]
+  const int32_t* ptr = nullptr;   // [n_cells + 1] into m / fix
+  const uint8_t* m = nullptr;     // local column of each fixed DOF of the cell
+  const int32_t* fix = nullptr;   // its fixed id
+  const double* u_fixed = nullptr;
+  const void* ke = nullptr;
+  double* fe = nullptr;
+};
+cudaError_t launch_lift(const LiftParams& lp, fe_precision prec, cudaStream_t st);
 
 // Threads per block of the adjoint kernel (one cell per thread); its per-block
 // partial sums of the compliance are what the reduction scratch holds.

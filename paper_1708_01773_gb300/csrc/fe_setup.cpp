@@ -255,13 +255,26 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
     *err = "n_cells * n_loc exceeds int32";
     return FE_ERR_UNSUPPORTED;
   }
-  int rc = number_dofs(p, ncomp, n_cells, cell_vertices, &hs->cell_dofs, &hs->n_dofs, err);
+  int64_t n_dofs = 0;
+  int rc = number_dofs(p, ncomp, n_cells, cell_vertices, &hs->cell_dofs, &n_dofs, err);
   if (rc) return rc;
-  const int64_t nd = hs->n_dofs;
+  return build_pattern(p, ncomp, n_cells, hs->cell_dofs.data(), nullptr, n_dofs, hs, err);
+}
+
+int build_pattern(int p, int ncomp, int64_t n_cells, const int32_t* cell_dofs, const int32_t* label,
+                  int64_t n_rows, HostSetup* hs, std::string* err) {
+  const int nb = (p + 1) * (p + 1) * (p + 1), nl = ncomp * nb;
+  // row of a global DOF: itself, or its label (negative = fixed, no row or column)
+  auto row_of = [label](int32_t d) -> int32_t { return label ? label[d] : d; };
+  hs->n_dofs = n_rows;
+  const int64_t nd = n_rows;
   const int64_t ninc = n_cells * nl;
   // slots by counting sort (cell-major scan keeps cells ascending per row)
   hs->slot_ptr.assign(nd + 1, 0);
-  for (int64_t i = 0; i < ninc; ++i) hs->slot_ptr[hs->cell_dofs[i] + 1]++;
+  for (int64_t i = 0; i < ninc; ++i) {
+    const int32_t r = row_of(cell_dofs[i]);
+    if (r >= 0) hs->slot_ptr[r + 1]++;
+  }
   int max_slots = 0;
   for (int64_t r = 0; r < nd; ++r) max_slots = std::max<int64_t>(max_slots, hs->slot_ptr[r + 1]);
   if (max_slots * nl > 32767) {
@@ -274,10 +287,13 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
   }
   hs->max_slots = max_slots;
   for (int64_t r = 0; r < nd; ++r) hs->slot_ptr[r + 1] += hs->slot_ptr[r];
-  hs->slots.assign(ninc, 0);
+  hs->slots.assign(hs->slot_ptr[nd], 0);
   {
     std::vector<int64_t> fill(hs->slot_ptr.begin(), hs->slot_ptr.end() - 1);
-    for (int64_t i = 0; i < ninc; ++i) hs->slots[fill[hs->cell_dofs[i]]++] = int32_t(i);
+    for (int64_t i = 0; i < ninc; ++i) {
+      const int32_t r = row_of(cell_dofs[i]);
+      if (r >= 0) hs->slots[fill[r]++] = int32_t(i);
+    }
   }
   const int nthreads = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
   // pass 1: nonzeros per row (stamp arrays per thread)
@@ -288,9 +304,11 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
       int64_t k = 0;
       for (int64_t s = hs->slot_ptr[r]; s < hs->slot_ptr[r + 1]; ++s) {
         const int64_t e = hs->slots[s] / nl;
-        const int32_t* dofs = hs->cell_dofs.data() + e * nl;
-        for (int m = 0; m < nl; ++m)
-          if (stamp[dofs[m]] != int32_t(r)) { stamp[dofs[m]] = int32_t(r); ++k; }
+        const int32_t* dofs = cell_dofs + e * nl;
+        for (int m = 0; m < nl; ++m) {
+          const int32_t c = row_of(dofs[m]);
+          if (c >= 0 && stamp[c] != int32_t(r)) { stamp[c] = int32_t(r); ++k; }
+        }
       }
       row_nnz[r] = k;
     }
@@ -302,16 +320,23 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
     hs->code_ptr[r + 1] = hs->code_ptr[r] + (((hs->slot_ptr[r + 1] - hs->slot_ptr[r]) * nl + 7) & ~int64_t(7));
   }
   hs->nnz = hs->row_ptr[nd];
+  hs->max_row_nnz = 0;
   for (int64_t r = 0; r < nd; ++r) hs->max_row_nnz = std::max(hs->max_row_nnz, row_nnz[r]);
   hs->n_codes = hs->code_ptr[nd];
-  hs->n_contrib = ninc * nl;
+  hs->n_contrib = hs->slot_ptr[nd] * nl;
   if (hs->nnz > (int64_t(1) << 40)) {
     *err = "too many nonzeros";
     return FE_ERR_UNSUPPORTED;
   }
+  // Contributions of fixed columns (label only) are left out of the codes and
+  // sent, in the slot-major positions, to the lane's private dummy accumulator
+  // of the slot-wise scatter: entry acc_stride + (m mod 32) of the row.
+  const int64_t acc_stride = (hs->max_row_nnz + 3) & ~int64_t(3);
+  hs->pos_ok = acc_stride + 32 <= 0x7fff;
   hs->col.assign(hs->nnz, 0);
   hs->cnt.assign(hs->nnz, 0);
   hs->codes.assign(hs->n_codes, 0);
+  if (label) hs->ncode.assign(nd, 0); else hs->ncode.clear();
   // 64 entries of padding: the scatter's lanes read whole 32-wide chunks of a
   // cell row's positions, past the end of the last row's block
   hs->pos.assign(hs->n_codes + 64, 0);
@@ -324,11 +349,17 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
       const int64_t s0 = hs->slot_ptr[r], ns = hs->slot_ptr[r + 1] - s0;
       for (int64_t s = 0; s < ns; ++s) {
         const int64_t e = hs->slots[s0 + s] / nl;
-        const int32_t* dofs = hs->cell_dofs.data() + e * nl;
-        for (int m = 0; m < nl; ++m)
-          keys.push_back((uint64_t(uint32_t(dofs[m])) << 16) | (uint64_t(s) << 8) | uint64_t(m));
+        const int32_t* dofs = cell_dofs + e * nl;
+        for (int m = 0; m < nl; ++m) {
+          const int32_t c = row_of(dofs[m]);
+          if (c >= 0)
+            keys.push_back((uint64_t(uint32_t(c)) << 16) | (uint64_t(s) << 8) | uint64_t(m));
+          else if (hs->pos_ok)
+            hs->pos[hs->code_ptr[r] + s * nl + m] = uint16_t(acc_stride + (m & 31));
+        }
       }
       std::sort(keys.begin(), keys.end());
+      if (label) hs->ncode[r] = int32_t(keys.size());
       int64_t k = hs->row_ptr[r] - 1;
       int64_t c = hs->code_ptr[r];
       int64_t prev = -1;
@@ -348,7 +379,7 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
       }
     }
   });
-  // The ncomp rows of one node (consecutive DOFs, components in order) lie in
+  // The ncomp rows of one node (consecutive rows, components in order) lie in
   // the same cells, at local rows i * nb + a, and so share their column
   // pattern and positions; the scatter then treats them together.
   hs->node_rows = false;

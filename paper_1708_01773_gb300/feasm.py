@@ -29,8 +29,11 @@ EXPORTS = [
     "fe_space_create", "fe_space_create_host", "fe_space_sizes", "fe_space_cell_dofs_host",
     "fe_space_csr_pattern_host", "fe_space_permutation_host", "fe_space_csr_pattern", "fe_assemble", "fe_assemble_ex", "fe_assemble_host",
     "fe_assemble_adjoint", "fe_assemble_adjoint_noalloc", "fe_space_set_kernel", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
-    "fe_batch_assemble", "fe_batch_destroy",
+    "fe_batch_assemble", "fe_batch_destroy", "fe_space_dof_points_host", "fe_dirichlet_create", "fe_dirichlet_sizes",
+    "fe_dirichlet_labels_host", "fe_dirichlet_csr_pattern_host", "fe_dirichlet_csr_pattern",
+    "fe_dirichlet_permutation_host", "fe_dirichlet_lift_host", "fe_assemble_dirichlet", "fe_dirichlet_destroy",
 ]
+_VOID = ("fe_space_destroy", "fe_last_error", "fe_batch_destroy", "fe_dirichlet_destroy")
 
 
 class FEError(RuntimeError):
@@ -77,8 +80,19 @@ def lib() -> ctypes.CDLL:
         L.fe_batch_assemble.argtypes = [V, V, V, V, V, I, V]
         L.fe_batch_destroy.argtypes = [V]
         L.fe_batch_destroy.restype = None
+        L.fe_space_dof_points_host.argtypes = [V, P(MeshDesc), V]
+        L.fe_dirichlet_create.argtypes = [V, V, P(V)]
+        L.fe_dirichlet_sizes.argtypes = [V, P(I64), P(I64), P(I64)]
+        L.fe_dirichlet_labels_host.argtypes = [V, V]
+        L.fe_dirichlet_csr_pattern_host.argtypes = [V, V, V]
+        L.fe_dirichlet_csr_pattern.argtypes = [V, V, V, V]
+        L.fe_dirichlet_permutation_host.argtypes = [V, V, V, V, V, V, V, V]
+        L.fe_dirichlet_lift_host.argtypes = [V, P(I64), P(I64), V, V, V, V]
+        L.fe_assemble_dirichlet.argtypes = [V, V, V, V, V, V, I, V]
+        L.fe_dirichlet_destroy.argtypes = [V]
+        L.fe_dirichlet_destroy.restype = None
         for n in EXPORTS:
-            if n not in ("fe_space_destroy", "fe_last_error", "fe_batch_destroy"):
+            if n not in _VOID:
                 getattr(L, n).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -239,6 +253,136 @@ def fe_batch_destroy(batch: int):
     lib().fe_batch_destroy(batch)
 
 
+def fe_space_dof_points_host(space: int, coords, cell_vertices) -> np.ndarray:
+    """Node position of every DOF, [n_dofs, 3] (host)."""
+    n_dofs = fe_space_sizes(space)[0]
+    d, keep = _mesh_desc(coords, cell_vertices)
+    out = np.zeros((n_dofs, 3), dtype=np.float64)
+    _check(lib().fe_space_dof_points_host(space, ctypes.byref(d), out.ctypes.data), "fe_space_dof_points_host")
+    del keep
+    return out
+
+
+def fe_dirichlet_create(space: int, fixed) -> int:
+    fx = np.ascontiguousarray(np.asarray(fixed).astype(np.uint8))
+    out = ctypes.c_void_p()
+    _check(lib().fe_dirichlet_create(space, fx.ctypes.data, ctypes.byref(out)), "fe_dirichlet_create")
+    return out.value
+
+
+def fe_dirichlet_sizes(d: int):
+    v = [ctypes.c_int64() for _ in range(3)]
+    _check(lib().fe_dirichlet_sizes(d, *[ctypes.byref(x) for x in v]), "fe_dirichlet_sizes")
+    return tuple(x.value for x in v)   # n_free, n_fixed, nnz
+
+
+def fe_dirichlet_labels_host(d: int, n_dofs: int) -> np.ndarray:
+    out = np.zeros(n_dofs, dtype=np.int32)
+    _check(lib().fe_dirichlet_labels_host(d, out.ctypes.data), "fe_dirichlet_labels_host")
+    return out
+
+
+def fe_dirichlet_csr_pattern_host(d: int):
+    n_free, _, nnz = fe_dirichlet_sizes(d)
+    rp = np.zeros(n_free + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    _check(lib().fe_dirichlet_csr_pattern_host(d, rp.ctypes.data, col.ctypes.data), "fe_dirichlet_csr_pattern_host")
+    return rp, col
+
+
+def fe_dirichlet_csr_pattern(d: int, row_ptr, col_idx, stream=None):
+    _check(lib().fe_dirichlet_csr_pattern(d, _ptr(row_ptr), _ptr(col_idx), _stream(stream)),
+           "fe_dirichlet_csr_pattern")
+
+
+def fe_dirichlet_permutation_host(d: int, n_slots: int):
+    """(cnt, code_ptr, codes, ncode, pos, slot_ptr, slots) of a host-only space's constrained system."""
+    n_free, _, nnz = fe_dirichlet_sizes(d)
+    cnt = np.zeros(nnz, dtype=np.uint8)
+    code_ptr = np.zeros(n_free + 1, dtype=np.int64)
+    ncode = np.zeros(n_free, dtype=np.int32)
+    slot_ptr = np.zeros(n_free + 1, dtype=np.int64)
+    slots = np.zeros(n_slots, dtype=np.int32)
+    args = [cnt.ctypes.data, code_ptr.ctypes.data]
+    _check(lib().fe_dirichlet_permutation_host(d, *args, None, ncode.ctypes.data, None, slot_ptr.ctypes.data,
+                                               slots.ctypes.data), "fe_dirichlet_permutation_host")
+    slots = slots[:int(slot_ptr[-1])]
+    codes = np.zeros(int(code_ptr[-1]), dtype=np.uint16)
+    pos = np.zeros(int(code_ptr[-1]), dtype=np.uint16)
+    _check(lib().fe_dirichlet_permutation_host(d, *args, codes.ctypes.data, ncode.ctypes.data, pos.ctypes.data,
+                                               slot_ptr.ctypes.data, slots.ctypes.data),
+           "fe_dirichlet_permutation_host")
+    return cnt, code_ptr, codes, ncode, pos, slot_ptr, slots
+
+
+def fe_dirichlet_lift_host(d: int):
+    """(cells, ptr, m, fix): the cells whose cell vectors are lifted and their fixed local columns."""
+    nc, ne = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().fe_dirichlet_lift_host(d, ctypes.byref(nc), ctypes.byref(ne), None, None, None, None),
+           "fe_dirichlet_lift_host")
+    cells = np.zeros(nc.value, dtype=np.int32)
+    ptr = np.zeros(nc.value + 1, dtype=np.int32)
+    m = np.zeros(ne.value, dtype=np.uint8)
+    fix = np.zeros(ne.value, dtype=np.int32)
+    _check(lib().fe_dirichlet_lift_host(d, None, None, cells.ctypes.data, ptr.ctypes.data, m.ctypes.data,
+                                        fix.ctypes.data), "fe_dirichlet_lift_host")
+    return cells, ptr, m, fix
+
+
+def fe_assemble_dirichlet(d: int, coefficients, body_force, u_fixed, csr_values, rhs, prec: int, stream=None):
+    f = np.ascontiguousarray(np.resize(np.asarray(body_force, dtype=np.float64), 3))
+    _check(lib().fe_assemble_dirichlet(d, _ptr(coefficients), f.ctypes.data, _ptr(u_fixed), _ptr(csr_values),
+                                       _ptr(rhs), prec, _stream(stream)), "fe_assemble_dirichlet")
+
+
+def fe_dirichlet_destroy(d: int):
+    lib().fe_dirichlet_destroy(d)
+
+
+class DirichletSystem:
+    """The constrained system of an FESpace with the DOFs of `fixed` prescribed
+    (strong Dirichlet conditions). Keeps its space alive."""
+
+    def __init__(self, space: "FESpace", fixed):
+        self.space = space
+        self.handle = fe_dirichlet_create(space.handle, fixed)
+        self.n_free, self.n_fixed, self.nnz = fe_dirichlet_sizes(self.handle)
+
+    def labels(self) -> np.ndarray:
+        return fe_dirichlet_labels_host(self.handle, self.space.n_dofs)
+
+    def pattern_host(self):
+        return fe_dirichlet_csr_pattern_host(self.handle)
+
+    def pattern(self, device="cuda"):
+        import torch
+        rp = torch.empty(self.n_free + 1, dtype=torch.int64, device=device)
+        col = torch.empty(self.nnz, dtype=torch.int32, device=device)
+        fe_dirichlet_csr_pattern(self.handle, rp, col)
+        return rp, col
+
+    def assemble(self, coef, u_fixed=None, values=None, rhs=None, prec: str = "fp32", force=None, stream=None):
+        import torch
+        if values is None:
+            values = torch.empty(self.nnz, dtype=torch.float64, device=coef.device)
+        if rhs is None:
+            rhs = torch.empty(self.n_free, dtype=torch.float64, device=coef.device)
+        fe_assemble_dirichlet(self.handle, coef, self.space.prob.force if force is None else force, u_fixed,
+                              values, rhs, PRECISIONS[prec], stream)
+        return values, rhs
+
+    def close(self):
+        if self.handle:
+            fe_dirichlet_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class FESpace:
     """Owns one fe_space handle built from a seeded workload (inputs.Problem)."""
 
@@ -282,6 +426,12 @@ class FESpace:
 
     def set_kernel(self, kernel: str):
         fe_space_set_kernel(self.handle, kernel)
+
+    def dof_points(self) -> np.ndarray:
+        return fe_space_dof_points_host(self.handle, self.prob.mesh.coords, self.prob.mesh.cell_vertices)
+
+    def dirichlet(self, fixed) -> DirichletSystem:
+        return DirichletSystem(self, fixed)
 
     def status(self, stream=None) -> int:
         return fe_status(self.handle, stream)
