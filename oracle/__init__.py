@@ -236,3 +236,28 @@ def dirichlet_reduce(row_ptr, col, val, rhs, fixed, u_fixed, rows=None):
     np.add.at(lift, row_of[fx], val[fx] * u_fixed[-1 - lab[col[fx]]])
     out_rhs = (np.asarray(rhs, dtype=np.float64) - lift)[keep_rows]
     return out_ptr, out_col.astype(np.int32), out_val, out_rhs
+
+
+# ----------------------------------------------------------------------------- self-adjoint compliance
+def compliance_solve(prob, fixed, cell_dofs=None, n_dofs=None):
+    """Compliance of the structure under its body force with the DOFs of `fixed`
+    clamped (u^D = 0): K(E) u = f on the free DOFs (Eq. dirichlet_bc_discrete_problem),
+    c = f^T u, and its gradient dc/dE_K = -u_K^T (A^K / E_K) u_K (c is self-adjoint:
+    dc/dE = f^T du/dE = -u^T (dK/dE) u, and K is linear in the cell coefficients,
+    Eq. assembly). The free system is solved directly (scipy's sparse LU) in FP64.
+    Returns (u over all DOFs with zeros at the fixed ones, c, dc/dE)."""
+    import scipy.sparse
+    import scipy.sparse.linalg
+    if cell_dofs is None:
+        cell_dofs, n_dofs = dof_numbering(prob.mesh, prob.order, prob.ncomp)
+    fixed = np.asarray(fixed).astype(bool)
+    rp, col, val, rhs = assemble_csr(prob, cell_dofs, n_dofs)
+    ptr, c_r, v_r, b_r = dirichlet_reduce(rp, col, val, rhs, fixed, np.zeros(int(fixed.sum())))
+    n_free = ptr.size - 1
+    K = scipy.sparse.csr_matrix((v_r, c_r, ptr), shape=(n_free, n_free))
+    u_free = scipy.sparse.linalg.spsolve(K.tocsc(), b_r)
+    u = np.zeros(n_dofs)
+    u[~fixed] = u_free
+    c = float(b_r @ u_free)
+    grad = -cell_energies(prob, u, cell_dofs)
+    return u, c, grad

@@ -596,3 +596,63 @@ def test_dirichlet_clamped_beam_is_spd_and_homogeneous_keeps_f():
     assert np.abs(A - A.T).max() < 1e-15 * np.abs(A).max()
     assert np.linalg.eigvalsh(A).min() > 0
     np.testing.assert_array_equal(b, rhs[~fixed])
+
+
+
+# ---------------------------------------------------------------- self-adjoint compliance
+def clamped_problem(p=1, shape=(4, 2, 2), seed=120):
+    prob = inputs.small_problem(shape, p, 1, seed=seed, extent=(2.0, 1.0, 1.0))
+    cd, n = oracle.dof_numbering(prob.mesh, p, 3)
+    pos, _ = node_positions(prob, cd, n)
+    return prob, cd, n, np.abs(pos[:, 0]) < 1e-12
+
+
+@pytest.mark.parametrize("p", [1, 2])
+def test_compliance_identities(p):
+    """c(E) = f^T u(E) with K(E) u = f: c = u^T K u (energy), c(sE) = c(E)/s (K is
+    linear in E), and Euler's identity for a function homogeneous of degree -1:
+    sum_K E_K dc/dE_K = -c. A wrong sign or a missing term in the gradient fails."""
+    prob, cd, n, fixed = clamped_problem(p)
+    u, c, g = oracle.compliance_solve(prob, fixed, cd, n)
+    assert c > 0 and np.all(u[fixed] == 0)
+    rp, col, val, rhs = oracle.assemble_csr(prob, cd, n)
+    A = csr_to_dense(rp, col, val, n)
+    assert abs(u @ A @ u - c) <= 1e-10 * c
+    assert abs(rhs @ u - c) <= 1e-12 * c                     # f^T u over the free DOFs (u = 0 on fixed)
+    assert np.all(g < 0)                                      # stiffer cells lower the compliance
+    assert abs(prob.coef @ g + c) <= 1e-10 * c
+    scaled = inputs.Problem("s", prob.mesh, p, p + 1, 1, 2.5 * prob.coef, prob.force)
+    _, c2, g2 = oracle.compliance_solve(scaled, fixed, cd, n)
+    assert abs(c2 - c / 2.5) <= 1e-10 * c
+    np.testing.assert_allclose(g2, g / 2.5 ** 2, rtol=1e-9)
+
+
+def test_compliance_gradient_central_differences():
+    prob, cd, n, fixed = clamped_problem(1, (3, 2, 2), seed=121)
+    u, c, g = oracle.compliance_solve(prob, fixed, cd, n)
+    for e in (0, 5, 11):
+        h = 1e-5 * prob.coef[e]
+        cp = prob.coef.copy(); cp[e] += h
+        cm = prob.coef.copy(); cm[e] -= h
+        c_p = oracle.compliance_solve(inputs.Problem("p", prob.mesh, 1, 2, 1, cp, prob.force), fixed, cd, n)[1]
+        c_m = oracle.compliance_solve(inputs.Problem("m", prob.mesh, 1, 2, 1, cm, prob.force), fixed, cd, n)[1]
+        fd = (c_p - c_m) / (2 * h)
+        assert abs(fd - g[e]) <= 1e-6 * abs(g[e])
+
+
+def test_compliance_of_a_bar_in_tension_closed_form():
+    """An undistorted bar [0,L]x[0,1]^2 clamped at x = 0 (all components) and pulled by
+    a uniform axial body force b: for nu = 0 the 3D problem is exactly the 1D bar
+    -E u'' = b, u(0) = 0, u'(L) = 0, whose solution u = b (L x - x^2/2)/E is quadratic,
+    hence exact in Q2; c = int b u dV = b^2 L^3 / (3 E)."""
+    L, E, b = 3.0, 2.0, 0.7
+    mesh = inputs.brick(3, 1, 1, L, 1.0, 1.0)
+    prob = inputs.Problem("bar", mesh, 2, 3, 1, np.full(mesh.n_cells, E), np.array([b, 0.0, 0.0]), nu=0.0)
+    cd, n = oracle.dof_numbering(mesh, 2, 3)
+    pos, comp = node_positions(prob, cd, n)
+    fixed = np.abs(pos[:, 0]) < 1e-12
+    u, c, g = oracle.compliance_solve(prob, fixed, cd, n)
+    exact_u = b * (L * pos[:, 0] - pos[:, 0] ** 2 / 2) / E
+    np.testing.assert_allclose(u[comp == 0], exact_u[comp == 0], rtol=0, atol=1e-12)
+    assert np.abs(u[comp != 0]).max() < 1e-12
+    assert abs(c - b * b * L ** 3 / (3 * E)) <= 1e-12 * c
