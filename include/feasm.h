@@ -56,7 +56,8 @@ enum {
   FE_ERR_OOM = -3,
   FE_ERR_NEG_JACOBIAN = -4,
   FE_ERR_TIMEOUT = -5,
-  FE_ERR_UNSUPPORTED = -6
+  FE_ERR_UNSUPPORTED = -6,
+  FE_ERR_NOT_CONVERGED = -7
 };
 
 typedef struct {
@@ -317,6 +318,41 @@ int fe_dirichlet_lift_host(const fe_dirichlet* d, int64_t* n_cells, int64_t* n_e
  * Deterministic like fe_assemble. */
 int fe_assemble_dirichlet(fe_dirichlet* d, const double* coefficients, const double* body_force,
                           const double* u_fixed, double* csr_values, double* rhs, fe_precision prec, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Self-adjoint compliance of a clamped structure (not in the paper; built on
+ * the constrained assembly above). With the fixed DOFs of `d` held at zero and
+ * the body force f, K(E) u = f on the free DOFs and
+ *   c(E) = f^T u,   dc/dE_K = -u_K^T (A^K / E_K) u_K
+ * (c = f^T K^-1 f, and K is linear in the cell coefficients, Eq. assembly).
+ * ------------------------------------------------------------------------ */
+
+/* Number of doubles of device workspace fe_compliance needs: the constrained
+ * matrix and right-hand side plus the solver's vectors and partial sums. */
+int fe_compliance_work_size(const fe_dirichlet* d, int64_t* n_doubles);
+
+/* Assembles the constrained system in precision `prec` (fe_assemble_dirichlet
+ * with u^D = 0), solves it by the conjugate gradient method with the Jacobi
+ * preconditioner in FP64 until ||r|| <= rtol ||f|| (checked every 8
+ * iterations) or max_iter iterations, and evaluates c and its gradient (the
+ * adjoint kernel of fe_assemble_adjoint with grad_scale -1; FP32 strain
+ * arithmetic for the FP32/BF16 forms, FP64 otherwise). Every reduction runs in
+ * a fixed order: the results are deterministic on any GPU.
+ *   coefficients  device [n_cells] E_K (or kappa_K).
+ *   body_force    host [ncomp].
+ *   work          device [fe_compliance_work_size] doubles, caller-owned.
+ *   u             device [n_dofs] FP64: the displacement over all DOFs (zero
+ *                 at the fixed ones).
+ *   compliance    device scalar FP64: c.
+ *   dc_dcoef      device [n_cells] FP64: dc/dE_K (may be NULL: no gradient).
+ *   iterations, rel_residual  host outputs (may be NULL).
+ * Synchronises `stream` (the host checks convergence). Errors:
+ * FE_ERR_NOT_CONVERGED (max_iter reached; u holds the last iterate),
+ * FE_ERR_INVALID_ARG (also: the constrained matrix is not positive definite,
+ * e.g. too few DOFs fixed), FE_ERR_CUDA. */
+int fe_compliance(fe_dirichlet* d, const double* coefficients, const double* body_force, fe_precision prec,
+                  double rtol, int max_iter, double* work, double* u, double* compliance, double* dc_dcoef,
+                  int* iterations, double* rel_residual, void* stream);
 
 /* Frees the constrained system (before its space). */
 void fe_dirichlet_destroy(fe_dirichlet* d);

@@ -43,6 +43,7 @@ struct fe_dirichlet {
   uint8_t* d_lift_m = nullptr;
   int32_t* d_lift_fix = nullptr;
   unsigned long long* d_sched = nullptr;  // scatter schedule counters of this pattern
+  int32_t* d_label = nullptr;             // [n_dofs] labels (free id or -1 - fixed id)
 };
 
 namespace feasm {
@@ -114,7 +115,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src, size_t extra = 0) {
 void free_device(fe_dirichlet* d) {
   void* ptrs[] = {d->d_row_ptr, d->d_col,   d->d_cnt,       d->d_code_ptr, d->d_codes,   d->d_pos,     d->d_slot_ptr,
                   d->d_slots,   d->d_ncode, d->d_lift_cell, d->d_lift_ptr, d->d_lift_m, d->d_lift_fix,
-                  d->d_sched};
+                  d->d_sched,   d->d_label};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -242,6 +243,7 @@ int fe_dirichlet_create(fe_space* s, const uint8_t* fixed, fe_dirichlet** out) {
     if (e == cudaSuccess) e = upload(&d->d_lift_m, d->lift_m);
     if (e == cudaSuccess) e = upload(&d->d_lift_fix, d->lift_fix);
     if (e == cudaSuccess) e = upload(&d->d_sched, std::vector<unsigned long long>(2, 0ull));
+    if (e == cudaSuccess) e = upload(&d->d_label, d->label);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
       free_device(d);
@@ -353,6 +355,50 @@ int fe_assemble_dirichlet(fe_dirichlet* d, const double* coefficients, const dou
   }
   cudaError_t e = feasm::launch_scatter_pattern(s, pattern_of(d), prec, csr_values, rhs, st);
   return e == cudaSuccess ? FE_OK : cuda_fail(e, "scatter kernel");
+}
+
+int fe_compliance_work_size(const fe_dirichlet* d, int64_t* n_doubles) {
+  if (!d || !n_doubles) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
+  *n_doubles = feasm::compliance_work_doubles(d->n_free, d->hs.nnz);
+  return FE_OK;
+}
+
+int fe_compliance(fe_dirichlet* d, const double* coefficients, const double* body_force, fe_precision prec,
+                  double rtol, int max_iter, double* work, double* u, double* compliance, double* dc_dcoef,
+                  int* iterations, double* rel_residual, void* stream) {
+  if (!d || !body_force || !work || !compliance || (d->s->hs.n_dofs && !u) || (d->s->n_cells && !coefficients))
+    return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
+  if (d->s->host_only) return feasm::set_error(FE_ERR_INVALID_ARG, "host-only space cannot compute");
+  if (!(rtol > 0.0) || max_iter < 0) return feasm::set_error(FE_ERR_INVALID_ARG, "rtol must be > 0, max_iter >= 0");
+  fe_space* s = d->s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  double* vals = work;
+  double* rhs = work + d->hs.nnz;
+  if (int rc = fe_assemble_dirichlet(d, coefficients, body_force, nullptr, vals, rhs, prec, stream)) return rc;
+  int it_local = 0;
+  double rel_local = 0.0;
+  feasm::ComplianceArgs a;
+  a.n_free = d->n_free;
+  a.nnz = d->hs.nnz;
+  a.n_dofs = s->hs.n_dofs;
+  a.row_ptr = d->d_row_ptr;
+  a.col = d->d_col;
+  a.label = d->d_label;
+  a.work = work;
+  a.rtol = rtol;
+  a.max_iter = max_iter;
+  a.u = u;
+  a.compliance = compliance;
+  a.iterations = iterations ? iterations : &it_local;
+  a.rel_residual = rel_residual ? rel_residual : &rel_local;
+  const int rc = feasm::compliance_solve(a, st);
+  if (rc) return rc;
+  if (dc_dcoef && s->n_cells) {
+    const fe_precision pa = prec == FE_PREC_FP64 ? FE_PREC_FP64 : FE_PREC_FP32;
+    cudaError_t e = feasm::launch_adjoint(s, u, coefficients, -1.0, dc_dcoef, nullptr, pa, st);
+    if (e != cudaSuccess) return cuda_fail(e, "compliance gradient");
+  }
+  return FE_OK;
 }
 
 void fe_dirichlet_destroy(fe_dirichlet* d) {

@@ -66,6 +66,25 @@ struct LiftParams {
 };
 cudaError_t launch_lift(const LiftParams& lp, fe_precision prec, cudaStream_t st);
 
+// Compliance of a clamped structure: PCG (Jacobi) on the constrained system
+// already assembled into work[0 .. nnz) (values) and work[nnz .. nnz + n_free)
+// (right-hand side), then u over all DOFs and c = f . u. Synchronises `st`.
+struct ComplianceArgs {
+  int64_t n_free = 0, nnz = 0, n_dofs = 0;
+  const int64_t* row_ptr = nullptr;
+  const int32_t* col = nullptr;
+  const int32_t* label = nullptr;  // device [n_dofs]
+  double* work = nullptr;          // compliance_work_doubles(n_free, nnz)
+  double rtol = 1e-10;
+  int max_iter = 0;
+  double* u = nullptr;             // device [n_dofs]
+  double* compliance = nullptr;    // device scalar
+  int* iterations = nullptr;       // host
+  double* rel_residual = nullptr;  // host
+};
+int64_t compliance_work_doubles(int64_t n_free, int64_t nnz);
+int compliance_solve(const ComplianceArgs& a, cudaStream_t st);
+
 // Threads per block of the adjoint kernel (one cell per thread); its per-block
 // partial sums of the compliance are what the reduction scratch holds.
 constexpr int kAdjointBlock = 128;

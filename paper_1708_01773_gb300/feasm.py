@@ -21,7 +21,7 @@ PRECISIONS = {"fp64": FE_PREC_FP64, "fp32": FE_PREC_FP32, "bf16": FE_PREC_BF16}
 
 ERRORS = {
     -1: "FE_ERR_INVALID_ARG", -2: "FE_ERR_CUDA", -3: "FE_ERR_OOM", -4: "FE_ERR_NEG_JACOBIAN",
-    -5: "FE_ERR_TIMEOUT", -6: "FE_ERR_UNSUPPORTED",
+    -5: "FE_ERR_TIMEOUT", -6: "FE_ERR_UNSUPPORTED", -7: "FE_ERR_NOT_CONVERGED",
 }
 
 # every entry point declared in include/feasm.h
@@ -32,6 +32,7 @@ EXPORTS = [
     "fe_batch_assemble", "fe_batch_destroy", "fe_space_dof_points_host", "fe_dirichlet_create", "fe_dirichlet_sizes",
     "fe_dirichlet_labels_host", "fe_dirichlet_csr_pattern_host", "fe_dirichlet_csr_pattern",
     "fe_dirichlet_permutation_host", "fe_dirichlet_lift_host", "fe_assemble_dirichlet", "fe_dirichlet_destroy",
+    "fe_compliance_work_size", "fe_compliance",
 ]
 _VOID = ("fe_space_destroy", "fe_last_error", "fe_batch_destroy", "fe_dirichlet_destroy")
 
@@ -89,6 +90,8 @@ def lib() -> ctypes.CDLL:
         L.fe_dirichlet_permutation_host.argtypes = [V, V, V, V, V, V, V, V]
         L.fe_dirichlet_lift_host.argtypes = [V, P(I64), P(I64), V, V, V, V]
         L.fe_assemble_dirichlet.argtypes = [V, V, V, V, V, V, I, V]
+        L.fe_compliance_work_size.argtypes = [V, P(I64)]
+        L.fe_compliance.argtypes = [V, V, V, I, D, I, V, V, V, V, P(I), P(D), V]
         L.fe_dirichlet_destroy.argtypes = [V]
         L.fe_dirichlet_destroy.restype = None
         for n in EXPORTS:
@@ -339,6 +342,23 @@ def fe_dirichlet_destroy(d: int):
     lib().fe_dirichlet_destroy(d)
 
 
+def fe_compliance_work_size(d: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().fe_compliance_work_size(d, ctypes.byref(n)), "fe_compliance_work_size")
+    return n.value
+
+
+def fe_compliance(d: int, coefficients, body_force, prec: int, rtol: float, max_iter: int, work, u, compliance,
+                  dc_dcoef, stream=None):
+    """Returns (iterations, relative residual)."""
+    f = np.ascontiguousarray(np.resize(np.asarray(body_force, dtype=np.float64), 3))
+    it, rel = ctypes.c_int(), ctypes.c_double()
+    _check(lib().fe_compliance(d, _ptr(coefficients), f.ctypes.data, prec, float(rtol), int(max_iter), _ptr(work),
+                               _ptr(u), _ptr(compliance), _ptr(dc_dcoef), ctypes.byref(it), ctypes.byref(rel),
+                               _stream(stream)), "fe_compliance")
+    return it.value, rel.value
+
+
 class DirichletSystem:
     """The constrained system of an FESpace with the DOFs of `fixed` prescribed
     (strong Dirichlet conditions). Keeps its space alive."""
@@ -370,6 +390,20 @@ class DirichletSystem:
         fe_assemble_dirichlet(self.handle, coef, self.space.prob.force if force is None else force, u_fixed,
                               values, rhs, PRECISIONS[prec], stream)
         return values, rhs
+
+    def compliance(self, coef, prec: str = "fp64", rtol: float = 1e-10, max_iter: int = 20000, force=None,
+                   gradient: bool = True, stream=None):
+        """(u over all DOFs, c, dc/dcoef or None, iterations, relative residual) of the
+        clamped structure (fixed DOFs at zero) under its body force."""
+        import torch
+        dev = coef.device
+        work = torch.empty(fe_compliance_work_size(self.handle), dtype=torch.float64, device=dev)
+        u = torch.empty(self.space.n_dofs, dtype=torch.float64, device=dev)
+        c = torch.empty(1, dtype=torch.float64, device=dev)
+        g = torch.empty(self.space.n_cells, dtype=torch.float64, device=dev) if gradient else None
+        it, rel = fe_compliance(self.handle, coef, self.space.prob.force if force is None else force,
+                                PRECISIONS[prec], rtol, max_iter, work, u, c, g, stream)
+        return u, c, g, it, rel
 
     def close(self):
         if self.handle:
