@@ -50,6 +50,9 @@ def parse():
                     help="also time the 128^3 Q1 elasticity assembly and the 64^3 cantilever adjoint")
     ap.add_argument("--batched", action="store_true",
                     help="also time the 64-mesh batched assembly (host setup takes minutes)")
+    ap.add_argument("--extra", action="append", default=None,
+                    help="time only this secondary workload (repeatable): elasticity_q2_beam_clamped, "
+                         "cantilever_q1_64_compliance, elasticity_q1_128, cantilever_q1_64_adjoint")
     return ap.parse_args()
 
 
@@ -328,13 +331,78 @@ def clamped_beam(dev, stream):
     return out
 
 
-def extra_workloads(args, dev, stream):
-    """Secondary measurements: the clamped Q2 beam (strong Dirichlet conditions), the
-    scatter-bound 128^3 Q1 elasticity assembly, the 64^3 Q1 cantilever compliance
-    adjoint and (optionally) the batched assembly."""
+def cantilever_compliance(dev, stream):
+    """The 64^3 Q1 cantilever clamped at x = 0 under its body force: fe_compliance
+    (assembly of the constrained system, Jacobi PCG in FP64 to ||r|| <= 1e-8 ||f||,
+    c and dc/dE). Per-iteration time = (call - assembly - gradient) / iterations,
+    against the algorithmic bytes of one iteration (compulsory traffic, below)."""
     import torch
     from paper_1708_01773_gb300 import feasm, inputs
-    out = {"elasticity_q2_beam_clamped": clamped_beam(dev, stream)}
+    prob = inputs.cantilever_q1_64()
+    sp = feasm.FESpace(prob)
+    fixed = np.abs(sp.dof_points()[:, 0]) < 1e-12
+    dsys = sp.dirichlet(fixed)
+    coef = torch.tensor(prob.coef, device=dev)
+    work = torch.empty(feasm.fe_compliance_work_size(dsys.handle), dtype=torch.float64, device=dev)
+    u = torch.empty(sp.n_dofs, dtype=torch.float64, device=dev)
+    c = torch.empty(1, dtype=torch.float64, device=dev)
+    g = torch.empty(sp.n_cells, dtype=torch.float64, device=dev)
+    vals = torch.empty(dsys.nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(dsys.n_free, dtype=torch.float64, device=dev)
+    n, nnz = dsys.n_free, dsys.nnz
+    # compulsory bytes: SpMV values + columns, row pointers, p read, q written (p's
+    # gathers hit the L2: 6.5 MB); update reads x, p, q, r, D^-1 and writes x, r, z;
+    # the p update reads z, p and writes p
+    iter_bytes = nnz * (8 + 4) + n * 8 * (3 + 8 + 3)
+    rec = {}
+    for prec in ("fp32", "fp64"):
+        pr = feasm.PRECISIONS[prec]
+        it_rel = [None]
+
+        def call():
+            it_rel[0] = feasm.fe_compliance(dsys.handle, coef, prob.force, pr, 1e-8, 100000, work, u, c, g, stream)
+        t_call = time_events(call, 3, stream)
+        t_asm = time_events(lambda: feasm.fe_assemble_dirichlet(dsys.handle, coef, prob.force, None, vals, rhs, pr,
+                                                                stream), 10, stream)
+        pa = feasm.PRECISIONS["fp64" if prec == "fp64" else "fp32"]
+        t_adj = time_events(lambda: feasm.fe_assemble_adjoint(sp.handle, u, coef, -1.0, g, None, pa, stream), 10,
+                            stream)
+        it, rel = it_rel[0]
+        t_it = (t_call - t_asm - t_adj) / it
+        rec[prec] = {"ms_per_call": t_call, "cells_per_s": sp.n_cells / (t_call / 1e3), "iterations": it,
+                     "rel_residual": rel, "assembly_ms": t_asm, "gradient_ms": t_adj, "ms_per_iteration": t_it,
+                     "iteration_algorithmic_bytes": int(iter_bytes),
+                     "iteration_gbs": iter_bytes / (t_it / 1e3) / 1e9, "compliance": float(c)}
+    out = {"cells": sp.n_cells, "n_free": n, "nnz": nnz, **rec}
+    dsys.close()
+    sp.close()
+    return out
+
+
+def extra_workloads(args, dev, stream):
+    """Secondary measurements (all, or those named by --extra): the clamped Q2 beam
+    (strong Dirichlet conditions), the clamped cantilever's self-adjoint compliance
+    solve, the scatter-bound 128^3 Q1 elasticity assembly, the 64^3 Q1 cantilever
+    compliance adjoint and (with --batched) the batched assembly."""
+    want = (lambda name: args.extra is None or name in args.extra)
+    out = {}
+    if want("elasticity_q2_beam_clamped"):
+        out["elasticity_q2_beam_clamped"] = clamped_beam(dev, stream)
+    if want("cantilever_q1_64_compliance"):
+        out["cantilever_q1_64_compliance"] = cantilever_compliance(dev, stream)
+    if want("elasticity_q1_128"):
+        out["elasticity_q1_128"] = q1_128(dev, stream)
+    if want("cantilever_q1_64_adjoint"):
+        out["cantilever_q1_64_adjoint"] = adjoint_64(dev, stream)
+    if args.batched:
+        out["batched64"] = batched(dev, stream)
+    return out
+
+
+def q1_128(dev, stream):
+    """The scatter-bound 128^3 Q1 elasticity assembly, FP32 and FP64 forms."""
+    import torch
+    from paper_1708_01773_gb300 import feasm, inputs
     prob = inputs.elasticity_q1_128()
     sp = feasm.FESpace(prob)
     coef = torch.tensor(prob.coef, device=dev)
@@ -346,9 +414,14 @@ def extra_workloads(args, dev, stream):
                                                    stream), 10, stream)
         rec[prec] = {"ms_per_step": ms, "cells_per_s": sp.n_cells / (ms / 1e3), "nnz_per_s": sp.nnz / (ms / 1e3),
                      **split_kernels(sp, coef, prob.force, vals, rhs, prec, stream)}
-    out["elasticity_q1_128"] = {"cells": sp.n_cells, "nnz": sp.nnz, **rec}
     sp.close()
-    del vals, rhs
+    return {"cells": sp.n_cells, "nnz": sp.nnz, **rec}
+
+
+def adjoint_64(dev, stream):
+    """The compliance adjoint on the 64^3 Q1 cantilever for a fixed seeded u."""
+    import torch
+    from paper_1708_01773_gb300 import feasm, inputs
     prob = inputs.cantilever_q1_64()
     sp = feasm.FESpace(prob)
     u = torch.tensor(inputs.unit_rms_field(sp.n_dofs, inputs.SEED_BASE + 5), device=dev)
@@ -360,30 +433,34 @@ def extra_workloads(args, dev, stream):
         ms = time_events(lambda: feasm.fe_assemble_adjoint(sp.handle, u, E, 1.0, g, c, feasm.PRECISIONS[prec],
                                                            stream), 20, stream)
         rec[prec] = {"ms_per_call": ms, "cells_per_s": sp.n_cells / (ms / 1e3)}
-    out["cantilever_q1_64_adjoint"] = {"cells": sp.n_cells, **rec}
     sp.close()
-    if args.batched:
-        probs = inputs.batched64()
-        t0 = time.perf_counter()
-        spaces = [feasm.FESpace(p) for p in probs]
-        setup = time.perf_counter() - t0
-        coefs = [torch.tensor(p.coef, device=dev) for p in probs]
-        vals = [torch.empty(s.nnz, dtype=torch.float64, device=dev) for s in spaces]
-        rhss = [torch.empty(s.n_dofs, dtype=torch.float64, device=dev) for s in spaces]
-        cells = sum(s.n_cells for s in spaces)
-        nnz = sum(s.nnz for s in spaces)
-        rec = {}
-        for prec in ("fp32", "fp64"):
-            b = feasm.fe_batch_create([s.handle for s in spaces])
-            ms = time_events(lambda: feasm.fe_batch_assemble(b, coefs, [p.force for p in probs], vals, rhss,
-                                                             feasm.PRECISIONS[prec], stream), 3, stream)
-            rec[prec] = {"ms_per_step": ms, "cells_per_s": cells / (ms / 1e3), "nnz_per_s": nnz / (ms / 1e3)}
-            feasm.fe_batch_destroy(b)
-        out["batched64"] = {"meshes": len(probs), "cells": cells, "nnz": nnz, "setup_s": setup,
-                            "redraw_attempt": probs[0].extra.get("attempt"), **rec}
-        for s in spaces:
-            s.close()
-    return out
+    return {"cells": sp.n_cells, **rec}
+
+
+def batched(dev, stream):
+    """The 64-mesh batched assembly (one persistent launch in a CUDA graph)."""
+    import torch
+    from paper_1708_01773_gb300 import feasm, inputs
+    probs = inputs.batched64()
+    t0 = time.perf_counter()
+    spaces = [feasm.FESpace(p) for p in probs]
+    setup = time.perf_counter() - t0
+    coefs = [torch.tensor(p.coef, device=dev) for p in probs]
+    vals = [torch.empty(s.nnz, dtype=torch.float64, device=dev) for s in spaces]
+    rhss = [torch.empty(s.n_dofs, dtype=torch.float64, device=dev) for s in spaces]
+    cells = sum(s.n_cells for s in spaces)
+    nnz = sum(s.nnz for s in spaces)
+    rec = {}
+    for prec in ("fp32", "fp64"):
+        b = feasm.fe_batch_create([s.handle for s in spaces])
+        ms = time_events(lambda: feasm.fe_batch_assemble(b, coefs, [p.force for p in probs], vals, rhss,
+                                                         feasm.PRECISIONS[prec], stream), 3, stream)
+        rec[prec] = {"ms_per_step": ms, "cells_per_s": cells / (ms / 1e3), "nnz_per_s": nnz / (ms / 1e3)}
+        feasm.fe_batch_destroy(b)
+    for s in spaces:
+        s.close()
+    return {"meshes": len(probs), "cells": cells, "nnz": nnz, "setup_s": setup,
+            "redraw_attempt": probs[0].extra.get("attempt"), **rec}
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -497,7 +574,7 @@ def main():
             "frac": kernels[dom]["frac"], "traffic": kernel_traffic(dom),
             "algorithmic_bytes": kernels[dom]["bytes"], "peak_source": peak_src + " (burst copy)"}
 
-    extras = extra_workloads(args, dev, stream) if (args.extras or args.batched) else None
+    extras = extra_workloads(args, dev, stream) if (args.extras or args.batched or args.extra) else None
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:

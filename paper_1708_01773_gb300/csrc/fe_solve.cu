@@ -6,7 +6,7 @@
 // every reduction in a fixed order (the result is deterministic on any GPU).
 //
 // One PCG iteration is three kernels:
-//   k_spmv_dot  q = A p (one warp per row), block partials of p.q
+//   k_spmv_dot  q = A p (G lanes per row), block partials of p.q
 //   k_update    alpha = rz / sum(p.q partials), summed by every block in the
 //               same fixed order; x += alpha p, r -= alpha q, z = D^-1 r;
 //               block partials of r.z and r.r
@@ -125,21 +125,48 @@ __global__ void k_cg_init_sums(CgParams p) {
   }
 }
 
-// q = A p, one warp per row (lanes stride the row, fixed xor butterfly), and
-// the block partials of p.q.
+// q = A p and the block partials of p.q. GB300 issues FP64 at 2 lanes per
+// clock per SM and charges a warp instruction in full whatever its active
+// lanes, so the kernel packs its FP64 work: a group of G lanes takes one row
+// (a warp 32/G consecutive rows), each lane summing every G-th nonzero of the
+// row (loads of 4 nonzeros in flight per lane), then a log2(G)-step xor
+// butterfly within the group. One warp per row would spend 3 multiply-add
+// rounds, 5 butterfly adds and a multiply per 81-entry row; G = 4 spends 21
+// rounds, 2 adds and one multiply per 8 rows. Fixed summation order
+// (deterministic).
+template <int G>
 __global__ void __launch_bounds__(kBlock) k_spmv_dot(CgParams p) {
   __shared__ double sh[kBlock / 32];
-  const int lane = threadIdx.x & 31;
+  constexpr int RPW = 32 / G;  // rows per warp pass
+  constexpr int U = 4;         // loads in flight per lane
+  const int lane = threadIdx.x & 31, j = lane % G, slot = lane / G;
   const int64_t w0 = (int64_t(blockIdx.x) * kBlock + threadIdx.x) >> 5;
   const int64_t nw = (int64_t(gridDim.x) * kBlock) >> 5;
   double pq = 0.0;
-  for (int64_t i = w0; i < p.n; i += nw) {
-    const int64_t k0 = p.row_ptr[i], k1 = p.row_ptr[i + 1];
+  for (int64_t base = w0 * RPW; base < p.n; base += nw * RPW) {
+    const int64_t i = base + slot;
+    int64_t k0 = 0, k1 = 0;
+    if (i < p.n) {
+      k0 = p.row_ptr[i];
+      k1 = p.row_ptr[i + 1];
+    }
     double acc = 0.0;
-    for (int64_t k = k0 + lane; k < k1; k += 32) acc = fma(__ldg(p.val + k), __ldg(p.p + __ldg(p.col + k)), acc);
+    for (int64_t k = k0 + j; k < k1; k += G * U) {
+      double v[U];
+      int c[U];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-    if (lane == 0) {
+      for (int t = 0; t < U; ++t) {
+        const int64_t kk = k + int64_t(t) * G;
+        v[t] = kk < k1 ? __ldg(p.val + kk) : 0.0;
+        c[t] = kk < k1 ? __ldg(p.col + kk) : 0;
+      }
+      // past the row's end v = 0 and c = 0: the multiply-add adds an exact zero
+#pragma unroll
+      for (int t = 0; t < U; ++t) acc = fma(v[t], __ldg(p.p + c[t]), acc);
+    }
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+    if (j == 0 && i < p.n) {
       p.q[i] = acc;
       pq += p.p[i] * acc;
     }
@@ -269,11 +296,15 @@ int compliance_solve(const ComplianceArgs& a, cudaStream_t st) {
     if (flag & kFlagNotSpd) return set_error(FE_ERR_INVALID_ARG, "compliance: a diagonal entry is not positive");
     int it = 0;
     double rel = 0.0;
+    const int64_t avg_row = a.nnz / n;  // lanes per row of the SpMV: 4 up to 128 nonzeros per row, else 8
     if (bb > 0.0) {
       rel = 1.0;
       while (it < a.max_iter && rel > a.rtol) {
         for (int j = 0; j < kCheckEvery && it < a.max_iter; ++j, ++it) {
-          k_spmv_dot<<<kGridBlocks, kBlock, 0, st>>>(p);
+          if (avg_row <= 128)
+            k_spmv_dot<4><<<kGridBlocks, kBlock, 0, st>>>(p);
+          else
+            k_spmv_dot<8><<<kGridBlocks, kBlock, 0, st>>>(p);
           k_update<<<kGridBlocks, kBlock, 0, st>>>(p, it & 1);
           k_pupdate<<<kGridBlocks, kBlock, 0, st>>>(p, it & 1);
         }
