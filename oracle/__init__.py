@@ -90,10 +90,15 @@ def lagrange_1d(p: int, x: float):
     return v, d
 
 
+def _n_local(problem: int, p: int) -> int:
+    if problem == 2:                        # Taylor-Hood: 3 (p+1)^3 velocity + p^3 pressure
+        return 3 * (p + 1) ** 3 + p ** 3
+    return (3 if problem == 1 else 1) * (p + 1) ** 3
+
+
 def cell_matrix(problem: int, p: int, nq1d: int, xv, coef: float, nu: float, force):
     """Cell matrix and vector of one hexahedron given its 8 vertices [8,3]."""
-    ncomp = 3 if problem == 1 else 1
-    nl = ncomp * (p + 1) ** 3
+    nl = _n_local(problem, p)
     Ke = np.zeros(nl * nl)
     fe = np.zeros(nl)
     f = _c(np.resize(np.asarray(force, dtype=np.float64), 3), np.float64)
@@ -118,6 +123,25 @@ def dof_numbering(mesh, p: int, ncomp: int):
     return cd, int(n)
 
 
+def stokes_dof_numbering(mesh, p: int):
+    """Taylor-Hood Q_p/Q_{p-1} space: the velocity field numbered by list_dofs,
+    then the pressure field by list_dofs, offset by the number of velocity DOFs
+    (the block layout of Sect. "The FE affine operator abstraction" with the
+    velocity block first). Returns (cell_dofs [cells][3 (p+1)^3 + p^3], n_dofs,
+    n_velocity)."""
+    cd_v, nv = dof_numbering(mesh, p, 3)
+    cd_p, npr = dof_numbering(mesh, p - 1, 1)
+    return np.hstack([cd_v, cd_p + nv]).astype(np.int32), nv + npr, nv
+
+
+def numbering(prob):
+    """(cell_dofs, n_dofs) of a workload's space."""
+    if prob.problem == 2:
+        cd, n, _ = stokes_dof_numbering(prob.mesh, prob.order)
+        return cd, n
+    return dof_numbering(prob.mesh, prob.order, prob.ncomp)
+
+
 def _force3(force):
     return _c(np.resize(np.asarray(force, dtype=np.float64), 3), np.float64)
 
@@ -127,7 +151,7 @@ def assemble_csr(prob, cell_dofs=None, n_dofs=None):
     L = lib()
     mesh = prob.mesh
     if cell_dofs is None:
-        cell_dofs, n_dofs = dof_numbering(mesh, prob.order, prob.ncomp)
+        cell_dofs, n_dofs = numbering(prob)
     cv = _c(mesh.cell_vertices, np.int32)
     xyz = _c(mesh.coords, np.float64).ravel()
     cd = _c(cell_dofs, np.int32).reshape(-1)
@@ -153,7 +177,7 @@ def assemble_rows(prob, rows, cell_dofs, n_dofs):
     L = lib()
     mesh = prob.mesh
     rows = _c(rows, np.int64)
-    nl = prob.ncomp * (prob.order + 1) ** 3
+    nl = _n_local(prob.problem, prob.order)
     cap = int(rows.size) * 8 * nl
     ptr = np.zeros(rows.size + 1, dtype=np.int64)
     col = np.zeros(cap, dtype=np.int32)

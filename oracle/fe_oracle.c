@@ -142,6 +142,8 @@ typedef struct {
   double phi[MAXNQ][MAXNB];
   double dphi[MAXNQ][MAXNB][3];
   double dN[MAXNQ][8][3]; /* trilinear geometry basis gradients */
+  int nbp;                 /* pressure basis Q_{p-1} (Taylor-Hood), p >= 2 */
+  double psi[MAXNQ][MAXNB];
 } ref_tables;
 
 static int make_tables(int p, int nq1d, ref_tables* T) {
@@ -164,8 +166,21 @@ static int make_tables(int p, int nq1d, ref_tables* T) {
         tp_basis(p, T->xq[q], T->phi[q], &T->dphi[q][0][0]);
         double gphi[8];
         tp_basis(1, T->xq[q], gphi, &T->dN[q][0][0]);
+        if (p >= 2) {
+          double dpsi[MAXNB][3];
+          tp_basis(p - 1, T->xq[q], T->psi[q], &dpsi[0][0]);
+        }
       }
+  T->nbp = p >= 2 ? p * p * p : 0;
   return OR_OK;
+}
+
+/* Local DOFs of a cell: Poisson nb, elasticity 3 nb, Stokes (Taylor-Hood
+ * Q_p velocity, Q_{p-1} pressure) 3 nb + p^3. */
+static int local_size(int problem, const ref_tables* T) {
+  if (problem == 1) return 3 * T->nb;
+  if (problem == 2) return 3 * T->nb + T->nbp;
+  return T->nb;
 }
 
 /* ------------------------------------------------------------------ */
@@ -287,10 +302,55 @@ static int cell_elasticity(const ref_tables* T, const double* xv, double E, doub
   return OR_OK;
 }
 
+/* Stokes (Example "Stokes problem"), Taylor-Hood: velocity u = phi_b e_j
+ * (Q_p, local index j*nb + b), pressure psi_c (Q_{p-1}, local index 3nb + c).
+ *   velocity-velocity  mu int eps(u) : eps(v)   (full 3x3 strain tensors)
+ *   velocity-pressure  - int (div v) p
+ *   pressure-velocity  - int q (div u)           (the symmetric reading)
+ *   pressure-pressure  0
+ * Right-hand side: int f . v on the velocity rows, 0 on the pressure rows. */
+static int cell_stokes(const ref_tables* T, const double* xv, double mu, const double* force, double* Ke,
+                       double* fe) {
+  int nb = T->nb, nbp = T->nbp, nv = 3 * nb, nl = nv + nbp;
+  if (nbp <= 0) return OR_ERR_ARG;
+  double g[MAXNB][3];
+  memset(Ke, 0, sizeof(double) * nl * nl);
+  memset(fe, 0, sizeof(double) * nl);
+  for (int q = 0; q < T->nq; ++q) {
+    double det = physical_gradients(T, q, xv, g);
+    if (!(det > 0.0)) return OR_ERR_NEG_JAC;
+    double dJw = det * T->w[q];
+    for (int j = 0; j < 3; ++j)
+      for (int b = 0; b < nb; ++b) {
+        double eu[3][3];
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) eu[k][l] = 0.5 * (((k == j) ? g[b][l] : 0.0) + ((l == j) ? g[b][k] : 0.0));
+        for (int i = 0; i < 3; ++i)
+          for (int a = 0; a < nb; ++a) {
+            double s = 0.0;
+            for (int k = 0; k < 3; ++k)
+              for (int l = 0; l < 3; ++l)
+                s += eu[k][l] * 0.5 * (((k == i) ? g[a][l] : 0.0) + ((l == i) ? g[a][k] : 0.0));
+            Ke[(i * nb + a) * nl + (j * nb + b)] += mu * s * dJw;
+          }
+        /* div(phi_b e_j) = d_j phi_b */
+        for (int c = 0; c < nbp; ++c) {
+          double bq = -T->psi[q][c] * g[b][j] * dJw;
+          Ke[(j * nb + b) * nl + (nv + c)] += bq;
+          Ke[(nv + c) * nl + (j * nb + b)] += bq;
+        }
+      }
+    for (int i = 0; i < 3; ++i)
+      for (int a = 0; a < nb; ++a) fe[i * nb + a] += force[i] * T->phi[q][a] * dJw;
+  }
+  return OR_OK;
+}
+
 static int cell_matrix_t(const ref_tables* T, int problem, const double* xv, double coef, double nu,
                          const double* force, double* Ke, double* fe) {
   if (problem == 0) return cell_poisson(T, xv, coef, force[0], Ke, fe);
   if (problem == 1) return cell_elasticity(T, xv, coef, nu, force, Ke, fe);
+  if (problem == 2) return cell_stokes(T, xv, coef, force, Ke, fe);
   return OR_ERR_ARG;
 }
 
@@ -517,12 +577,11 @@ int64_t or_assemble_csr(int problem, int p, int nq1d, int64_t n_cells, const int
                         const double* coords, const int32_t* cell_dofs, int64_t n_dofs,
                         const double* coef, double nu, const double* force,
                         int64_t* row_ptr, int32_t* col_idx, double* values, double* rhs) {
-  int ncomp = problem == 1 ? 3 : 1;
   ref_tables* T = (ref_tables*)malloc(sizeof(ref_tables));
   if (!T) return OR_ERR_OOM;
   int rc = make_tables(p, nq1d, T);
   if (rc) { free(T); return rc; }
-  int nl = ncomp * T->nb;
+  int nl = local_size(problem, T);
   int64_t ncoo = n_cells * (int64_t)nl * nl;
   coo_t* coo = (coo_t*)malloc(sizeof(coo_t) * (ncoo > 0 ? ncoo : 1));
   double* Ke = (double*)malloc(sizeof(double) * nl * nl);
@@ -587,12 +646,11 @@ int64_t or_assemble_rows(int problem, int p, int nq1d, int64_t n_cells, const in
                          const double* coef, double nu, const double* force,
                          int64_t n_req, const int64_t* rows, int64_t cap,
                          int64_t* out_ptr, int32_t* out_col, double* out_val, double* out_rhs) {
-  int ncomp = problem == 1 ? 3 : 1;
   ref_tables* T = (ref_tables*)malloc(sizeof(ref_tables));
   if (!T) return OR_ERR_OOM;
   int rc = make_tables(p, nq1d, T);
   if (rc) { free(T); return rc; }
-  int nl = ncomp * T->nb;
+  int nl = local_size(problem, T);
   /* DOF -> (cell, local) incidence, cells ascending, by counting sort */
   int64_t ninc = n_cells * nl;
   int64_t* ptr = (int64_t*)calloc((size_t)(n_dofs + 1), sizeof(int64_t));
@@ -651,12 +709,11 @@ done:
  * A is linear in the cell coefficients (Eq. assembly). */
 int or_cell_energies(int problem, int p, int nq1d, int64_t n_cells, const int32_t* cell_vertices,
                      const double* coords, const int32_t* cell_dofs, double nu, const double* u, double* g) {
-  int ncomp = problem == 1 ? 3 : 1;
   ref_tables* T = (ref_tables*)malloc(sizeof(ref_tables));
   if (!T) return OR_ERR_OOM;
   int rc = make_tables(p, nq1d, T);
   if (rc) { free(T); return rc; }
-  int nl = ncomp * T->nb;
+  int nl = local_size(problem, T);
   double* Ke = (double*)malloc(sizeof(double) * nl * nl);
   double* fe = (double*)malloc(sizeof(double) * nl);
   double zero[3] = {0.0, 0.0, 0.0};

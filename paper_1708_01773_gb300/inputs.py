@@ -25,6 +25,8 @@ problems, all synthetic):
   redrawn while the estimated GPU footprint exceeds half of the GPU memory.
 * ``cantilever_q1_64`` Elasticity Q1, 64^3 cells of the unit cube, E ~ U[0.1,1],
   nu = 0.3, shifts up to 0.2h, u ~ N(0,1) per DOF rescaled to unit RMS.
+* ``stokes_q2q1_32``   Stokes, Taylor-Hood Q2/Q1, 32^3 cells of the unit cube,
+  shifts up to 0.15h, viscosity mu ~ U[0.5, 2], f = (0, 0, -1), 3^3 Gauss.
 """
 from __future__ import annotations
 
@@ -36,6 +38,7 @@ SEED_BASE = 20171773
 
 POISSON = 0
 ELASTICITY = 1
+STOKES = 2        # Taylor-Hood: velocity Q_p (3 components), pressure Q_{p-1}
 
 
 @dataclass
@@ -64,15 +67,22 @@ class Problem:
     mesh: Mesh
     order: int
     quad_1d: int
-    problem: int                 # POISSON or ELASTICITY
-    coef: np.ndarray             # [n_cells] float64 (kappa_K or E_K)
+    problem: int                 # POISSON, ELASTICITY or STOKES
+    coef: np.ndarray             # [n_cells] float64 (kappa_K, E_K or the viscosity mu_K)
     force: np.ndarray            # [ncomp] float64, constant body force / source
     nu: float = 0.3
     extra: dict = field(default_factory=dict)
 
     @property
     def ncomp(self) -> int:
-        return 3 if self.problem == ELASTICITY else 1
+        """Components of the (velocity) field."""
+        return 1 if self.problem == POISSON else 3
+
+    @property
+    def n_local(self) -> int:
+        """Local DOFs of a cell: ncomp (p+1)^3, plus p^3 pressure nodes for Stokes."""
+        n = self.ncomp * (self.order + 1) ** 3
+        return n + self.order ** 3 if self.problem == STOKES else n
 
 
 def brick(nx: int, ny: int, nz: int, lx: float = 1.0, ly: float = 1.0, lz: float = 1.0) -> Mesh:
@@ -206,6 +216,13 @@ def cantilever_q1_64(n: int = 64, seed_offset: int = 5) -> Problem:
     return Problem("cantilever_q1_64", mesh, 1, 2, ELASTICITY, coef, np.array([0.0, 0.0, -1.0]))
 
 
+def stokes_q2q1_32(n: int = 32, seed_offset: int = 6) -> Problem:
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    mesh = perturb_interior(brick(n, n, n), 0.15, rng)
+    coef = rng.uniform(0.5, 2.0, size=mesh.n_cells)
+    return Problem("stokes_q2q1_32", mesh, 2, 3, STOKES, coef, np.array([0.0, 0.0, -1.0]))
+
+
 def unit_rms_field(n_dofs: int, seed: int) -> np.ndarray:
     """u_i ~ N(0,1) i.i.d., rescaled so that sqrt(mean(u^2)) = 1."""
     rng = np.random.default_rng(seed)
@@ -221,6 +238,9 @@ def small_problem(n: tuple, order: int, problem: int, alpha: float = 0.2, seed: 
     if problem == POISSON:
         coef = _log_uniform(rng, 0.1, 10.0, mesh.n_cells)
         force = np.array([1.0])
+    elif problem == STOKES:
+        coef = rng.uniform(0.5, 2.0, size=mesh.n_cells)
+        force = np.array([0.3, -0.2, -1.0])
     else:
         coef = rng.uniform(1.0, 10.0, size=mesh.n_cells)
         force = np.array([0.0, 0.0, -1.0])
@@ -232,4 +252,5 @@ WORKLOADS = {
     "elasticity_q2_beam": elasticity_q2_beam,
     "elasticity_q1_128": elasticity_q1_128,
     "cantilever_q1_64": cantilever_q1_64,
+    "stokes_q2q1_32": stokes_q2q1_32,
 }

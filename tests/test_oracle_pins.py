@@ -274,6 +274,27 @@ def numpy_cell_matrix(problem, p, nq1d, xv, coef, nu):
     nb = n1 ** 3
     if problem == 0:
         return coef * (Gm[0, 0] + Gm[1, 1] + Gm[2, 2])
+    if problem == 2:
+        # Taylor-Hood: mu eps:eps = mu/2 (delta_ij tr G + G^{ji}); pressure Q_{p-1}
+        # on the nodes k/(p-1); coupling -int psi_c d_j phi_b in both off-diagonal blocks
+        nbp = p ** 3
+        pn = np.arange(p) / (p - 1)
+        Vp = np.ones((nq1d, p))
+        for m in range(p):
+            for s_ in range(p):
+                if s_ != m:
+                    Vp[:, m] *= (x1 - pn[s_]) / (pn[m] - pn[s_])
+        pi = np.array(list(itertools.product(range(p), repeat=3)))[:, ::-1]
+        psi = Vp[qi[:, 0]][:, pi[:, 0]] * Vp[qi[:, 1]][:, pi[:, 1]] * Vp[qi[:, 2]][:, pi[:, 2]]
+        K = np.zeros((3 * nb + nbp, 3 * nb + nbp))
+        tr = Gm[0, 0] + Gm[1, 1] + Gm[2, 2]
+        for i in range(3):
+            for j in range(3):
+                K[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb] = 0.5 * coef * (Gm[j, i] + (tr if i == j else 0))
+        Bm = -np.einsum("q,qc,qbj->cjb", c, psi, g).reshape(nbp, 3 * nb)
+        K[3 * nb:, :3 * nb] = Bm
+        K[:3 * nb, 3 * nb:] = Bm.T
+        return K
     lh, mh = lame_hat(nu)
     K = np.zeros((3 * nb, 3 * nb))
     tr = Gm[0, 0] + Gm[1, 1] + Gm[2, 2]
@@ -656,3 +677,89 @@ def test_compliance_of_a_bar_in_tension_closed_form():
     np.testing.assert_allclose(u[comp == 0], exact_u[comp == 0], rtol=0, atol=1e-12)
     assert np.abs(u[comp != 0]).max() < 1e-12
     assert abs(c - b * b * L ** 3 / (3 * E)) <= 1e-12 * c
+
+
+
+# ---------------------------------------------------------------- Stokes (Taylor-Hood)
+@pytest.mark.parametrize("p", [2, 3])
+def test_stokes_cell_vs_numpy_brute_force(p):
+    """A distorted Taylor-Hood cell against the numpy Gram-block implementation."""
+    rng = np.random.default_rng(130 + p)
+    xv = UNIT * np.array([1.1, 0.8, 1.2]) + 0.15 * rng.uniform(-1, 1, (8, 3))
+    K, fe = oracle.cell_matrix(2, p, p + 1, xv, 1.7, 0.0, [0.2, -0.5, 1.0])
+    Kn = numpy_cell_matrix(2, p, p + 1, xv, 1.7, 0.0)
+    np.testing.assert_allclose(K, Kn, rtol=0, atol=1e-13 * np.abs(Kn).max())
+    nv = 3 * (p + 1) ** 3
+    assert np.all(K[nv:, nv:] == 0) and np.all(fe[nv:] == 0)
+
+
+def stokes_system(shape=(3, 2, 2), p=2, seed=140, mu=None):
+    prob = inputs.small_problem(shape, p, inputs.STOKES, seed=seed)
+    if mu is not None:
+        prob.coef[:] = mu
+    cd, n, nv = oracle.stokes_dof_numbering(prob.mesh, p)
+    rp, col, val, rhs = oracle.assemble_csr(prob, cd, n)
+    A = csr_to_dense(rp, col, val, n)
+    return prob, cd, n, nv, A, rhs
+
+
+def stokes_positions(prob, cd, n, nv):
+    """Node position and component of every velocity DOF, position of every
+    pressure DOF (independent numpy evaluation of the trilinear map)."""
+    p = prob.order
+    nb = (p + 1) ** 3
+    vel = inputs.Problem("v", prob.mesh, p, p + 1, 1, prob.coef, prob.force)
+    pos_v, comp = node_positions(vel, cd[:, :3 * nb], nv)
+    pre = inputs.Problem("q", prob.mesh, p - 1, p, 0, prob.coef, prob.force)
+    pos_p, _ = node_positions(pre, cd[:, 3 * nb:] - nv, n - nv)
+    return pos_v, comp, pos_p
+
+
+def test_stokes_assembled_invariants():
+    """Symmetric (the symmetric reading), zero pressure-pressure block, the six rigid
+    velocity modes in the kernel of every row, a constant pressure orthogonal to the
+    interior velocity rows and summing to zero per component, and the body force on
+    the velocity rows only."""
+    prob, cd, n, nv, A, rhs = stokes_system()
+    sc = np.abs(A).max()
+    assert np.abs(A - A.T).max() <= 1e-15 * sc
+    assert np.all(A[nv:, nv:] == 0)
+    pos_v, comp, pos_p = stokes_positions(prob, cd, n, nv)
+    for c in range(3):
+        t = np.zeros(n); t[:nv][comp == c] = 1.0
+        assert np.abs(A @ t).max() <= 1e-12 * sc
+    for w in np.eye(3):
+        r = np.zeros(n)
+        disp = np.cross(w[None, :], pos_v)
+        r[:nv] = disp[np.arange(nv), comp]
+        assert np.abs(A @ r).max() <= 1e-12 * sc
+    one_p = np.zeros(n); one_p[nv:] = 1.0
+    bt = (A @ one_p)[:nv]
+    interior = ~boundary_dofs(pos_v)
+    assert np.abs(bt[interior]).max() <= 1e-12 * sc
+    for c in range(3):
+        assert abs(bt[comp == c].sum()) <= 1e-12 * sc
+    vol = 1.0
+    f = prob.force
+    for c in range(3):
+        assert abs(rhs[:nv][comp == c].sum() - f[c] * vol) <= 1e-13
+    assert np.all(rhs[nv:] == 0)
+
+
+def test_stokes_linear_velocity_closed_forms():
+    """u = Bx + t, zero pressure, constant viscosity mu: the pressure rows give
+    -tr(B) int psi_c, summing to -tr(B) vol; the interior velocity rows vanish
+    (constant strain); u^T A u = mu |sym B|^2 vol."""
+    mu = 1.3
+    prob, cd, n, nv, A, rhs = stokes_system(mu=mu, seed=141)
+    pos_v, comp, pos_p = stokes_positions(prob, cd, n, nv)
+    Bm = np.array([[0.3, -0.2, 0.1], [0.4, -0.5, 0.2], [-0.1, 0.25, 0.6]])
+    disp = pos_v @ Bm.T + np.array([0.1, 0.2, -0.3])
+    u = np.zeros(n)
+    u[:nv] = disp[np.arange(nv), comp]
+    r = A @ u
+    vol = 1.0
+    assert abs(r[nv:].sum() + np.trace(Bm) * vol) <= 1e-12
+    assert np.abs(r[:nv][~boundary_dofs(pos_v)]).max() <= 1e-11 * np.abs(A).max()
+    sym = 0.5 * (Bm + Bm.T)
+    assert abs(u @ r - mu * np.sum(sym * sym) * vol) <= 1e-12 * mu * np.sum(sym * sym)
