@@ -52,7 +52,8 @@ def parse():
                     help="also time the 64-mesh batched assembly (host setup takes minutes)")
     ap.add_argument("--extra", action="append", default=None,
                     help="time only this secondary workload (repeatable): elasticity_q2_beam_clamped, "
-                         "cantilever_q1_64_compliance, elasticity_q1_128, cantilever_q1_64_adjoint")
+                         "cantilever_q1_64_compliance, stokes_q2q1_32, elasticity_q1_128, "
+                         "cantilever_q1_64_adjoint")
     return ap.parse_args()
 
 
@@ -382,7 +383,7 @@ def cantilever_compliance(dev, stream):
 def extra_workloads(args, dev, stream):
     """Secondary measurements (all, or those named by --extra): the clamped Q2 beam
     (strong Dirichlet conditions), the clamped cantilever's self-adjoint compliance
-    solve, the scatter-bound 128^3 Q1 elasticity assembly, the 64^3 Q1 cantilever
+    solve, the Stokes Taylor-Hood assembly, the scatter-bound 128^3 Q1 elasticity assembly, the 64^3 Q1 cantilever
     compliance adjoint and (with --batched) the batched assembly."""
     want = (lambda name: args.extra is None or name in args.extra)
     out = {}
@@ -390,6 +391,8 @@ def extra_workloads(args, dev, stream):
         out["elasticity_q2_beam_clamped"] = clamped_beam(dev, stream)
     if want("cantilever_q1_64_compliance"):
         out["cantilever_q1_64_compliance"] = cantilever_compliance(dev, stream)
+    if want("stokes_q2q1_32"):
+        out["stokes_q2q1_32"] = stokes_32(dev, stream)
     if want("elasticity_q1_128"):
         out["elasticity_q1_128"] = q1_128(dev, stream)
     if want("cantilever_q1_64_adjoint"):
@@ -397,6 +400,31 @@ def extra_workloads(args, dev, stream):
     if args.batched:
         out["batched64"] = batched(dev, stream)
     return out
+
+
+def stokes_32(dev, stream):
+    """Stokes, Taylor-Hood Q2/Q1 on 32^3 cells (the paper's driver workload),
+    FP32 and FP64 forms: step time, cell and scatter kernels, their algorithmic
+    bytes."""
+    import torch
+    from paper_1708_01773_gb300 import feasm, inputs
+    prob = inputs.stokes_q2q1_32()
+    sp = feasm.FESpace(prob)
+    coef = torch.tensor(prob.coef, device=dev)
+    vals = torch.empty(sp.nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(sp.n_dofs, dtype=torch.float64, device=dev)
+    rec = {}
+    for prec in ("fp32", "fp64"):
+        ms = time_events(lambda: feasm.fe_assemble(sp.handle, coef, prob.force, vals, rhs, feasm.PRECISIONS[prec],
+                                                   stream), 10, stream)
+        split = split_kernels(sp, coef, prob.force, vals, rhs, prec, stream)
+        sb, cb = scatter_bytes(sp, prec), cell_bytes(sp, prec)
+        rec[prec] = {"ms_per_step": ms, "cells_per_s": sp.n_cells / (ms / 1e3), "nnz_per_s": sp.nnz / (ms / 1e3),
+                     **split, "scatter_gbs": sb / (split["scatter_ms"] / 1e3) / 1e9,
+                     "cell_gbs": cb / (split["cell_ms"] / 1e3) / 1e9, "scatter_algorithmic_bytes": sb,
+                     "cell_algorithmic_bytes": cb}
+    sp.close()
+    return {"cells": sp.n_cells, "dofs": sp.n_dofs, "velocity_dofs": sp.n_first, "nnz": sp.nnz, **rec}
 
 
 def q1_128(dev, stream):

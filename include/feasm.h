@@ -40,7 +40,23 @@ extern "C" {
 typedef struct fe_space fe_space; /* opaque, library-owned */
 typedef struct fe_batch fe_batch; /* opaque, library-owned */
 
-typedef enum { FE_POISSON = 0, FE_ELASTICITY = 1 } fe_problem;
+/* FE_STOKES: the Taylor-Hood pair of the paper's Stokes driver (Example
+ * "Stokes problem", Sect. "Driver example for the Stokes problem"): velocity
+ * Q_p (3 components, p = order = 2 or 3) and pressure Q_{p-1}, with the
+ * (p+1)^3 Gauss rule; coefficients are the cell viscosities mu_K; the cell
+ * matrix is
+ *   velocity-velocity  mu int eps(u) : eps(v)
+ *   velocity-pressure  - int (div v) p,  pressure-velocity  - int q (div u)
+ *   pressure-pressure  0 (stored: every field pair is coupled, as by default
+ *                      in the paper's block layout)
+ * and the right-hand side int f . v on the velocity rows, 0 on the pressure
+ * rows. Local DOFs: the 3 nb velocity ones (i*nb + a), then the p^3 pressure
+ * ones. Global numbering: all velocity DOFs (list_dofs), then all pressure
+ * DOFs (list_dofs), so the matrix has the 2x2 block layout velocity/pressure
+ * with the split at fe_space_block_offset. FP64 and FP32 forms (BF16:
+ * FE_ERR_UNSUPPORTED); the adjoint, the compliance and the batch take
+ * Poisson and elasticity spaces only. */
+typedef enum { FE_POISSON = 0, FE_ELASTICITY = 1, FE_STOKES = 2 } fe_problem;
 
 /* Arithmetic of the cell-matrix contraction. The geometry (Jacobian,
  * determinant, cofactors) and the global CSR accumulation are always FP64.
@@ -74,10 +90,12 @@ typedef struct {
  * generation"), the CSR sparsity pattern (every DOF pair sharing a cell, columns
  * ascending; Sect. "Linear algebra": pattern built once and reused) and the
  * cell-to-nonzero assembly permutation used by fe_assemble.
- *   order           p in 1..3.
+ *   order           p in 1..3 (Stokes: the velocity order, 2 or 3).
  *   quad_points_1d  Gauss points per direction, 0 = p+1 (exact mass matrix on
  *                   affine cells), else 1..6.
- *   problem         FE_POISSON (1 component) or FE_ELASTICITY (3 components).
+ *   problem         FE_POISSON (1 component), FE_ELASTICITY (3 components) or
+ *                   FE_STOKES (Taylor-Hood, see fe_problem; quad_points_1d 0
+ *                   or p+1).
  *   nu              Poisson ratio (elasticity only, 0 <= nu < 0.5).
  *   out             receives the new space; destroy with fe_space_destroy.
  * Uses the current CUDA device. Host work is multi-threaded. Errors:
@@ -99,8 +117,13 @@ int fe_space_create_host(const fe_mesh_desc* mesh, int order, int quad_points_1d
 int fe_space_sizes(const fe_space* s, int64_t* n_dofs, int64_t* nnz, int64_t* n_cells,
                    int64_t* n_contrib);
 
+/* Number of DOFs of the first field: the velocity block of a Stokes space
+ * (pressure DOFs are n_first .. n_dofs-1); n_dofs for the other problems. */
+int fe_space_block_offset(const fe_space* s, int64_t* n_first);
+
 /* Copies the cell-to-DOF map [n_cells * n_loc] (host, int32, local order
- * i*nb + a) into caller memory (Sect. "Global DOF numbering generation"). */
+ * i*nb + a, then the pressure DOFs for Stokes) into caller memory (Sect.
+ * "Global DOF numbering generation"). */
 int fe_space_cell_dofs_host(const fe_space* s, int32_t* cell_dofs);
 
 /* Copies the CSR pattern into caller memory: row_ptr [n_dofs+1] int64 and

@@ -42,7 +42,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 void free_device(fe_space* s) {
   void* ptrs[] = {s->d_xv, s->d_w, s->d_xq, s->d_phi, s->d_dphi, s->d_dphi32, s->d_phi2, s->d_cell_dofs, s->d_row_ptr,
                   s->d_col, s->d_cnt, s->d_code_ptr, s->d_codes, s->d_pos, s->d_slot_ptr, s->d_slots, s->d_ke, s->d_fe,
-                  s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs, s->d_sched};
+                  s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs, s->d_sched, s->d_psi};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -57,7 +57,10 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
   if (order < 1 || order > feasm::kMaxOrder) return fail(FE_ERR_INVALID_ARG, "order must be 1..3");
   const int nq1d = quad_points_1d == 0 ? order + 1 : quad_points_1d;
   if (nq1d < 1 || nq1d > feasm::kMaxQ1d) return fail(FE_ERR_INVALID_ARG, "quad_points_1d must be 0 or 1..6");
-  if (problem != FE_POISSON && problem != FE_ELASTICITY) return fail(FE_ERR_INVALID_ARG, "unknown problem");
+  if (problem != FE_POISSON && problem != FE_ELASTICITY && problem != FE_STOKES)
+    return fail(FE_ERR_INVALID_ARG, "unknown problem");
+  if (problem == FE_STOKES && (order < 2 || nq1d != order + 1))
+    return fail(FE_ERR_UNSUPPORTED, "Stokes (Taylor-Hood) needs velocity order 2 or 3 and the (p+1)^3 rule");
   if (problem == FE_ELASTICITY && !(nu >= 0.0 && nu < 0.5)) return fail(FE_ERR_INVALID_ARG, "nu must be in [0, 0.5)");
   if (mesh->n_vertices > INT32_MAX) return fail(FE_ERR_UNSUPPORTED, "more than 2^31-1 vertices");
   fe_space* s = new (std::nothrow) fe_space();
@@ -65,7 +68,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
   s->order = order;
   s->nq1d = nq1d;
   s->problem = problem;
-  s->ncomp = problem == FE_ELASTICITY ? 3 : 1;
+  s->ncomp = problem == FE_POISSON ? 1 : 3;
   s->nu = nu;
   s->n_cells = mesh->n_cells;
   s->n_vertices = mesh->n_vertices;
@@ -73,12 +76,13 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
   feasm::build_ref_tables(order, nq1d, &s->tab);
   s->nb = s->tab.nb;
   s->nq = s->tab.nq;
-  s->nl = s->ncomp * s->nb;
+  s->nbp = problem == FE_STOKES ? order * order * order : 0;
+  s->nl = s->ncomp * s->nb + s->nbp;
   s->nlp = (s->nl + 3) & ~3;
   std::string err;
   int rc;
   try {
-    rc = feasm::build_host_setup(order, s->ncomp, mesh->n_cells, mesh->n_vertices, mesh->cell_vertices, &s->hs, &err);
+    rc = feasm::build_host_setup(order, problem, mesh->n_cells, mesh->n_vertices, mesh->cell_vertices, &s->hs, &err);
   } catch (const std::bad_alloc&) {
     rc = FE_ERR_OOM;
     err = "host allocation failed during setup";
@@ -89,8 +93,8 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
   }
   if (!host_only) {
     const int cpb = feasm::cells_per_block(s->nb, s->nq);
-    if (feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP64, cpb) < 0 ||
-        feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP32, cpb) < 0) {
+    if (problem != FE_STOKES && (feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP64, cpb) < 0 ||
+                                 feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP32, cpb) < 0)) {
       delete s;
       return fail(FE_ERR_UNSUPPORTED, "quadrature too large for one block at this order");
     }
@@ -118,6 +122,11 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     if (e == cudaSuccess) e = upload(&s->d_dphi, s->tab.dphi.data(), s->tab.dphi.size());
     if (e == cudaSuccess) e = upload(&s->d_dphi32, dphi32.data(), dphi32.size());
     if (e == cudaSuccess) e = upload(&s->d_phi2, phi2.data(), phi2.size());
+    if (e == cudaSuccess && problem == FE_STOKES) {
+      feasm::RefTables tp;  // pressure basis Q_{p-1} at the same quadrature points
+      feasm::build_ref_tables(order - 1, nq1d, &tp);
+      e = upload(&s->d_psi, tp.phi.data(), tp.phi.size());
+    }
     if (e == cudaSuccess) e = upload(&s->d_cell_dofs, hs.cell_dofs.data(), hs.cell_dofs.size());
     if (e == cudaSuccess) e = upload(&s->d_row_ptr, hs.row_ptr.data(), hs.row_ptr.size());
     if (e == cudaSuccess) e = upload(&s->d_col, hs.col.data(), hs.col.size());
@@ -161,6 +170,12 @@ namespace feasm {
 int set_error(int code, const char* msg) { return fail(code, msg); }
 
 int cell_stage(fe_space* s, const double* coef, const double force[3], fe_precision prec, cudaStream_t st) {
+  if (s->problem == FE_STOKES) {
+    if (prec == FE_PREC_BF16) return fail(FE_ERR_UNSUPPORTED, "Stokes cell integration has FP64 and FP32 forms only");
+    if (s->cell_kernel == FE_KERNEL_TENSOR_CORE) return fail(FE_ERR_UNSUPPORTED, "no tensor-core Stokes kernel");
+    FE_CUDA(launch_cell_stokes(s, coef, force, prec, st));
+    return FE_OK;
+  }
   const bool tc = cell_tc_applicable(s, prec) && s->cell_kernel != FE_KERNEL_CUDA_CORE;
   if (s->cell_kernel == FE_KERNEL_TENSOR_CORE && !tc)
     return fail(FE_ERR_UNSUPPORTED, "no tensor-core cell kernel for this order / problem / precision");
@@ -184,6 +199,12 @@ int fe_space_create(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_
 int fe_space_create_host(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem, double nu,
                          fe_space** out) {
   return create_common(mesh, order, quad_points_1d, problem, nu, true, out);
+}
+
+int fe_space_block_offset(const fe_space* s, int64_t* n_first) {
+  if (!s || !n_first) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+  *n_first = s->hs.n_first;
+  return FE_OK;
 }
 
 int fe_space_sizes(const fe_space* s, int64_t* n_dofs, int64_t* nnz, int64_t* n_cells, int64_t* n_contrib) {
@@ -283,6 +304,7 @@ int fe_assemble_host(fe_space* s, const double* coefficients, const double* body
 int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients, double grad_scale,
                         double* dc_dcoef, double* compliance, fe_precision prec, void* stream) {
   if (int rc = check_compute_space(s)) return rc;
+  if (s->problem == FE_STOKES) return fail(FE_ERR_UNSUPPORTED, "the compliance adjoint is for Poisson and elasticity");
   if (s->n_cells && (!u || !dc_dcoef)) return fail(FE_ERR_INVALID_ARG, "NULL u or dc_dcoef");
   if (compliance && !coefficients) return fail(FE_ERR_INVALID_ARG, "compliance requested without coefficients");
   if (prec != FE_PREC_FP64 && prec != FE_PREC_FP32) return fail(FE_ERR_INVALID_ARG, "adjoint precision must be FP64 or FP32");

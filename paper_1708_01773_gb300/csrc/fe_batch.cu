@@ -416,6 +416,7 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
     if (!s || s->host_only) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL or host-only space in the batch");
     if (s->device != device) return feasm::set_error(FE_ERR_INVALID_ARG, "spaces of a batch must share the current device");
     if (s->hs.max_slots > 32) return feasm::set_error(FE_ERR_UNSUPPORTED, "batched scatter needs at most 32 cells per DOF");
+    if (s->problem == FE_STOKES) return feasm::set_error(FE_ERR_UNSUPPORTED, "the batch takes Poisson and elasticity spaces");
     if (int64_t(s->n_cells) > INT32_MAX) return feasm::set_error(FE_ERR_UNSUPPORTED, "space too large for a batch");
   }
   fe_batch* b = new fe_batch();

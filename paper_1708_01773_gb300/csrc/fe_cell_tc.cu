@@ -796,7 +796,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
 }  // namespace tc
 
 bool cell_tc_applicable(const fe_space* s, fe_precision prec) {
-  return s->order == 2 && s->ncomp == 3 && s->nq1d == 3 && prec != FE_PREC_FP64;
+  return s->problem == FE_ELASTICITY && s->order == 2 && s->nq1d == 3 && prec != FE_PREC_FP64;
 }
 
 cudaError_t launch_cell_tc(const fe_space* s, const double* coef, const double force[3], fe_precision prec,

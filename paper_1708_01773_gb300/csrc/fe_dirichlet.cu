@@ -194,8 +194,8 @@ int fe_dirichlet_create(fe_space* s, const uint8_t* fixed, fe_dirichlet** out) {
     d->label.resize(nd);
     for (int64_t g = 0; g < nd; ++g)
       d->label[g] = fixed[g] ? int32_t(-1 - d->n_fixed++) : int32_t(d->n_free++);
-    rc = feasm::build_pattern(s->order, s->ncomp, s->n_cells, s->hs.cell_dofs.data(), d->label.data(), d->n_free,
-                              &d->hs, &err);
+    rc = feasm::build_pattern(s->nl, s->nb, s->problem == FE_ELASTICITY ? 3 : 1, s->n_cells, s->hs.cell_dofs.data(),
+                              d->label.data(), d->n_free, &d->hs, &err);
     // lifting lists: every cell with a fixed and a free DOF, its fixed local columns ascending
     d->lift_ptr.push_back(0);
     for (int64_t e = 0; e < s->n_cells && rc == FE_OK; ++e) {
@@ -369,6 +369,8 @@ int fe_compliance(fe_dirichlet* d, const double* coefficients, const double* bod
   if (!d || !body_force || !work || !compliance || (d->s->hs.n_dofs && !u) || (d->s->n_cells && !coefficients))
     return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
   if (d->s->host_only) return feasm::set_error(FE_ERR_INVALID_ARG, "host-only space cannot compute");
+  if (d->s->problem == FE_STOKES)
+    return feasm::set_error(FE_ERR_UNSUPPORTED, "the compliance is for Poisson and elasticity (Stokes is indefinite)");
   if (!(rtol > 0.0) || max_iter < 0) return feasm::set_error(FE_ERR_INVALID_ARG, "rtol must be > 0, max_iter >= 0");
   fe_space* s = d->s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

@@ -27,6 +27,7 @@ struct RefTables {
 // Products of the host setup of one space.
 struct HostSetup {
   int64_t n_dofs = 0, nnz = 0, n_contrib = 0, n_codes = 0;
+  int64_t n_first = 0;              // DOFs of the first field (Stokes: the velocity block)
   int max_slots = 0;
   int64_t max_row_nnz = 0;
   bool node_rows = false;           // the ncomp rows of each node share cells and positions
@@ -45,21 +46,26 @@ struct HostSetup {
 };
 
 void build_ref_tables(int p, int nq1d, RefTables* t);
-// Returns 0 or an FE_ERR_* code (message in *err).
-int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
+// Numbering, pattern and permutation of a space of order p for `problem`
+// (FE_POISSON, FE_ELASTICITY, FE_STOKES). Returns 0 or an FE_ERR_* code
+// (message in *err).
+int build_host_setup(int p, int problem, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
                      HostSetup* hs, std::string* err);
-// Sparsity pattern and assembly permutation from a cell-to-DOF map. With
-// label == nullptr the rows and columns are the DOFs themselves (n_rows =
-// n_dofs); otherwise DOF d is row/column label[d] if label[d] >= 0 and is
-// dropped if label[d] < 0 (a fixed DOF), n_rows being the number of kept DOFs.
-// Fills everything in *hs except cell_dofs.
-int build_pattern(int p, int ncomp, int64_t n_cells, const int32_t* cell_dofs, const int32_t* label,
+// Sparsity pattern and assembly permutation from a cell-to-DOF map with nl
+// local DOFs per cell. With label == nullptr the rows and columns are the DOFs
+// themselves (n_rows = n_dofs); otherwise DOF d is row/column label[d] if
+// label[d] >= 0 and is dropped if label[d] < 0 (a fixed DOF), n_rows being the
+// number of kept DOFs. ncomp > 1 checks whether the ncomp rows of each node
+// (local rows i * nb + a) can be scattered together. Fills everything in *hs
+// except cell_dofs and n_first.
+int build_pattern(int nl, int nb, int ncomp, int64_t n_cells, const int32_t* cell_dofs, const int32_t* label,
                   int64_t n_rows, HostSetup* hs, std::string* err);
 
 }  // namespace feasm
 
 struct fe_space {
   int order = 0, nq1d = 0, problem = 0, ncomp = 1, nb = 0, nq = 0, nl = 0;
+  int nbp = 0;  // Stokes: pressure nodes per cell (Q_{p-1}); local pressure DOFs follow the 3 nb velocity ones
   int nlp = 0;  // row stride of a cell matrix: nl rounded up to a multiple of 4 (16-byte rows)
   double nu = 0.0;
   int64_t n_cells = 0, n_vertices = 0;
@@ -76,6 +82,7 @@ struct fe_space {
   double* d_dphi = nullptr;      // [nq][nb][3]
   float* d_dphi32 = nullptr;     // [nq][nb][3]
   float* d_phi2 = nullptr;       // [nq][nb][2] phihat as FP32 hi + lo
+  double* d_psi = nullptr;       // Stokes: [nq][nbp] pressure basis at the quadrature points
   int32_t* d_cell_dofs = nullptr;
   int64_t* d_row_ptr = nullptr;
   int32_t* d_col = nullptr;

@@ -450,6 +450,8 @@ cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, 
         case 325: return launch(k_scatter_slots<81, 1, true>, bytes);
         case 326: return launch(k_scatter_slots<81, 3, false>, bytes);
         case 327: return launch(k_scatter_slots<81, 3, true>, bytes);
+        case 356: return launch(k_scatter_slots<89, 1, false>, bytes);   // Stokes Q2/Q1
+        case 357: return launch(k_scatter_slots<89, 1, true>, bytes);
         case 768: return launch(k_scatter_slots<192, 1, false>, bytes);
         case 769: return launch(k_scatter_slots<192, 1, true>, bytes);
         case 770: return launch(k_scatter_slots<192, 3, false>, bytes);

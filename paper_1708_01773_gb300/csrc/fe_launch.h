@@ -41,6 +41,10 @@ struct ScatterPattern {
 };
 ScatterPattern space_pattern(const fe_space* s);
 
+// Stokes (Taylor-Hood) cell integration, FP64 or FP32 form; writes s->d_ke and s->d_fe.
+cudaError_t launch_cell_stokes(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
+                               cudaStream_t st);
+
 // Deterministic scatter of the cell matrices/vectors into CSR values / RHS.
 cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st);
 cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, fe_precision prec, double* values,

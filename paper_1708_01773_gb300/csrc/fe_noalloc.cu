@@ -48,6 +48,8 @@ extern "C" int fe_assemble_adjoint_noalloc(fe_space* s, const double* u, const d
                                            double grad_scale, double* dc_dcoef, double* compliance,
                                            fe_precision prec, void* stream) {
   if (!s) return feasm::set_error(FE_ERR_INVALID_ARG, "space is NULL");
+  if (s->problem == FE_STOKES)
+    return feasm::set_error(FE_ERR_UNSUPPORTED, "the compliance adjoint is for Poisson and elasticity");
   if (s->host_only) return feasm::set_error(FE_ERR_INVALID_ARG, "host-only space cannot compute");
   if (s->n_cells && (!u || !dc_dcoef)) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL u or dc_dcoef");
   if (compliance && !coefficients)

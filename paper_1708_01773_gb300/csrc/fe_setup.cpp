@@ -243,9 +243,11 @@ static int number_dofs(int p, int ncomp, int64_t n_cells, const int32_t* cv, std
 // contribution of each nonzero in slot order), for the slot-wise scatter.
 static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body);
 
-int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
+int build_host_setup(int p, int problem, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
                      HostSetup* hs, std::string* err) {
-  const int nb = (p + 1) * (p + 1) * (p + 1), nl = ncomp * nb;
+  const int ncomp = problem == FE_POISSON ? 1 : 3;
+  const int nb = (p + 1) * (p + 1) * (p + 1), nbp = problem == FE_STOKES ? p * p * p : 0;
+  const int nl = ncomp * nb + nbp;
   for (int64_t i = 0; i < 8 * n_cells; ++i)
     if (cell_vertices[i] < 0 || cell_vertices[i] >= n_vertices) {
       *err = "cell_vertices entry out of range";
@@ -258,12 +260,33 @@ int build_host_setup(int p, int ncomp, int64_t n_cells, int64_t n_vertices, cons
   int64_t n_dofs = 0;
   int rc = number_dofs(p, ncomp, n_cells, cell_vertices, &hs->cell_dofs, &n_dofs, err);
   if (rc) return rc;
-  return build_pattern(p, ncomp, n_cells, hs->cell_dofs.data(), nullptr, n_dofs, hs, err);
+  hs->n_first = n_dofs;
+  if (problem == FE_STOKES) {
+    // Taylor-Hood: the pressure field (Q_{p-1}) numbered by list_dofs after all
+    // velocity DOFs; cell DOFs are the velocity ones (3 nb), then the pressure ones
+    std::vector<int32_t> cdp;
+    int64_t np = 0;
+    rc = number_dofs(p - 1, 1, n_cells, cell_vertices, &cdp, &np, err);
+    if (rc) return rc;
+    if (n_dofs + np > INT32_MAX) {
+      *err = "more than 2^31-1 DOFs";
+      return FE_ERR_UNSUPPORTED;
+    }
+    std::vector<int32_t> cd(size_t(n_cells) * nl);
+    for (int64_t e = 0; e < n_cells; ++e) {
+      std::copy(hs->cell_dofs.begin() + e * ncomp * nb, hs->cell_dofs.begin() + (e + 1) * ncomp * nb,
+                cd.begin() + e * nl);
+      for (int c = 0; c < nbp; ++c) cd[e * nl + ncomp * nb + c] = int32_t(n_dofs + cdp[e * nbp + c]);
+    }
+    hs->cell_dofs.swap(cd);
+    n_dofs += np;
+  }
+  return build_pattern(nl, nb, problem == FE_ELASTICITY ? 3 : 1, n_cells, hs->cell_dofs.data(), nullptr, n_dofs,
+                       hs, err);
 }
 
-int build_pattern(int p, int ncomp, int64_t n_cells, const int32_t* cell_dofs, const int32_t* label,
+int build_pattern(int nl, int nb, int ncomp, int64_t n_cells, const int32_t* cell_dofs, const int32_t* label,
                   int64_t n_rows, HostSetup* hs, std::string* err) {
-  const int nb = (p + 1) * (p + 1) * (p + 1), nl = ncomp * nb;
   // row of a global DOF: itself, or its label (negative = fixed, no row or column)
   auto row_of = [label](int32_t d) -> int32_t { return label ? label[d] : d; };
   hs->n_dofs = n_rows;

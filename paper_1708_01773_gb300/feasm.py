@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libfeasm.so")
 
-FE_POISSON, FE_ELASTICITY = 0, 1
+FE_POISSON, FE_ELASTICITY, FE_STOKES = 0, 1, 2
 FE_PREC_FP64, FE_PREC_FP32, FE_PREC_BF16 = 0, 1, 2
 PRECISIONS = {"fp64": FE_PREC_FP64, "fp32": FE_PREC_FP32, "bf16": FE_PREC_BF16}
 
@@ -32,7 +32,7 @@ EXPORTS = [
     "fe_batch_assemble", "fe_batch_destroy", "fe_space_dof_points_host", "fe_dirichlet_create", "fe_dirichlet_sizes",
     "fe_dirichlet_labels_host", "fe_dirichlet_csr_pattern_host", "fe_dirichlet_csr_pattern",
     "fe_dirichlet_permutation_host", "fe_dirichlet_lift_host", "fe_assemble_dirichlet", "fe_dirichlet_destroy",
-    "fe_compliance_work_size", "fe_compliance",
+    "fe_compliance_work_size", "fe_compliance", "fe_space_block_offset",
 ]
 _VOID = ("fe_space_destroy", "fe_last_error", "fe_batch_destroy", "fe_dirichlet_destroy")
 
@@ -91,6 +91,7 @@ def lib() -> ctypes.CDLL:
         L.fe_dirichlet_lift_host.argtypes = [V, P(I64), P(I64), V, V, V, V]
         L.fe_assemble_dirichlet.argtypes = [V, V, V, V, V, V, I, V]
         L.fe_compliance_work_size.argtypes = [V, P(I64)]
+        L.fe_space_block_offset.argtypes = [V, P(I64)]
         L.fe_compliance.argtypes = [V, V, V, I, D, I, V, V, V, V, P(I), P(D), V]
         L.fe_dirichlet_destroy.argtypes = [V]
         L.fe_dirichlet_destroy.restype = None
@@ -342,6 +343,12 @@ def fe_dirichlet_destroy(d: int):
     lib().fe_dirichlet_destroy(d)
 
 
+def fe_space_block_offset(space: int) -> int:
+    n = ctypes.c_int64()
+    _check(lib().fe_space_block_offset(space, ctypes.byref(n)), "fe_space_block_offset")
+    return n.value
+
+
 def fe_compliance_work_size(d: int) -> int:
     n = ctypes.c_int64()
     _check(lib().fe_compliance_work_size(d, ctypes.byref(n)), "fe_compliance_work_size")
@@ -425,7 +432,8 @@ class FESpace:
         self.handle = fe_space_create(prob.mesh.coords, prob.mesh.cell_vertices, prob.order, prob.quad_1d,
                                       prob.problem, prob.nu, host_only=host_only)
         self.n_dofs, self.nnz, self.n_cells, self.n_contrib = fe_space_sizes(self.handle)
-        self.nl = prob.ncomp * (prob.order + 1) ** 3
+        self.nl = prob.n_local
+        self.n_first = fe_space_block_offset(self.handle)
 
     def cell_dofs(self) -> np.ndarray:
         return fe_space_cell_dofs_host(self.handle, self.n_cells, self.nl)

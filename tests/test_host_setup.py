@@ -39,6 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 CASES = [
     ((3, 2, 2), 1, 0), ((2, 2, 3), 1, 1), ((2, 3, 2), 2, 0), ((3, 2, 2), 2, 1), ((2, 2, 2), 3, 0), ((2, 1, 2), 3, 1),
+    ((3, 2, 2), 2, 2), ((2, 1, 2), 3, 2),
 ]
 
 
@@ -46,7 +47,7 @@ CASES = [
 def test_numbering_pattern_permutation_match_oracle(shape, p, problem):
     prob = inputs.small_problem(shape, p, problem, seed=3 * p + problem)
     sp = feasm.FESpace(prob, host_only=True)
-    cd_o, n_o = oracle.dof_numbering(prob.mesh, p, prob.ncomp)
+    cd_o, n_o = oracle.numbering(prob)
     cd = sp.cell_dofs()
     assert sp.n_dofs == n_o
     np.testing.assert_array_equal(cd, cd_o)                      # list_dofs, bit-exact
@@ -54,7 +55,7 @@ def test_numbering_pattern_permutation_match_oracle(shape, p, problem):
     rp, col = sp.pattern_host()
     np.testing.assert_array_equal(rp, rp_o)
     np.testing.assert_array_equal(col, col_o)
-    nl = prob.ncomp * (p + 1) ** 3
+    nl = prob.n_local
     assert sp.n_contrib == prob.mesh.n_cells * nl * nl
     # emulate the scatter on the CPU with the oracle's own FP64 cell matrices
     cnt, code_ptr, codes, slot_ptr, slots = feasm.fe_space_permutation_host(sp.handle)
@@ -86,7 +87,7 @@ def test_numbering_pattern_permutation_match_oracle(shape, p, problem):
             vals[k] = Kflat[src].sum()
         assert c == code_ptr[r] + len(sl) * nl
     assert np.all(seen == 1)                                     # a permutation of all contributions
-    if prob.ncomp == 3:
+    if problem == 1:
         # the three rows of a node (consecutive DOFs) lie in the same cells at local rows
         # i*nb + a and share columns and codes: the scatter reads one position block per node
         nb = (p + 1) ** 3
