@@ -2,7 +2,7 @@
 // driver (Example "Stokes problem"; Sect. "Driver example for the Stokes
 // problem"): velocity Q_P (3 components), pressure Q_{P-1}, (P+1)^3 Gauss
 // points. With the cofactor gradients gh_a = cof(J) gradhat(phihat_a), so
-// that grad(phi_a) = gh_a / det J (Eq. shape_grad):
+// that grad(phi_a) = gh_a / det J (Eq. shape_grad), and gw_a = (w/det J) gh_a:
 //   G_ab[k][l] = sum_q (w_q / det J_q) gh_{a,k} gh_{b,l}
 //   velocity-velocity  A_(a,i),(b,j) = mu/2 (delta_ij tr G_ab + G_ab[j][i])
 //                      (mu int eps(u):eps(v), the elasticity contraction with
@@ -13,10 +13,14 @@
 //   pressure-pressure  0
 //   cell vector        f_i sum_q w_q det J_q phihat_a on the velocity rows, 0
 //                      on the pressure rows (FP64)
-// One block per cell (persistent loop); the geometry is FP64; the FP64 form
-// keeps everything in FP64, the FP32 form rounds the cofactor gradients to FP32
-// and sums the Gram entries in FP32 per slab of (P+1)^2 points with
-// compensated (Kahan) addition of the slab sums.
+// One block per cell (persistent loop; the layout allows CPB cells per
+// block). Q2/Q1 cell matrices are staged in shared memory and copied out with
+// coalesced 16-byte stores. The geometry is FP64. The velocity
+// block is symmetric: only node pairs a <= b are summed, each writing both
+// blocks. The FP64 form keeps everything in FP64; the FP32 form rounds the
+// cofactors to FP32 on the integer bits, forms w/det J in FP32, and sums the
+// Gram entries in FP32 per slab of (P+1)^2 points with compensated (Kahan)
+// addition of the slab sums.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -50,22 +54,39 @@ template <int P, typename T>
 struct Layout {
   static constexpr int N1 = P + 1, NB = N1 * N1 * N1, NQ = NB, NBP = P * P * P, NV = 3 * NB, NL = NV + NBP;
   static constexpr int NLP = (NL + 3) & ~3;
-  // shared memory: xv[24], a[21], wdet[NQ] (double); cof[NQ][9], wod[NQ], wq[NQ] (T); gh[NQ][3][NB] (T);
-  // the pressure basis psi[NQ][NBP] (T)
-  static constexpr size_t OFF_A = 24 * sizeof(double);
-  static constexpr size_t OFF_WDET = OFF_A + 24 * sizeof(double);
-  static constexpr size_t OFF_COF = OFF_WDET + NQ * sizeof(double);
-  static constexpr size_t OFF_WOD = OFF_COF + size_t(NQ) * 9 * sizeof(T);
-  static constexpr size_t OFF_WQ = OFF_WOD + NQ * sizeof(T);
-  static constexpr size_t OFF_GH = (OFF_WQ + NQ * sizeof(T) + 15) & ~size_t(15);
-  static constexpr size_t OFF_PSI = OFF_GH + size_t(NQ) * 3 * NB * sizeof(T);
-  static constexpr size_t BYTES = OFF_PSI + size_t(NQ) * NBP * sizeof(T);
+  static constexpr int NPAIR = NB * (NB + 1) / 2;  // node pairs a <= b
+  // Q2/Q1: the cell matrices are staged in shared memory and written out with
+  // coalesced 16-byte stores (the symmetric half's transposed entries would
+  // otherwise be stride-NLP stores, one sector per lane); Q3/Q2 matrices do not
+  // fit and are stored directly. Cells integrated together by one block: one
+  // (measured on Q2/Q1 FP32: 4 blocks of one cell per SM, 0.77 ms, against 2
+  // blocks of two cells, 0.87 ms, and 0.95 ms for unstaged stores).
+  static constexpr bool STAGE = P == 2;
+  static constexpr int CPB = 1;
+  static constexpr int GS = NQ * 3 * NB;  // gradient entries per cell
+  // shared memory, per cell c < CPB: xv[c][24], a[c][24], wdet[c][NQ] (double);
+  // cof[c][NQ][9], wod[c][NQ], wq[c][NQ], mu/2 [c] (T); gh[c][NQ][3][NB] and
+  // gw[c][NQ][3][NB] = (w/det) gh (T); then, shared by the cells, the pressure
+  // basis psi[NQ][NBP] (T) and the node pairs a <= b
+  static constexpr size_t OFF_A = size_t(CPB) * 24 * sizeof(double);
+  static constexpr size_t OFF_WDET = OFF_A + size_t(CPB) * 24 * sizeof(double);
+  static constexpr size_t OFF_COF = OFF_WDET + size_t(CPB) * NQ * sizeof(double);
+  static constexpr size_t OFF_WOD = OFF_COF + size_t(CPB) * NQ * 9 * sizeof(T);
+  static constexpr size_t OFF_WQ = OFF_WOD + size_t(CPB) * NQ * sizeof(T);
+  static constexpr size_t OFF_MU = OFF_WQ + size_t(CPB) * NQ * sizeof(T);
+  static constexpr size_t OFF_GH = (OFF_MU + CPB * sizeof(T) + 15) & ~size_t(15);
+  static constexpr size_t OFF_GW = OFF_GH + size_t(CPB) * GS * sizeof(T);
+  static constexpr size_t OFF_PSI = OFF_GW + size_t(CPB) * GS * sizeof(T);
+  static constexpr size_t OFF_PAIR = OFF_PSI + size_t(NQ) * NBP * sizeof(T);
+  static constexpr size_t OFF_KS = (OFF_PAIR + size_t(NPAIR) * sizeof(uint16_t) + 15) & ~size_t(15);
+  static constexpr size_t BYTES = OFF_KS + (STAGE ? size_t(CPB) * NL * NLP * sizeof(T) : 0);
 };
 
 template <int P, typename T>
 __global__ void __launch_bounds__(kThreads) k_cell_stokes(Params p) {
   using L = Layout<P, T>;
   constexpr int N1 = L::N1, NB = L::NB, NQ = L::NQ, NBP = L::NBP, NV = L::NV, NL = L::NL, NLP = L::NLP;
+  constexpr int CPB = L::CPB, GS = L::GS, NPAIR = L::NPAIR;
   constexpr bool F32 = std::is_same<T, float>::value;
   extern __shared__ __align__(16) unsigned char sm[];
   double* xv = reinterpret_cast<double*>(sm);
@@ -74,48 +95,84 @@ __global__ void __launch_bounds__(kThreads) k_cell_stokes(Params p) {
   T* cof = reinterpret_cast<T*>(sm + L::OFF_COF);
   T* wod = reinterpret_cast<T*>(sm + L::OFF_WOD);
   T* wq = reinterpret_cast<T*>(sm + L::OFF_WQ);
+  T* smu = reinterpret_cast<T*>(sm + L::OFF_MU);
   T* gh = reinterpret_cast<T*>(sm + L::OFF_GH);
+  T* gw = reinterpret_cast<T*>(sm + L::OFF_GW);
   T* spsi = reinterpret_cast<T*>(sm + L::OFF_PSI);
+  uint16_t* pairs = reinterpret_cast<uint16_t*>(sm + L::OFF_PAIR);
   T* K = static_cast<T*>(p.ke);
+  T* Ks = reinterpret_cast<T*>(sm + L::OFF_KS);
+  // destination of cell c's matrix: the staging buffer or the cell-matrix scratch
+  auto kdst = [&](int64_t e0, int c) -> T* {
+    if constexpr (L::STAGE) return Ks + size_t(c) * NL * NLP;
+    else return K + (e0 + c) * int64_t(NL) * NLP;
+  };
   const int t = threadIdx.x;
   for (int i = t; i < NQ * NBP; i += kThreads) spsi[i] = T(p.psi[i]);
-  for (int64_t e = blockIdx.x; e < p.n_cells; e += gridDim.x) {
-    if (t < 24) xv[t] = p.xv[e * 24 + t];
+  if (t == 0) {
+    int n = 0;
+    for (int a0 = 0; a0 < NB; ++a0)
+      for (int b0 = a0; b0 < NB; ++b0) pairs[n++] = uint16_t(a0 << 8 | b0);
+  }
+  for (int64_t e0 = int64_t(blockIdx.x) * CPB; e0 < p.n_cells; e0 += int64_t(gridDim.x) * CPB) {
+    const int nc = int(p.n_cells - e0 < CPB ? p.n_cells - e0 : CPB);
+    for (int i = t; i < nc * 24; i += kThreads) xv[i] = p.xv[e0 * 24 + i];
     __syncthreads();
-    if (t < 3) trilinear_coefficients(xv, t, a);
+    if (t < 3 * nc) trilinear_coefficients(xv + (t / 3) * 24, t % 3, a + (t / 3) * 24);
     __syncthreads();
-    // 1. geometry per quadrature point (FP64)
-    if (t < NQ) {
-      double c[9], det;
-      geometry_at(a, p.xq[3 * t], p.xq[3 * t + 1], p.xq[3 * t + 2], c, &det);
+    // 1. geometry per (cell, quadrature point), FP64
+    for (int i = t; i < nc * NQ; i += kThreads) {
+      const int c = i / NQ, q = i % NQ;
+      double cf[9], det;
+      geometry_at(a + c * 24, p.xq[3 * q], p.xq[3 * q + 1], p.xq[3 * q + 2], cf, &det);
       if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
-      const double w = p.w[t];
-      wdet[t] = w * det;
-      wod[t] = T(w / det);
-      wq[t] = T(w);
+      const double w = p.w[q];
+      wdet[i] = w * det;
+      if constexpr (F32) {
+        // FP32 form: conversions on the integer bits, the quotient in FP32
+        const float w32 = d2f_rn(w);
+        wod[i] = w32 / d2f_rn(det);
+        wq[i] = w32;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) cof[t * 9 + k] = T(c[k]);
+        for (int k = 0; k < 9; ++k) cof[i * 9 + k] = d2f_rn(cf[k]);
+      } else {
+        wod[i] = w / det;
+        wq[i] = w;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) cof[i * 9 + k] = cf[k];
+      }
+    }
+    if (t < nc) {
+      const double mh = 0.5 * p.coef[e0 + t];
+      if constexpr (F32) smu[t] = d2f_rn(mh); else smu[t] = mh;
     }
     __syncthreads();
-    // 2. cofactor gradients gh[q][k][a] = sum_d cof[q][k][d] gradhat_d phihat_a(x_q)
-    for (int i = t; i < NQ * NB; i += kThreads) {
-      const int q = i / NB, b = i % NB;
+    // 2. cofactor gradients gh[c][q][k][a] = sum_d cof[c][q][k][d] gradhat_d phihat_a(x_q), gw = (w/det) gh
+    for (int i = t; i < nc * NQ * NB; i += kThreads) {
+      const int c = i / (NQ * NB), r = i % (NQ * NB), q = r / NB, b = r % NB;
       T g[3];
       if constexpr (F32) {
-        g[0] = p.dphi32[3 * i]; g[1] = p.dphi32[3 * i + 1]; g[2] = p.dphi32[3 * i + 2];
+        g[0] = p.dphi32[3 * r]; g[1] = p.dphi32[3 * r + 1]; g[2] = p.dphi32[3 * r + 2];
       } else {
-        g[0] = p.dphi[3 * i]; g[1] = p.dphi[3 * i + 1]; g[2] = p.dphi[3 * i + 2];
+        g[0] = p.dphi[3 * r]; g[1] = p.dphi[3 * r + 1]; g[2] = p.dphi[3 * r + 2];
       }
-      const T* cq = cof + q * 9;
+      const T* cq = cof + (c * NQ + q) * 9;
+      const T wv = wod[c * NQ + q];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) gh[(q * 3 + k) * NB + b] = cq[3 * k] * g[0] + cq[3 * k + 1] * g[1] + cq[3 * k + 2] * g[2];
+      for (int k = 0; k < 3; ++k) {
+        const T v = cq[3 * k] * g[0] + cq[3 * k + 1] * g[1] + cq[3 * k + 2] * g[2];
+        gh[c * GS + (q * 3 + k) * NB + b] = v;
+        gw[c * GS + (q * 3 + k) * NB + b] = wv * v;
+      }
     }
     __syncthreads();
-    const T mu_half = T(0.5 * p.coef[e]);
-    T* Ke = K + e * int64_t(NL) * NLP;
-    // 3. velocity-velocity block, one node pair per item
-    for (int i = t; i < NB * NB; i += kThreads) {
-      const int an = i / NB, bn = i % NB;
+    // 3. velocity-velocity block, one (cell, node pair a <= b) per item; the
+    //    block is symmetric (A_(b,j),(a,i) = A_(a,i),(b,j)), so (a, b) and (b, a)
+    //    are written from the same sums
+    for (int i = t; i < nc * NPAIR; i += kThreads) {
+      const int c = i / NPAIR, pr = pairs[i % NPAIR], an = pr >> 8, bn = pr & 255;
+      const T* ghc = gh + c * GS;
+      const T* gwc = gw + c * GS;
       T S[3][3], C[3][3];
 #pragma unroll
       for (int k = 0; k < 3; ++k)
@@ -128,12 +185,11 @@ __global__ void __launch_bounds__(kThreads) k_cell_stokes(Params p) {
 #pragma unroll
           for (int l = 0; l < 3; ++l) G[k][l] = T(0);
         for (int q = s0; q < s0 + N1 * N1; ++q) {
-          const T wv = wod[q];
           T ga[3], gb[3];
 #pragma unroll
           for (int k = 0; k < 3; ++k) {
-            ga[k] = wv * gh[(q * 3 + k) * NB + an];
-            gb[k] = gh[(q * 3 + k) * NB + bn];
+            ga[k] = gwc[(q * 3 + k) * NB + an];
+            gb[k] = ghc[(q * 3 + k) * NB + bn];
           }
 #pragma unroll
           for (int k = 0; k < 3; ++k)
@@ -147,49 +203,67 @@ __global__ void __launch_bounds__(kThreads) k_cell_stokes(Params p) {
             if constexpr (F32) kahan_add(S[k][l], C[k][l], G[k][l]); else S[k][l] += G[k][l];
           }
       }
-      const T tr = S[0][0] + S[1][1] + S[2][2];
+      const T tr = S[0][0] + S[1][1] + S[2][2], mh = smu[c];
+      T* Ke = kdst(e0, c);
 #pragma unroll
       for (int ii = 0; ii < 3; ++ii)
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
           T v = S[jj][ii];
           if (ii == jj) v += tr;
-          Ke[size_t(ii * NB + an) * NLP + jj * NB + bn] = mu_half * v;
+          v *= mh;
+          Ke[size_t(ii * NB + an) * NLP + jj * NB + bn] = v;
+          if (an != bn) Ke[size_t(jj * NB + bn) * NLP + ii * NB + an] = v;
         }
     }
-    // 4. pressure coupling, one (pressure node, velocity node) pair per item
-    for (int i = t; i < NBP * NB; i += kThreads) {
-      const int c = i / NB, bn = i % NB;
+    // 4. pressure coupling, one (cell, pressure node, velocity node) per item
+    for (int i = t; i < nc * NBP * NB; i += kThreads) {
+      const int c = i / (NBP * NB), r = i % (NBP * NB), cp = r / NB, bn = r % NB;
+      const T* ghc = gh + c * GS;
+      const T* wqc = wq + c * NQ;
       T S[3] = {T(0), T(0), T(0)}, C[3] = {T(0), T(0), T(0)};
       for (int s0 = 0; s0 < NQ; s0 += N1 * N1) {
         T G[3] = {T(0), T(0), T(0)};
         for (int q = s0; q < s0 + N1 * N1; ++q) {
-          const T wp = wq[q] * spsi[q * NBP + c];
+          const T wp = wqc[q] * spsi[q * NBP + cp];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) G[k] = fma(wp, gh[(q * 3 + k) * NB + bn], G[k]);
+          for (int k = 0; k < 3; ++k) G[k] = fma(wp, ghc[(q * 3 + k) * NB + bn], G[k]);
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           if constexpr (F32) kahan_add(S[k], C[k], G[k]); else S[k] += G[k];
         }
       }
+      T* Ke = kdst(e0, c);
 #pragma unroll
       for (int jj = 0; jj < 3; ++jj) {
-        Ke[size_t(jj * NB + bn) * NLP + NV + c] = -S[jj];
-        Ke[size_t(NV + c) * NLP + jj * NB + bn] = -S[jj];
+        Ke[size_t(jj * NB + bn) * NLP + NV + cp] = -S[jj];
+        Ke[size_t(NV + cp) * NLP + jj * NB + bn] = -S[jj];
       }
     }
-    // 5. pressure-pressure block
-    for (int i = t; i < NBP * NBP; i += kThreads) Ke[size_t(NV + i / NBP) * NLP + NV + i % NBP] = T(0);
-    // 6. cell vector (FP64)
-    if (t < NB) {
+    // 5. pressure-pressure blocks
+    for (int i = t; i < nc * NBP * NBP; i += kThreads) {
+      const int c = i / (NBP * NBP), r = i % (NBP * NBP);
+      kdst(e0, c)[size_t(NV + r / NBP) * NLP + NV + r % NBP] = T(0);
+    }
+    // 6. cell vectors (FP64), one (cell, node) per item
+    for (int i = t; i < nc * NB; i += kThreads) {
+      const int c = i / NB, an = i % NB;
       double s = 0.0;
-      for (int q = 0; q < NQ; ++q) s = fma(wdet[q], p.phi[q * NB + t], s);
-      double* fe = p.fe + e * NL;
+      for (int q = 0; q < NQ; ++q) s = fma(wdet[c * NQ + q], p.phi[q * NB + an], s);
+      double* fe = p.fe + (e0 + c) * NL;
 #pragma unroll
-      for (int ii = 0; ii < 3; ++ii) fe[ii * NB + t] = p.f[ii] * s;
-    } else if (t < NB + NBP) {
-      p.fe[e * NL + NV + (t - NB)] = 0.0;
+      for (int ii = 0; ii < 3; ++ii) fe[ii * NB + an] = p.f[ii] * s;
+    }
+    for (int i = t; i < nc * NBP; i += kThreads) p.fe[(e0 + i / NBP) * NL + NV + i % NBP] = 0.0;
+    if constexpr (L::STAGE) {
+      // 7. staged cell matrices -> scratch, 16-byte coalesced (the cells of a group
+      //    are consecutive: one contiguous range; row padding is copied as is)
+      __syncthreads();
+      constexpr int N16 = int(size_t(NL) * NLP * sizeof(T) / 16);
+      const uint4* src = reinterpret_cast<const uint4*>(Ks);
+      uint4* dst = reinterpret_cast<uint4*>(K + e0 * int64_t(NL) * NLP);
+      for (int i = t; i < nc * N16; i += kThreads) dst[i] = src[i];
     }
     __syncthreads();
   }
@@ -205,7 +279,8 @@ cudaError_t launch(const fe_space* s, const Params& prm, cudaStream_t st) {
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, L::BYTES);
   if (e != cudaSuccess) return e;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s->device);
-  const int blocks = int(std::min<int64_t>(s->n_cells, int64_t(nsm) * std::max(1, per_sm)));
+  const int64_t groups = (s->n_cells + L::CPB - 1) / L::CPB;
+  const int blocks = int(std::min<int64_t>(groups, int64_t(nsm) * std::max(1, per_sm)));
   kern<<<blocks, kThreads, L::BYTES, st>>>(prm);
   return cudaGetLastError();
 }
