@@ -64,6 +64,9 @@ def lib():
         L.or_cell_energies.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _i32p, _f64p,
                                        _i32p, ctypes.c_double, _f64p, _f64p]
         L.or_cell_energies.restype = ctypes.c_int
+        L.or_dg_assemble.argtypes = [ctypes.c_int, ctypes.c_int64, _i32p, _f64p, ctypes.c_double, ctypes.c_double,
+                                     ctypes.c_double, _f64p, vp, vp, vp, vp]
+        L.or_dg_assemble.restype = ctypes.c_int64
         _lib = L
     return _lib
 
@@ -285,3 +288,26 @@ def compliance_solve(prob, fixed, cell_dofs=None, n_dofs=None):
     c = float(b_r @ u_free)
     grad = -cell_energies(prob, u, cell_dofs)
     return u, c, grad
+
+
+# ----------------------------------------------------------------------------- interior penalty DG
+def dg_assemble(mesh, p: int, tau: float, gamma: float, f: float = 0.0, ud=(0.0, 0.0, 0.0, 0.0)):
+    """IP-DG Poisson system of Eq. ip_dg_formulations on a hexahedral mesh
+    (cell-local DOFs K*(p+1)^3 + a): CSR (row_ptr, col, val) and the right-hand
+    side with the source f and the weak Dirichlet data u_D(x) = ud[0] + ud[1:] . x."""
+    L = lib()
+    cv = _c(mesh.cell_vertices, np.int32)
+    xyz = _c(mesh.coords, np.float64).ravel()
+    u = _c(ud, np.float64)
+    nnz = L.or_dg_assemble(p, mesh.n_cells, cv, xyz, float(tau), float(gamma), float(f), u, None, None, None, None)
+    if nnz < 0:
+        raise ValueError(f"or_dg_assemble -> {nnz}")
+    n = mesh.n_cells * (p + 1) ** 3
+    row_ptr = np.zeros(n + 1, dtype=np.int64)
+    col = np.zeros(nnz, dtype=np.int32)
+    val = np.zeros(nnz)
+    rhs = np.zeros(n)
+    nnz2 = L.or_dg_assemble(p, mesh.n_cells, cv, xyz, float(tau), float(gamma), float(f), u,
+                            row_ptr.ctypes.data, col.ctypes.data, val.ctypes.data, rhs.ctypes.data)
+    assert nnz2 == nnz
+    return row_ptr, col, val, rhs

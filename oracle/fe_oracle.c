@@ -732,3 +732,224 @@ int or_cell_energies(int problem, int p, int nq1d, int64_t n_cells, const int32_
   free(T); free(Ke); free(fe);
   return rc;
 }
+
+/* ------------------------------------------------------------------ */
+/* Interior penalty DG for the Poisson problem (Sect. "Non-conforming   */
+/* methods", Eq. ip_dg_formulations, Eq. mean_and_jump_ops, Eq.         */
+/* local_to_face_matrix). DOFs are cell-local: DOF a of cell K is       */
+/* K*nb + a. Local face f = 2 d + s lies on xhat_d = s; its parameters  */
+/* are the other two reference coordinates in increasing axis order.    */
+/* ------------------------------------------------------------------ */
+static void face_point(int f, double s, double t, double xh[3]) {
+  int d = f / 2, d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+  xh[d] = (double)(f % 2);
+  xh[d1] = s;
+  xh[d2] = t;
+}
+
+static void map_point(const double* xv, const double xh[3], double x[3]) {
+  double N[8], dN[8][3];
+  tp_basis(1, xh, N, &dN[0][0]);
+  for (int k = 0; k < 3; ++k) {
+    x[k] = 0.0;
+    for (int v = 0; v < 8; ++v) x[k] += N[v] * xv[3 * v + k];
+  }
+}
+
+static void jacobian_at(const double* xv, const double xh[3], double J[3][3]) {
+  double N[8], dN[8][3];
+  tp_basis(1, xh, N, &dN[0][0]);
+  for (int k = 0; k < 3; ++k)
+    for (int d = 0; d < 3; ++d) {
+      J[k][d] = 0.0;
+      for (int v = 0; v < 8; ++v) J[k][d] += xv[3 * v + k] * dN[v][d];
+    }
+}
+
+/* Reference point of the physical point x in the cell (Newton on the
+ * trilinear map from the cell centre). */
+static int inverse_map(const double* xv, const double x[3], double xh[3]) {
+  xh[0] = xh[1] = xh[2] = 0.5;
+  for (int it = 0; it < 100; ++it) {
+    double y[3], J[3][3], Ji[3][3];
+    map_point(xv, xh, y);
+    jacobian_at(xv, xh, J);
+    double det = det3(J);
+    if (!(fabs(det) > 0.0)) return OR_ERR_NEG_JAC;
+    inv3(J, det, Ji);
+    double step = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      double dx = 0.0;
+      for (int k = 0; k < 3; ++k) dx += Ji[d][k] * (x[k] - y[k]);
+      xh[d] += dx;
+      step += fabs(dx);
+    }
+    if (step < 1e-15) return OR_OK;
+  }
+  return OR_OK;
+}
+
+/* Values and physical gradients of the nb shape functions at xh. */
+static void basis_phys(int p, const double* xv, const double xh[3], double* phi, double g[][3]) {
+  double dphi[MAXNB][3], J[3][3], Ji[3][3];
+  tp_basis(p, xh, phi, &dphi[0][0]);
+  jacobian_at(xv, xh, J);
+  inv3(J, det3(J), Ji);
+  int nb = (p + 1) * (p + 1) * (p + 1);
+  for (int a = 0; a < nb; ++a)
+    for (int k = 0; k < 3; ++k) {
+      g[a][k] = 0.0;
+      for (int d = 0; d < 3; ++d) g[a][k] += dphi[a][d] * Ji[d][k];
+    }
+}
+
+/* The 4 corner vertices of local face f (reference corners with xhat_d = s). */
+static void face_vertices(const int32_t* cv, int f, int32_t out[4]) {
+  int d = f / 2, s = f % 2, n = 0;
+  for (int v = 0; v < 8; ++v)
+    if (((v >> d) & 1) == s) out[n++] = cv[v];
+}
+
+typedef struct {
+  int32_t key[4];
+  int64_t cell;
+  int face;
+} face_rec;
+
+static int cmp_face(const void* pa, const void* pb) {
+  const face_rec* a = (const face_rec*)pa;
+  const face_rec* b = (const face_rec*)pb;
+  for (int i = 0; i < 4; ++i)
+    if (a->key[i] != b->key[i]) return a->key[i] < b->key[i] ? -1 : 1;
+  if (a->cell != b->cell) return a->cell < b->cell ? -1 : 1;
+  return 0;
+}
+
+static int cmp_i32(const void* pa, const void* pb) {
+  int32_t a = *(const int32_t*)pa, b = *(const int32_t*)pb;
+  return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* Assembles the IP-DG system: the cell terms int grad u . grad v and int f v,
+ * the interior facets (K+, the lower cell id, and K-) with the four blocks of
+ * Eq. local_to_face_matrix (row: test function, column: trial function),
+ * the boundary facets with the degenerate one-sided block, and on the
+ * right-hand side the weak Dirichlet terms for u_D(x) = ud[0] + ud[1..3] . x.
+ * The normal and the surface element come from the cross product of the face
+ * tangents; the reference point of a facet point in K- is found by inverting
+ * K-'s trilinear map. n_dofs = n_cells (p+1)^3. Call with row_ptr == NULL to
+ * get nnz only. Returns nnz or a negative error code. */
+int64_t or_dg_assemble(int p, int64_t n_cells, const int32_t* cell_vertices, const double* coords, double tau,
+                       double gamma, double f, const double* ud, int64_t* row_ptr, int32_t* col_idx, double* values,
+                       double* rhs) {
+  ref_tables* T = (ref_tables*)malloc(sizeof(ref_tables));
+  if (!T) return OR_ERR_OOM;
+  int rc = make_tables(p, p + 1, T);
+  if (rc) { free(T); return rc; }
+  const int nb = T->nb, n1 = p + 1;
+  double gx[MAXQ1D], gw[MAXQ1D];
+  or_gauss_legendre(n1, gx, gw);
+  face_rec* fr = (face_rec*)malloc(sizeof(face_rec) * (n_cells > 0 ? 6 * n_cells : 1));
+  /* entries: nb^2 per cell, 4 nb^2 per interior and nb^2 per boundary facet;
+   * 2 F_int + F_bnd = 6 n_cells and F_int <= 3 n_cells give at most 13 n_cells nb^2 */
+  int64_t cap = n_cells * (int64_t)nb * nb * 13 + 1;
+  coo_t* coo = (coo_t*)malloc(sizeof(coo_t) * cap);
+  double* Ke = (double*)malloc(sizeof(double) * nb * nb);
+  double* fe = (double*)malloc(sizeof(double) * nb);
+  double* M = (double*)malloc(sizeof(double) * 4 * nb * nb);
+  if (!fr || !coo || !Ke || !fe || !M) { free(T); free(fr); free(coo); free(Ke); free(fe); free(M); return OR_ERR_OOM; }
+  const int64_t n_dofs = n_cells * nb;
+  if (rhs) memset(rhs, 0, sizeof(double) * n_dofs);
+  int64_t t = 0;
+  for (int64_t e = 0; e < n_cells && !rc; ++e) {
+    double xv[24];
+    cell_coords(cell_vertices + 8 * e, coords, xv);
+    rc = cell_poisson(T, xv, 1.0, f, Ke, fe);
+    for (int a = 0; a < nb && !rc; ++a) {
+      for (int b = 0; b < nb; ++b) {
+        coo[t].row = e * nb + a; coo[t].col = e * nb + b; coo[t].val = Ke[a * nb + b]; t++;
+      }
+      if (rhs) rhs[e * nb + a] += fe[a];
+    }
+    for (int lf = 0; lf < 6; ++lf) {
+      face_rec* r = &fr[6 * e + lf];
+      face_vertices(cell_vertices + 8 * e, lf, r->key);
+      qsort(r->key, 4, sizeof(int32_t), cmp_i32);
+      r->cell = e;
+      r->face = lf;
+    }
+  }
+  if (!rc) qsort(fr, (size_t)(6 * n_cells), sizeof(face_rec), cmp_face);
+  for (int64_t i = 0; i < 6 * n_cells && !rc; ++i) {
+    const int interior = i + 1 < 6 * n_cells && memcmp(fr[i].key, fr[i + 1].key, sizeof(fr[i].key)) == 0;
+    int64_t K[2] = {fr[i].cell, interior ? fr[i + 1].cell : -1};
+    double xvp[24], xvm[24];
+    cell_coords(cell_vertices + 8 * K[0], coords, xvp);
+    if (interior) cell_coords(cell_vertices + 8 * K[1], coords, xvm);
+    const int lf = fr[i].face, d = lf / 2, d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+    const double sgn = (d == 1 ? -1.0 : 1.0) * (lf % 2 ? 1.0 : -1.0);
+    /* two passes: the facet area |F|, then the entries */
+    double area = 0.0;
+    const int ns = interior ? 2 : 1;
+    memset(M, 0, sizeof(double) * 4 * nb * nb);
+    for (int pass = 0; pass < 2; ++pass)
+      for (int qs = 0; qs < n1; ++qs)
+        for (int qt = 0; qt < n1; ++qt) {
+          double xh[3], x[3], J[3][3];
+          face_point(lf, gx[qs], gx[qt], xh);
+          map_point(xvp, xh, x);
+          jacobian_at(xvp, xh, J);
+          double t1[3] = {J[0][d1], J[1][d1], J[2][d1]}, t2[3] = {J[0][d2], J[1][d2], J[2][d2]};
+          double nd[3] = {t1[1] * t2[2] - t1[2] * t2[1], t1[2] * t2[0] - t1[0] * t2[2], t1[0] * t2[1] - t1[1] * t2[0]};
+          double len = sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
+          double dS = len * gw[qs] * gw[qt], n[3] = {sgn * nd[0] / len, sgn * nd[1] / len, sgn * nd[2] / len};
+          if (pass == 0) { area += dS; continue; }
+          double phi[2][MAXNB], g[2][MAXNB][3], gn[2][MAXNB];
+          basis_phys(p, xvp, xh, phi[0], g[0]);
+          if (interior) {
+            double xm[3];
+            inverse_map(xvm, x, xm);
+            basis_phys(p, xvm, xm, phi[1], g[1]);
+          }
+          for (int s = 0; s < ns; ++s)
+            for (int a = 0; a < nb; ++a) gn[s][a] = g[s][a][0] * n[0] + g[s][a][1] * n[1] + g[s][a][2] * n[2];
+          const double half = interior ? 0.5 : 1.0, pen = gamma / area;
+          for (int sa = 0; sa < ns; ++sa)
+            for (int sb = 0; sb < ns; ++sb) {
+              const double ga = sa == 0 ? 1.0 : -1.0, gb = sb == 0 ? 1.0 : -1.0;
+              double* Mb = M + (sa * 2 + sb) * nb * nb;
+              for (int a = 0; a < nb; ++a)
+                for (int b = 0; b < nb; ++b)
+                  Mb[a * nb + b] += dS * (-ga * phi[sa][a] * half * gn[sb][b] - tau * gb * phi[sb][b] * half * gn[sa][a]
+                                          + pen * ga * gb * phi[sa][a] * phi[sb][b]);
+            }
+          if (!interior && rhs) {
+            double u = ud[0] + ud[1] * x[0] + ud[2] * x[1] + ud[3] * x[2];
+            for (int a = 0; a < nb; ++a) rhs[K[0] * nb + a] += dS * (-tau * u * gn[0][a] + pen * u * phi[0][a]);
+          }
+        }
+    for (int sa = 0; sa < ns; ++sa)
+      for (int sb = 0; sb < ns; ++sb)
+        for (int a = 0; a < nb; ++a)
+          for (int b = 0; b < nb; ++b) {
+            coo[t].row = K[sa] * nb + a; coo[t].col = K[sb] * nb + b; coo[t].val = M[(sa * 2 + sb) * nb * nb + a * nb + b]; t++;
+          }
+    if (interior) ++i;
+  }
+  int64_t nnz = 0;
+  if (!rc) {
+    qsort(coo, (size_t)t, sizeof(coo_t), cmp_coo);
+    if (row_ptr) for (int64_t r = 0; r <= n_dofs; ++r) row_ptr[r] = 0;
+    for (int64_t i = 0; i < t; ++i) {
+      if (i == 0 || coo[i].row != coo[i - 1].row || coo[i].col != coo[i - 1].col) {
+        if (row_ptr) { col_idx[nnz] = (int32_t)coo[i].col; values[nnz] = coo[i].val; row_ptr[coo[i].row + 1]++; }
+        nnz++;
+      } else if (row_ptr) {
+        values[nnz - 1] += coo[i].val;
+      }
+    }
+    if (row_ptr) for (int64_t r = 0; r < n_dofs; ++r) row_ptr[r + 1] += row_ptr[r];
+  }
+  free(T); free(fr); free(coo); free(Ke); free(fe); free(M);
+  return rc ? rc : nnz;
+}

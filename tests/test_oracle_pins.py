@@ -763,3 +763,91 @@ def test_stokes_linear_velocity_closed_forms():
     assert np.abs(r[:nv][~boundary_dofs(pos_v)]).max() <= 1e-11 * np.abs(A).max()
     sym = 0.5 * (Bm + Bm.T)
     assert abs(u @ r - mu * np.sum(sym * sym) * vol) <= 1e-12 * mu * np.sum(sym * sym)
+
+
+# ---------------------------------------------------------------- interior penalty DG
+def dg_node_positions(mesh, p):
+    """Position of every DG DOF (K, a): Phi_K(alpha_a / p), K-major."""
+    n1 = p + 1
+    al = np.array([[a % n1, (a // n1) % n1, a // (n1 * n1)] for a in range(n1 ** 3)]) / p
+    N = np.ones((n1 ** 3, 8))
+    for v in range(8):
+        for d in range(3):
+            N[:, v] *= al[:, d] if (v >> d) & 1 else 1 - al[:, d]
+    return np.einsum("av,evk->eak", N, mesh.coords[mesh.cell_vertices]).reshape(-1, 3)
+
+
+def proper_rotations():
+    """The 24 rotations of the unit cube as (axis permutation, flips) with det +1."""
+    out = []
+    for perm in itertools.permutations(range(3)):
+        for flips in itertools.product((0, 1), repeat=3):
+            M = np.zeros((3, 3))
+            for i in range(3):
+                M[i, perm[i]] = -1.0 if flips[i] else 1.0
+            if np.linalg.det(M) > 0:
+                out.append((perm, flips))
+    return out
+
+
+def rotated_mesh(mesh, seed):
+    """The same cells with each local vertex order turned by a random proper rotation."""
+    rng = np.random.default_rng(seed)
+    rots = proper_rotations()
+    cv = mesh.cell_vertices.copy()
+    for e in range(mesh.n_cells):
+        perm, flips = rots[rng.integers(len(rots))]
+        new = np.empty(8, dtype=np.int32)
+        for w in range(8):
+            r = [(w >> i) & 1 for i in range(3)]
+            rr = [1 - r[perm[i]] if flips[i] else r[perm[i]] for i in range(3)]
+            new[w] = mesh.cell_vertices[e][rr[0] + 2 * rr[1] + 4 * rr[2]]
+        cv[e] = new
+    return inputs.Mesh(mesh.coords, cv, mesh.shape, mesh.extent)
+
+
+@pytest.mark.parametrize("p,shape,rotate", [(1, (3, 2, 2), False), (2, (2, 2, 2), False), (3, (2, 1, 2), False),
+                                            (2, (2, 2, 2), True), (1, (3, 3, 2), True)])
+@pytest.mark.parametrize("tau", [1.0, -1.0, 0.0])
+def test_dg_consistency_with_linear_solution(p, shape, rotate, tau):
+    """u = g linear solves -Lap u = 0 with u = g on the boundary; IP-DG is consistent
+    and its cell, facet and boundary integrals are exact for g on trilinear cells,
+    so A u_g equals the right-hand side with f = 0 and u_D = g, to rounding. A wrong
+    sign, normal, mean or jump factor, or a mismatched neighbour point fails."""
+    mesh = inputs.small_problem(shape, p, 0, seed=150 + p).mesh
+    if rotate:
+        mesh = rotated_mesh(mesh, 160 + p)
+    ud = np.array([0.4, 1.3, -0.7, 2.1])
+    rp, col, val, rhs = oracle.dg_assemble(mesh, p, tau, 7.0, 0.0, ud)
+    x = dg_node_positions(mesh, p)
+    u = ud[0] + x @ ud[1:]
+    r = csr_matvec(rp, col, val, u)
+    assert np.abs(r - rhs).max() <= 1e-11 * np.abs(rhs).max()
+
+
+def csr_matvec(rp, col, val, v):
+    rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
+    out = np.zeros(rp.size - 1)
+    np.add.at(out, rows, val * v[col])
+    return out
+
+
+def test_dg_symmetry_linearity_and_coercivity():
+    """SIPG (tau = 1) is symmetric and, with a large enough penalty, positive
+    definite; the matrix is affine in tau and in gamma; the pattern couples each
+    cell with itself and its face neighbours."""
+    mesh = inputs.small_problem((3, 2, 2), 2, 0, seed=170).mesh
+    n = mesh.n_cells * 27
+    A = {}
+    for tau, gamma in ((1.0, 10.0), (0.0, 10.0), (-1.0, 10.0), (1.0, 30.0)):
+        rp, col, val, _ = oracle.dg_assemble(mesh, 2, tau, gamma)
+        A[tau, gamma] = csr_to_dense(rp, col, val, n)
+    S = A[1.0, 10.0]
+    sc = np.abs(S).max()
+    assert np.abs(S - S.T).max() <= 1e-14 * sc
+    assert np.abs(A[1.0, 10.0] + A[-1.0, 10.0] - 2 * A[0.0, 10.0]).max() <= 1e-14 * sc
+    P = (A[1.0, 30.0] - A[1.0, 10.0]) / 20.0                   # the penalty matrix per unit gamma
+    assert np.abs(P - P.T).max() <= 1e-14 * sc and np.linalg.eigvalsh(P).min() > -1e-12 * sc
+    assert np.linalg.eigvalsh(A[1.0, 30.0]).min() > 0
+    interior = (2 * 2 * 2) + (3 * 1 * 2) + (3 * 2 * 1)
+    assert rp[-1] == 27 * 27 * (mesh.n_cells + 2 * interior)
