@@ -380,6 +380,59 @@ int fe_compliance(fe_dirichlet* d, const double* coefficients, const double* bod
 /* Frees the constrained system (before its space). */
 void fe_dirichlet_destroy(fe_dirichlet* d);
 
+/* ------------------------------------------------------------------------
+ * Interior penalty discontinuous Galerkin for the Poisson problem (paper,
+ * Sect. "Non-conforming methods", Eq. ip_dg_formulations, Eq.
+ * mean_and_jump_ops, Eq. local_to_face_matrix). The space is discontinuous
+ * Q_p on the mesh: DOF a of cell K is K*(p+1)^3 + a (a lexicographic). The
+ * operator is
+ *   sum_K int_K grad u . grad v
+ *   + sum_{interior F} ( - int [v].{grad u} - tau int [u].{grad v} + gamma/|F| int [u].[v] )
+ *   + sum_{boundary F} ( - int v grad u.n - tau int u grad v.n + gamma/|F| int u v ),
+ * the right-hand side int f v (homogeneous weak Dirichlet data, u_D = 0).
+ * Interior facets take K+ = the lower cell id; each contributes the four
+ * blocks (K+K+, K+K-, K-K+, K-K-), row = test function, column = trial
+ * function. Facet integrals use (p+1)^2 Gauss points; every facet integral is
+ * FP64.
+ * ------------------------------------------------------------------------ */
+typedef struct fe_dg fe_dg; /* opaque, library-owned */
+
+/* Builds the DG space on a conforming hexahedral mesh (any local vertex
+ * orientation): the cell integration of the Poisson Q_p element, the facets
+ * (neighbours matched by their 4 vertex ids) and the CSR pattern (each row of
+ * cell K: the DOFs of K and of its face neighbours, columns ascending).
+ * _host: no GPU use (inspection: sizes, pattern, facets). Errors as for
+ * fe_space_create. */
+int fe_dg_create(const fe_mesh_desc* mesh, int order, fe_dg** out);
+int fe_dg_create_host(const fe_mesh_desc* mesh, int order, fe_dg** out);
+
+/* Numbers of DOFs, CSR nonzeros, interior and boundary facets (any may be NULL). */
+int fe_dg_sizes(const fe_dg* g, int64_t* n_dofs, int64_t* nnz, int64_t* n_interior, int64_t* n_boundary);
+
+/* CSR pattern: row_ptr [n_dofs+1] int64, col_idx [nnz] int32. _host: host
+ * pointers; plain: device pointers, copied asynchronously on `stream`. */
+int fe_dg_csr_pattern_host(const fe_dg* g, int64_t* row_ptr, int32_t* col_idx);
+int fe_dg_csr_pattern(const fe_dg* g, int64_t* row_ptr, int32_t* col_idx, void* stream);
+
+/* Facets (host): interior facet i joins cells plus[i] < minus[i] through local
+ * faces plus_face[i], minus_face[i] (face f lies on xhat_{f/2} = f%2);
+ * boundary facet j is face bnd_face[j] of cell bnd_cell[j]. Arrays may be NULL. */
+int fe_dg_facets_host(const fe_dg* g, int32_t* plus, int32_t* minus, uint8_t* plus_face, uint8_t* minus_face,
+                      int32_t* bnd_cell, uint8_t* bnd_face);
+
+/* Assembles the DG system: tau (the method: 1 symmetric, -1 non-symmetric, 0
+ * incomplete IP), gamma > 0 (penalty), source f (constant). prec selects the
+ * arithmetic of the cell integrals (as in fe_assemble); facet integrals and
+ * the sums into CSR are FP64, in a fixed order (deterministic).
+ *   csr_values  device [nnz] FP64, overwritten.
+ *   rhs         device [n_dofs] FP64, overwritten; may be NULL.
+ * The facet blocks go to device scratch allocated by fe_dg_create
+ * (4 (p+1)^6 doubles per interior and (p+1)^6 per boundary facet). */
+int fe_dg_assemble(fe_dg* g, double tau, double gamma, double source, double* csr_values, double* rhs,
+                   fe_precision prec, void* stream);
+
+void fe_dg_destroy(fe_dg* g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -46,6 +46,8 @@ struct HostSetup {
 };
 
 void build_ref_tables(int p, int nq1d, RefTables* t);
+// n-point Gauss-Legendre rule on [0,1].
+void gauss_rule(int n, double* x, double* w);
 // Numbering, pattern and permutation of a space of order p for `problem`
 // (FE_POISSON, FE_ELASTICITY, FE_STOKES). Returns 0 or an FE_ERR_* code
 // (message in *err).

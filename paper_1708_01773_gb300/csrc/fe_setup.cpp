@@ -72,6 +72,8 @@ static void lagrange_01(int p, double x, double* val, double* der) {
   }
 }
 
+void gauss_rule(int n, double* x, double* w) { gauss_rule_01(n, x, w); }
+
 void build_ref_tables(int p, int nq1d, RefTables* t) {
   t->p = p;
   t->nq1d = nq1d;

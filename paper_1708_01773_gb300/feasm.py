@@ -32,9 +32,11 @@ EXPORTS = [
     "fe_batch_assemble", "fe_batch_destroy", "fe_space_dof_points_host", "fe_dirichlet_create", "fe_dirichlet_sizes",
     "fe_dirichlet_labels_host", "fe_dirichlet_csr_pattern_host", "fe_dirichlet_csr_pattern",
     "fe_dirichlet_permutation_host", "fe_dirichlet_lift_host", "fe_assemble_dirichlet", "fe_dirichlet_destroy",
-    "fe_compliance_work_size", "fe_compliance", "fe_space_block_offset",
+    "fe_compliance_work_size", "fe_compliance", "fe_space_block_offset", "fe_dg_create", "fe_dg_create_host",
+    "fe_dg_sizes", "fe_dg_csr_pattern_host", "fe_dg_csr_pattern", "fe_dg_facets_host", "fe_dg_assemble",
+    "fe_dg_destroy",
 ]
-_VOID = ("fe_space_destroy", "fe_last_error", "fe_batch_destroy", "fe_dirichlet_destroy")
+_VOID = ("fe_space_destroy", "fe_last_error", "fe_batch_destroy", "fe_dirichlet_destroy", "fe_dg_destroy")
 
 
 class FEError(RuntimeError):
@@ -92,6 +94,15 @@ def lib() -> ctypes.CDLL:
         L.fe_assemble_dirichlet.argtypes = [V, V, V, V, V, V, I, V]
         L.fe_compliance_work_size.argtypes = [V, P(I64)]
         L.fe_space_block_offset.argtypes = [V, P(I64)]
+        L.fe_dg_create.argtypes = [P(MeshDesc), I, P(V)]
+        L.fe_dg_create_host.argtypes = [P(MeshDesc), I, P(V)]
+        L.fe_dg_sizes.argtypes = [V, P(I64), P(I64), P(I64), P(I64)]
+        L.fe_dg_csr_pattern_host.argtypes = [V, V, V]
+        L.fe_dg_csr_pattern.argtypes = [V, V, V, V]
+        L.fe_dg_facets_host.argtypes = [V, V, V, V, V, V, V]
+        L.fe_dg_assemble.argtypes = [V, D, D, D, V, V, I, V]
+        L.fe_dg_destroy.argtypes = [V]
+        L.fe_dg_destroy.restype = None
         L.fe_compliance.argtypes = [V, V, V, I, D, I, V, V, V, V, P(I), P(D), V]
         L.fe_dirichlet_destroy.argtypes = [V]
         L.fe_dirichlet_destroy.restype = None
@@ -481,6 +492,65 @@ class FESpace:
     def close(self):
         if self.handle:
             fe_space_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class DGSpace:
+    """Interior penalty DG (Poisson) space on a mesh: cell-local DOFs K*(p+1)^3 + a."""
+
+    def __init__(self, mesh, order: int, host_only: bool = False):
+        d, keep = _mesh_desc(mesh.coords, mesh.cell_vertices)
+        out = ctypes.c_void_p()
+        fn = lib().fe_dg_create_host if host_only else lib().fe_dg_create
+        _check(fn(ctypes.byref(d), int(order), ctypes.byref(out)), "fe_dg_create")
+        del keep
+        self.handle = out.value
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(lib().fe_dg_sizes(self.handle, *[ctypes.byref(x) for x in v]), "fe_dg_sizes")
+        self.n_dofs, self.nnz, self.n_interior, self.n_boundary = (x.value for x in v)
+
+    def pattern_host(self):
+        rp = np.zeros(self.n_dofs + 1, dtype=np.int64)
+        col = np.zeros(self.nnz, dtype=np.int32)
+        _check(lib().fe_dg_csr_pattern_host(self.handle, rp.ctypes.data, col.ctypes.data), "fe_dg_csr_pattern_host")
+        return rp, col
+
+    def pattern(self, device="cuda"):
+        import torch
+        rp = torch.empty(self.n_dofs + 1, dtype=torch.int64, device=device)
+        col = torch.empty(self.nnz, dtype=torch.int32, device=device)
+        _check(lib().fe_dg_csr_pattern(self.handle, _ptr(rp), _ptr(col), _stream(None)), "fe_dg_csr_pattern")
+        return rp, col
+
+    def facets(self):
+        ni, nb = self.n_interior, self.n_boundary
+        plus, minus = np.zeros(ni, np.int32), np.zeros(ni, np.int32)
+        pf, mf = np.zeros(ni, np.uint8), np.zeros(ni, np.uint8)
+        bc, bf = np.zeros(nb, np.int32), np.zeros(nb, np.uint8)
+        _check(lib().fe_dg_facets_host(self.handle, plus.ctypes.data, minus.ctypes.data, pf.ctypes.data,
+                                       mf.ctypes.data, bc.ctypes.data, bf.ctypes.data), "fe_dg_facets_host")
+        return plus, minus, pf, mf, bc, bf
+
+    def assemble(self, tau: float, gamma: float, source: float = 0.0, values=None, rhs=None, prec: str = "fp64",
+                 stream=None, device="cuda"):
+        import torch
+        if values is None:
+            values = torch.empty(self.nnz, dtype=torch.float64, device=device)
+        if rhs is None:
+            rhs = torch.empty(self.n_dofs, dtype=torch.float64, device=device)
+        _check(lib().fe_dg_assemble(self.handle, float(tau), float(gamma), float(source), _ptr(values), _ptr(rhs),
+                                    PRECISIONS[prec], _stream(stream)), "fe_dg_assemble")
+        return values, rhs
+
+    def close(self):
+        if self.handle:
+            lib().fe_dg_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

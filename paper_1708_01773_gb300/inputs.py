@@ -223,6 +223,13 @@ def stokes_q2q1_32(n: int = 32, seed_offset: int = 6) -> Problem:
     return Problem("stokes_q2q1_32", mesh, 2, 3, STOKES, coef, np.array([0.0, 0.0, -1.0]))
 
 
+def dg_q2_32(n: int = 32, seed_offset: int = 7) -> Mesh:
+    """Mesh of the interior penalty DG workload: 32^3 cells of the unit cube,
+    interior shifts up to 0.15h (discontinuous Q2, tau = 1, gamma = 10, f = 1)."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    return perturb_interior(brick(n, n, n), 0.15, rng)
+
+
 def unit_rms_field(n_dofs: int, seed: int) -> np.ndarray:
     """u_i ~ N(0,1) i.i.d., rescaled so that sqrt(mean(u^2)) = 1."""
     rng = np.random.default_rng(seed)
