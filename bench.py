@@ -52,7 +52,7 @@ def parse():
                     help="also time the 64-mesh batched assembly (host setup takes minutes)")
     ap.add_argument("--extra", action="append", default=None,
                     help="time only this secondary workload (repeatable): elasticity_q2_beam_clamped, "
-                         "cantilever_q1_64_compliance, stokes_q2q1_32, elasticity_q1_128, "
+                         "cantilever_q1_64_compliance, stokes_q2q1_32, dg_q2_32, elasticity_q1_128, "
                          "cantilever_q1_64_adjoint")
     return ap.parse_args()
 
@@ -383,7 +383,8 @@ def cantilever_compliance(dev, stream):
 def extra_workloads(args, dev, stream):
     """Secondary measurements (all, or those named by --extra): the clamped Q2 beam
     (strong Dirichlet conditions), the clamped cantilever's self-adjoint compliance
-    solve, the Stokes Taylor-Hood assembly, the scatter-bound 128^3 Q1 elasticity assembly, the 64^3 Q1 cantilever
+    solve, the Stokes Taylor-Hood assembly, the interior penalty DG assembly, the
+    scatter-bound 128^3 Q1 elasticity assembly, the 64^3 Q1 cantilever
     compliance adjoint and (with --batched) the batched assembly."""
     want = (lambda name: args.extra is None or name in args.extra)
     out = {}
@@ -393,6 +394,8 @@ def extra_workloads(args, dev, stream):
         out["cantilever_q1_64_compliance"] = cantilever_compliance(dev, stream)
     if want("stokes_q2q1_32"):
         out["stokes_q2q1_32"] = stokes_32(dev, stream)
+    if want("dg_q2_32"):
+        out["dg_q2_32"] = dg_32(dev, stream)
     if want("elasticity_q1_128"):
         out["elasticity_q1_128"] = q1_128(dev, stream)
     if want("cantilever_q1_64_adjoint"):
@@ -425,6 +428,32 @@ def stokes_32(dev, stream):
                      "cell_algorithmic_bytes": cb}
     sp.close()
     return {"cells": sp.n_cells, "dofs": sp.n_dofs, "velocity_dofs": sp.n_first, "nnz": sp.nnz, **rec}
+
+
+def dg_32(dev, stream):
+    """Interior penalty DG (Poisson, discontinuous Q2) on 32^3 cells, tau = 1,
+    gamma = 10, f = 1: assembly time per call (cell integrals, facet blocks, block
+    rows), and the algorithmic bytes of the facet and row kernels."""
+    import torch
+    from paper_1708_01773_gb300 import feasm, inputs
+    mesh = inputs.dg_q2_32()
+    g = feasm.DGSpace(mesh, 2)
+    vals = torch.empty(g.nnz, dtype=torch.float64, device=dev)
+    rhs = torch.empty(g.n_dofs, dtype=torch.float64, device=dev)
+    nb2 = 27 * 27
+    facet_bytes = (4 * g.n_interior + g.n_boundary) * nb2 * 8 + mesh.n_cells * 24 * 8
+    rec = {}
+    for prec in ("fp32", "fp64"):
+        tk = 8 if prec == "fp64" else 4
+        ms = time_events(lambda: g.assemble(1.0, 10.0, 1.0, vals, rhs, prec=prec, stream=stream), 10, stream)
+        row_bytes = (mesh.n_cells * nb2 * tk + (4 * g.n_interior + g.n_boundary) * nb2 * 8 + g.nnz * 8
+                     + (g.n_dofs + 1) * 8 + g.n_dofs * 16)
+        rec[prec] = {"ms_per_step": ms, "cells_per_s": mesh.n_cells / (ms / 1e3), "nnz_per_s": g.nnz / (ms / 1e3),
+                     "facet_algorithmic_bytes": int(facet_bytes), "row_algorithmic_bytes": int(row_bytes)}
+    out = {"cells": mesh.n_cells, "dofs": g.n_dofs, "nnz": g.nnz, "interior_facets": g.n_interior,
+           "boundary_facets": g.n_boundary, **rec}
+    g.close()
+    return out
 
 
 def q1_128(dev, stream):

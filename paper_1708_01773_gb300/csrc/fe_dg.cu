@@ -5,7 +5,8 @@
 // GB300 form: the cell integrals come from the Poisson cell kernels of an
 // internal fe_space of the same order (FP64 or FP32 form); the facet
 // integrals from k_dg_facets (FP64, one block per facet: its four nb x nb
-// blocks, or one for a boundary facet); k_dg_rows then writes each cell's
+// blocks, or one for a boundary facet, through small products over the face
+// nodes, where the shape functions do not vanish); k_dg_rows then writes each cell's
 // block row of the CSR matrix in one pass, the diagonal block being the cell
 // matrix plus the cell's six facet diagonal blocks in face order, the others
 // copies of facet off-diagonal blocks (fixed order: deterministic).
@@ -52,6 +53,7 @@ struct fe_dg {
   int32_t* d_fplus = nullptr;
   int32_t* d_fminus = nullptr;
   uint8_t* d_fpf = nullptr;
+  uint8_t* d_fmf = nullptr;
   uint8_t* d_fcorner = nullptr;
   int32_t* d_bcell = nullptr;
   uint8_t* d_bface = nullptr;
@@ -168,6 +170,7 @@ struct FacetParams {
   const int32_t* fplus;
   const int32_t* fminus;
   const uint8_t* fpf;
+  const uint8_t* fmf;
   const uint8_t* fcorner;
   const int32_t* bcell;
   const uint8_t* bface;
@@ -197,97 +200,185 @@ __device__ __forceinline__ void lagrange(double x, double* v, double* d) {
   }
 }
 
-// One block per facet (interior facets first, then boundary facets). Per
-// quadrature point and side: the reference point (K-: the bilinear blend of
-// the reference corners that carry K+'s face corners), FP64 geometry, the
-// physical normal and surface element from cof(J+) nhat (det J+ J+^{-T} nhat),
-// the shape values and normal derivatives; then every entry of the facet
-// blocks as a sum over the points in a fixed order.
+// Shared memory of k_dg_facets for order P (doubles unless noted).
+template <int P>
+struct FacetLayout {
+  static constexpr int N1 = P + 1, NB = N1 * N1 * N1, NQF = N1 * N1, NBF = N1 * N1;
+  static constexpr size_t GN = 0;                                        // [2][NQF][NB]   grad phi . n
+  static constexpr size_t PF = GN + size_t(2) * NQF * NB * 8;            // [2][NQF][NBF]  dS phi (face nodes)
+  static constexpr size_t FF = PF + size_t(2) * NQF * NBF * 8;           // [2][NQF][NBF]  phi (face nodes)
+  static constexpr size_t X1 = FF + size_t(2) * NQF * NBF * 8;           // [4][NBF][NB]
+  static constexpr size_t YY = X1 + size_t(4) * NBF * NB * 8;            // [4][NBF][NBF]
+  static constexpr size_t NRM = YY + size_t(4) * NBF * NBF * 8;          // [NQF][3]
+  static constexpr size_t DS = NRM + size_t(NQF) * 3 * 8;                // [NQF]
+  static constexpr size_t CN = DS + size_t(NQF) * 8 + 8;                 // [2][NQF][3]    cof^T n / det
+  static constexpr size_t VD = CN + size_t(2) * NQF * 3 * 8;             // [2][NQF][2][3][N1] Lagrange values, derivatives
+  static constexpr size_t COF0 = VD + size_t(2) * NQF * 6 * N1 * 8;      // [NQF][10] side 0: cofactors, det
+  static constexpr size_t CIDX = COF0 + size_t(NQF) * 10 * 8;            // int [2][NB] compact face index or -1
+  static constexpr size_t BYTES = CIDX + size_t(2) * NB * sizeof(int);
+};
+
+// One block per facet (interior facets first, then boundary facets).
+//   1. per quadrature point of side 0: the physical normal and surface element
+//      from cof(J+) nhat = det J+ J+^{-T} nhat; the facet area |F|;
+//   2. per (side, point): the reference point (side 1: the bilinear blend of
+//      the reference corners that carry K+'s face corners, with the coordinate
+//      normal to K-'s face set exactly), FP64 geometry, the normal derivatives
+//      of all shape functions and the values of the (p+1)^2 face nodes (the
+//      other shape functions vanish on the face);
+//   3. the products X_{sa,sb} = sum_q dS phi^{sa}_{a'} (grad phi^{sb}_b . n)
+//      (a' a face node of side sa) and Y_{sa,sb} = sum_q dS phi^{sa}_{a'} phi^{sb}_{b'};
+//   4. block (sa, sb), row a, column b:
+//      -s_a/2 X_{sa,sb}[a'][b] - tau s_b/2 X_{sb,sa}[b'][a] + gamma/|F| s_a s_b Y_{sa,sb}[a'][b']
+//      (terms whose face node is missing are zero; boundary facets: one side,
+//      s = 1 and the factor 1/2 dropped), Eq. local_to_face_matrix.
 template <int P>
 __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
-  constexpr int N1 = P + 1, NB = N1 * N1 * N1, NQF = N1 * N1;
-  __shared__ double phi[2][NQF][NB], gn[2][NQF][NB];
-  __shared__ double nrm[NQF][3], dS[NQF];
-  __shared__ double s_area;
+  using L = FacetLayout<P>;
+  constexpr int N1 = L::N1, NB = L::NB, NQF = L::NQF, NBF = L::NBF;
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* gn = reinterpret_cast<double*>(sm + L::GN);
+  double* pf = reinterpret_cast<double*>(sm + L::PF);
+  double* ff = reinterpret_cast<double*>(sm + L::FF);
+  double* x1 = reinterpret_cast<double*>(sm + L::X1);
+  double* yy = reinterpret_cast<double*>(sm + L::YY);
+  double* nrm = reinterpret_cast<double*>(sm + L::NRM);
+  double* dS = reinterpret_cast<double*>(sm + L::DS);
+  double* s_area = dS + NQF;
+  int* cidx = reinterpret_cast<int*>(sm + L::CIDX);
   const int t = threadIdx.x;
   for (int64_t id = blockIdx.x; id < fp.n_int + fp.n_bnd; id += gridDim.x) {
     const bool interior = id < fp.n_int;
     const int64_t i = interior ? id : id - fp.n_int;
     const int ns = interior ? 2 : 1;
-    const int fplus_face = interior ? fp.fpf[i] : fp.bface[i];
+    const int face[2] = {interior ? int(fp.fpf[i]) : int(fp.bface[i]), interior ? int(fp.fmf[i]) : 0};
+    const int64_t cell[2] = {interior ? int64_t(fp.fplus[i]) : int64_t(fp.bcell[i]),
+                             interior ? int64_t(fp.fminus[i]) : 0};
+    // compact index of each side's face nodes (node index along the face normal = the face's side)
+    for (int it = t; it < ns * NB; it += blockDim.x) {
+      const int s = it / NB, a = it % NB, d = face[s] / 2;
+      const int ad = (a / (d == 0 ? 1 : (d == 1 ? N1 : N1 * N1))) % N1;
+      int c = -1;
+      if (ad == (face[s] % 2) * P) {
+        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+        const int st1 = d1 == 0 ? 1 : (d1 == 1 ? N1 : N1 * N1), st2 = d2 == 0 ? 1 : (d2 == 1 ? N1 : N1 * N1);
+        c = (a / st1) % N1 + N1 * ((a / st2) % N1);
+      }
+      cidx[s * NB + a] = c;
+    }
+    double* cnv = reinterpret_cast<double*>(sm + L::CN);
+    double* vd = reinterpret_cast<double*>(sm + L::VD);
+    double* cof0 = reinterpret_cast<double*>(sm + L::COF0);
+    // 1. side 0 per point: geometry, normal, surface element; then |F|
+    // 2a. per (side, point): geometry (side 0 from step 1), cof^T n / det, Lagrange data
     for (int pass = 0; pass < 2; ++pass) {
-      // pass 0: side 0 only, the normal and surface element; pass 1: shape data of both sides
       for (int it = t; it < (pass == 0 ? 1 : ns) * NQF; it += blockDim.x) {
         const int side = it / NQF, q = it % NQF, qs = q % N1, qt = q / N1;
         const double s = fp.gx[qs], tt = fp.gx[qt];
-        const int64_t cell = side == 0 ? (interior ? fp.fplus[i] : fp.bcell[i]) : fp.fminus[i];
         double xh[3];
         if (side == 0) {
-          const int d = fplus_face / 2, d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-          xh[d] = double(fplus_face % 2);
+          const int d = face[0] / 2, d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+          xh[d] = double(face[0] % 2);
           xh[d1] = s;
           xh[d2] = tt;
         } else {
-          const double L[4] = {(1 - s) * (1 - tt), s * (1 - tt), (1 - s) * tt, s * tt};
+          const double Lw[4] = {(1 - s) * (1 - tt), s * (1 - tt), (1 - s) * tt, s * tt};
           xh[0] = xh[1] = xh[2] = 0.0;
 #pragma unroll
           for (int c = 0; c < 4; ++c) {
             const int v = fp.fcorner[4 * i + c];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) xh[k] += L[c] * double((v >> k) & 1);
+            for (int k = 0; k < 3; ++k) xh[k] += Lw[c] * double((v >> k) & 1);
           }
+          xh[face[1] / 2] = double(face[1] % 2);
         }
-        double xv[24], a[21], cof[9], det;
+        double cof[9], det;
+        if (pass == 1 && side == 0) {
 #pragma unroll
-        for (int k = 0; k < 24; ++k) xv[k] = fp.xv[cell * 24 + k];
+          for (int k = 0; k < 9; ++k) cof[k] = cof0[q * 10 + k];
+          det = cof0[q * 10 + 9];
+        } else {
+          double xv[24], a[21];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) trilinear_coefficients(xv, k, a);
-        geometry_at(a, xh[0], xh[1], xh[2], cof, &det);
-        if (!(det > 0.0)) atomicOr(fp.err, kErrNegJacobian);
+          for (int k = 0; k < 24; ++k) xv[k] = fp.xv[cell[side] * 24 + k];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) trilinear_coefficients(xv, k, a);
+          geometry_at(a, xh[0], xh[1], xh[2], cof, &det);
+          if (!(det > 0.0)) atomicOr(fp.err, kErrNegJacobian);
+        }
         if (pass == 0) {
-          const int d = fplus_face / 2;
-          const double sg = fplus_face % 2 ? 1.0 : -1.0;
+          const int d = face[0] / 2;
+          const double sg = face[0] % 2 ? 1.0 : -1.0;
           const double nd[3] = {sg * cof[d], sg * cof[3 + d], sg * cof[6 + d]};
           const double len = sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
           dS[q] = len * fp.gw[qs] * fp.gw[qt];
 #pragma unroll
-          for (int k = 0; k < 3; ++k) nrm[q][k] = nd[k] / len;
+          for (int k = 0; k < 3; ++k) nrm[q * 3 + k] = nd[k] / len;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) cof0[q * 10 + k] = cof[k];
+          cof0[q * 10 + 9] = det;
           continue;
         }
-        double V[3][N1], D[3][N1];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) lagrange<P>(xh[k], V[k], D[k]);
         const double rdet = 1.0 / det;
-        for (int b = 0; b < NB; ++b) {
-          const int b0 = b % N1, b1 = (b / N1) % N1, b2 = b / (N1 * N1);
-          const double gr[3] = {D[0][b0] * V[1][b1] * V[2][b2], V[0][b0] * D[1][b1] * V[2][b2],
-                                V[0][b0] * V[1][b1] * D[2][b2]};
-          double g = 0.0;
 #pragma unroll
-          for (int k = 0; k < 3; ++k)
-            g += nrm[q][k] * (cof[3 * k] * gr[0] + cof[3 * k + 1] * gr[1] + cof[3 * k + 2] * gr[2]);
-          phi[side][q][b] = V[0][b0] * V[1][b1] * V[2][b2];
-          gn[side][q][b] = g * rdet;
-        }
+        for (int d = 0; d < 3; ++d)
+          cnv[(side * NQF + q) * 3 + d] =
+              (cof[d] * nrm[q * 3] + cof[3 + d] * nrm[q * 3 + 1] + cof[6 + d] * nrm[q * 3 + 2]) * rdet;
+        double* V = vd + (side * NQF + q) * 6 * N1;  // V[k][m] at k*N1 + m, D at (3 + k)*N1 + m
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lagrange<P>(xh[k], V + k * N1, V + (3 + k) * N1);
       }
       __syncthreads();
       if (pass == 0 && t == 0) {
         double ar = 0.0;
         for (int q = 0; q < NQF; ++q) ar += dS[q];
-        s_area = ar;
+        *s_area = ar;
       }
       __syncthreads();
     }
-    const double pen = fp.gamma / s_area, half = interior ? 0.5 : 1.0;
-    // entries: block blk = 2 sa + sb (rows: side sa, columns: side sb), row a, column b
-    for (int it = t; it < ns * ns * NB * NB; it += blockDim.x) {
-      const int blk = it / (NB * NB), sa_ = blk >> 1, sb_ = blk & 1;
-      const int a = (it / NB) % NB, b = it % NB;
-      const double sga = sa_ ? -1.0 : 1.0, sgb = sb_ ? -1.0 : 1.0;
+    // 2b. per (side, point, node): normal derivative; value and dS value on face nodes
+    for (int it = t; it < ns * NQF * NB; it += blockDim.x) {
+      const int side = it / (NQF * NB), q = (it / NB) % NQF, b = it % NB;
+      const int b0 = b % N1, b1 = (b / N1) % N1, b2 = b / (N1 * N1);
+      const double* V = vd + (side * NQF + q) * 6 * N1;
+      const double* D = V + 3 * N1;
+      const double* cn = cnv + (side * NQF + q) * 3;
+      const double v0 = V[b0], v1 = V[N1 + b1], v2 = V[2 * N1 + b2];
+      gn[(side * NQF + q) * NB + b] = cn[0] * D[b0] * v1 * v2 + cn[1] * v0 * D[N1 + b1] * v2 + cn[2] * v0 * v1 * D[2 * N1 + b2];
+      const int c = cidx[side * NB + b];
+      if (c >= 0) {
+        const double ph = v0 * v1 * v2;
+        ff[(side * NQF + q) * NBF + c] = ph;
+        pf[(side * NQF + q) * NBF + c] = dS[q] * ph;
+      }
+    }
+    __syncthreads();
+    // 3. X_{sa,sb} scaled by -s_a/2 (boundary: -1) and Y_{sa,sb} scaled by s_a s_b
+    const double half = interior ? 0.5 : 1.0;
+    for (int it = t; it < ns * ns * NBF * NB; it += blockDim.x) {
+      const int blk = it / (NBF * NB), sa = blk >> 1, sb = blk & 1, c = (it / NB) % NBF, b = it % NB;
       double v = 0.0;
-      for (int q = 0; q < NQF; ++q)
-        v += dS[q] * (-sga * phi[sa_][q][a] * half * gn[sb_][q][b] - fp.tau * sgb * phi[sb_][q][b] * half * gn[sa_][q][a]
-                      + pen * sga * sgb * phi[sa_][q][a] * phi[sb_][q][b]);
+      for (int q = 0; q < NQF; ++q) v += pf[(sa * NQF + q) * NBF + c] * gn[(sb * NQF + q) * NB + b];
+      x1[(blk * NBF + c) * NB + b] = (sa ? half : -half) * v;
+    }
+    for (int it = t; it < ns * ns * NBF * NBF; it += blockDim.x) {
+      const int blk = it / (NBF * NBF), sa = blk >> 1, sb = blk & 1, c = (it / NBF) % NBF, e = it % NBF;
+      double v = 0.0;
+      for (int q = 0; q < NQF; ++q) v += pf[(sa * NQF + q) * NBF + c] * ff[(sb * NQF + q) * NBF + e];
+      yy[(blk * NBF + c) * NBF + e] = sa == sb ? v : -v;
+    }
+    __syncthreads();
+    // 4. the facet blocks: X term, tau times the transposed X term of the
+    //    swapped block, gamma/|F| times the Y term (entries with no face node:
+    //    zero, no arithmetic)
+    const double pen = fp.gamma / *s_area;
+    for (int it = t; it < ns * ns * NB * NB; it += blockDim.x) {
+      const int blk = it / (NB * NB), sa = blk >> 1, sb = blk & 1, a = (it / NB) % NB, b = it % NB;
+      const int ca = cidx[sa * NB + a], cb = cidx[sb * NB + b];
+      double v = 0.0;
+      if (ca >= 0) v = x1[(blk * NBF + ca) * NB + b];
+      if (cb >= 0) v = fma(fp.tau, x1[(((sb << 1) | sa) * NBF + cb) * NB + a], v);
+      if (ca >= 0 && cb >= 0) v = fma(pen, yy[(blk * NBF + ca) * NBF + cb], v);
       if (interior)
         fp.fblk[(i * 4 + blk) * NB * NB + a * NB + b] = v;
       else
@@ -368,6 +459,7 @@ cudaError_t launch(const fe_dg* g, double tau, double gamma, double* values, dou
   fp.fplus = g->d_fplus;
   fp.fminus = g->d_fminus;
   fp.fpf = g->d_fpf;
+  fp.fmf = g->d_fmf;
   fp.fcorner = g->d_fcorner;
   fp.bcell = g->d_bcell;
   fp.bface = g->d_bface;
@@ -379,8 +471,12 @@ cudaError_t launch(const fe_dg* g, double tau, double gamma, double* values, dou
   fp.bblk = g->d_bblk;
   fp.err = g->s->d_err;
   const int64_t nf = fp.n_int + fp.n_bnd;
-  if (nf > 0)
-    k_dg_facets<P><<<int(std::min<int64_t>(nf, int64_t(nsm) * 16)), 128, 0, st>>>(fp);
+  if (nf > 0) {
+    constexpr size_t smem = FacetLayout<P>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(k_dg_facets<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_dg_facets<P><<<int(std::min<int64_t>(nf, int64_t(nsm) * 16)), 128, smem, st>>>(fp);
+  }
   RowParams rp;
   rp.n_cells = g->n_cells;
   rp.nb = NB;
@@ -418,7 +514,7 @@ cudaError_t upload_vec(T** dst, const std::vector<T>& src) {
 }
 
 void free_dg(fe_dg* g) {
-  void* ptrs[] = {g->d_fplus, g->d_fminus, g->d_fpf, g->d_fcorner, g->d_bcell, g->d_bface, g->d_face_code,
+  void* ptrs[] = {g->d_fplus, g->d_fminus, g->d_fpf, g->d_fmf, g->d_fcorner, g->d_bcell, g->d_bface, g->d_face_code,
                   g->d_slots, g->d_nslot, g->d_row_ptr, g->d_col, g->d_ones, g->d_fblk, g->d_bblk, g->d_gx, g->d_gw};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -466,6 +562,7 @@ int dg_create(const fe_mesh_desc* mesh, int order, bool host_only, fe_dg** out) 
     cudaError_t e = upload_vec(&g->d_fplus, g->fplus);
     if (e == cudaSuccess) e = upload_vec(&g->d_fminus, g->fminus);
     if (e == cudaSuccess) e = upload_vec(&g->d_fpf, g->fpf);
+    if (e == cudaSuccess) e = upload_vec(&g->d_fmf, g->fmf);
     if (e == cudaSuccess) e = upload_vec(&g->d_fcorner, g->fcorner);
     if (e == cudaSuccess) e = upload_vec(&g->d_bcell, g->bcell);
     if (e == cudaSuccess) e = upload_vec(&g->d_bface, g->bface);
