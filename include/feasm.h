@@ -392,8 +392,8 @@ void fe_dirichlet_destroy(fe_dirichlet* d);
  * the right-hand side int f v (homogeneous weak Dirichlet data, u_D = 0).
  * Interior facets take K+ = the lower cell id; each contributes the four
  * blocks (K+K+, K+K-, K-K+, K-K-), row = test function, column = trial
- * function. Facet integrals use (p+1)^2 Gauss points; every facet integral is
- * FP64.
+ * function. Facet integrals use (p+1)^2 Gauss points and FP64 geometry; their
+ * products are FP64 in the FP64 form and FP32 in the FP32 and BF16 forms.
  * ------------------------------------------------------------------------ */
 typedef struct fe_dg fe_dg; /* opaque, library-owned */
 
@@ -422,12 +422,14 @@ int fe_dg_facets_host(const fe_dg* g, int32_t* plus, int32_t* minus, uint8_t* pl
 
 /* Assembles the DG system: tau (the method: 1 symmetric, -1 non-symmetric, 0
  * incomplete IP), gamma > 0 (penalty), source f (constant). prec selects the
- * arithmetic of the cell integrals (as in fe_assemble); facet integrals and
- * the sums into CSR are FP64, in a fixed order (deterministic).
+ * arithmetic of the cell integrals (as in fe_assemble) and of the facet
+ * products; each CSR value is formed in a fixed order (deterministic), the
+ * diagonal blocks' sums exactly rounded to FP64 in the FP32 forms.
  *   csr_values  device [nnz] FP64, overwritten.
  *   rhs         device [n_dofs] FP64, overwritten; may be NULL.
  * The facet blocks go to device scratch allocated by fe_dg_create
- * (4 (p+1)^6 doubles per interior and (p+1)^6 per boundary facet). */
+ * (4 (p+1)^6 doubles per interior and (p+1)^6 per boundary facet; the FP32
+ * forms use half of it). */
 int fe_dg_assemble(fe_dg* g, double tau, double gamma, double source, double* csr_values, double* rhs,
                    fe_precision prec, void* stream);
 

@@ -4,9 +4,10 @@
 //
 // GB300 form: the cell integrals come from the Poisson cell kernels of an
 // internal fe_space of the same order (FP64 or FP32 form); the facet
-// integrals from k_dg_facets (FP64, one block per facet: its four nb x nb
+// integrals from k_dg_facets (one block per facet: its four nb x nb
 // blocks, or one for a boundary facet, through small products over the face
-// nodes, where the shape functions do not vanish); k_dg_rows then writes each cell's
+// nodes, where the shape functions do not vanish; FP64 geometry, products in
+// FP64 for the FP64 form and in FP32 for the FP32 forms); k_dg_rows then writes each cell's
 // block row of the CSR matrix in one pass, the diagonal block being the cell
 // matrix plus the cell's six facet diagonal blocks in face order, the others
 // copies of facet off-diagonal blocks (fixed order: deterministic).
@@ -18,6 +19,7 @@
 #include <map>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fe_device.cuh"
@@ -177,8 +179,8 @@ struct FacetParams {
   const double* gx;  // face Gauss points [n1] on [0,1]
   const double* gw;
   double tau, gamma;
-  double* fblk;
-  double* bblk;
+  void* fblk;  // [n_int][4][nb][nb], double (FP64 form) or float
+  void* bblk;  // [n_bnd][nb][nb]
   int* err;
 };
 
@@ -200,16 +202,18 @@ __device__ __forceinline__ void lagrange(double x, double* v, double* d) {
   }
 }
 
-// Shared memory of k_dg_facets for order P (doubles unless noted).
-template <int P>
+// Shared memory of k_dg_facets for order P: the products' operands and
+// results in TB (FP64 form: double; FP32 forms: float), the rest double.
+template <int P, typename TB>
 struct FacetLayout {
   static constexpr int N1 = P + 1, NB = N1 * N1 * N1, NQF = N1 * N1, NBF = N1 * N1;
+  static constexpr size_t S = sizeof(TB);
   static constexpr size_t GN = 0;                                        // [2][NQF][NB]   grad phi . n
-  static constexpr size_t PF = GN + size_t(2) * NQF * NB * 8;            // [2][NQF][NBF]  dS phi (face nodes)
-  static constexpr size_t FF = PF + size_t(2) * NQF * NBF * 8;           // [2][NQF][NBF]  phi (face nodes)
-  static constexpr size_t X1 = FF + size_t(2) * NQF * NBF * 8;           // [4][NBF][NB]
-  static constexpr size_t YY = X1 + size_t(4) * NBF * NB * 8;            // [4][NBF][NBF]
-  static constexpr size_t NRM = YY + size_t(4) * NBF * NBF * 8;          // [NQF][3]
+  static constexpr size_t PF = GN + size_t(2) * NQF * NB * S;            // [2][NQF][NBF]  dS phi (face nodes)
+  static constexpr size_t FF = PF + size_t(2) * NQF * NBF * S;           // [2][NQF][NBF]  phi (face nodes)
+  static constexpr size_t X1 = FF + size_t(2) * NQF * NBF * S;           // [4][NBF][NB]
+  static constexpr size_t YY = X1 + size_t(4) * NBF * NB * S;            // [4][NBF][NBF]
+  static constexpr size_t NRM = (YY + size_t(4) * NBF * NBF * S + 15) & ~size_t(15);  // [NQF][3]
   static constexpr size_t DS = NRM + size_t(NQF) * 3 * 8;                // [NQF]
   static constexpr size_t CN = DS + size_t(NQF) * 8 + 8;                 // [2][NQF][3]    cof^T n / det
   static constexpr size_t VD = CN + size_t(2) * NQF * 3 * 8;             // [2][NQF][2][3][N1] Lagrange values, derivatives
@@ -232,16 +236,22 @@ struct FacetLayout {
 //      -s_a/2 X_{sa,sb}[a'][b] - tau s_b/2 X_{sb,sa}[b'][a] + gamma/|F| s_a s_b Y_{sa,sb}[a'][b']
 //      (terms whose face node is missing are zero; boundary facets: one side,
 //      s = 1 and the factor 1/2 dropped), Eq. local_to_face_matrix.
-template <int P>
+// FP32 forms (TB = float): geometry, normals and shape data in FP64, rounded
+// to FP32 on the integer bits for steps 3 and 4, blocks stored in FP32.
+template <int P, typename TB>
 __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
-  using L = FacetLayout<P>;
+  using L = FacetLayout<P, TB>;
+  constexpr bool F32 = std::is_same<TB, float>::value;
+  auto cvt = [](double x) -> TB {
+    if constexpr (F32) return d2f_rn(x); else return x;
+  };
   constexpr int N1 = L::N1, NB = L::NB, NQF = L::NQF, NBF = L::NBF;
   extern __shared__ __align__(16) unsigned char sm[];
-  double* gn = reinterpret_cast<double*>(sm + L::GN);
-  double* pf = reinterpret_cast<double*>(sm + L::PF);
-  double* ff = reinterpret_cast<double*>(sm + L::FF);
-  double* x1 = reinterpret_cast<double*>(sm + L::X1);
-  double* yy = reinterpret_cast<double*>(sm + L::YY);
+  TB* gn = reinterpret_cast<TB*>(sm + L::GN);
+  TB* pf = reinterpret_cast<TB*>(sm + L::PF);
+  TB* ff = reinterpret_cast<TB*>(sm + L::FF);
+  TB* x1 = reinterpret_cast<TB*>(sm + L::X1);
+  TB* yy = reinterpret_cast<TB*>(sm + L::YY);
   double* nrm = reinterpret_cast<double*>(sm + L::NRM);
   double* dS = reinterpret_cast<double*>(sm + L::DS);
   double* s_area = dS + NQF;
@@ -344,45 +354,47 @@ __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
       const double* D = V + 3 * N1;
       const double* cn = cnv + (side * NQF + q) * 3;
       const double v0 = V[b0], v1 = V[N1 + b1], v2 = V[2 * N1 + b2];
-      gn[(side * NQF + q) * NB + b] = cn[0] * D[b0] * v1 * v2 + cn[1] * v0 * D[N1 + b1] * v2 + cn[2] * v0 * v1 * D[2 * N1 + b2];
+      gn[(side * NQF + q) * NB + b] = cvt(cn[0] * D[b0] * v1 * v2 + cn[1] * v0 * D[N1 + b1] * v2 + cn[2] * v0 * v1 * D[2 * N1 + b2]);
       const int c = cidx[side * NB + b];
       if (c >= 0) {
         const double ph = v0 * v1 * v2;
-        ff[(side * NQF + q) * NBF + c] = ph;
-        pf[(side * NQF + q) * NBF + c] = dS[q] * ph;
+        ff[(side * NQF + q) * NBF + c] = cvt(ph);
+        pf[(side * NQF + q) * NBF + c] = cvt(dS[q] * ph);
       }
     }
     __syncthreads();
     // 3. X_{sa,sb} scaled by -s_a/2 (boundary: -1) and Y_{sa,sb} scaled by s_a s_b
-    const double half = interior ? 0.5 : 1.0;
+    const TB half = interior ? TB(0.5) : TB(1);
     for (int it = t; it < ns * ns * NBF * NB; it += blockDim.x) {
       const int blk = it / (NBF * NB), sa = blk >> 1, sb = blk & 1, c = (it / NB) % NBF, b = it % NB;
-      double v = 0.0;
-      for (int q = 0; q < NQF; ++q) v += pf[(sa * NQF + q) * NBF + c] * gn[(sb * NQF + q) * NB + b];
+      TB v = TB(0);
+      for (int q = 0; q < NQF; ++q) v = fma(pf[(sa * NQF + q) * NBF + c], gn[(sb * NQF + q) * NB + b], v);
       x1[(blk * NBF + c) * NB + b] = (sa ? half : -half) * v;
     }
     for (int it = t; it < ns * ns * NBF * NBF; it += blockDim.x) {
       const int blk = it / (NBF * NBF), sa = blk >> 1, sb = blk & 1, c = (it / NBF) % NBF, e = it % NBF;
-      double v = 0.0;
-      for (int q = 0; q < NQF; ++q) v += pf[(sa * NQF + q) * NBF + c] * ff[(sb * NQF + q) * NBF + e];
+      TB v = TB(0);
+      for (int q = 0; q < NQF; ++q) v = fma(pf[(sa * NQF + q) * NBF + c], ff[(sb * NQF + q) * NBF + e], v);
       yy[(blk * NBF + c) * NBF + e] = sa == sb ? v : -v;
     }
     __syncthreads();
     // 4. the facet blocks: X term, tau times the transposed X term of the
     //    swapped block, gamma/|F| times the Y term (entries with no face node:
     //    zero, no arithmetic)
-    const double pen = fp.gamma / *s_area;
+    const TB pen = cvt(fp.gamma / *s_area), tau = cvt(fp.tau);
+    TB* fblk = static_cast<TB*>(fp.fblk);
+    TB* bblk = static_cast<TB*>(fp.bblk);
     for (int it = t; it < ns * ns * NB * NB; it += blockDim.x) {
       const int blk = it / (NB * NB), sa = blk >> 1, sb = blk & 1, a = (it / NB) % NB, b = it % NB;
       const int ca = cidx[sa * NB + a], cb = cidx[sb * NB + b];
-      double v = 0.0;
+      TB v = TB(0);
       if (ca >= 0) v = x1[(blk * NBF + ca) * NB + b];
-      if (cb >= 0) v = fma(fp.tau, x1[(((sb << 1) | sa) * NBF + cb) * NB + a], v);
+      if (cb >= 0) v = fma(tau, x1[(((sb << 1) | sa) * NBF + cb) * NB + a], v);
       if (ca >= 0 && cb >= 0) v = fma(pen, yy[(blk * NBF + ca) * NBF + cb], v);
       if (interior)
-        fp.fblk[(i * 4 + blk) * NB * NB + a * NB + b] = v;
+        fblk[(i * 4 + blk) * NB * NB + a * NB + b] = v;
       else
-        fp.bblk[i * NB * NB + a * NB + b] = v;
+        bblk[i * NB * NB + a * NB + b] = v;
     }
     __syncthreads();
   }
@@ -403,8 +415,8 @@ struct RowParams {
   const uint8_t* slots;
   const uint8_t* nslot;
   const int64_t* row_ptr;
-  const double* fblk;
-  const double* bblk;
+  const void* fblk;  // facet blocks in T (the facet kernel's storage type)
+  const void* bblk;
   double* values;
   double* rhs;
 };
@@ -412,10 +424,22 @@ struct RowParams {
 // One block per cell: every entry (block slot j, row a, column b) of the
 // cell's block row. The diagonal block is the cell matrix plus the diagonal
 // blocks of the cell's six facets in face order; a neighbour's block is the
-// facet's off-diagonal block (rows: this cell's side).
+// facet's off-diagonal block (rows: this cell's side). T is the storage of the
+// cell and facet blocks: FP64, or FP32, whose seven terms are summed as an
+// FP32 pair (TwoSum) and rounded once to FP64, and whose single terms convert
+// exactly on the integer bits.
+// Exact FP32 -> FP64 on the integer bits: the short path for zeros and normal
+// numbers, the general one otherwise.
+__device__ __forceinline__ double to_f64(float x) {
+  return f32_zero_or_normal(x) ? f32_to_f64_normal(x) : f32_to_f64_exact(x);
+}
+
 template <int NB, typename T>
 __global__ void __launch_bounds__(256) k_dg_rows(RowParams rp) {
+  constexpr bool F32 = std::is_same<T, float>::value;
   const T* ke = static_cast<const T*>(rp.ke);
+  const T* fblk = static_cast<const T*>(rp.fblk);
+  const T* bblk = static_cast<const T*>(rp.bblk);
   for (int64_t e = blockIdx.x; e < rp.n_cells; e += gridDim.x) {
     const int ns = rp.nslot[e];
     for (int it = threadIdx.x; it < ns * NB * NB; it += blockDim.x) {
@@ -423,21 +447,26 @@ __global__ void __launch_bounds__(256) k_dg_rows(RowParams rp) {
       const int slot = rp.slots[e * 7 + j];
       double v;
       if (slot == kSelf) {
-        v = double(ke[(e * NB + a) * int64_t(rp.nlp) + b]);
+        T hi = ke[(e * NB + a) * int64_t(rp.nlp) + b], lo = T(0);
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
           const int32_t code = rp.face_code[e * 6 + f];
-          if (code >= 0) {
-            const int side = code & 1;
-            v += rp.fblk[(int64_t(code >> 1) * 4 + 3 * side) * NB * NB + a * NB + b];
+          const T x = code >= 0 ? fblk[(int64_t(code >> 1) * 4 + 3 * (code & 1)) * NB * NB + a * NB + b]
+                                : bblk[int64_t(-1 - code) * NB * NB + a * NB + b];
+          if constexpr (F32) {
+            const T sum = hi + x, bp = sum - hi;
+            lo += (hi - (sum - bp)) + (x - bp);
+            hi = sum;
           } else {
-            v += rp.bblk[int64_t(-1 - code) * NB * NB + a * NB + b];
+            hi += x;
           }
         }
+        if constexpr (F32) v = to_f64(hi) + to_f64(lo); else v = hi;
       } else {
         const int32_t code = rp.face_code[e * 6 + slot];
         const int side = code & 1;  // this cell's side; the neighbour is on the other
-        v = rp.fblk[(int64_t(code >> 1) * 4 + 2 * side + (1 - side)) * NB * NB + a * NB + b];
+        const T x = fblk[(int64_t(code >> 1) * 4 + 2 * side + (1 - side)) * NB * NB + a * NB + b];
+        if constexpr (F32) v = to_f64(x); else v = x;
       }
       rp.values[rp.row_ptr[e * NB + a] + j * NB + b] = v;
     }
@@ -471,11 +500,17 @@ cudaError_t launch(const fe_dg* g, double tau, double gamma, double* values, dou
   fp.bblk = g->d_bblk;
   fp.err = g->s->d_err;
   const int64_t nf = fp.n_int + fp.n_bnd;
-  if (nf > 0) {
-    constexpr size_t smem = FacetLayout<P>::BYTES;
-    cudaError_t e = cudaFuncSetAttribute(k_dg_facets<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const int fblocks = int(std::min<int64_t>(std::max<int64_t>(nf, 1), int64_t(nsm) * 16));
+  if (nf > 0 && prec == FE_PREC_FP64) {
+    constexpr size_t smem = FacetLayout<P, double>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(k_dg_facets<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    k_dg_facets<P><<<int(std::min<int64_t>(nf, int64_t(nsm) * 16)), 128, smem, st>>>(fp);
+    k_dg_facets<P, double><<<fblocks, 128, smem, st>>>(fp);
+  } else if (nf > 0) {
+    constexpr size_t smem = FacetLayout<P, float>::BYTES;
+    cudaError_t e = cudaFuncSetAttribute(k_dg_facets<P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    k_dg_facets<P, float><<<fblocks, 128, smem, st>>>(fp);
   }
   RowParams rp;
   rp.n_cells = g->n_cells;
