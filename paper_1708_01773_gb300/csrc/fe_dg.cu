@@ -117,6 +117,17 @@ int setup_dg(fe_dg* g, const fe_mesh_desc* mesh, std::string* err) {
         }
         g->fcorner.push_back(uint8_t(lv));
       }
+      // K+'s face corners (s, t) = (0,0), (1,0), (0,1), (1,1) on K-'s reference
+      // corners: a symmetry of the square, i.e. corner (1,1) = (1,0) + (0,1) - (0,0)
+      // in every reference coordinate (the facet kernel relies on it)
+      const uint8_t* fc = g->fcorner.data() + g->fcorner.size() - 4;
+      for (int k = 0; k < 3; ++k) {
+        const int b[4] = {(fc[0] >> k) & 1, (fc[1] >> k) & 1, (fc[2] >> k) & 1, (fc[3] >> k) & 1};
+        if (b[3] != b[1] + b[2] - b[0]) {
+          *err = "facet corners of the two cells are not related by a symmetry of the square";
+          return FE_ERR_INVALID_ARG;
+        }
+      }
       g->face_code[size_t(kp) * 6 + fp] = 2 * i;
       g->face_code[size_t(e) * 6 + f] = 2 * i + 1;
     }
@@ -184,18 +195,18 @@ struct FacetParams {
   int* err;
 };
 
-// 1D Lagrange polynomials on the nodes m/P and their derivatives at x.
-template <int P>
-__device__ __forceinline__ void lagrange(double x, double* v, double* d) {
+// 1D Lagrange polynomials on the nodes m/P and their derivatives at x, in T.
+template <int P, typename T>
+__device__ __forceinline__ void lagrange(T x, T* v, T* d) {
 #pragma unroll
   for (int m = 0; m <= P; ++m) {
-    double val = 1.0, der = 0.0;
+    T val = T(1), der = T(0);
 #pragma unroll
     for (int s = 0; s <= P; ++s) {
       if (s == m) continue;
-      const double den = double(m - s) / P;
-      der = der * ((x - double(s) / P) / den) + val / den;
-      val *= (x - double(s) / P) / den;
+      const T den = T(m - s) / T(P);
+      der = der * ((x - T(s) / T(P)) / den) + val / den;
+      val *= (x - T(s) / T(P)) / den;
     }
     v[m] = val;
     d[m] = der;
@@ -203,41 +214,49 @@ __device__ __forceinline__ void lagrange(double x, double* v, double* d) {
 }
 
 // Shared memory of k_dg_facets for order P: the products' operands and
-// results in TB (FP64 form: double; FP32 forms: float), the rest double.
+// results, and the per-point shape data, in TB (FP64 form: double; FP32
+// forms: float); the trilinear coefficients and the facet area in double.
 template <int P, typename TB>
 struct FacetLayout {
   static constexpr int N1 = P + 1, NB = N1 * N1 * N1, NQF = N1 * N1, NBF = N1 * N1;
   static constexpr size_t S = sizeof(TB);
-  static constexpr size_t GN = 0;                                        // [2][NQF][NB]   grad phi . n
+  static constexpr size_t ACO = 0;                                       // double [2][21] trilinear coefficients
+  static constexpr size_t AREA = ACO + size_t(2) * 21 * 8;               // double |F|
+  static constexpr size_t GN = AREA + 8;                                 // [2][NQF][NB]   grad phi . n
   static constexpr size_t PF = GN + size_t(2) * NQF * NB * S;            // [2][NQF][NBF]  dS phi (face nodes)
   static constexpr size_t FF = PF + size_t(2) * NQF * NBF * S;           // [2][NQF][NBF]  phi (face nodes)
   static constexpr size_t X1 = FF + size_t(2) * NQF * NBF * S;           // [4][NBF][NB]
   static constexpr size_t YY = X1 + size_t(4) * NBF * NB * S;            // [4][NBF][NBF]
-  static constexpr size_t NRM = (YY + size_t(4) * NBF * NBF * S + 15) & ~size_t(15);  // [NQF][3]
-  static constexpr size_t DS = NRM + size_t(NQF) * 3 * 8;                // [NQF]
-  static constexpr size_t CN = DS + size_t(NQF) * 8 + 8;                 // [2][NQF][3]    cof^T n / det
-  static constexpr size_t VD = CN + size_t(2) * NQF * 3 * 8;             // [2][NQF][2][3][N1] Lagrange values, derivatives
-  static constexpr size_t COF0 = VD + size_t(2) * NQF * 6 * N1 * 8;      // [NQF][10] side 0: cofactors, det
-  static constexpr size_t CIDX = COF0 + size_t(NQF) * 10 * 8;            // int [2][NB] compact face index or -1
+  static constexpr size_t CN = YY + size_t(4) * NBF * NBF * S;           // [2][NQF][3]    cof^T n / det
+  static constexpr size_t VD = CN + size_t(2) * NQF * 3 * S;             // [2][NQF][2][3][N1] Lagrange values, derivatives
+  static constexpr size_t DS = VD + size_t(2) * NQF * 6 * N1 * S;        // [NQF] surface element x weight
+  static constexpr size_t CIDX = (DS + size_t(NQF) * S + 3) & ~size_t(3);  // int [2][NB] compact face index or -1
   static constexpr size_t BYTES = CIDX + size_t(2) * NB * sizeof(int);
 };
 
 // One block per facet (interior facets first, then boundary facets).
-//   1. per quadrature point of side 0: the physical normal and surface element
-//      from cof(J+) nhat = det J+ J+^{-T} nhat; the facet area |F|;
-//   2. per (side, point): the reference point (side 1: the bilinear blend of
-//      the reference corners that carry K+'s face corners, with the coordinate
-//      normal to K-'s face set exactly), FP64 geometry, the normal derivatives
-//      of all shape functions and the values of the (p+1)^2 face nodes (the
-//      other shape functions vanish on the face);
-//   3. the products X_{sa,sb} = sum_q dS phi^{sa}_{a'} (grad phi^{sb}_b . n)
+//   1. the trilinear coefficients of each side's map (one thread per side and
+//      coordinate) and each side's compact face-node index;
+//   2. one lane of warp 0 per (side, point) (2 (p+1)^2 <= 32): the reference
+//      point (side 1: each coordinate s, 1 - s, t, 1 - t or the face's side,
+//      read off the reference corners of K- that carry K+'s face corners),
+//      FP64 geometry, the physical normal and surface element of the
+//      point from cof(J+) nhat = det J+ J+^{-T} nhat (side-0 lanes; shuffled to
+//      the side-1 lane of the same point), |F| (a butterfly sum over the side-0
+//      lanes), cof^T n / det and the 1D Lagrange values and derivatives;
+//   3. per (side, point, node): the normal derivative of every shape function
+//      and the values of the (p+1)^2 face nodes (the other shape functions
+//      vanish on the face);
+//   4. the products X_{sa,sb} = sum_q dS phi^{sa}_{a'} (grad phi^{sb}_b . n)
 //      (a' a face node of side sa) and Y_{sa,sb} = sum_q dS phi^{sa}_{a'} phi^{sb}_{b'};
-//   4. block (sa, sb), row a, column b:
+//   5. block (sa, sb), row a, column b:
 //      -s_a/2 X_{sa,sb}[a'][b] - tau s_b/2 X_{sb,sa}[b'][a] + gamma/|F| s_a s_b Y_{sa,sb}[a'][b']
 //      (terms whose face node is missing are zero; boundary facets: one side,
 //      s = 1 and the factor 1/2 dropped), Eq. local_to_face_matrix.
-// FP32 forms (TB = float): geometry, normals and shape data in FP64, rounded
-// to FP32 on the integer bits for steps 3 and 4, blocks stored in FP32.
+// FP32 forms (TB = float): geometry, normals, |F| and the 1D shape data in
+// FP64, rounded to FP32 on the integer bits; steps 3 to 5 in FP32, blocks
+// stored in FP32. GB300 issues FP64 at 2 lanes per clock per SM, so the FP64
+// work is kept to one warp pass per facet.
 template <int P, typename TB>
 __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
   using L = FacetLayout<P, TB>;
@@ -246,17 +265,31 @@ __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
     if constexpr (F32) return d2f_rn(x); else return x;
   };
   constexpr int N1 = L::N1, NB = L::NB, NQF = L::NQF, NBF = L::NBF;
+  static_assert(2 * NQF <= 32, "one lane per (side, point)");
   extern __shared__ __align__(16) unsigned char sm[];
+  double* aco = reinterpret_cast<double*>(sm + L::ACO);
+  double* s_area = reinterpret_cast<double*>(sm + L::AREA);
   TB* gn = reinterpret_cast<TB*>(sm + L::GN);
   TB* pf = reinterpret_cast<TB*>(sm + L::PF);
   TB* ff = reinterpret_cast<TB*>(sm + L::FF);
   TB* x1 = reinterpret_cast<TB*>(sm + L::X1);
   TB* yy = reinterpret_cast<TB*>(sm + L::YY);
-  double* nrm = reinterpret_cast<double*>(sm + L::NRM);
-  double* dS = reinterpret_cast<double*>(sm + L::DS);
-  double* s_area = dS + NQF;
+  TB* cnv = reinterpret_cast<TB*>(sm + L::CN);
+  TB* vd = reinterpret_cast<TB*>(sm + L::VD);
+  TB* dsw = reinterpret_cast<TB*>(sm + L::DS);
   int* cidx = reinterpret_cast<int*>(sm + L::CIDX);
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  constexpr int NW = 128 / 32, NBJ = (NB + 31) / 32;
+  // steps 3 and 5 give each warp whole rows and each lane the columns
+  // b = lane + 32 j; the tensor-product digits of those columns, once
+  int bd[NBJ][3];
+#pragma unroll
+  for (int j = 0; j < NBJ; ++j) {
+    const int b = lane + 32 * j;
+    bd[j][0] = b % N1;
+    bd[j][1] = N1 + (b / N1) % N1;
+    bd[j][2] = 2 * N1 + (b / (N1 * N1)) % N1;
+  }
   for (int64_t id = blockIdx.x; id < fp.n_int + fp.n_bnd; id += gridDim.x) {
     const bool interior = id < fp.n_int;
     const int64_t i = interior ? id : id - fp.n_int;
@@ -264,7 +297,8 @@ __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
     const int face[2] = {interior ? int(fp.fpf[i]) : int(fp.bface[i]), interior ? int(fp.fmf[i]) : 0};
     const int64_t cell[2] = {interior ? int64_t(fp.fplus[i]) : int64_t(fp.bcell[i]),
                              interior ? int64_t(fp.fminus[i]) : 0};
-    // compact index of each side's face nodes (node index along the face normal = the face's side)
+    // 1. compact index of each side's face nodes (node index along the face
+    //    normal = the face's side); the sides' trilinear coefficients
     for (int it = t; it < ns * NB; it += blockDim.x) {
       const int s = it / NB, a = it % NB, d = face[s] / 2;
       const int ad = (a / (d == 0 ? 1 : (d == 1 ? N1 : N1 * N1))) % N1;
@@ -276,125 +310,171 @@ __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
       }
       cidx[s * NB + a] = c;
     }
-    double* cnv = reinterpret_cast<double*>(sm + L::CN);
-    double* vd = reinterpret_cast<double*>(sm + L::VD);
-    double* cof0 = reinterpret_cast<double*>(sm + L::COF0);
-    // 1. side 0 per point: geometry, normal, surface element; then |F|
-    // 2a. per (side, point): geometry (side 0 from step 1), cof^T n / det, Lagrange data
-    for (int pass = 0; pass < 2; ++pass) {
-      for (int it = t; it < (pass == 0 ? 1 : ns) * NQF; it += blockDim.x) {
-        const int side = it / NQF, q = it % NQF, qs = q % N1, qt = q / N1;
-        const double s = fp.gx[qs], tt = fp.gx[qt];
-        double xh[3];
-        if (side == 0) {
-          const int d = face[0] / 2, d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-          xh[d] = double(face[0] % 2);
-          xh[d1] = s;
-          xh[d2] = tt;
-        } else {
-          const double Lw[4] = {(1 - s) * (1 - tt), s * (1 - tt), (1 - s) * tt, s * tt};
-          xh[0] = xh[1] = xh[2] = 0.0;
+    if (t < 3 * ns) trilinear_coefficients(fp.xv + cell[t / 3] * 24, t % 3, aco + (t / 3) * 21);
+    __syncthreads();
+    // 2. one lane per (side, point), warp 0
+    if (t < 32) {
+      const bool act = t < ns * NQF;
+      const int side = act ? t / NQF : 0, q = t % NQF, qs = q % N1, qt = q / N1;
+      const double s = fp.gx[qs], tt = fp.gx[qt];
+      // (selects, not indexing by the face's direction, so that xh, cof and
+      // nd stay in registers)
+      double xh[3];
+      if (side == 0) {
+        const int d = face[0] / 2;
+        const double fv = double(face[0] % 2);
+        xh[0] = d == 0 ? fv : s;
+        xh[1] = d == 1 ? fv : (d == 0 ? s : tt);
+        xh[2] = d == 2 ? fv : tt;
+      } else {
+        // the corners of K+'s face sit on K-'s reference corners v0 (s, t) =
+        // (0, 0), v1 (1, 0), v2 (0, 1), v3 = v1 + v2 - v0 (a symmetry of the
+        // square, checked at setup), so each reference coordinate of K-'s
+        // point is v0 + (v1 - v0) s + (v2 - v0) t: one of s, 1 - s, t, 1 - t
+        // or the face's side
+        const int v0 = fp.fcorner[4 * i], v1 = fp.fcorner[4 * i + 1], v2 = fp.fcorner[4 * i + 2];
+        const double sm1 = 1.0 - s, tm1 = 1.0 - tt;
+        const int d = face[1] / 2;
+        const double fv = double(face[1] % 2);
 #pragma unroll
-          for (int c = 0; c < 4; ++c) {
-            const int v = fp.fcorner[4 * i + c];
-#pragma unroll
-            for (int k = 0; k < 3; ++k) xh[k] += Lw[c] * double((v >> k) & 1);
-          }
-          xh[face[1] / 2] = double(face[1] % 2);
+        for (int k = 0; k < 3; ++k) {
+          const int b0 = (v0 >> k) & 1, d1 = ((v1 >> k) & 1) - b0, d2 = ((v2 >> k) & 1) - b0;
+          xh[k] = k == d ? fv : (d1 > 0 ? s : d1 < 0 ? sm1 : d2 > 0 ? tt : d2 < 0 ? tm1 : double(b0));
         }
-        double cof[9], det;
-        if (pass == 1 && side == 0) {
+      }
+      double cof[9], det;
+      geometry_at(aco + side * 21, xh[0], xh[1], xh[2], cof, &det);
+      if (act && !(det > 0.0)) atomicOr(fp.err, kErrNegJacobian);
+      // the normal of point q: cof(J+) nhat on the side-0 lane q
+      const int d = face[0] / 2;
+      const double sg = face[0] % 2 ? 1.0 : -1.0;
+      double nd[3];
 #pragma unroll
-          for (int k = 0; k < 9; ++k) cof[k] = cof0[q * 10 + k];
-          det = cof0[q * 10 + 9];
-        } else {
-          double xv[24], a[21];
+      for (int k = 0; k < 3; ++k) {
+        nd[k] = sg * (d == 0 ? cof[3 * k] : (d == 1 ? cof[3 * k + 1] : cof[3 * k + 2]));
+        nd[k] = __shfl_sync(kFull, nd[k], q);
+      }
+      const double l2 = nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2];
+      const double rl = rsqrt(l2), len = l2 * rl;
+      const double dsq = len * fp.gw[qs] * fp.gw[qt];
+      double ar = t < NQF ? dsq : 0.0;
 #pragma unroll
-          for (int k = 0; k < 24; ++k) xv[k] = fp.xv[cell[side] * 24 + k];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) trilinear_coefficients(xv, k, a);
-          geometry_at(a, xh[0], xh[1], xh[2], cof, &det);
-          if (!(det > 0.0)) atomicOr(fp.err, kErrNegJacobian);
-        }
-        if (pass == 0) {
-          const int d = face[0] / 2;
-          const double sg = face[0] % 2 ? 1.0 : -1.0;
-          const double nd[3] = {sg * cof[d], sg * cof[3 + d], sg * cof[6 + d]};
-          const double len = sqrt(nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2]);
-          dS[q] = len * fp.gw[qs] * fp.gw[qt];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) nrm[q * 3 + k] = nd[k] / len;
-#pragma unroll
-          for (int k = 0; k < 9; ++k) cof0[q * 10 + k] = cof[k];
-          cof0[q * 10 + 9] = det;
-          continue;
-        }
+      for (int off = 16; off > 0; off >>= 1) ar += __shfl_xor_sync(kFull, ar, off);
+      if (act) {
         const double rdet = 1.0 / det;
+        const double n0 = nd[0] * rl, n1 = nd[1] * rl, n2 = nd[2] * rl;
 #pragma unroll
-        for (int d = 0; d < 3; ++d)
-          cnv[(side * NQF + q) * 3 + d] =
-              (cof[d] * nrm[q * 3] + cof[3 + d] * nrm[q * 3 + 1] + cof[6 + d] * nrm[q * 3 + 2]) * rdet;
-        double* V = vd + (side * NQF + q) * 6 * N1;  // V[k][m] at k*N1 + m, D at (3 + k)*N1 + m
+        for (int k = 0; k < 3; ++k) cnv[t * 3 + k] = cvt((cof[k] * n0 + cof[3 + k] * n1 + cof[6 + k] * n2) * rdet);
+        // the 1D shape data; FP32 forms with p <= 2 evaluate them in FP32 at the
+        // rounded reference point (nodes 0, 1/2, 1 exact, every Gauss point
+        // and its mirror at least 0.11 from a node); for p = 3 a 4-point Gauss
+        // abscissa lies 0.003 from the node 1/3, so x - 1/3 is formed in FP64
+        TB* vt = vd + t * 6 * N1;  // V[k][m] at k*N1 + m, D at (3 + k)*N1 + m
+        if constexpr (F32 && P <= 2) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) lagrange<P>(xh[k], V + k * N1, V + (3 + k) * N1);
+          for (int k = 0; k < 3; ++k) lagrange<P, float>(d2f_rn(xh[k]), vt + k * N1, vt + (3 + k) * N1);
+        } else {
+          double V[3][N1], D[3][N1];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) lagrange<P, double>(xh[k], V[k], D[k]);
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int m = 0; m < N1; ++m) {
+              vt[k * N1 + m] = cvt(V[k][m]);
+              vt[(3 + k) * N1 + m] = cvt(D[k][m]);
+            }
+        }
+        if (side == 0) dsw[q] = cvt(dsq);
       }
-      __syncthreads();
-      if (pass == 0 && t == 0) {
-        double ar = 0.0;
-        for (int q = 0; q < NQF; ++q) ar += dS[q];
-        *s_area = ar;
-      }
-      __syncthreads();
+      if (t == 0) *s_area = ar;
     }
-    // 2b. per (side, point, node): normal derivative; value and dS value on face nodes
-    for (int it = t; it < ns * NQF * NB; it += blockDim.x) {
-      const int side = it / (NQF * NB), q = (it / NB) % NQF, b = it % NB;
-      const int b0 = b % N1, b1 = (b / N1) % N1, b2 = b / (N1 * N1);
-      const double* V = vd + (side * NQF + q) * 6 * N1;
-      const double* D = V + 3 * N1;
-      const double* cn = cnv + (side * NQF + q) * 3;
-      const double v0 = V[b0], v1 = V[N1 + b1], v2 = V[2 * N1 + b2];
-      gn[(side * NQF + q) * NB + b] = cvt(cn[0] * D[b0] * v1 * v2 + cn[1] * v0 * D[N1 + b1] * v2 + cn[2] * v0 * v1 * D[2 * N1 + b2]);
-      const int c = cidx[side * NB + b];
-      if (c >= 0) {
-        const double ph = v0 * v1 * v2;
-        ff[(side * NQF + q) * NBF + c] = cvt(ph);
-        pf[(side * NQF + q) * NBF + c] = cvt(dS[q] * ph);
+    __syncthreads();
+    // the face-node index of the lane's columns on each side
+    int cbl[2][NBJ];
+#pragma unroll
+    for (int j = 0; j < NBJ; ++j) {
+      const int b = lane + 32 * j;
+      cbl[0][j] = b < NB ? cidx[b] : -1;
+      cbl[1][j] = b < NB && ns == 2 ? cidx[NB + b] : -1;
+    }
+    // 3. row (side, point), column node b: normal derivative; value and dS
+    //    value on face nodes
+    for (int r = warp; r < ns * NQF; r += NW) {
+      const int side = r / NQF, q = r % NQF;
+      const TB* V = vd + r * 6 * N1;  // values at 0..3 N1, derivatives 3 N1 further
+      const TB c0 = cnv[r * 3], c1 = cnv[r * 3 + 1], c2 = cnv[r * 3 + 2], dq = dsw[q];
+#pragma unroll
+      for (int j = 0; j < NBJ; ++j) {
+        const int b = lane + 32 * j;
+        if (b < NB) {
+          const TB v0 = V[bd[j][0]], v1 = V[bd[j][1]], v2 = V[bd[j][2]];
+          const TB d0 = V[3 * N1 + bd[j][0]], d1 = V[3 * N1 + bd[j][1]], d2 = V[3 * N1 + bd[j][2]];
+          gn[r * NB + b] = c0 * d0 * v1 * v2 + c1 * v0 * d1 * v2 + c2 * v0 * v1 * d2;
+          const int c = side ? cbl[1][j] : cbl[0][j];
+          if (c >= 0) {
+            const TB ph = v0 * v1 * v2;
+            ff[r * NBF + c] = ph;
+            pf[r * NBF + c] = dq * ph;
+          }
+        }
       }
     }
     __syncthreads();
-    // 3. X_{sa,sb} scaled by -s_a/2 (boundary: -1) and Y_{sa,sb} scaled by s_a s_b
+    // 4. X_{sa,sb} scaled by -s_a/2 (boundary: -1), row (block, face node c),
+    //    column b; Y_{sa,sb} scaled by s_a s_b
     const TB half = interior ? TB(0.5) : TB(1);
-    for (int it = t; it < ns * ns * NBF * NB; it += blockDim.x) {
-      const int blk = it / (NBF * NB), sa = blk >> 1, sb = blk & 1, c = (it / NB) % NBF, b = it % NB;
-      TB v = TB(0);
-      for (int q = 0; q < NQF; ++q) v = fma(pf[(sa * NQF + q) * NBF + c], gn[(sb * NQF + q) * NB + b], v);
-      x1[(blk * NBF + c) * NB + b] = (sa ? half : -half) * v;
+    for (int r = warp; r < ns * ns * NBF; r += NW) {
+      const int blk = r / NBF, c = r % NBF, sa = blk >> 1, sb = blk & 1;
+      TB pq[NQF];
+#pragma unroll
+      for (int q = 0; q < NQF; ++q) pq[q] = pf[(sa * NQF + q) * NBF + c];
+      const TB* g = gn + sb * NQF * NB;
+      const TB sc = sa ? half : -half;
+#pragma unroll
+      for (int j = 0; j < NBJ; ++j) {
+        const int b = lane + 32 * j;
+        if (b < NB) {
+          TB v = TB(0);
+#pragma unroll
+          for (int q = 0; q < NQF; ++q) v = fma(pq[q], g[q * NB + b], v);
+          x1[r * NB + b] = sc * v;
+        }
+      }
     }
     for (int it = t; it < ns * ns * NBF * NBF; it += blockDim.x) {
       const int blk = it / (NBF * NBF), sa = blk >> 1, sb = blk & 1, c = (it / NBF) % NBF, e = it % NBF;
       TB v = TB(0);
+#pragma unroll
       for (int q = 0; q < NQF; ++q) v = fma(pf[(sa * NQF + q) * NBF + c], ff[(sb * NQF + q) * NBF + e], v);
       yy[(blk * NBF + c) * NBF + e] = sa == sb ? v : -v;
     }
     __syncthreads();
-    // 4. the facet blocks: X term, tau times the transposed X term of the
-    //    swapped block, gamma/|F| times the Y term (entries with no face node:
-    //    zero, no arithmetic)
+    // 5. the facet blocks, row (block, a), column b: X term, tau times the
+    //    transposed X term of the swapped block, gamma/|F| times the Y term
+    //    (entries with no face node: zero, no arithmetic)
     const TB pen = cvt(fp.gamma / *s_area), tau = cvt(fp.tau);
-    TB* fblk = static_cast<TB*>(fp.fblk);
-    TB* bblk = static_cast<TB*>(fp.bblk);
-    for (int it = t; it < ns * ns * NB * NB; it += blockDim.x) {
-      const int blk = it / (NB * NB), sa = blk >> 1, sb = blk & 1, a = (it / NB) % NB, b = it % NB;
-      const int ca = cidx[sa * NB + a], cb = cidx[sb * NB + b];
-      TB v = TB(0);
-      if (ca >= 0) v = x1[(blk * NBF + ca) * NB + b];
-      if (cb >= 0) v = fma(tau, x1[(((sb << 1) | sa) * NBF + cb) * NB + a], v);
-      if (ca >= 0 && cb >= 0) v = fma(pen, yy[(blk * NBF + ca) * NBF + cb], v);
-      if (interior)
-        fblk[(i * 4 + blk) * NB * NB + a * NB + b] = v;
-      else
-        bblk[i * NB * NB + a * NB + b] = v;
+    for (int r = warp; r < ns * ns * NB; r += NW) {
+      const int blk = r / NB, a = r % NB, sa = blk >> 1, sb = blk & 1;
+      const int ca = cidx[sa * NB + a];
+      const TB* xr = x1 + (blk * NBF + (ca >= 0 ? ca : 0)) * NB;
+      const TB* xt = x1 + ((sb << 1) | sa) * NBF * NB + a;
+      const TB* yr = yy + (blk * NBF + (ca >= 0 ? ca : 0)) * NBF;
+      TB* out = interior ? static_cast<TB*>(fp.fblk) + ((i * 4 + blk) * NB + a) * NB
+                         : static_cast<TB*>(fp.bblk) + (i * NB + a) * NB;
+#pragma unroll
+      for (int j = 0; j < NBJ; ++j) {
+        const int b = lane + 32 * j;
+        if (b < NB) {
+          const int cb = sb ? cbl[1][j] : cbl[0][j];
+          TB v = ca >= 0 ? xr[b] : TB(0);
+          if (cb >= 0) {
+            v = fma(tau, xt[cb * NB], v);
+            if (ca >= 0) v = fma(pen, yr[cb], v);
+          }
+          out[b] = v;
+        }
+      }
     }
     __syncthreads();
   }
@@ -500,17 +580,20 @@ cudaError_t launch(const fe_dg* g, double tau, double gamma, double* values, dou
   fp.bblk = g->d_bblk;
   fp.err = g->s->d_err;
   const int64_t nf = fp.n_int + fp.n_bnd;
-  const int fblocks = int(std::min<int64_t>(std::max<int64_t>(nf, 1), int64_t(nsm) * 16));
-  if (nf > 0 && prec == FE_PREC_FP64) {
-    constexpr size_t smem = FacetLayout<P, double>::BYTES;
-    cudaError_t e = cudaFuncSetAttribute(k_dg_facets<P, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  // a persistent grid of the resident blocks (one wave; facets cost alike)
+  auto facets = [&](auto kern, size_t smem) -> cudaError_t {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    int per_sm = 1;
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem);
     if (e != cudaSuccess) return e;
-    k_dg_facets<P, double><<<fblocks, 128, smem, st>>>(fp);
-  } else if (nf > 0) {
-    constexpr size_t smem = FacetLayout<P, float>::BYTES;
-    cudaError_t e = cudaFuncSetAttribute(k_dg_facets<P, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    const int fblocks = int(std::min<int64_t>(nf, int64_t(nsm) * std::max(per_sm, 1)));
+    kern<<<fblocks, 128, smem, st>>>(fp);
+    return cudaSuccess;
+  };
+  if (nf > 0) {
+    const cudaError_t e = prec == FE_PREC_FP64 ? facets(k_dg_facets<P, double>, FacetLayout<P, double>::BYTES)
+                                               : facets(k_dg_facets<P, float>, FacetLayout<P, float>::BYTES);
     if (e != cudaSuccess) return e;
-    k_dg_facets<P, float><<<fblocks, 128, smem, st>>>(fp);
   }
   RowParams rp;
   rp.n_cells = g->n_cells;

@@ -39,3 +39,21 @@ def test_dg_pattern_and_facets_match_oracle(p, shape, rotate):
         vm = {cv[minus[i]][v] for v in range(8) if (v >> (mf[i] // 2)) & 1 == mf[i] % 2}
         assert vp == vm and len(vp) == 4
     g.close()
+
+
+def test_dg_twisted_facet_rejected():
+    """Two cells whose shared face carries the same four vertices, but with two
+    adjacent corners swapped in the second cell: K+'s face corners do not land
+    on K-'s by a symmetry of the square, so setup refuses the mesh (the facet
+    kernel reads K-'s reference point off that symmetry)."""
+    mesh = inputs.small_problem((2, 1, 1), 1, 0, seed=195).mesh
+    cv = mesh.cell_vertices.copy()
+    cv[1, [0, 2]] = cv[1, [2, 0]]
+    twisted = inputs.Mesh(mesh.coords, cv, mesh.shape, mesh.extent)
+    with pytest.raises(feasm.FEError, match="symmetry of the square"):
+        feasm.DGSpace(twisted, 1, host_only=True)
+    # a half-turn of the shared face (diagonal corners swapped) is a symmetry
+    cv = mesh.cell_vertices.copy()
+    cv[1, [0, 6]] = cv[1, [6, 0]]
+    cv[1, [2, 4]] = cv[1, [4, 2]]
+    feasm.DGSpace(inputs.Mesh(mesh.coords, cv, mesh.shape, mesh.extent), 1, host_only=True).close()
