@@ -218,6 +218,46 @@ def oracle_rate(prob, target_s: float, max_cells: int | None = None):
     return n_target / dt, n_target, dt
 
 
+def _oracle_worker(workload, lo, hi, barrier, results):
+    """One host core's share of the all-cores oracle timing: the same oracle call
+    as oracle_rate on cells [lo, hi) of the workload, started together with the
+    other workers."""
+    import oracle
+    from paper_1708_01773_gb300 import inputs
+    prob = inputs.WORKLOADS[workload]()
+    sub = inputs.Problem(prob.name, inputs.Mesh(prob.mesh.coords, prob.mesh.cell_vertices[lo:hi]), prob.order,
+                         prob.quad_1d, prob.problem, prob.coef[lo:hi], prob.force, prob.nu)
+    barrier.wait()
+    t = time.perf_counter()
+    oracle.assemble_csr(sub)
+    results.put((hi - lo, time.perf_counter() - t))
+
+
+def oracle_rate_all_cores(workload: str, n_cells: int, cells_per_core: int):
+    """The single-threaded oracle run as one process per host core (spawned, so
+    that no CUDA state is inherited), each on its own range of cells_per_core
+    cells, all released together. Returns (cells/s over the slowest worker,
+    cores, seconds)."""
+    import multiprocessing as mp
+    cores = len(os.sched_getaffinity(0))
+    ctx = mp.get_context("spawn")
+    barrier, results = ctx.Barrier(cores), ctx.Queue()
+    span = max(1, n_cells - cells_per_core)
+    procs = []
+    for i in range(cores):
+        lo = (i * cells_per_core) % span
+        procs.append(ctx.Process(target=_oracle_worker,
+                                 args=(workload, lo, min(n_cells, lo + cells_per_core), barrier, results)))
+    for pr in procs:
+        pr.start()
+    got = [results.get(timeout=600) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+    cells = sum(c for c, _ in got)
+    wall = max(dt for _, dt in got)
+    return cells / wall, cores, wall
+
+
 def reference_arm(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -633,12 +673,18 @@ def main():
 
     extras = extra_workloads(args, dev, stream) if (args.extras or args.batched or args.extra) else None
 
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, n, dt = oracle_rate(prob, 12.0)
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"first {n} cells of {args.workload} ({dt:.1f} s), single-threaded C oracle: "
                          f"numbering + cell loop + COO compress"}
+        # the same oracle on every host core: one process per core, each on its own cell range
+        per_core = max(1, int(rate * 6.0))
+        rate_all, cores, wall = oracle_rate_all_cores(args.workload, int(prob.mesh.n_cells), per_core)
+        cpu_all = {"value": rate_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{cores} processes x {per_core} cells of {args.workload} ({wall:.1f} s), "
+                             f"the single-threaded C oracle per process on its own cell range"}
 
     if rank == 0:
         out = {
@@ -659,6 +705,7 @@ def main():
             "comparators": comparators,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
+            "cpu_baseline_all_cores": cpu_all,
         }
         if extras:
             out["extra_workloads"] = extras

@@ -37,3 +37,14 @@ def test_single_rank_passthrough():
     import bench
     assert bench.max_over_ranks(3.5) == 3.5
     assert bench.whole_job_rate(100, 1, 10, 1000.0) == pytest.approx(1000.0)
+
+
+def test_oracle_all_cores_leg():
+    """The all-cores oracle leg: one spawned process per host core, each on its own
+    cell range; every worker reports, and the rate is the cells over the slowest."""
+    import bench
+    import oracle
+    oracle.build()
+    rate, cores, wall = bench.oracle_rate_all_cores("poisson_q1_8", 512, 16)
+    assert cores == len(os.sched_getaffinity(0))
+    assert wall > 0 and rate == pytest.approx(cores * 16 / wall)
