@@ -666,6 +666,17 @@ def main():
     for k in kernels.values():
         k["gbs"] = k["bytes"] / (k["ms"] / 1e3) / 1e9
         k["frac"] = k["gbs"] / hbm
+    if prob.problem == inputs.ELASTICITY and prob.order == 2 and args.prec != "fp64":
+        # the contraction runs on tcgen05 (3xTF32 for the FP32 form, BF16): its
+        # algorithmic flops (3 nb)^2 nq 2 per cell, times the passes of the split,
+        # against the dtype's peak (TF32: the measured BF16 burst x 1.1 / 2.25)
+        passes, peak_tf = (3, bf16_tf * 1.1 / 2.25) if args.prec == "fp32" else (1, bf16_tf)
+        flops = sp.n_cells * sp.nl * sp.nl * prob.quad_1d ** 3 * 2
+        tflops = passes * flops / (cell_avg / 1e3) / 1e12
+        kernels["k_cell"].update({"contraction_flops": int(flops), "tensor_passes": passes,
+                                  "tensor_tflops": tflops, "tensor_peak_tflops": peak_tf,
+                                  "tensor_frac": tflops / peak_tf,
+                                  "tensor_dtype": "tf32 (3xTF32)" if args.prec == "fp32" else "bf16"})
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm, "unit": "GB/s",
             "frac": kernels[dom]["frac"], "traffic": kernel_traffic(dom),
