@@ -507,7 +507,8 @@ struct RowParams {
 // facet's off-diagonal block (rows: this cell's side). T is the storage of the
 // cell and facet blocks: FP64, or FP32, whose seven terms are summed as an
 // FP32 pair (TwoSum) and rounded once to FP64, and whose single terms convert
-// exactly on the integer bits.
+// exactly on the integer bits. The block locations and the CSR row starts are
+// resolved once per cell into shared memory.
 // Exact FP32 -> FP64 on the integer bits: the short path for zeros and normal
 // numbers, the general one otherwise.
 __device__ __forceinline__ double to_f64(float x) {
@@ -520,19 +521,39 @@ __global__ void __launch_bounds__(256) k_dg_rows(RowParams rp) {
   const T* ke = static_cast<const T*>(rp.ke);
   const T* fblk = static_cast<const T*>(rp.fblk);
   const T* bblk = static_cast<const T*>(rp.bblk);
+  // per cell, resolved once: the diagonal block of its facet on face f, the
+  // source block of slot j (nullptr: the diagonal) and the CSR row starts
+  __shared__ const T* s_diag[6];
+  __shared__ const T* s_blk[7];
+  __shared__ int64_t s_rp[NB];
+  const int t = threadIdx.x;
   for (int64_t e = blockIdx.x; e < rp.n_cells; e += gridDim.x) {
     const int ns = rp.nslot[e];
-    for (int it = threadIdx.x; it < ns * NB * NB; it += blockDim.x) {
-      const int j = it / (NB * NB), a = (it / NB) % NB, b = it % NB;
-      const int slot = rp.slots[e * 7 + j];
+    if (t < 6) {
+      const int32_t code = rp.face_code[e * 6 + t];
+      s_diag[t] = code >= 0 ? fblk + (int64_t(code >> 1) * 4 + 3 * (code & 1)) * NB * NB
+                            : bblk + int64_t(-1 - code) * NB * NB;
+    } else if (t >= 32 && t < 32 + ns) {
+      const int j = t - 32, slot = rp.slots[e * 7 + j];
+      const T* src = nullptr;
+      if (slot != kSelf) {
+        const int32_t code = rp.face_code[e * 6 + slot];
+        const int side = code & 1;  // this cell's side; the neighbour is on the other
+        src = fblk + (int64_t(code >> 1) * 4 + 2 * side + (1 - side)) * NB * NB;
+      }
+      s_blk[j] = src;
+    }
+    for (int a = t; a < NB; a += blockDim.x) s_rp[a] = rp.row_ptr[e * NB + a];
+    __syncthreads();
+    for (int it = t; it < ns * NB * NB; it += blockDim.x) {
+      const int j = it / (NB * NB), ab = it % (NB * NB), a = ab / NB, b = ab % NB;
+      const T* src = s_blk[j];
       double v;
-      if (slot == kSelf) {
+      if (src == nullptr) {
         T hi = ke[(e * NB + a) * int64_t(rp.nlp) + b], lo = T(0);
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-          const int32_t code = rp.face_code[e * 6 + f];
-          const T x = code >= 0 ? fblk[(int64_t(code >> 1) * 4 + 3 * (code & 1)) * NB * NB + a * NB + b]
-                                : bblk[int64_t(-1 - code) * NB * NB + a * NB + b];
+          const T x = s_diag[f][ab];
           if constexpr (F32) {
             const T sum = hi + x, bp = sum - hi;
             lo += (hi - (sum - bp)) + (x - bp);
@@ -543,15 +564,13 @@ __global__ void __launch_bounds__(256) k_dg_rows(RowParams rp) {
         }
         if constexpr (F32) v = to_f64(hi) + to_f64(lo); else v = hi;
       } else {
-        const int32_t code = rp.face_code[e * 6 + slot];
-        const int side = code & 1;  // this cell's side; the neighbour is on the other
-        const T x = fblk[(int64_t(code >> 1) * 4 + 2 * side + (1 - side)) * NB * NB + a * NB + b];
-        if constexpr (F32) v = to_f64(x); else v = x;
+        if constexpr (F32) v = to_f64(src[ab]); else v = src[ab];
       }
-      rp.values[rp.row_ptr[e * NB + a] + j * NB + b] = v;
+      rp.values[s_rp[a] + j * NB + b] = v;
     }
     if (rp.rhs)
-      for (int a = threadIdx.x; a < NB; a += blockDim.x) rp.rhs[e * NB + a] = rp.fe[e * NB + a];
+      for (int a = t; a < NB; a += blockDim.x) rp.rhs[e * NB + a] = rp.fe[e * NB + a];
+    __syncthreads();
   }
 }
 
