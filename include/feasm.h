@@ -402,7 +402,10 @@ typedef struct fe_dg fe_dg; /* opaque, library-owned */
  * (neighbours matched by their 4 vertex ids) and the CSR pattern (each row of
  * cell K: the DOFs of K and of its face neighbours, columns ascending).
  * _host: no GPU use (inspection: sizes, pattern, facets). Errors as for
- * fe_space_create. */
+ * fe_space_create, and FE_ERR_INVALID_ARG when two cells share a face's four
+ * vertices but their corners do not correspond by a symmetry of the square
+ * (a twisted face: the facet integrals read the neighbour's reference point
+ * off that symmetry). */
 int fe_dg_create(const fe_mesh_desc* mesh, int order, fe_dg** out);
 int fe_dg_create_host(const fe_mesh_desc* mesh, int order, fe_dg** out);
 
