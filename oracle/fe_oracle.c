@@ -30,8 +30,11 @@
  * Parity pins (tests): closed-form Q1 unit-cube stiffness, Gauss exactness,
  * partition of unity, patch test, zero row sums, rigid-body modes, symmetry,
  * RHS sums, uniform-strain energy, and high-order brute-force quadrature on
- * affine cells. Entry values of perturbed cells beyond these invariants are
- * pinned only through them ("parity unpinned" beyond the invariants).
+ * affine cells. On distorted (non-affine) cells the Gauss sums have no closed
+ * form; there the entries are fixed by the patch test, the rigid-body modes,
+ * the uniform-strain energy, zero row sums, symmetry and the convergence of
+ * the rule, each of which a dropped term, a wrong sign or index or a
+ * transposed Jacobian breaks.
  */
 #include <math.h>
 #include <stdint.h>
