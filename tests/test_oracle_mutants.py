@@ -1,0 +1,75 @@
+"""The oracle's pins catch plausible mistakes: each case plants one slip in a
+copy of fe_oracle.c (a transposed operand, a wrong sign, a dropped term or
+factor, a wrong index), compiles that copy and runs the pin file against it;
+at least one pin must fail. The oracle source itself is not changed. Every
+slip changes the computed result (an unsymmetrised trial strain, for one,
+would not: sigma(u) : eps(v) only sees the symmetric part of grad u, since
+eps(v) is symmetric and tr grad u = div u)."""
+import concurrent.futures
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "fe_oracle.c")
+PINS = os.path.join(ROOT, "tests", "test_oracle_pins.py")
+
+# (what is planted, text in fe_oracle.c, replacement, occurrences replaced: 0 = all)
+MUTANTS = [
+    ("J^-1 transposed in grad phi", "s += T->dphi[q][a][d] * Ji[d][k];", "s += T->dphi[q][a][d] * Ji[k][d];", 0),
+    ("Jacobian transposed", "s += xv[3 * v + k] * T->dN[q][v][d];", "s += xv[3 * v + d] * T->dN[q][v][k];", 0),
+    ("sign of one entry of J^-1", "Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;",
+     "Ji[1][2] = (J[0][0] * J[1][2] - J[0][2] * J[1][0]) / det;", 0),
+    ("det J dropped from the weight", "double dJw = det * T->w[q];", "double dJw = T->w[q];", 0),
+    ("lambda term on every entry of sigma", "+ (k == l ? lambda * tr : 0.0);", "+ lambda * tr;", 0),
+    ("sign of the lambda term", "su[k][l] = 2.0 * mu * eu[k][l] + (k == l ? lambda * tr : 0.0);",
+     "su[k][l] = 2.0 * mu * eu[k][l] - (k == l ? lambda * tr : 0.0);", 0),
+    ("factor 2 of the mu term dropped", "su[k][l] = 2.0 * mu * eu[k][l] +", "su[k][l] = mu * eu[k][l] +", 0),
+    ("shape function dropped from the Poisson RHS", "fe[a] += f * T->phi[q][a] * dJw;", "fe[a] += f * dJw;", 0),
+    ("Gauss weights of [-1,1] not halved", "w[n - 1 - i] = 0.5 * wt;", "w[n - 1 - i] = wt;", 0),
+    ("compress keeps the last duplicate", "      values[nnz - 1] += coo[i].val;", "      values[nnz - 1] = coo[i].val;", 1),
+    ("Stokes coupling missing from the pressure rows", "          Ke[(nv + c) * nl + (j * nb + b)] += bq;",
+     "          (void)bq;", 0),
+    ("Lagrange derivative: removed factor kept", "        if (s == m || s == r) continue;", "        if (s == m) continue;", 0),
+    ("Stokes coupling sign", "double bq = -T->psi[q][c] * g[b][j] * dJw;", "double bq = T->psi[q][c] * g[b][j] * dJw;", 0),
+    ("DG neighbour's reference point: one Newton step only",
+     "  for (int it = 0; it < 100; ++it) {\n    double y[3], J[3][3], Ji[3][3];",
+     "  for (int it = 0; it < 1; ++it) {\n    double y[3], J[3][3], Ji[3][3];", 0),
+    ("DG normal sign flipped", "n[3] = {sgn * nd[0] / len, sgn * nd[1] / len, sgn * nd[2] / len};",
+     "n[3] = {-sgn * nd[0] / len, -sgn * nd[1] / len, -sgn * nd[2] / len};", 0),
+    ("DG mean without the factor 1/2", "const double half = interior ? 0.5 : 1.0, pen = gamma / area;",
+     "const double half = 1.0, pen = gamma / area;", 0),
+    ("DG jump sign dropped on one side", "+ pen * ga * gb * phi[sa][a] * phi[sb][b]);",
+     "+ pen * ga * phi[sa][a] * phi[sb][b]);", 0),
+    ("DG tau term with the other side's derivative", "- tau * gb * phi[sb][b] * half * gn[sa][a]",
+     "- tau * gb * phi[sb][b] * half * gn[sb][a]", 0),
+    ("DG penalty not divided by the facet area", "pen = gamma / area;", "pen = gamma;", 0),
+]
+
+
+def _run(case, tmp):
+    name, old, new, count = case
+    src = open(SRC).read()
+    assert old in src, f"planting site not found: {name}"
+    mutant = src.replace(old, new) if count == 0 else src.replace(old, new, count)
+    tag = str(abs(hash(name)))
+    c_file = os.path.join(tmp, f"m{tag}.c")
+    so = os.path.join(tmp, f"liboracle_m{tag}.so")
+    with open(c_file, "w") as f:
+        f.write(mutant)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", c_file, "-o", so, "-lm"])
+    env = dict(os.environ, ORACLE_LIB=so)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", PINS], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=900)
+    return name, r.returncode
+
+
+def test_pins_catch_planted_mistakes(tmp_path):
+    workers = max(1, min(len(MUTANTS), len(os.sched_getaffinity(0))))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(lambda c: _run(c, str(tmp_path)), MUTANTS))
+    survivors = [name for name, rc in results if rc == 0]
+    assert not survivors, f"pins pass with these planted mistakes: {survivors}"
+    assert all(rc == 1 for _, rc in results), results  # 1 = tests failed (not a collection or usage error)

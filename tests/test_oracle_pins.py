@@ -832,6 +832,24 @@ def csr_matvec(rp, col, val, v):
     return out
 
 
+@pytest.mark.parametrize("h", [0.5, 2.0])
+def test_dg_penalty_closed_form_q1_cube(h):
+    """The penalty part of the IP-DG matrix on one axis-aligned Q1 cube of side h
+    (every face a boundary facet): per face gamma/|F| times the Q1 face mass
+    matrix |F| (4, 2, 2, 1)/36 (same vertex, edge neighbours, diagonal), so per
+    unit gamma the sum over the six faces is 1/3, 1/9, 1/36, 0 by the Hamming
+    distance of the two vertices, whatever h (Eq. ip_dg_formulations)."""
+    bits = np.array([[v & 1, (v >> 1) & 1, (v >> 2) & 1] for v in range(8)], dtype=np.float64)
+    mesh = inputs.Mesh(h * bits, np.arange(8, dtype=np.int32).reshape(1, 8), (1, 1, 1), (h, h, h))
+    A = {}
+    for gamma in (1.0, 3.0):
+        rp, col, val, _ = oracle.dg_assemble(mesh, 1, 1.0, gamma)
+        A[gamma] = csr_to_dense(rp, col, val, 8)
+    P = (A[3.0] - A[1.0]) / 2.0
+    expect = np.array([[(1 / 3, 1 / 9, 1 / 36, 0.0)[bin(a ^ b).count("1")] for b in range(8)] for a in range(8)])
+    np.testing.assert_allclose(P, expect, rtol=0, atol=1e-14)
+
+
 def test_dg_symmetry_linearity_and_coercivity():
     """SIPG (tau = 1) is symmetric and, with a large enough penalty, positive
     definite; the matrix is affine in tau and in gamma; the pattern couples each
