@@ -49,6 +49,37 @@ MUTANTS = [
 ]
 
 
+# the oracle's Python part (strong Dirichlet conditions, compliance): one
+# text replacement in one function, applied in the pytest process by conftest
+PY_MUTANTS = [
+    ("lifting sign", "dirichlet_reduce", "(np.asarray(rhs, dtype=np.float64) - lift)",
+     "(np.asarray(rhs, dtype=np.float64) + lift)"),
+    ("constrained columns keep the global ids", "dirichlet_reduce", "out_col = lab[col[kept]]", "out_col = col[kept]"),
+    ("prescribed value of the wrong fixed DOF", "dirichlet_reduce", "u_fixed[-1 - lab[col[fx]]]",
+     "u_fixed[(-1 - lab[col[fx]] + 1) % u_fixed.size]"),
+    ("fixed labels start at 0", "dirichlet_labels", "lab[fixed] = -1 - np.arange", "lab[fixed] = -np.arange"),
+    ("compliance gradient sign", "compliance_solve", "grad = -cell_energies(", "grad = cell_energies("),
+    ("compliance as u^T u", "compliance_solve", "c = float(b_r @ u_free)", "c = float(u_free @ u_free)"),
+]
+
+
+def _run_py(case):
+    name, fn, old, new = case
+    env = dict(os.environ, ORACLE_PY_MUTANT=f"{fn}|{old}|{new}")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", PINS, "-k",
+                        "dirichlet or compliance"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
+    return name, r.returncode
+
+
+def test_pins_catch_planted_mistakes_python_part():
+    workers = max(1, min(len(PY_MUTANTS), len(os.sched_getaffinity(0))))
+    with concurrent.futures.ThreadPoolExecutor(workers) as ex:
+        results = list(ex.map(_run_py, PY_MUTANTS))
+    survivors = [name for name, rc in results if rc == 0]
+    assert not survivors, f"pins pass with these planted mistakes: {survivors}"
+    assert all(rc == 1 for _, rc in results), results
+
+
 def _run(case, tmp):
     name, old, new, count = case
     src = open(SRC).read()
