@@ -213,50 +213,190 @@ __device__ __forceinline__ void lagrange(T x, T* v, T* d) {
   }
 }
 
-// Shared memory of k_dg_facets for order P: the products' operands and
-// results, and the per-point shape data, in TB (FP64 form: double; FP32
-// forms: float); the trilinear coefficients and the facet area in double.
+// Shared memory of k_dg_facets for order P. The per-facet point data are
+// double-buffered (the point warp fills facet n+1's while the other warps use
+// facet n's): the sides' trilinear coefficients and |F| in double; cof^T n /
+// det, the 1D Lagrange data, the surface elements (TB) and the face-node
+// indices. The products' operands and results (TB: FP64 form double, FP32
+// forms float) belong to the product warps alone.
 template <int P, typename TB>
 struct FacetLayout {
   static constexpr int N1 = P + 1, NB = N1 * N1 * N1, NQF = N1 * N1, NBF = N1 * N1;
   static constexpr size_t S = sizeof(TB);
-  static constexpr size_t ACO = 0;                                       // double [2][21] trilinear coefficients
-  static constexpr size_t AREA = ACO + size_t(2) * 21 * 8;               // double |F|
-  static constexpr size_t GN = AREA + 8;                                 // [2][NQF][NB]   grad phi . n
-  static constexpr size_t PF = GN + size_t(2) * NQF * NB * S;            // [2][NQF][NBF]  dS phi (face nodes)
-  static constexpr size_t FF = PF + size_t(2) * NQF * NBF * S;           // [2][NQF][NBF]  phi (face nodes)
-  static constexpr size_t X1 = FF + size_t(2) * NQF * NBF * S;           // [4][NBF][NB]
-  static constexpr size_t YY = X1 + size_t(4) * NBF * NB * S;            // [4][NBF][NBF]
-  static constexpr size_t CN = YY + size_t(4) * NBF * NBF * S;           // [2][NQF][3]    cof^T n / det
-  static constexpr size_t VD = CN + size_t(2) * NQF * 3 * S;             // [2][NQF][2][3][N1] Lagrange values, derivatives
-  static constexpr size_t DS = VD + size_t(2) * NQF * 6 * N1 * S;        // [NQF] surface element x weight
-  static constexpr size_t CIDX = (DS + size_t(NQF) * S + 3) & ~size_t(3);  // int [2][NB] compact face index or -1
-  static constexpr size_t BYTES = CIDX + size_t(2) * NB * sizeof(int);
+  // one point-data buffer
+  static constexpr size_t B_ACO = 0;                                      // double [2][21]
+  static constexpr size_t B_AREA = B_ACO + size_t(2) * 21 * 8;           // double |F|
+  static constexpr size_t B_CN = B_AREA + 8;                              // TB [2][NQF][3]
+  static constexpr size_t B_VD = B_CN + size_t(2) * NQF * 3 * S;          // TB [2][NQF][2][3][N1]
+  static constexpr size_t B_DS = B_VD + size_t(2) * NQF * 6 * N1 * S;     // TB [NQF]
+  static constexpr size_t B_CIDX = (B_DS + size_t(NQF) * S + 3) & ~size_t(3);  // int [2][NB]
+  static constexpr size_t B_BYTES = (B_CIDX + size_t(2) * NB * 4 + 15) & ~size_t(15);
+  static constexpr size_t PT = 0;                                         // two buffers
+  static constexpr size_t GN = PT + 2 * B_BYTES;                          // [2][NQF][NB]   grad phi . n
+  static constexpr size_t PF = GN + size_t(2) * NQF * NB * S;             // [2][NQF][NBF]  dS phi (face nodes)
+  static constexpr size_t FF = PF + size_t(2) * NQF * NBF * S;            // [2][NQF][NBF]  phi (face nodes)
+  static constexpr size_t X1 = FF + size_t(2) * NQF * NBF * S;            // [4][NBF][NB]
+  static constexpr size_t YY = X1 + size_t(4) * NBF * NB * S;             // [4][NBF][NBF]
+  static constexpr size_t BYTES = YY + size_t(4) * NBF * NBF * S;
 };
 
-// One block per facet (interior facets first, then boundary facets).
-//   1. the trilinear coefficients of each side's map (one thread per side and
-//      coordinate) and each side's compact face-node index;
-//   2. one lane of warp 0 per (side, point) (2 (p+1)^2 <= 32): the reference
-//      point (side 1: each coordinate s, 1 - s, t, 1 - t or the face's side,
-//      read off the reference corners of K- that carry K+'s face corners),
-//      FP64 geometry, the physical normal and surface element of the
-//      point from cof(J+) nhat = det J+ J+^{-T} nhat (side-0 lanes; shuffled to
-//      the side-1 lane of the same point), |F| (a butterfly sum over the side-0
-//      lanes), cof^T n / det and the 1D Lagrange values and derivatives;
-//   3. per (side, point, node): the normal derivative of every shape function
-//      and the values of the (p+1)^2 face nodes (the other shape functions
-//      vanish on the face);
-//   4. the products X_{sa,sb} = sum_q dS phi^{sa}_{a'} (grad phi^{sb}_b . n)
-//      (a' a face node of side sa) and Y_{sa,sb} = sum_q dS phi^{sa}_{a'} phi^{sb}_{b'};
-//   5. block (sa, sb), row a, column b:
-//      -s_a/2 X_{sa,sb}[a'][b] - tau s_b/2 X_{sb,sa}[b'][a] + gamma/|F| s_a s_b Y_{sa,sb}[a'][b']
-//      (terms whose face node is missing are zero; boundary facets: one side,
-//      s = 1 and the factor 1/2 dropped), Eq. local_to_face_matrix.
-// FP32 forms (TB = float): geometry, normals, |F| and the 1D shape data in
-// FP64, rounded to FP32 on the integer bits; steps 3 to 5 in FP32, blocks
-// stored in FP32. GB300 issues FP64 at 2 lanes per clock per SM, so the FP64
-// work is kept to one warp pass per facet.
+// The facet named by id (interior facets first, then boundary facets).
+struct FacetRef {
+  bool interior;
+  int64_t i;  // index among the interior or the boundary facets
+  int ns;     // sides
+  int face[2];
+  int64_t cell[2];
+};
+
+__device__ __forceinline__ FacetRef facet_ref(const FacetParams& fp, int64_t id) {
+  FacetRef f;
+  f.interior = id < fp.n_int;
+  f.i = f.interior ? id : id - fp.n_int;
+  f.ns = f.interior ? 2 : 1;
+  f.face[0] = f.interior ? int(fp.fpf[f.i]) : int(fp.bface[f.i]);
+  f.face[1] = f.interior ? int(fp.fmf[f.i]) : 0;
+  f.cell[0] = f.interior ? int64_t(fp.fplus[f.i]) : int64_t(fp.bcell[f.i]);
+  f.cell[1] = f.interior ? int64_t(fp.fminus[f.i]) : 0;
+  return f;
+}
+
+// Point data of facet id into buffer b (all 32 lanes of the point warp):
+// each side's compact face-node index (node index along the face normal =
+// the face's side) and trilinear coefficients; then one lane per (side,
+// point) (2 (p+1)^2 <= 32): the reference point (side 1: each coordinate s,
+// 1 - s, t, 1 - t or the face's side, read off the reference corners of K-
+// that carry K+'s face corners), FP64 geometry, the physical normal and
+// surface element of the point from cof(J+) nhat = det J+ J+^{-T} nhat
+// (side-0 lanes; shuffled to the side-1 lane of the same point), |F| (a
+// butterfly sum over the side-0 lanes), cof^T n / det and the 1D Lagrange
+// data.
+template <int P, typename TB>
+__device__ __forceinline__ void facet_points(const FacetParams& fp, int64_t id, unsigned char* b, int lane) {
+  using L = FacetLayout<P, TB>;
+  constexpr bool F32 = std::is_same<TB, float>::value;
+  constexpr int N1 = L::N1, NB = L::NB, NQF = L::NQF;
+  static_assert(2 * NQF <= 32, "one lane per (side, point)");
+  auto cvt = [](double x) -> TB {
+    if constexpr (F32) return d2f_rn(x); else return x;
+  };
+  double* aco = reinterpret_cast<double*>(b + L::B_ACO);
+  TB* cnv = reinterpret_cast<TB*>(b + L::B_CN);
+  TB* vd = reinterpret_cast<TB*>(b + L::B_VD);
+  TB* dsw = reinterpret_cast<TB*>(b + L::B_DS);
+  int* cidx = reinterpret_cast<int*>(b + L::B_CIDX);
+  const FacetRef f = facet_ref(fp, id);
+  for (int it = lane; it < f.ns * NB; it += 32) {
+    const int s = it / NB, a = it % NB, d = f.face[s] / 2;
+    const int ad = (a / (d == 0 ? 1 : (d == 1 ? N1 : N1 * N1))) % N1;
+    int c = -1;
+    if (ad == (f.face[s] % 2) * P) {
+      const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
+      const int st1 = d1 == 0 ? 1 : (d1 == 1 ? N1 : N1 * N1), st2 = d2 == 0 ? 1 : (d2 == 1 ? N1 : N1 * N1);
+      c = (a / st1) % N1 + N1 * ((a / st2) % N1);
+    }
+    cidx[s * NB + a] = c;
+  }
+  if (lane < 3 * f.ns) trilinear_coefficients(fp.xv + f.cell[lane / 3] * 24, lane % 3, aco + (lane / 3) * 21);
+  __syncwarp();
+    const bool act = lane < f.ns * NQF;
+    const int side = act ? lane / NQF : 0, q = lane % NQF, qs = q % N1, qt = q / N1;
+    const double s = fp.gx[qs], tt = fp.gx[qt];
+    // (selects, not indexing by the face's direction, so that xh, cof and
+    // nd stay in registers)
+    double xh[3];
+    if (side == 0) {
+      const int d = f.face[0] / 2;
+      const double fv = double(f.face[0] % 2);
+      xh[0] = d == 0 ? fv : s;
+      xh[1] = d == 1 ? fv : (d == 0 ? s : tt);
+      xh[2] = d == 2 ? fv : tt;
+    } else {
+      // the corners of K+'s face sit on K-'s reference corners v0 (s, t) =
+      // (0, 0), v1 (1, 0), v2 (0, 1), v3 = v1 + v2 - v0 (a symmetry of the
+      // square, checked at setup), so each reference coordinate of K-'s
+      // point is v0 + (v1 - v0) s + (v2 - v0) t: one of s, 1 - s, t, 1 - t
+      // or the face's side
+      const int v0 = fp.fcorner[4 * f.i], v1 = fp.fcorner[4 * f.i + 1], v2 = fp.fcorner[4 * f.i + 2];
+      const double sm1 = 1.0 - s, tm1 = 1.0 - tt;
+      const int d = f.face[1] / 2;
+      const double fv = double(f.face[1] % 2);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int b0 = (v0 >> k) & 1, d1 = ((v1 >> k) & 1) - b0, d2 = ((v2 >> k) & 1) - b0;
+        xh[k] = k == d ? fv : (d1 > 0 ? s : d1 < 0 ? sm1 : d2 > 0 ? tt : d2 < 0 ? tm1 : double(b0));
+      }
+    }
+    double cof[9], det;
+    geometry_at(aco + side * 21, xh[0], xh[1], xh[2], cof, &det);
+    if (act && !(det > 0.0)) atomicOr(fp.err, kErrNegJacobian);
+    // the normal of point q: cof(J+) nhat on the side-0 lane q
+    const int d = f.face[0] / 2;
+    const double sg = f.face[0] % 2 ? 1.0 : -1.0;
+    double nd[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      nd[k] = sg * (d == 0 ? cof[3 * k] : (d == 1 ? cof[3 * k + 1] : cof[3 * k + 2]));
+      nd[k] = __shfl_sync(kFull, nd[k], q);
+    }
+    const double l2 = nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2];
+    const double rl = rsqrt(l2), len = l2 * rl;
+    const double dsq = len * fp.gw[qs] * fp.gw[qt];
+    double ar = lane < NQF ? dsq : 0.0;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) ar += __shfl_xor_sync(kFull, ar, off);
+    if (act) {
+      const double rdet = 1.0 / det;
+      const double n0 = nd[0] * rl, n1 = nd[1] * rl, n2 = nd[2] * rl;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cnv[lane * 3 + k] = cvt((cof[k] * n0 + cof[3 + k] * n1 + cof[6 + k] * n2) * rdet);
+      // the 1D shape data; FP32 forms with p <= 2 evaluate them in FP32 at the
+      // rounded reference point (nodes 0, 1/2, 1 exact, every Gauss point
+      // and its mirror at least 0.11 from a node); for p = 3 a 4-point Gauss
+      // abscissa lies 0.003 from the node 1/3, so x - 1/3 is formed in FP64
+      TB* vt = vd + lane * 6 * N1;  // V[k][m] at k*N1 + m, D at (3 + k)*N1 + m
+      if constexpr (F32 && P <= 2) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lagrange<P, float>(d2f_rn(xh[k]), vt + k * N1, vt + (3 + k) * N1);
+      } else {
+        double V[3][N1], D[3][N1];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lagrange<P, double>(xh[k], V[k], D[k]);
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+#pragma unroll
+          for (int m = 0; m < N1; ++m) {
+            vt[k * N1 + m] = cvt(V[k][m]);
+            vt[(3 + k) * N1 + m] = cvt(D[k][m]);
+          }
+      }
+      if (side == 0) dsw[q] = cvt(dsq);
+    }
+    if (lane == 0) *reinterpret_cast<double*>(b + L::B_AREA) = ar;
+}
+
+__device__ __forceinline__ void product_barrier() { asm volatile("bar.sync 1, 96;" ::: "memory"); }
+
+// One block of 128 threads per facet at a time, persistent, with warp roles:
+//   warp 3      the point data of the block's next facet (facet_points) into
+//               the other buffer;
+//   warps 0-2   with facet n's point data:
+//     3. per (side, point) row and node column: the normal derivative of every
+//        shape function and the values of the (p+1)^2 face nodes (the other
+//        shape functions vanish on the face);
+//     4. the products X_{sa,sb} = sum_q dS phi^{sa}_{a'} (grad phi^{sb}_b . n)
+//        (a' a face node of side sa) and Y_{sa,sb} = sum_q dS phi^{sa}_{a'} phi^{sb}_{b'};
+//     5. block (sa, sb), row a, column b:
+//        -s_a/2 X_{sa,sb}[a'][b] - tau s_b/2 X_{sb,sa}[b'][a] + gamma/|F| s_a s_b Y_{sa,sb}[a'][b']
+//        (terms whose face node is missing are zero; boundary facets: one side,
+//        s = 1 and the factor 1/2 dropped), Eq. local_to_face_matrix;
+//     named barrier 1 (96 threads) between the steps.
+// One block barrier per facet hands the buffers over; every thread runs the
+// same facet loop, so each barrier sees all of its threads. FP32 forms (TB =
+// float): geometry, normals, |F| and the 1D shape data (for p = 3; p <= 2
+// forms them in FP32) in FP64, rounded to FP32 on the integer bits; steps 3
+// to 5 in FP32, blocks stored in FP32. GB300 issues FP64 at 2 lanes per clock
+// per SM: the point warp's FP64 chain is the part the roles overlap.
 template <int P, typename TB>
 __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
   using L = FacetLayout<P, TB>;
@@ -265,214 +405,125 @@ __global__ void __launch_bounds__(128) k_dg_facets(FacetParams fp) {
     if constexpr (F32) return d2f_rn(x); else return x;
   };
   constexpr int N1 = L::N1, NB = L::NB, NQF = L::NQF, NBF = L::NBF;
-  static_assert(2 * NQF <= 32, "one lane per (side, point)");
+  constexpr int NW = 3, NBJ = (NB + 31) / 32;
   extern __shared__ __align__(16) unsigned char sm[];
-  double* aco = reinterpret_cast<double*>(sm + L::ACO);
-  double* s_area = reinterpret_cast<double*>(sm + L::AREA);
   TB* gn = reinterpret_cast<TB*>(sm + L::GN);
   TB* pf = reinterpret_cast<TB*>(sm + L::PF);
   TB* ff = reinterpret_cast<TB*>(sm + L::FF);
   TB* x1 = reinterpret_cast<TB*>(sm + L::X1);
   TB* yy = reinterpret_cast<TB*>(sm + L::YY);
-  TB* cnv = reinterpret_cast<TB*>(sm + L::CN);
-  TB* vd = reinterpret_cast<TB*>(sm + L::VD);
-  TB* dsw = reinterpret_cast<TB*>(sm + L::DS);
-  int* cidx = reinterpret_cast<int*>(sm + L::CIDX);
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  constexpr int NW = 128 / 32, NBJ = (NB + 31) / 32;
-  // steps 3 and 5 give each warp whole rows and each lane the columns
+  const int64_t n_fac = fp.n_int + fp.n_bnd;
+  // steps 3 and 5 give each product warp whole rows and each lane the columns
   // b = lane + 32 j; the tensor-product digits of those columns, once
   int bd[NBJ][3];
 #pragma unroll
   for (int j = 0; j < NBJ; ++j) {
-    const int b = lane + 32 * j;
-    bd[j][0] = b % N1;
-    bd[j][1] = N1 + (b / N1) % N1;
-    bd[j][2] = 2 * N1 + (b / (N1 * N1)) % N1;
+    const int bb = lane + 32 * j;
+    bd[j][0] = bb % N1;
+    bd[j][1] = N1 + (bb / N1) % N1;
+    bd[j][2] = 2 * N1 + (bb / (N1 * N1)) % N1;
   }
-  for (int64_t id = blockIdx.x; id < fp.n_int + fp.n_bnd; id += gridDim.x) {
-    const bool interior = id < fp.n_int;
-    const int64_t i = interior ? id : id - fp.n_int;
-    const int ns = interior ? 2 : 1;
-    const int face[2] = {interior ? int(fp.fpf[i]) : int(fp.bface[i]), interior ? int(fp.fmf[i]) : 0};
-    const int64_t cell[2] = {interior ? int64_t(fp.fplus[i]) : int64_t(fp.bcell[i]),
-                             interior ? int64_t(fp.fminus[i]) : 0};
-    // 1. compact index of each side's face nodes (node index along the face
-    //    normal = the face's side); the sides' trilinear coefficients
-    for (int it = t; it < ns * NB; it += blockDim.x) {
-      const int s = it / NB, a = it % NB, d = face[s] / 2;
-      const int ad = (a / (d == 0 ? 1 : (d == 1 ? N1 : N1 * N1))) % N1;
-      int c = -1;
-      if (ad == (face[s] % 2) * P) {
-        const int d1 = d == 0 ? 1 : 0, d2 = d == 2 ? 1 : 2;
-        const int st1 = d1 == 0 ? 1 : (d1 == 1 ? N1 : N1 * N1), st2 = d2 == 0 ? 1 : (d2 == 1 ? N1 : N1 * N1);
-        c = (a / st1) % N1 + N1 * ((a / st2) % N1);
+  if (warp == 3 && blockIdx.x < n_fac) facet_points<P, TB>(fp, blockIdx.x, sm + L::PT, lane);
+  __syncthreads();
+  int buf = 0;
+  for (int64_t id = blockIdx.x; id < n_fac; id += gridDim.x, buf ^= 1) {
+    if (warp == 3) {
+      const int64_t nx = id + gridDim.x;
+      if (nx < n_fac) facet_points<P, TB>(fp, nx, sm + L::PT + (buf ^ 1) * L::B_BYTES, lane);
+    } else {
+      const unsigned char* b = sm + L::PT + buf * L::B_BYTES;
+      const TB* cnv = reinterpret_cast<const TB*>(b + L::B_CN);
+      const TB* vd = reinterpret_cast<const TB*>(b + L::B_VD);
+      const TB* dsw = reinterpret_cast<const TB*>(b + L::B_DS);
+      const int* cidx = reinterpret_cast<const int*>(b + L::B_CIDX);
+      const double area = *reinterpret_cast<const double*>(b + L::B_AREA);
+      const FacetRef f = facet_ref(fp, id);
+      const int ns = f.ns;
+      // the face-node index of the lane's columns on each side
+      int cbl[2][NBJ];
+#pragma unroll
+      for (int j = 0; j < NBJ; ++j) {
+        const int bb = lane + 32 * j;
+        cbl[0][j] = bb < NB ? cidx[bb] : -1;
+        cbl[1][j] = bb < NB && ns == 2 ? cidx[NB + bb] : -1;
       }
-      cidx[s * NB + a] = c;
-    }
-    if (t < 3 * ns) trilinear_coefficients(fp.xv + cell[t / 3] * 24, t % 3, aco + (t / 3) * 21);
-    __syncthreads();
-    // 2. one lane per (side, point), warp 0
-    if (t < 32) {
-      const bool act = t < ns * NQF;
-      const int side = act ? t / NQF : 0, q = t % NQF, qs = q % N1, qt = q / N1;
-      const double s = fp.gx[qs], tt = fp.gx[qt];
-      // (selects, not indexing by the face's direction, so that xh, cof and
-      // nd stay in registers)
-      double xh[3];
-      if (side == 0) {
-        const int d = face[0] / 2;
-        const double fv = double(face[0] % 2);
-        xh[0] = d == 0 ? fv : s;
-        xh[1] = d == 1 ? fv : (d == 0 ? s : tt);
-        xh[2] = d == 2 ? fv : tt;
-      } else {
-        // the corners of K+'s face sit on K-'s reference corners v0 (s, t) =
-        // (0, 0), v1 (1, 0), v2 (0, 1), v3 = v1 + v2 - v0 (a symmetry of the
-        // square, checked at setup), so each reference coordinate of K-'s
-        // point is v0 + (v1 - v0) s + (v2 - v0) t: one of s, 1 - s, t, 1 - t
-        // or the face's side
-        const int v0 = fp.fcorner[4 * i], v1 = fp.fcorner[4 * i + 1], v2 = fp.fcorner[4 * i + 2];
-        const double sm1 = 1.0 - s, tm1 = 1.0 - tt;
-        const int d = face[1] / 2;
-        const double fv = double(face[1] % 2);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          const int b0 = (v0 >> k) & 1, d1 = ((v1 >> k) & 1) - b0, d2 = ((v2 >> k) & 1) - b0;
-          xh[k] = k == d ? fv : (d1 > 0 ? s : d1 < 0 ? sm1 : d2 > 0 ? tt : d2 < 0 ? tm1 : double(b0));
-        }
-      }
-      double cof[9], det;
-      geometry_at(aco + side * 21, xh[0], xh[1], xh[2], cof, &det);
-      if (act && !(det > 0.0)) atomicOr(fp.err, kErrNegJacobian);
-      // the normal of point q: cof(J+) nhat on the side-0 lane q
-      const int d = face[0] / 2;
-      const double sg = face[0] % 2 ? 1.0 : -1.0;
-      double nd[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        nd[k] = sg * (d == 0 ? cof[3 * k] : (d == 1 ? cof[3 * k + 1] : cof[3 * k + 2]));
-        nd[k] = __shfl_sync(kFull, nd[k], q);
-      }
-      const double l2 = nd[0] * nd[0] + nd[1] * nd[1] + nd[2] * nd[2];
-      const double rl = rsqrt(l2), len = l2 * rl;
-      const double dsq = len * fp.gw[qs] * fp.gw[qt];
-      double ar = t < NQF ? dsq : 0.0;
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) ar += __shfl_xor_sync(kFull, ar, off);
-      if (act) {
-        const double rdet = 1.0 / det;
-        const double n0 = nd[0] * rl, n1 = nd[1] * rl, n2 = nd[2] * rl;
-#pragma unroll
-        for (int k = 0; k < 3; ++k) cnv[t * 3 + k] = cvt((cof[k] * n0 + cof[3 + k] * n1 + cof[6 + k] * n2) * rdet);
-        // the 1D shape data; FP32 forms with p <= 2 evaluate them in FP32 at the
-        // rounded reference point (nodes 0, 1/2, 1 exact, every Gauss point
-        // and its mirror at least 0.11 from a node); for p = 3 a 4-point Gauss
-        // abscissa lies 0.003 from the node 1/3, so x - 1/3 is formed in FP64
-        TB* vt = vd + t * 6 * N1;  // V[k][m] at k*N1 + m, D at (3 + k)*N1 + m
-        if constexpr (F32 && P <= 2) {
-#pragma unroll
-          for (int k = 0; k < 3; ++k) lagrange<P, float>(d2f_rn(xh[k]), vt + k * N1, vt + (3 + k) * N1);
-        } else {
-          double V[3][N1], D[3][N1];
-#pragma unroll
-          for (int k = 0; k < 3; ++k) lagrange<P, double>(xh[k], V[k], D[k]);
-#pragma unroll
-          for (int k = 0; k < 3; ++k)
-#pragma unroll
-            for (int m = 0; m < N1; ++m) {
-              vt[k * N1 + m] = cvt(V[k][m]);
-              vt[(3 + k) * N1 + m] = cvt(D[k][m]);
+      // 3. row (side, point), column node b: normal derivative; value and dS
+      //    value on face nodes
+      for (int r = warp; r < ns * NQF; r += NW) {
+        const int side = r / NQF, q = r % NQF;
+        const TB* V = vd + r * 6 * N1;  // values at 0..3 N1, derivatives 3 N1 further
+        const TB c0 = cnv[r * 3], c1 = cnv[r * 3 + 1], c2 = cnv[r * 3 + 2], dq = dsw[q];
+  #pragma unroll
+        for (int j = 0; j < NBJ; ++j) {
+          const int b = lane + 32 * j;
+          if (b < NB) {
+            const TB v0 = V[bd[j][0]], v1 = V[bd[j][1]], v2 = V[bd[j][2]];
+            const TB d0 = V[3 * N1 + bd[j][0]], d1 = V[3 * N1 + bd[j][1]], d2 = V[3 * N1 + bd[j][2]];
+            gn[r * NB + b] = c0 * d0 * v1 * v2 + c1 * v0 * d1 * v2 + c2 * v0 * v1 * d2;
+            const int c = side ? cbl[1][j] : cbl[0][j];
+            if (c >= 0) {
+              const TB ph = v0 * v1 * v2;
+              ff[r * NBF + c] = ph;
+              pf[r * NBF + c] = dq * ph;
             }
-        }
-        if (side == 0) dsw[q] = cvt(dsq);
-      }
-      if (t == 0) *s_area = ar;
-    }
-    __syncthreads();
-    // the face-node index of the lane's columns on each side
-    int cbl[2][NBJ];
-#pragma unroll
-    for (int j = 0; j < NBJ; ++j) {
-      const int b = lane + 32 * j;
-      cbl[0][j] = b < NB ? cidx[b] : -1;
-      cbl[1][j] = b < NB && ns == 2 ? cidx[NB + b] : -1;
-    }
-    // 3. row (side, point), column node b: normal derivative; value and dS
-    //    value on face nodes
-    for (int r = warp; r < ns * NQF; r += NW) {
-      const int side = r / NQF, q = r % NQF;
-      const TB* V = vd + r * 6 * N1;  // values at 0..3 N1, derivatives 3 N1 further
-      const TB c0 = cnv[r * 3], c1 = cnv[r * 3 + 1], c2 = cnv[r * 3 + 2], dq = dsw[q];
-#pragma unroll
-      for (int j = 0; j < NBJ; ++j) {
-        const int b = lane + 32 * j;
-        if (b < NB) {
-          const TB v0 = V[bd[j][0]], v1 = V[bd[j][1]], v2 = V[bd[j][2]];
-          const TB d0 = V[3 * N1 + bd[j][0]], d1 = V[3 * N1 + bd[j][1]], d2 = V[3 * N1 + bd[j][2]];
-          gn[r * NB + b] = c0 * d0 * v1 * v2 + c1 * v0 * d1 * v2 + c2 * v0 * v1 * d2;
-          const int c = side ? cbl[1][j] : cbl[0][j];
-          if (c >= 0) {
-            const TB ph = v0 * v1 * v2;
-            ff[r * NBF + c] = ph;
-            pf[r * NBF + c] = dq * ph;
           }
         }
       }
-    }
-    __syncthreads();
-    // 4. X_{sa,sb} scaled by -s_a/2 (boundary: -1), row (block, face node c),
-    //    column b; Y_{sa,sb} scaled by s_a s_b
-    const TB half = interior ? TB(0.5) : TB(1);
-    for (int r = warp; r < ns * ns * NBF; r += NW) {
-      const int blk = r / NBF, c = r % NBF, sa = blk >> 1, sb = blk & 1;
-      TB pq[NQF];
-#pragma unroll
-      for (int q = 0; q < NQF; ++q) pq[q] = pf[(sa * NQF + q) * NBF + c];
-      const TB* g = gn + sb * NQF * NB;
-      const TB sc = sa ? half : -half;
-#pragma unroll
-      for (int j = 0; j < NBJ; ++j) {
-        const int b = lane + 32 * j;
-        if (b < NB) {
-          TB v = TB(0);
-#pragma unroll
-          for (int q = 0; q < NQF; ++q) v = fma(pq[q], g[q * NB + b], v);
-          x1[r * NB + b] = sc * v;
+      product_barrier();
+      // 4. X_{sa,sb} scaled by -s_a/2 (boundary: -1), row (block, face node c),
+      //    column b; Y_{sa,sb} scaled by s_a s_b
+      const TB half = f.interior ? TB(0.5) : TB(1);
+      for (int r = warp; r < ns * ns * NBF; r += NW) {
+        const int blk = r / NBF, c = r % NBF, sa = blk >> 1, sb = blk & 1;
+        TB pq[NQF];
+  #pragma unroll
+        for (int q = 0; q < NQF; ++q) pq[q] = pf[(sa * NQF + q) * NBF + c];
+        const TB* g = gn + sb * NQF * NB;
+        const TB sc = sa ? half : -half;
+  #pragma unroll
+        for (int j = 0; j < NBJ; ++j) {
+          const int b = lane + 32 * j;
+          if (b < NB) {
+            TB v = TB(0);
+  #pragma unroll
+            for (int q = 0; q < NQF; ++q) v = fma(pq[q], g[q * NB + b], v);
+            x1[r * NB + b] = sc * v;
+          }
         }
       }
-    }
-    for (int it = t; it < ns * ns * NBF * NBF; it += blockDim.x) {
-      const int blk = it / (NBF * NBF), sa = blk >> 1, sb = blk & 1, c = (it / NBF) % NBF, e = it % NBF;
-      TB v = TB(0);
-#pragma unroll
-      for (int q = 0; q < NQF; ++q) v = fma(pf[(sa * NQF + q) * NBF + c], ff[(sb * NQF + q) * NBF + e], v);
-      yy[(blk * NBF + c) * NBF + e] = sa == sb ? v : -v;
-    }
-    __syncthreads();
-    // 5. the facet blocks, row (block, a), column b: X term, tau times the
-    //    transposed X term of the swapped block, gamma/|F| times the Y term
-    //    (entries with no face node: zero, no arithmetic)
-    const TB pen = cvt(fp.gamma / *s_area), tau = cvt(fp.tau);
-    for (int r = warp; r < ns * ns * NB; r += NW) {
-      const int blk = r / NB, a = r % NB, sa = blk >> 1, sb = blk & 1;
-      const int ca = cidx[sa * NB + a];
-      const TB* xr = x1 + (blk * NBF + (ca >= 0 ? ca : 0)) * NB;
-      const TB* xt = x1 + ((sb << 1) | sa) * NBF * NB + a;
-      const TB* yr = yy + (blk * NBF + (ca >= 0 ? ca : 0)) * NBF;
-      TB* out = interior ? static_cast<TB*>(fp.fblk) + ((i * 4 + blk) * NB + a) * NB
-                         : static_cast<TB*>(fp.bblk) + (i * NB + a) * NB;
-#pragma unroll
-      for (int j = 0; j < NBJ; ++j) {
-        const int b = lane + 32 * j;
-        if (b < NB) {
-          const int cb = sb ? cbl[1][j] : cbl[0][j];
-          TB v = ca >= 0 ? xr[b] : TB(0);
-          if (cb >= 0) {
-            v = fma(tau, xt[cb * NB], v);
-            if (ca >= 0) v = fma(pen, yr[cb], v);
+      for (int it = t; it < ns * ns * NBF * NBF; it += 32 * NW) {
+        const int blk = it / (NBF * NBF), sa = blk >> 1, sb = blk & 1, c = (it / NBF) % NBF, e = it % NBF;
+        TB v = TB(0);
+  #pragma unroll
+        for (int q = 0; q < NQF; ++q) v = fma(pf[(sa * NQF + q) * NBF + c], ff[(sb * NQF + q) * NBF + e], v);
+        yy[(blk * NBF + c) * NBF + e] = sa == sb ? v : -v;
+      }
+      product_barrier();
+      // 5. the facet blocks, row (block, a), column b: X term, tau times the
+      //    transposed X term of the swapped block, gamma/|F| times the Y term
+      //    (entries with no face node: zero, no arithmetic)
+      const TB pen = cvt(fp.gamma / area), tau = cvt(fp.tau);
+      for (int r = warp; r < ns * ns * NB; r += NW) {
+        const int blk = r / NB, a = r % NB, sa = blk >> 1, sb = blk & 1;
+        const int ca = cidx[sa * NB + a];
+        const TB* xr = x1 + (blk * NBF + (ca >= 0 ? ca : 0)) * NB;
+        const TB* xt = x1 + ((sb << 1) | sa) * NBF * NB + a;
+        const TB* yr = yy + (blk * NBF + (ca >= 0 ? ca : 0)) * NBF;
+        TB* out = f.interior ? static_cast<TB*>(fp.fblk) + ((f.i * 4 + blk) * NB + a) * NB
+                           : static_cast<TB*>(fp.bblk) + (f.i * NB + a) * NB;
+  #pragma unroll
+        for (int j = 0; j < NBJ; ++j) {
+          const int b = lane + 32 * j;
+          if (b < NB) {
+            const int cb = sb ? cbl[1][j] : cbl[0][j];
+            TB v = ca >= 0 ? xr[b] : TB(0);
+            if (cb >= 0) {
+              v = fma(tau, xt[cb * NB], v);
+              if (ca >= 0) v = fma(pen, yr[cb], v);
+            }
+            out[b] = v;
           }
-          out[b] = v;
         }
       }
     }
