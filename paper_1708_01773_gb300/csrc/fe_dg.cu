@@ -4,9 +4,10 @@
 //
 // GB300 form: the cell integrals come from the Poisson cell kernels of an
 // internal fe_space of the same order (FP64 or FP32 form); the facet
-// integrals from k_dg_facets (one block per facet: its four nb x nb
-// blocks, or one for a boundary facet, through small products over the face
-// nodes, where the shape functions do not vanish; FP64 geometry, products in
+// integrals from k_dg_facets (persistent blocks, one facet at a time: its
+// four nb x nb blocks, or one for a boundary facet, through small products
+// over the face nodes, where the shape functions do not vanish; one warp forms
+// the next facet's FP64 point data while the others form the products, in
 // FP64 for the FP64 form and in FP32 for the FP32 forms); k_dg_rows then writes each cell's
 // block row of the CSR matrix in one pass, the diagonal block being the cell
 // matrix plus the cell's six facet diagonal blocks in face order, the others
