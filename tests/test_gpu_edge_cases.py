@@ -1,6 +1,8 @@
 """GPU edge cases of the constrained, Stokes and DG paths: every DOF fixed
 (an empty system), nothing fixed (the unconstrained system, bit for bit), a
-single cell (DG: boundary facets only; Stokes), and an empty mesh."""
+single cell (DG: boundary facets only; Stokes), an empty mesh; and the
+largest single mesh of the batched recipe (Q3 elasticity on 40^3 cells: more
+contributions than an int32 can index)."""
 import numpy as np
 import pytest
 import torch
@@ -8,6 +10,7 @@ import torch
 import oracle
 from metrics import TOL, row_scaled_error, vec_error
 from paper_1708_01773_gb300 import build, feasm, inputs
+from test_gpu_parity import check_rows, sampled_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -78,3 +81,18 @@ def test_empty_mesh_dg_and_dirichlet():
                rhs=torch.empty(1, dtype=torch.float64, device="cuda"))
     torch.cuda.synchronize()
     g.close()
+
+
+def test_maximum_size_q3_elasticity_int64():
+    """Q3 elasticity on 40^3 cells (5.3M DOFs, 1.95e9 nonzeros, 2.36e9
+    contributions: 64-bit positions throughout), FP32 form: sampled rows,
+    the last ones included, against the oracle."""
+    prob = inputs.small_problem((40, 40, 40), 3, inputs.ELASTICITY, seed=950)
+    sp = feasm.FESpace(prob)
+    assert sp.n_contrib > 2 ** 31 and sp.nnz > 2 ** 30
+    coef = torch.tensor(prob.coef, device="cuda")
+    vals, rhs = sp.assemble(coef, prec="fp32")
+    torch.cuda.synchronize()
+    assert sp.status() == 0
+    check_rows(prob, sp, vals.cpu().numpy(), rhs.cpu().numpy(), "fp32", sampled_rows(sp.n_dofs, k=12))
+    sp.close()
