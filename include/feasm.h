@@ -220,8 +220,11 @@ int fe_space_set_kernel(fe_space* s, int cell_kernel);
  *   - with `compliance` non-NULL the space may have at most 8,388,608 cells
  *     (FE_ERR_UNSUPPORTED with a message otherwise); without it, any size;
  *   - the current device must be the space's device;
- *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture;
+ *   - every call looks up the array's device address in the current context
+ *     (cudaGetSymbolAddress, which allocates nothing), so the call stays
+ *     correct after the application resets the device (cudaDeviceReset); the
+ *     first call on a device may also load the library's device code there,
+ *     so make that first call before any stream capture of your own;
  *   - all calls share the one array, so calls that overlap on the GPU (on
  *     different streams, or from different threads) race and may return a
  *     wrong compliance: serialise them. Nothing in the array needs clearing:

@@ -30,7 +30,8 @@
 //   warps 12-19 accumulators of cell n -> shared staging -> cell matrix.
 // Hand-offs use mbarriers (full/empty per slot or stage); every wait is
 // bounded (about one second of clock cycles), after which the role sets
-// FE_ERR_TIMEOUT, leaves its loop, and the CTA frees tensor memory and exits.
+// FE_ERR_TIMEOUT and leaves its loop; the MMA thread then waits (bounded) for
+// its last MMAs to complete, and the CTA frees tensor memory and exits.
 #include <cuda_bf16.h>
 
 #include "fe_launch.h"
@@ -67,9 +68,9 @@ constexpr int OFF_KS = (OFF_PHI + NQ * NB * 8 + 15) & ~15;                 // [2
 constexpr int KS_BYTES = NL * NLP * 4;                                      // 27,216: a multiple of 16
 constexpr int OFF_PAIRS = OFF_KS + 2 * KS_BYTES;  // [PAIR_GROUPS][32] u16 node pairs (kPairTable)
 constexpr int OFF_BAR = (OFF_PAIRS + PAIR_GROUPS * 32 * 2 + 7) & ~7;
-// mbarriers: geo_full[4], geo_empty[4], op_full[2], op_empty[2], acc_full[2], acc_empty[2]
+// mbarriers: geo_full[4], geo_empty[4], op_full[2], op_empty[2], acc_full[2], acc_empty[2], drain
 constexpr int BAR_GEO_FULL = 0, BAR_GEO_EMPTY = 4, BAR_OP_FULL = 8, BAR_OP_EMPTY = 10, BAR_ACC_FULL = 12,
-              BAR_ACC_EMPTY = 14, N_BARS = 16;
+              BAR_ACC_EMPTY = 14, BAR_DRAIN = 16, N_BARS = 17;
 constexpr int OFF_TMEM = OFF_BAR + N_BARS * 8;  // tensor-memory base address, then the abort flag
 constexpr int SMEM_USED = OFF_TMEM + 8;
 constexpr int SMEM_BYTES = SMEM_USED + 1024;  // + alignment slack; > half of the SM: one CTA per SM
@@ -556,6 +557,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
       mbar_init(bar(BAR_ACC_FULL + i), 1);
       mbar_init(bar(BAR_ACC_EMPTY + i), EPI_THREADS);
     }
+    mbar_init(bar(BAR_DRAIN), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
@@ -617,6 +619,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tc(Params p) {
         mma_commit(bar(BAR_OP_EMPTY + st));   // operands may be overwritten
         mma_commit(bar(BAR_ACC_FULL + st));   // accumulators ready for the epilogue
       }
+      // Every MMA this thread issued completes before the tensor memory is
+      // freed: on the normal path the epilogue has already waited for all of
+      // them; after a timeout elsewhere the last cell's MMAs may still be in
+      // flight, and this commit arrives only once they are done (bounded wait).
+      mma_commit(bar(BAR_DRAIN));
+      if (!mbar_wait(bar(BAR_DRAIN), 0)) failed = true;
     }
     __syncwarp();
   } else if (warp >= W_GEO0 && warp < W_GEO0 + N_GEO) {

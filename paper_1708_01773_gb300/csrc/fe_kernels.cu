@@ -658,41 +658,7 @@ static cudaError_t launch_adj_p(const AdjParams& prm, bool fp32, int blocks, cud
 
 cudaError_t launch_adjoint(const fe_space* s, const double* u, const double* coef, double grad_scale, double* g,
                            double* compliance, fe_precision prec, cudaStream_t st) {
-  if (s->n_cells == 0) return cudaSuccess;
-  AdjParams prm;
-  prm.n_cells = s->n_cells;
-  prm.nq = s->nq;
-  prm.xv = s->d_xv;
-  prm.w = s->d_w;
-  prm.xq = s->d_xq;
-  prm.dphi = s->d_dphi;
-  prm.dphi32 = s->d_dphi32;
-  prm.cell_dofs = s->d_cell_dofs;
-  prm.u = u;
-  prm.coef = coef;
-  prm.grad_scale = grad_scale;
-  prm.lam_hat = s->nu / ((1.0 + s->nu) * (1.0 - 2.0 * s->nu));
-  prm.mu_hat = 1.0 / (2.0 * (1.0 + s->nu));
-  prm.g = g;
-  prm.err = s->d_err;
-  const int blocks = int((s->n_cells + kAdjThreads - 1) / kAdjThreads);
-  const bool want_c = compliance != nullptr && coef != nullptr;
-  prm.partials = want_c ? s->d_partials : nullptr;
-  if (want_c && blocks > s->n_partials) return cudaErrorInvalidValue;
-  const bool fp32 = prec != FE_PREC_FP64;
-  cudaError_t e;
-  switch (s->order * 10 + s->ncomp) {
-    case 11: e = launch_adj_p<1, 1>(prm, fp32, blocks, st); break;
-    case 13: e = launch_adj_p<1, 3>(prm, fp32, blocks, st); break;
-    case 21: e = launch_adj_p<2, 1>(prm, fp32, blocks, st); break;
-    case 23: e = launch_adj_p<2, 3>(prm, fp32, blocks, st); break;
-    case 31: e = launch_adj_p<3, 1>(prm, fp32, blocks, st); break;
-    case 33: e = launch_adj_p<3, 3>(prm, fp32, blocks, st); break;
-    default: return cudaErrorInvalidValue;
-  }
-  if (e != cudaSuccess || !want_c) return e;
-  k_sum_partials<<<1, 256, 0, st>>>(s->d_partials, blocks, compliance);
-  return cudaGetLastError();
+  return launch_adjoint_with_scratch(s, u, coef, grad_scale, g, compliance, prec, s->d_partials, s->n_partials, st);
 }
 
 cudaError_t launch_adjoint_with_scratch(const fe_space* s, const double* u, const double* coef, double grad_scale,

@@ -9,8 +9,6 @@
 // still built once by fe_space_create, outside such a loop.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "fe_launch.h"
 
 // Partial sums of the compliance, one per block of feasm::kAdjointBlock cells:
@@ -22,23 +20,17 @@ static __device__ __align__(256) double g_noalloc_partials[kNoAllocPartials];
 
 namespace {
 
-// Device address of the array, looked up once per device. In host code the
-// name g_noalloc_partials is only a host-side stand-in: passing it to a kernel
-// would be wrong, so the address comes from cudaGetSymbolAddress with that
-// device current.
-constexpr int kMaxDevices = 128;
-std::mutex g_mu;
-double* g_addr[kMaxDevices] = {nullptr};
-
-cudaError_t scratch_address(int device, double** out) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (g_addr[device] == nullptr) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess) return e;
-    g_addr[device] = static_cast<double*>(p);
-  }
-  *out = g_addr[device];
+// Device address of the array in the current context. In host code the name
+// g_noalloc_partials is only a host-side stand-in: passing it to a kernel would
+// be wrong, so the address comes from cudaGetSymbolAddress with the space's
+// device current. It is looked up on every call (the lookup allocates
+// nothing): a cached address would dangle once the application resets the
+// device (cudaDeviceReset), which tears down the context that held the array.
+cudaError_t scratch_address(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -66,9 +58,8 @@ extern "C" int fe_assemble_adjoint_noalloc(fe_space* s, const double* u, const d
   if (e != cudaSuccess) return feasm::set_error(FE_ERR_CUDA, cudaGetErrorString(e));
   if (device != s->device)
     return feasm::set_error(FE_ERR_INVALID_ARG, "the current device is not the device of the space");
-  if (device < 0 || device >= kMaxDevices) return feasm::set_error(FE_ERR_UNSUPPORTED, "device ordinal too large");
   double* scratch = nullptr;
-  e = scratch_address(device, &scratch);
+  e = scratch_address(&scratch);
   if (e != cudaSuccess) return feasm::set_error(FE_ERR_CUDA, cudaGetErrorString(e));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (s->n_cells == 0) {

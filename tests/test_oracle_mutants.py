@@ -46,6 +46,10 @@ MUTANTS = [
     ("DG tau term with the other side's derivative", "- tau * gb * phi[sb][b] * half * gn[sa][a]",
      "- tau * gb * phi[sb][b] * half * gn[sb][a]", 0),
     ("DG penalty not divided by the facet area", "pen = gamma / area;", "pen = gamma;", 0),
+    ("smallest det J: vertices not sampled", "for (int q = 0; q < 8; ++q) { jacobian(V, q, xv, J);",
+     "for (int q = 0; q < 0; ++q) { jacobian(V, q, xv, J);", 0),
+    ("smallest det J: corner table left at the Gauss points",
+     "    tp_basis(1, xh, phi, &V->dN[q][0][0]);", "    (void)xh; (void)phi;", 0),
 ]
 
 

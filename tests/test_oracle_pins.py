@@ -869,3 +869,59 @@ def test_dg_symmetry_linearity_and_coercivity():
     assert np.linalg.eigvalsh(A[1.0, 30.0]).min() > 0
     interior = (2 * 2 * 2) + (3 * 1 * 2) + (3 * 2 * 1)
     assert rp[-1] == 27 * 27 * (mesh.n_cells + 2 * interior)
+
+
+# ---------------------------------------------------------------- smallest det J (mesh validity)
+def _single_cell(corners):
+    """One hexahedron from its 8 vertices in x-fastest local order."""
+    return inputs.Mesh(np.asarray(corners, dtype=np.float64), np.arange(8, dtype=np.int32)[None, :])
+
+
+def _unit_corners():
+    return np.array([[v & 1, (v >> 1) & 1, (v >> 2) & 1] for v in range(8)], dtype=np.float64)
+
+
+def test_min_det_brick_cells():
+    """Axis-aligned brick cells of sides (hx, hy, hz): J = diag(hx, hy, hz) at every
+    point and vertex, so det J = hx hy hz; over several cells the smallest product."""
+    m = inputs.brick(3, 2, 2, 0.6, 0.5, 2.0)                 # cells 0.2 x 0.25 x 1.0
+    for nq1d in (1, 2, 3, 4):
+        assert abs(oracle.min_det_jacobian(m, nq1d) - 0.2 * 0.25 * 1.0) <= 1e-15
+    sizes = [(0.5, 2.0, 1.5), (0.3, 0.7, 0.2), (1.0, 1.0, 0.9)]
+    xs, cvs = [], []
+    for i, h in enumerate(sizes):
+        xs.append(_unit_corners() * np.array(h) + np.array([5.0 * i, -1.0, 2.0]))
+        cvs.append(np.arange(8, dtype=np.int32) + 8 * i)
+    m2 = inputs.Mesh(np.concatenate(xs), np.stack(cvs).astype(np.int32))
+    assert abs(oracle.min_det_jacobian(m2, 2) - 0.3 * 0.7 * 0.2) <= 1e-15
+
+
+def test_min_det_affine_cell():
+    """An affine cell x = A xhat + b has J = A everywhere: det J = det A exactly."""
+    A = np.array([[0.9, 0.2, -0.1], [0.15, 1.1, 0.3], [-0.2, 0.1, 0.8]])
+    detA = (A[0, 0] * (A[1, 1] * A[2, 2] - A[1, 2] * A[2, 1]) - A[0, 1] * (A[1, 0] * A[2, 2] - A[1, 2] * A[2, 0])
+            + A[0, 2] * (A[1, 0] * A[2, 1] - A[1, 1] * A[2, 0]))
+    m = _single_cell(_unit_corners() @ A.T + np.array([0.3, -0.7, 1.1]))
+    for nq1d in (2, 3):
+        assert abs(oracle.min_det_jacobian(m, nq1d) - detA) <= 1e-14 * abs(detA)
+
+
+def test_min_det_inverted_cell_is_negative():
+    """Mirroring a brick along x while keeping the local vertex order inverts the
+    map: det J = -hx hy hz < 0 everywhere."""
+    m = _single_cell(_unit_corners() * np.array([-0.5, 0.4, 0.25]))
+    assert abs(oracle.min_det_jacobian(m, 2) + 0.5 * 0.4 * 0.25) <= 1e-15
+
+
+def test_min_det_reached_at_a_vertex():
+    """Unit cube with vertex 7 moved to (t, t, t): at that vertex the Jacobian columns
+    are x7 - x6, x7 - x5, x7 - x3, i.e. I + (t - 1) 11^T, whose determinant is 3t - 2
+    (eigenvalues 1, 1, 3t - 2); every other vertex and every Gauss point has a larger
+    det J, so the minimum over the sampled points is 3t - 2 only if the vertices are
+    sampled as well as the quadrature points."""
+    t = 0.9
+    x = _unit_corners()
+    x[7] = [t, t, t]
+    m = _single_cell(x)
+    for nq1d in (2, 3, 4):
+        assert abs(oracle.min_det_jacobian(m, nq1d) - (3 * t - 2)) <= 1e-14
