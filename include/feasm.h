@@ -266,6 +266,18 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
 int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const double* body_force,
                       double* const* csr_values, double* const* rhs, fe_precision prec, void* stream);
 
+/* Test hook of the batch's bounded wait (a check of the failure path, not
+ * part of the method): later fe_batch_assemble calls limit each row item's
+ * wait to `wait_cycles` clock cycles (0 restores the default, about one
+ * second) and make it wait for `extra_cells` more integrated cells than its
+ * space has (0 restores the normal target). With extra_cells > 0 no row item
+ * can start: each gives up after its limit, its block leaves the launch, the
+ * launch ends, and fe_status of every space of the batch returns
+ * FE_ERR_TIMEOUT; the CSR values of that call are then incomplete. Takes
+ * effect at the next fe_batch_assemble (no recapture). FE_ERR_INVALID_ARG
+ * for negative arguments. */
+int fe_batch_set_wait(fe_batch* b, long long wait_cycles, int extra_cells);
+
 void fe_batch_destroy(fe_batch* b);
 
 /* ------------------------------------------------------------------------

@@ -37,7 +37,11 @@ struct Space {
   ScatterParams scat;
   int order, ncomp, nl, pad;
   int64_t n_cells, n_rows;
+  int64_t wait_target;     // integrated cells a row item waits for (n_cells; more only under the test hook)
+  long long wait_cycles;   // limit of that wait in clock cycles
 };
+
+constexpr long long kDefaultWaitCycles = 1ll << 31;  // about one second
 
 struct Item {
   int32_t space, kind;  // kind 0: cells [begin, end), kind 1: rows [begin, end)
@@ -192,8 +196,8 @@ __global__ void __launch_bounds__(kThreads) k_batch(const Space* sp, int n_space
     } else {
       if (tid == 0) {
         const long long t0 = clock64();
-        while (atomicAdd(&counters[1 + item.space], 0) < int(S.n_cells)) {
-          if (clock64() - t0 > (1ll << 31)) {
+        while (atomicAdd(&counters[1 + item.space], 0) < S.wait_target) {
+          if (clock64() - t0 > S.wait_cycles) {
             s_abort = 1;
             break;
           }
@@ -433,6 +437,8 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
     S.pad = 0;
     S.n_cells = s->n_cells;
     S.n_rows = s->hs.n_dofs;
+    S.wait_target = s->n_cells;
+    S.wait_cycles = feasm::batch::kDefaultWaitCycles;
     feasm::CellParams& c = S.cell;
     c.n_cells = s->n_cells;
     c.nq = s->nq;
@@ -507,6 +513,17 @@ int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const doub
   }
   e = cudaGraphLaunch(pl.exec, st);
   if (e != cudaSuccess) return feasm::set_error(FE_ERR_CUDA, cudaGetErrorString(e));
+  return FE_OK;
+}
+
+int fe_batch_set_wait(fe_batch* b, long long wait_cycles, int extra_cells) {
+  if (!b) return feasm::set_error(FE_ERR_INVALID_ARG, "batch is NULL");
+  if (wait_cycles < 0 || extra_cells < 0) return feasm::set_error(FE_ERR_INVALID_ARG, "negative wait or extra cells");
+  for (size_t i = 0; i < b->h_spaces.size(); ++i) {
+    Space& S = b->h_spaces[i];
+    S.wait_cycles = wait_cycles > 0 ? wait_cycles : feasm::batch::kDefaultWaitCycles;
+    S.wait_target = S.n_cells + extra_cells;
+  }
   return FE_OK;
 }
 

@@ -44,7 +44,7 @@ extern "C" int fe_assemble_adjoint_noalloc(fe_space* s, const double* u, const d
     return feasm::set_error(FE_ERR_UNSUPPORTED, "the compliance adjoint is for Poisson and elasticity");
   if (s->host_only) return feasm::set_error(FE_ERR_INVALID_ARG, "host-only space cannot compute");
   if (s->n_cells && (!u || !dc_dcoef)) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL u or dc_dcoef");
-  if (compliance && !coefficients)
+  if (compliance && !coefficients && s->n_cells)
     return feasm::set_error(FE_ERR_INVALID_ARG, "compliance requested without coefficients");
   if (prec != FE_PREC_FP64 && prec != FE_PREC_FP32)
     return feasm::set_error(FE_ERR_INVALID_ARG, "adjoint precision must be FP64 or FP32");

@@ -68,3 +68,80 @@ def test_batch_fixed_item_size_and_empty(small_batch):
     empty = feasm.fe_batch_create([])
     feasm.fe_batch_assemble(empty, [], [], [], [], feasm.FE_PREC_FP32)
     feasm.fe_batch_destroy(empty)
+
+
+def _sampled_rows(n, k=24, seed=0):
+    rng = np.random.default_rng(seed)
+    return np.unique(np.concatenate([[0, 1, n // 2, n - 1], rng.integers(0, n, k)])).astype(np.int64)
+
+
+# orders and problems of the batched recipe at sizes where items hold many cell
+# blocks: Q3 elasticity on 20^3 cells (the autotuner's candidates are 1, 4 or 16
+# cell blocks per item; a fixed item of 256 cells is compared bit for bit too)
+MIX = [((20, 20, 20), 3, 1), ((16, 16, 16), 2, 1), ((24, 24, 24), 1, 0), ((14, 14, 14), 3, 0), ((20, 20, 20), 1, 1),
+       ((18, 18, 18), 2, 0)]
+
+
+@pytest.fixture(scope="module")
+def mixed_batch():
+    build.build()
+    assert torch.cuda.is_available()
+    probs = [inputs.small_problem(n, p, pr, seed=600 + i) for i, (n, p, pr) in enumerate(MIX)]
+    spaces = [feasm.FESpace(p) for p in probs]
+    yield probs, spaces
+    for s in spaces:
+        s.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64", "bf16"])
+def test_batch_realistic_mix_sampled_rows(mixed_batch, prec):
+    probs, spaces = mixed_batch
+    auto = feasm.fe_batch_create([s.handle for s in spaces])
+    vals, rhs = batch_run(auto, probs, spaces, prec)
+    fixed = feasm.fe_batch_create([s.handle for s in spaces], cells_per_item=256)
+    vals2, rhs2 = batch_run(fixed, probs, spaces, prec)
+    for i, (p, s) in enumerate(zip(probs, spaces)):
+        assert torch.equal(vals[i], vals2[i]) and torch.equal(rhs[i], rhs2[i]), p.name
+        rows = _sampled_rows(s.n_dofs, seed=i)
+        ptr, col_o, val_o, rhs_o = oracle.assemble_rows(p, rows, s.cell_dofs(), s.n_dofs)
+        rp, col = s.pattern_host()
+        v = vals[i].cpu().numpy()
+        worst = 0.0
+        for q, r in enumerate(rows):
+            np.testing.assert_array_equal(col[rp[r]:rp[r + 1]], col_o[ptr[q]:ptr[q + 1]])
+            ref = val_o[ptr[q]:ptr[q + 1]]
+            worst = max(worst, np.abs(v[rp[r]:rp[r + 1]] - ref).max() / np.abs(ref).max())
+        assert worst <= TOL[prec], (p.name, prec, worst)
+        r_gpu = rhs[i].cpu().numpy()[rows]
+        assert np.abs(r_gpu - rhs_o).max() <= 1e-12 * max(np.abs(rhs_o).max(), 1e-300), p.name
+    feasm.fe_batch_destroy(auto)
+    feasm.fe_batch_destroy(fixed)
+
+
+def test_batch_bounded_wait_runs_out(small_batch):
+    """The failure path of the persistent launch: with the test hook, every row item
+    waits for one integrated cell more than its space has, gives up after 1e5
+    clock cycles, and its block leaves; the launch ends, fe_status reports
+    FE_ERR_TIMEOUT for the spaces, and the next normal call on the same batch (same
+    captured graph) matches the oracle again. No GPU fault is involved."""
+    probs, spaces = small_batch
+    batch = feasm.fe_batch_create([s.handle for s in spaces])
+    batch_run(batch, probs, spaces, "fp32")                       # tunes and captures
+    feasm.fe_batch_set_wait(batch, 100000, 1)
+    coefs = [torch.tensor(p.coef, device="cuda") for p in probs]
+    vals = [torch.full((s.nnz,), np.nan, dtype=torch.float64, device="cuda") for s in spaces]
+    rhs = [torch.full((s.n_dofs,), np.nan, dtype=torch.float64, device="cuda") for s in spaces]
+    feasm.fe_batch_assemble(batch, coefs, [p.force for p in probs], vals, rhs, feasm.FE_PREC_FP32)
+    torch.cuda.synchronize()
+    codes = [s.status() for s in spaces]
+    assert all(c == -5 for c in codes), codes                   # FE_ERR_TIMEOUT
+    assert all(s.status() == 0 for s in spaces)                  # the words are cleared
+    feasm.fe_batch_set_wait(batch, 0, 0)
+    vals, rhs = batch_run(batch, probs, spaces, "fp32")
+    for i, p in enumerate(probs):
+        rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(p)
+        assert row_scaled_error(rp_o, col_o, vals[i].cpu().numpy(), val_o) <= TOL["fp32"], p.name
+        assert vec_error(rhs[i].cpu().numpy(), rhs_o) <= 1e-12
+    with pytest.raises(feasm.FEError):
+        feasm.fe_batch_set_wait(batch, -1, 0)
+    feasm.fe_batch_destroy(batch)

@@ -1,9 +1,11 @@
 """GPU parity of the interior penalty DG assembly (fe_dg_assemble) against the
 oracle: every entry and the RHS on small meshes (p = 1..3, rotated cell
-orderings, tau = 1 and -1, FP64/FP32/BF16 cell integrals; facet integrals are
-FP64 in every form), and at the 32^3 Q2 size the consistency property (a
-linear u gives zero rows away from the boundary), SIPG symmetry and
-determinism."""
+orderings, tau = 1 and -1, FP64/FP32/BF16 forms: geometry FP64 in every form,
+facet products and blocks FP64 in the FP64 form and FP32 in the FP32 and BF16
+forms), every entry on meshes large enough that each persistent facet block
+takes several facets and each block-row block several cells, and at the 32^3
+Q2 size the consistency property (a linear u gives zero rows away from the
+boundary), SIPG symmetry and determinism."""
 import numpy as np
 import pytest
 import torch
@@ -31,6 +33,32 @@ def test_small_dg_meshes(p, shape, rotate):
     g = feasm.DGSpace(mesh, p)
     rp, col = g.pattern()
     for tau in (1.0, -1.0):
+        rp_o, col_o, val_o, rhs_o = oracle.dg_assemble(mesh, p, tau, 8.0, 1.5)
+        np.testing.assert_array_equal(rp.cpu().numpy(), rp_o)
+        np.testing.assert_array_equal(col.cpu().numpy(), col_o)
+        for prec in ("fp64", "fp32", "bf16"):
+            vals, rhs = g.assemble(tau, 8.0, 1.5, prec=prec)
+            torch.cuda.synchronize()
+            v = vals.cpu().numpy()
+            assert row_scaled_error(rp_o, col_o, v, val_o) <= TOL[prec], (tau, prec)
+            assert vec_error(rhs.cpu().numpy(), rhs_o) <= 1e-12
+    g.close()
+
+
+@pytest.mark.parametrize("p,n,taus", [(2, 14, (1.0, -1.0)), (1, 16, (1.0, -1.0)), (3, 11, (1.0,))])
+def test_dg_every_entry_with_several_facets_per_block(p, n, taus):
+    """Rotated n^3 meshes: k_dg_facets runs one wave of at most 152 x 16 resident
+    blocks over (3 (n-1) + 6) n^2 facets (p = 2: 8,820 facets, at least 3.6 per block
+    at any occupancy), so every block forms the point data of its next facet on
+    the helper warp while the current one is reduced (the double buffer); k_dg_rows
+    runs at most 1,216 blocks over n^3 cells (p = 1: 4,096 cells, p = 2: 2,744), so
+    blocks loop over cells. Every entry and the RHS against the oracle, three forms."""
+    mesh = inputs.small_problem((n, n, n), p, 0, seed=900 + p).mesh
+    mesh = rotated_mesh(mesh, 910 + p)
+    g = feasm.DGSpace(mesh, p)
+    assert g.n_interior + g.n_boundary == (3 * (n - 1) + 6) * n * n
+    rp, col = g.pattern()
+    for tau in taus:
         rp_o, col_o, val_o, rhs_o = oracle.dg_assemble(mesh, p, tau, 8.0, 1.5)
         np.testing.assert_array_equal(rp.cpu().numpy(), rp_o)
         np.testing.assert_array_equal(col.cpu().numpy(), col_o)
