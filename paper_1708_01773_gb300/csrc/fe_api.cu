@@ -181,6 +181,8 @@ int cell_stage(fe_space* s, const double* coef, const double force[3], fe_precis
     return fail(FE_ERR_UNSUPPORTED, "no tensor-core cell kernel for this order / problem / precision");
   if (tc)
     FE_CUDA(launch_cell_tc(s, coef, force, prec, st));
+  else if (q1e_applicable(s, prec))
+    FE_CUDA(launch_cell_q1e(s, coef, force, prec, st));
   else
     FE_CUDA(launch_cell_integration(s, coef, force, prec, st));
   return FE_OK;
@@ -306,7 +308,7 @@ int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients
   if (int rc = check_compute_space(s)) return rc;
   if (s->problem == FE_STOKES) return fail(FE_ERR_UNSUPPORTED, "the compliance adjoint is for Poisson and elasticity");
   if (s->n_cells && (!u || !dc_dcoef)) return fail(FE_ERR_INVALID_ARG, "NULL u or dc_dcoef");
-  if (compliance && !coefficients) return fail(FE_ERR_INVALID_ARG, "compliance requested without coefficients");
+  if (compliance && !coefficients && s->n_cells) return fail(FE_ERR_INVALID_ARG, "compliance requested without coefficients");
   if (prec != FE_PREC_FP64 && prec != FE_PREC_FP32) return fail(FE_ERR_INVALID_ARG, "adjoint precision must be FP64 or FP32");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (s->n_cells == 0) {

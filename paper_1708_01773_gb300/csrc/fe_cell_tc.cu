@@ -36,6 +36,7 @@
 
 #include "fe_launch.h"
 #include "fe_pair_table.h"
+#include "fe_sync.cuh"
 
 namespace feasm {
 
@@ -81,11 +82,6 @@ static_assert(G_BYTES % 16 == 0 && OFF_GEO % 16 == 0 && GEO_SLOT_BYTES % 16 == 0
               "layout");
 static_assert(SMEM_BYTES > 114 * 1024, "one CTA per SM (512 tensor-memory columns)");
 static_assert(GEO_SLOTS == N_GEO, "geometry warp w owns geometry slot w");
-constexpr long long WAIT_CYCLES = 1ll << 31;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
 
 // Byte offset of element (row, kbyte) in a K-major operand with 128-byte rows
 // and the 128-byte swizzle: 8-row atoms of 1024 bytes, 16-byte chunk c of row
@@ -133,34 +129,8 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
                : "memory");
 }
 
-// Bulk copy (TMA engine) of `bytes` from shared to global memory, tracked by
-// this thread's bulk-async groups; both addresses 16-byte aligned, bytes a
-// multiple of 16.
-__device__ __forceinline__ void bulk_store(void* gdst, uint32_t ssrc, uint32_t bytes) {
-  asm volatile(
-      "{\n.reg .u64 g;\ncvta.to.global.u64 g, %0;\n"
-      "cp.async.bulk.global.shared::cta.bulk_group [g], [%1], %2;\n"
-      "cp.async.bulk.commit_group;\n}\n" ::"l"(gdst),
-      "r"(ssrc), "r"(bytes)
-      : "memory");
-}
-// Waits until the shared-memory source of every committed bulk copy has been read.
-__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
-// Waits until every committed bulk copy has completed.
-__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 
 // 16 consecutive accumulator columns of this thread's lane; the wait is tied
 // to the registers so no use can be scheduled before it.
@@ -299,23 +269,6 @@ __device__ __forceinline__ float d2f_rn(double x) {
   const uint32_t rem = uint32_t(mant & 0x1fffffffu);
   if (rem > 0x10000000u || (rem == 0x10000000u && (body & 1u))) ++body;  // carries into the exponent
   return __uint_as_float((uint32_t(u >> 63) << 31) | body);
-}
-
-// Bounded wait on an mbarrier phase; false after about one second.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (clock64() - t0 > WAIT_CYCLES) return false;
-  }
-  return true;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
 
 // Named-barrier OR-reduction over the `count` threads of barrier `id`.

@@ -23,6 +23,13 @@ bool cell_tc_applicable(const fe_space* s, fe_precision prec);
 cudaError_t launch_cell_tc(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
                            cudaStream_t st);
 
+// Q1 elasticity (2^3 rule), FP32 and BF16 forms, with the automatic kernel
+// choice: the warp-role cell kernel (FP64 geometry on its own warps); same
+// outputs as launch_cell_integration.
+bool q1e_applicable(const fe_space* s, fe_precision prec);
+cudaError_t launch_cell_q1e(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
+                            cudaStream_t st);
+
 // Device arrays and host-side sizes of one assembly permutation: the space's
 // own (every DOF a row) or a constrained one (free DOFs only).
 struct ScatterPattern {
