@@ -167,17 +167,33 @@ def source_sha(files) -> str:
     return h.hexdigest()[:16]
 
 
-def kernel_traffic(kernel: str):
-    """DRAM traffic per launch from a committed ncu summary, if the kernel sources
-    are unchanged since the counters were taken (else None)."""
+def kernel_traffic(workload: str, kernel: str, cells: int):
+    """DRAM traffic per launch from a committed ncu summary of this workload's
+    kernel, if the kernel sources are unchanged since the counters were taken
+    (else None). A capture taken on a smaller mesh of the same kernels is scaled
+    by the number of cells (the traffic of these kernels grows in proportion)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
-        d = json.load(f).get(kernel)
-    if not d:
+        d = json.load(f).get(f"{workload}:{kernel}")
+    if not d or source_sha(d["sources"]) != d["sources_sha"]:
         return None
-    return d["bytes_per_launch"] if source_sha(d["sources"]) == d["sources_sha"] else None
+    return int(round(d["bytes_per_launch"] * cells / d.get("cells", cells)))
+
+
+def kernel_names(prob, prec: str):
+    """Names of the cell and scatter kernels fe_assemble launches for a workload
+    (the automatic kernel choice)."""
+    from paper_1708_01773_gb300 import inputs
+    el = prob.problem == inputs.ELASTICITY
+    if prec == "fp64":
+        return f"k_cell<{prob.order},{3 if el else 1},0>", "k_scatter_rows<double>"
+    if el and prob.order == 1 and prob.quad_1d == 2:
+        return "q1e::k_cell_q1e", "k_scatter_slots<24,3>"
+    if el and prob.order == 2 and prob.quad_1d == 3:
+        return "tc::k_cell_tc", "k_scatter_slots<81,1>"
+    return "k_cell", "k_scatter_slots"
 
 
 def scatter_bytes(sp, prec: str) -> int:
@@ -670,9 +686,10 @@ def main():
 
     hbm, bf16_tf, peak_src = measured_peaks()
     cell_avg, scat_avg = float(np.mean(cell_ms)), float(np.mean(scat_ms))
+    cell_name, scat_name = kernel_names(prob, args.prec)
     kernels = {
-        "k_scatter": {"ms": scat_avg, "bytes": scatter_bytes(sp, args.prec)},
-        "k_cell": {"ms": cell_avg, "bytes": cell_bytes(sp, args.prec)},
+        "k_scatter": {"ms": scat_avg, "bytes": scatter_bytes(sp, args.prec), "name": scat_name},
+        "k_cell": {"ms": cell_avg, "bytes": cell_bytes(sp, args.prec), "name": cell_name},
     }
     for k in kernels.values():
         k["gbs"] = k["bytes"] / (k["ms"] / 1e3) / 1e9
@@ -689,8 +706,8 @@ def main():
                                   "tensor_frac": tflops / peak_tf,
                                   "tensor_dtype": "tf32 (3xTF32)" if args.prec == "fp32" else "bf16"})
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
-    roof = {"kernel": dom, "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm, "unit": "GB/s",
-            "frac": kernels[dom]["frac"], "traffic": kernel_traffic(dom),
+    roof = {"kernel": kernels[dom]["name"], "bound": "hbm", "achieved": kernels[dom]["gbs"], "peak": hbm,
+            "unit": "GB/s", "frac": kernels[dom]["frac"], "traffic": kernel_traffic(args.workload, dom, sp.n_cells),
             "algorithmic_bytes": kernels[dom]["bytes"], "peak_source": peak_src + " (burst copy)"}
 
     extras = extra_workloads(args, dev, stream) if (args.extras or args.batched or args.extra) else None

@@ -173,9 +173,12 @@ int fe_assemble_ex(fe_space* s, const double* coefficients, const double* body_f
 
 /* fe_assemble with HOST buffers: coefficients [n_cells], csr_values [nnz] and
  * rhs [n_dofs] (may be NULL) are host memory (pinned memory gives full copy
- * speed). The copies run on `stream` through device staging buffers that the
- * space allocates on its first host-buffer call; the call returns after the
- * results are in host memory. */
+ * speed). The results pass through device staging buffers that the space
+ * allocates on its first host-buffer call. The scatter runs in row ranges;
+ * each range's values and RHS are copied to the host on a second stream (also
+ * created on the first call) as soon as its scatter launch completes, so that
+ * the device-to-host copy overlaps the rest of the assembly. The call returns
+ * after the results are in host memory. */
 int fe_assemble_host(fe_space* s, const double* coefficients, const double* body_force,
                      double* csr_values, double* rhs, fe_precision prec, void* stream);
 
@@ -279,6 +282,19 @@ int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const doub
 int fe_batch_set_wait(fe_batch* b, long long wait_cycles, int extra_cells);
 
 void fe_batch_destroy(fe_batch* b);
+
+/* Self-test of the library's integer-bit conversions against the hardware
+ * conversions (a check of its arithmetic; the paper has no counterpart). For
+ * each device FP64 input x[i], i < n, writes (device buffers):
+ *   out32[8 i + 0..7] = hardware FP32 rounding h of x; the general integer-bit
+ *     rounding; the branch-free one; its out-of-range flags (1: the branch-free
+ *     rounding, 2: the remainder); the branch-free remainder x - h rounded to
+ *     FP32; the hardware remainder; the TF32 split hi, lo of h;
+ *   out64[5 i + 0..4] = the pair (h, hardware remainder) rounded once to FP64 by
+ *     the integer path, by the fixed-point sum, and by one hardware FP64
+ *     addition; h converted to FP64 on the integer bits and by the hardware.
+ * Asynchronous on `stream`; FE_ERR_INVALID_ARG for NULL buffers with n > 0. */
+int fe_selftest_conversions(const double* x, int64_t n, float* out32, double* out64, void* stream);
 
 /* ------------------------------------------------------------------------
  * Strong Dirichlet conditions (paper, Sect. "Strong imposition of boundary

@@ -45,6 +45,9 @@ void free_device(fe_space* s) {
                   s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs, s->d_sched, s->d_psi};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (void* ev : s->range_done)
+    if (ev) cudaEventDestroy(static_cast<cudaEvent_t>(ev));
+  if (s->copy_stream) cudaStreamDestroy(static_cast<cudaStream_t>(s->copy_stream));
 }
 
 int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem, double nu,
@@ -286,19 +289,51 @@ int fe_assemble_ex(fe_space* s, const double* coefficients, const double* body_f
 int fe_assemble_host(fe_space* s, const double* coefficients, const double* body_force, double* csr_values,
                      double* rhs, fe_precision prec, void* stream) {
   if (int rc = check_compute_space(s)) return rc;
+  if (prec != FE_PREC_FP64 && prec != FE_PREC_FP32 && prec != FE_PREC_BF16)
+    return fail(FE_ERR_INVALID_ARG, "unknown precision");
   if ((s->n_cells && !coefficients) || (s->hs.nnz && !csr_values))
     return fail(FE_ERR_INVALID_ARG, "NULL coefficients or csr_values");
+  if (rhs && !body_force) return fail(FE_ERR_INVALID_ARG, "rhs requested without body_force");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  constexpr int kRanges = 8;
   if (!s->d_stage_coef) {
     FE_CUDA(cudaMalloc(&s->d_stage_coef, std::max<int64_t>(1, s->n_cells) * sizeof(double)));
     FE_CUDA(cudaMalloc(&s->d_stage_vals, std::max<int64_t>(1, s->hs.nnz) * sizeof(double)));
     FE_CUDA(cudaMalloc(&s->d_stage_rhs, std::max<int64_t>(1, s->hs.n_dofs) * sizeof(double)));
+    cudaStream_t cs = nullptr;
+    FE_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    s->copy_stream = cs;
+    for (int i = 0; i < kRanges; ++i) {
+      cudaEvent_t ev = nullptr;
+      FE_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+      s->range_done[i] = ev;
+    }
   }
+  double f[3] = {0.0, 0.0, 0.0};
+  if (body_force)
+    for (int k = 0; k < s->ncomp; ++k) f[k] = body_force[k];
+  double* dr = rhs ? s->d_stage_rhs : nullptr;
   FE_CUDA(cudaMemcpyAsync(s->d_stage_coef, coefficients, s->n_cells * sizeof(double), cudaMemcpyHostToDevice, st));
-  int rc = fe_assemble(s, s->d_stage_coef, body_force, s->d_stage_vals, rhs ? s->d_stage_rhs : nullptr, prec, stream);
-  if (rc) return rc;
-  FE_CUDA(cudaMemcpyAsync(csr_values, s->d_stage_vals, s->hs.nnz * sizeof(double), cudaMemcpyDeviceToHost, st));
-  if (rhs) FE_CUDA(cudaMemcpyAsync(rhs, s->d_stage_rhs, s->hs.n_dofs * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (int rc = feasm::cell_stage(s, s->d_stage_coef, f, prec, st)) return rc;
+  // scatter in row ranges (whole items: rows of one node together), each
+  // range's results copied out on the copy stream once its launch is done
+  cudaStream_t cs = static_cast<cudaStream_t>(s->copy_stream);
+  const feasm::ScatterPattern pt = feasm::space_pattern(s);
+  const int64_t n = s->hs.n_dofs, unit = s->ncomp;
+  const int64_t* rp = s->hs.row_ptr.data();
+  for (int c = 0; c < kRanges; ++c) {
+    const int64_t r0 = (n * c / kRanges) / unit * unit, r1 = c + 1 == kRanges ? n : (n * (c + 1) / kRanges) / unit * unit;
+    if (r1 <= r0) continue;
+    FE_CUDA(feasm::launch_scatter_rows(s, pt, prec, s->d_stage_vals, dr, r0, r1, st));
+    cudaEvent_t ev = static_cast<cudaEvent_t>(s->range_done[c]);
+    FE_CUDA(cudaEventRecord(ev, st));
+    FE_CUDA(cudaStreamWaitEvent(cs, ev, 0));
+    FE_CUDA(cudaMemcpyAsync(csr_values + rp[r0], s->d_stage_vals + rp[r0], (rp[r1] - rp[r0]) * sizeof(double),
+                            cudaMemcpyDeviceToHost, cs));
+    if (rhs)
+      FE_CUDA(cudaMemcpyAsync(rhs + r0, s->d_stage_rhs + r0, (r1 - r0) * sizeof(double), cudaMemcpyDeviceToHost, cs));
+  }
+  FE_CUDA(cudaStreamSynchronize(cs));
   FE_CUDA(cudaStreamSynchronize(st));
   return FE_OK;
 }

@@ -34,7 +34,7 @@
 // its last MMAs to complete, and the CTA frees tensor memory and exits.
 #include <cuda_bf16.h>
 
-#include "fe_launch.h"
+#include "fe_device.cuh"
 #include "fe_pair_table.h"
 #include "fe_sync.cuh"
 
@@ -209,30 +209,6 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ta, uint32_t tb, float (&va
   }
 }
 
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// FP32 -> FP64, exact, on the integer bits for zero and normal numbers (the
-// exponent is rebiased by 1023 - 127 = 896); other values take the hardware
-// conversion.
-__device__ __noinline__ double f2d_slow(float x);
-__device__ __forceinline__ double f2d(float x) {
-  const uint32_t u = __float_as_uint(x), mag = u & 0x7fffffffu, e = mag >> 23;
-  if (mag == 0) return __longlong_as_double(static_cast<long long>(uint64_t(u >> 31) << 63));
-  if (e == 0 || e == 0xffu) return f2d_slow(x);
-  return __longlong_as_double(
-      static_cast<long long>((uint64_t(u >> 31) << 63) | ((uint64_t(mag) << 29) + (uint64_t(896) << 52))));
-}
-
-// hi + lo (FP32 pair) rounded once to FP64: both parts convert exactly, one
-// FP64 addition rounds their sum.
-__device__ __forceinline__ double feasm_df_to_double(float hi, float lo) {
-  return __dadd_rn(f2d(hi), f2d(lo));
-}
-
 struct Params {
   int64_t n_cells;
   const double* xv;
@@ -247,29 +223,6 @@ struct Params {
   double* fe;
   int* err;
 };
-
-// Out-of-line hardware conversions for the rare operands of the integer
-// conversions below (a real branch: FP64-pipe instructions on a predicated
-// path would still occupy the pipe).
-__device__ __noinline__ float d2f_slow(double x) { return __double2float_rn(x); }
-__device__ __noinline__ double f2d_slow(float x) { return double(x); }
-
-// FP64 -> FP32 round to nearest even on the integer bits (zero and results in
-// the FP32 normal range; other values take the hardware conversion). Keeps
-// the conversions of the FP64 geometry off the FP64 pipe.
-__device__ __forceinline__ float d2f_rn(double x) {
-  const uint64_t u = uint64_t(__double_as_longlong(x));
-  const int e = int((u >> 52) & 0x7ffu) - 896;
-  if (e <= 0 || e >= 255) {
-    if ((u << 1) == 0) return __uint_as_float(uint32_t(u >> 63) << 31);
-    return d2f_slow(x);
-  }
-  const uint64_t mant = u & 0xfffffffffffffull;
-  uint32_t body = (uint32_t(e) << 23) | uint32_t(mant >> 29);
-  const uint32_t rem = uint32_t(mant & 0x1fffffffu);
-  if (rem > 0x10000000u || (rem == 0x10000000u && (body & 1u))) ++body;  // carries into the exponent
-  return __uint_as_float((uint32_t(u >> 63) << 31) | body);
-}
 
 // Named-barrier OR-reduction over the `count` threads of barrier `id`.
 template <int ID, int COUNT>
@@ -386,7 +339,7 @@ __device__ __forceinline__ void cell_geometry(const Params& p, const GeoLane& g,
     const double wd = g.wq * det;
     const float hi = d2f_rn(wd);
     djw[2 * q] = hi;
-    djw[2 * q + 1] = d2f_rn(wd - f2d(hi));
+    djw[2 * q + 1] = d2f_rn(wd - f32_to_f64_exact(hi));
   }
 }
 
@@ -418,7 +371,7 @@ __device__ __forceinline__ void cell_vector(const Params& p, int64_t e, int a, c
     h = sum;
     l += err + sl[r];
   }
-  const double f = feasm_df_to_double(h, l);
+  const double f = __dadd_rn(f32_to_f64_exact(h), f32_to_f64_exact(l));  // h + l rounded once
   double* fe = p.fe + e * NL;
 #pragma unroll
   for (int k = 0; k < 3; ++k) fe[k * NB + a] = p.f[k] * f;

@@ -410,11 +410,13 @@ struct ItemStream {
 };
 
 
-// Exact FP32 -> FP64 conversion of any finite float on the integer bits
-// (denormals included), without the FP64 pipe.
+// Exact FP32 -> FP64 conversion on the integer bits (denormals included),
+// without the FP64 pipe; infinities and NaNs take the hardware conversion.
+static __device__ __noinline__ double f2d_slow(float x) { return double(x); }
 __device__ __forceinline__ double f32_to_f64_exact(float x) {
   double d;
   if (f32_to_f64_bits(x, d)) return d;
+  if ((__float_as_uint(x) & 0x7f800000u) == 0x7f800000u) return f2d_slow(x);
   uint64_t m;
   int ex;
   bool ng;
@@ -473,6 +475,83 @@ __device__ __forceinline__ float d2f_rn(double x) {
   const uint32_t rem = uint32_t(mant & 0x1fffffffu);
   if (rem > 0x10000000u || (rem == 0x10000000u && (body & 1u))) ++body;  // carries into the exponent
   return __uint_as_float((uint32_t(u >> 63) << 31) | body);
+}
+
+// FP64 -> FP32 round to nearest even on the 32-bit words of x, branch-free, for
+// a result that is zero or an FP32 normal number; `odd` is set where it is not
+// (the tile's geometry is then recomputed with the general conversions).
+__device__ __forceinline__ float d2f_fast(double x, bool& odd) {
+  const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x));
+  const uint32_t ahi = hi & 0x7fffffffu;
+  const int e = int(ahi >> 20) - 896;
+  const bool zero = (ahi | lo) == 0;
+  odd |= (e <= 0 || e >= 255) && !zero;
+  uint32_t body = (uint32_t(e) << 23) | ((ahi & 0xfffffu) << 3) | (lo >> 29);
+  const uint32_t rem = lo & 0x1fffffffu;
+  body += (rem > 0x10000000u || (rem == 0x10000000u && (body & 1u))) ? 1u : 0u;
+  return __uint_as_float((hi & 0x80000000u) | (zero ? 0u : body));
+}
+
+// x - d2f_fast(x), the part of x below its FP32 rounding, itself rounded to
+// FP32, on the 32-bit words: the low 29 mantissa bits minus the rounding
+// carry, times 2^(exponent - 1075), normalised on the integer bits. For x with
+// an FP32-normal rounding; `odd` is set where the result leaves the FP32
+// normal range (the tile is then recomputed with the general conversions).
+__device__ __forceinline__ float d2f_rest(double x, bool& odd) {
+  const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x));
+  const int E = int((hi & 0x7fffffffu) >> 20);
+  const uint32_t rem = lo & 0x1fffffffu;
+  const uint32_t body = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  const bool up = rem > 0x10000000u || (rem == 0x10000000u && (body & 1u));
+  // r = rem - up 2^29, |r| <= 2^28; the value is r 2^(E - 1075), sign of x, negated if up
+  const uint32_t m = up ? (0x20000000u - rem) : rem;
+  const int lz = __clz(m | 1u);            // >= 3
+  const int sh = lz - 8;                   // normalise the leading 1 to bit 23
+  const int rs = sh < 0 ? -sh : 1;         // 25..29 significant bits: round to nearest even
+  const uint32_t t = m >> rs, rb = m & ((1u << rs) - 1u), half = 1u << (rs - 1);
+  const uint32_t rnd = t + ((rb > half || (rb == half && (t & 1u))) ? 1u : 0u);
+  const bool carry = sh < 0 && (rnd >> 24) != 0;
+  const uint32_t mm = sh >= 0 ? (m << sh) : (carry ? rnd >> 1 : rnd);
+  const int er = E - 948 + (31 - lz) + (carry ? 1 : 0);  // biased exponent of m 2^(E - 1075)
+  odd |= m != 0 && (er <= 0 || er >= 255);
+  const uint32_t sgn = (hi & 0x80000000u) ^ (up ? 0x80000000u : 0u);
+  return __uint_as_float(m == 0 ? 0u : (sgn | (uint32_t(er) << 23) | (mm & 0x7fffffu)));
+}
+
+// TF32 rounding of x (to nearest, ties away from zero), the hi part of the
+// 3xTF32 split; the lo part is to_tf32(x - hi).
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Exact sum of N FP32 terms held in registers, rounded once to FP64 (the
+// fixed-point accumulation of fx_sum), on the integer bits.
+template <int N>
+__device__ __forceinline__ double fx_sum_regs_f32(const float (&v)[N]) {
+  using Tr = FxTraits<float>;
+  int emax = 1;
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    uint64_t m;
+    int ex;
+    bool ng;
+    Tr::split(v[t], m, ex, ng);
+    if (m != 0 && ex > emax) emax = ex;
+  }
+  int64_t S = 0;
+#pragma unroll
+  for (int t = 0; t < N; ++t) {
+    uint64_t m;
+    int ex;
+    bool ng;
+    Tr::split(v[t], m, ex, ng);
+    const int sh = Tr::kShift0 - (emax - ex);
+    const uint64_t a = sh >= 0 ? (m << sh) : (sh > -64 ? (m >> (-sh)) : 0ull);
+    S += ng ? -int64_t(a) : int64_t(a);
+  }
+  return fx_to_double(S, emax - Tr::kScale);
 }
 
 // Shared-memory layout of the FP32/BF16 cell block (byte offsets; host and

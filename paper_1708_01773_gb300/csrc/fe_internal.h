@@ -100,8 +100,10 @@ struct fe_space {
   unsigned long long* d_sched = nullptr;  // [2] scatter schedule counters (zero between launches)
   double* d_partials = nullptr;  // reduction scratch for the compliance
   int n_partials = 0;
-  // staging buffers of fe_assemble_host
+  // staging buffers of fe_assemble_host, its copy stream and one event per row range
   double* d_stage_coef = nullptr;
   double* d_stage_vals = nullptr;
   double* d_stage_rhs = nullptr;
+  void* copy_stream = nullptr;           // cudaStream_t
+  void* range_done[16] = {nullptr};     // cudaEvent_t
 };

@@ -388,6 +388,19 @@ cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values,
   return launch_scatter_pattern(s, space_pattern(s), prec, values, rhs, st);
 }
 
+cudaError_t launch_scatter_rows(const fe_space* s, const ScatterPattern& pt, fe_precision prec, double* values,
+                                double* rhs, int64_t r0, int64_t r1, cudaStream_t st) {
+  // every row-indexed array is offset to r0; positions within values, codes,
+  // slots and cell data are absolute, so the kernels run unchanged
+  ScatterPattern q = pt;
+  q.n_rows = r1 - r0;
+  q.row_ptr = pt.row_ptr + r0;
+  q.code_ptr = pt.code_ptr + r0;
+  q.slot_ptr = pt.slot_ptr + r0;
+  if (pt.ncode) q.ncode = pt.ncode + r0;
+  return launch_scatter_pattern(s, q, prec, values, rhs ? rhs + r0 : nullptr, st);
+}
+
 cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, fe_precision prec, double* values,
                                    double* rhs, cudaStream_t st) {
   if (pt.n_rows == 0) return cudaSuccess;

@@ -56,6 +56,11 @@ cudaError_t launch_cell_stokes(const fe_space* s, const double* coef, const doub
 cudaError_t launch_scatter(const fe_space* s, fe_precision prec, double* values, double* rhs, cudaStream_t st);
 cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, fe_precision prec, double* values,
                                    double* rhs, cudaStream_t st);
+// The scatter of rows [r0, r1) only (r0, r1 multiples of the rows per item of
+// the pattern: ncomp for node-wise patterns); values are still indexed by the
+// CSR positions of the whole pattern, rhs by the row.
+cudaError_t launch_scatter_rows(const fe_space* s, const ScatterPattern& pt, fe_precision prec, double* values,
+                                double* rhs, int64_t r0, int64_t r1, cudaStream_t st);
 
 // Integrates every cell of `s` into its cell-matrix and cell-vector scratch
 // with the kernel chosen by the space's kernel selection. Returns an FE code.

@@ -29,7 +29,7 @@ EXPORTS = [
     "fe_space_create", "fe_space_create_host", "fe_space_sizes", "fe_space_cell_dofs_host",
     "fe_space_csr_pattern_host", "fe_space_permutation_host", "fe_space_csr_pattern", "fe_assemble", "fe_assemble_ex", "fe_assemble_host",
     "fe_assemble_adjoint", "fe_assemble_adjoint_noalloc", "fe_space_set_kernel", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
-    "fe_batch_assemble", "fe_batch_set_wait", "fe_batch_destroy", "fe_space_dof_points_host", "fe_dirichlet_create", "fe_dirichlet_sizes",
+    "fe_batch_assemble", "fe_batch_set_wait", "fe_batch_destroy", "fe_selftest_conversions", "fe_space_dof_points_host", "fe_dirichlet_create", "fe_dirichlet_sizes",
     "fe_dirichlet_labels_host", "fe_dirichlet_csr_pattern_host", "fe_dirichlet_csr_pattern",
     "fe_dirichlet_permutation_host", "fe_dirichlet_lift_host", "fe_assemble_dirichlet", "fe_dirichlet_destroy",
     "fe_compliance_work_size", "fe_compliance", "fe_space_block_offset", "fe_dg_create", "fe_dg_create_host",
@@ -82,6 +82,7 @@ def lib() -> ctypes.CDLL:
         L.fe_batch_create.argtypes = [V, I, I, P(V)]
         L.fe_batch_assemble.argtypes = [V, V, V, V, V, I, V]
         L.fe_batch_set_wait.argtypes = [V, ctypes.c_longlong, I]
+        L.fe_selftest_conversions.argtypes = [V, I64, V, V, V]
         L.fe_batch_destroy.argtypes = [V]
         L.fe_batch_destroy.restype = None
         L.fe_space_dof_points_host.argtypes = [V, P(MeshDesc), V]
@@ -267,6 +268,11 @@ def fe_batch_assemble(batch: int, coefficients, body_forces, csr_values, rhs, pr
 
 def fe_batch_set_wait(batch: int, wait_cycles: int, extra_cells: int):
     _check(lib().fe_batch_set_wait(batch, int(wait_cycles), int(extra_cells)), "fe_batch_set_wait")
+
+
+def fe_selftest_conversions(x, out32, out64, stream=None):
+    _check(lib().fe_selftest_conversions(_ptr(x), int(x.numel()), _ptr(out32), _ptr(out64), _stream(stream)),
+           "fe_selftest_conversions")
 
 
 def fe_batch_destroy(batch: int):
