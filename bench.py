@@ -198,15 +198,19 @@ def kernel_names(prob, prec: str):
 
 def scatter_bytes(sp, prec: str) -> int:
     """Algorithmic bytes of one scatter launch: every cell-matrix entry read once
-    (FP32, or FP64 for the FP64 form), one 16-bit permutation entry per
-    contribution (slot-major positions; destination-sorted codes plus one count
-    byte per nonzero for the FP64 form), the FP64 values written, the slot lists,
-    cell vectors and row descriptors read, the RHS written."""
+    (FP32, or FP64 for the FP64 form), the FP64 values written, the row
+    descriptors (row, slot and code pointers), cell vectors and slot lists read,
+    the RHS written, and the permutation: for the FP32/BF16 forms one 16-bit
+    slot-major position per contribution, shared by the three rows of a node
+    where they are scattered together (3-component Q1 rows); for the FP64 form
+    one 16-bit destination-sorted code per contribution plus one count byte per
+    nonzero."""
     nl = sp.nl
-    common = sp.nnz * 8 + sp.n_cells * nl * (4 + 8) + (sp.n_dofs + 1) * 8 * 3 + sp.n_dofs * 8
+    rows_per_item = 3 if (prec != "fp64" and sp.prob.ncomp == 3 and sp.prob.problem != 2 and nl <= 32) else 1
+    common = sp.nnz * 8 + sp.n_cells * nl * 8 + (sp.n_dofs + 1) * 8 * 3 + sp.n_dofs * 8
     if prec == "fp64":
-        return int(sp.n_cells * nl * nl * 8 + sp.n_contrib * 2 + sp.nnz + common)
-    return int(sp.n_cells * nl * nl * 4 + sp.n_contrib * 2 + common)
+        return int(sp.n_cells * nl * nl * 8 + sp.n_contrib * 2 + sp.nnz + sp.n_cells * nl * 4 + common)
+    return int(sp.n_cells * nl * nl * 4 + (sp.n_contrib * 2 + sp.n_cells * nl * 4) // rows_per_item + common)
 
 
 def cell_bytes(sp, prec: str) -> int:
