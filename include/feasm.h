@@ -201,11 +201,15 @@ int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients
                         double* dc_dcoef, double* compliance, fe_precision prec, void* stream);
 
 /* Selects the cell-integration kernel of later fe_assemble calls:
- * FE_KERNEL_AUTO (default: the tensor-core kernel where one exists for the
- * order, problem, rule and precision, else the CUDA-core kernel),
+ * FE_KERNEL_AUTO (default: the tensor-core kernel for Q2 elasticity and Q3
+ * Poisson, the warp-role CUDA-core kernel for Q1 elasticity, else the general
+ * CUDA-core kernel; Q2 Poisson stays on the CUDA cores, measured faster there),
  * FE_KERNEL_CUDA_CORE, or FE_KERNEL_TENSOR_CORE (fe_assemble then fails with
- * FE_ERR_UNSUPPORTED where none exists: Q2 elasticity with 3^3 points, FP32
- * or BF16). Both kernels give results within the stated tolerances. */
+ * FE_ERR_UNSUPPORTED where none exists; tensor-core kernels exist for Q2
+ * elasticity and Q2 / Q3 Poisson with the (p+1)^3 rule, FP32 or BF16). With
+ * FE_KERNEL_AUTO, Q1 elasticity with the 2^3 rule (FP32 or BF16) takes a
+ * CUDA-core kernel with warp roles. All kernels give results within the stated
+ * tolerances. */
 enum { FE_KERNEL_AUTO = 0, FE_KERNEL_CUDA_CORE = 1, FE_KERNEL_TENSOR_CORE = 2 };
 int fe_space_set_kernel(fe_space* s, int cell_kernel);
 

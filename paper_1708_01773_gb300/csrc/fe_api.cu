@@ -179,10 +179,16 @@ int cell_stage(fe_space* s, const double* coef, const double force[3], fe_precis
     FE_CUDA(launch_cell_stokes(s, coef, force, prec, st));
     return FE_OK;
   }
-  const bool tc = cell_tc_applicable(s, prec) && s->cell_kernel != FE_KERNEL_CUDA_CORE;
+  // Poisson on the tensor cores: Q3 by default, Q2 on request (measured slower
+  // than the CUDA-core kernel for Q2's 27 x 27 cell blocks)
+  const bool tcp = cell_tcp_applicable(s, prec) && (s->cell_kernel == FE_KERNEL_TENSOR_CORE ||
+                                                    (s->cell_kernel == FE_KERNEL_AUTO && s->order == 3));
+  const bool tc = (cell_tc_applicable(s, prec) || cell_tcp_applicable(s, prec)) && s->cell_kernel != FE_KERNEL_CUDA_CORE;
   if (s->cell_kernel == FE_KERNEL_TENSOR_CORE && !tc)
     return fail(FE_ERR_UNSUPPORTED, "no tensor-core cell kernel for this order / problem / precision");
-  if (tc)
+  if (tcp)
+    FE_CUDA(launch_cell_tcp(s, coef, force, prec, st));
+  else if (tc && cell_tc_applicable(s, prec))
     FE_CUDA(launch_cell_tc(s, coef, force, prec, st));
   else if (q1e_applicable(s, prec))
     FE_CUDA(launch_cell_q1e(s, coef, force, prec, st));

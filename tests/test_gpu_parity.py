@@ -43,7 +43,7 @@ def test_small_meshes_all_precisions(shape, p, problem):
     rp, col = sp.pattern()
     np.testing.assert_array_equal(rp.cpu().numpy(), rp_o)
     np.testing.assert_array_equal(col.cpu().numpy(), col_o)
-    kernels = ["cuda_core", "tensor_core"] if (p == 2 and problem == 1) else ["auto"]
+    kernels = ["cuda_core", "tensor_core"] if (p >= 2 and (problem == 0 or p == 2)) else ["auto"]
     for kern in kernels:
         sp.set_kernel(kern)
         for prec in ("fp64", "fp32", "bf16"):
@@ -71,6 +71,29 @@ def test_tensor_core_pipeline_wraps():
         assert row_scaled_error(rp_o, col_o, vals, val_o) <= TOL[prec], prec
         assert energy_error(rp_o, col_o, vals, val_o) <= TOL[prec], prec
         assert vec_error(rhs, rhs_o) <= 1e-12
+    sp.close()
+
+
+@pytest.mark.parametrize("shape,p", [((15, 13, 11), 2), ((11, 9, 7), 3)])
+def test_poisson_tensor_core_tiles_wrap(shape, p):
+    """Poisson Q2 (4 cells per 128-row tile) and Q3 (2 cells per tile) on the
+    tensor cores: 2,145 and 693 cells, i.e. more tiles than CTAs (each persistent
+    CTA loops over several tiles, reusing both operand stages and its tensor
+    memory) and a ragged last tile; every entry against the oracle, the general
+    CUDA-core kernel on the same space, and run-to-run bitwise reproducibility."""
+    prob = inputs.small_problem(shape, p, 0, seed=30 + p)
+    rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob)
+    sp = feasm.FESpace(prob)
+    for kern in ("tensor_core", "cuda_core"):
+        sp.set_kernel(kern)
+        for prec in ("fp32", "bf16"):
+            vals, rhs = run(sp, prob, prec)
+            assert row_scaled_error(rp_o, col_o, vals, val_o) <= TOL[prec], (kern, prec)
+            assert energy_error(rp_o, col_o, vals, val_o) <= TOL[prec], (kern, prec)
+            assert vec_error(rhs, rhs_o) <= 1e-12
+            if kern == "tensor_core":
+                again, rhs2 = run(sp, prob, prec)
+                assert np.array_equal(vals, again) and np.array_equal(rhs, rhs2)
     sp.close()
 
 
