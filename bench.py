@@ -193,6 +193,8 @@ def kernel_names(prob, prec: str):
         return "q1e::k_cell_q1e", "k_scatter_slots<24,3>"
     if el and prob.order == 2 and prob.quad_1d == 3:
         return "tc::k_cell_tc", "k_scatter_slots<81,1>"
+    if not el and prob.order == 3 and prob.quad_1d == 4:
+        return "tcp::k_cell_tcp<3>", "k_scatter_slots<64,1>"
     return "k_cell", "k_scatter_slots"
 
 
@@ -698,12 +700,17 @@ def main():
     for k in kernels.values():
         k["gbs"] = k["bytes"] / (k["ms"] / 1e3) / 1e9
         k["frac"] = k["gbs"] / hbm
-    if prob.problem == inputs.ELASTICITY and prob.order == 2 and args.prec != "fp64":
+    on_tc = args.prec != "fp64" and ((prob.problem == inputs.ELASTICITY and prob.order == 2) or
+                                     (prob.problem == inputs.POISSON and prob.order == 3))
+    if on_tc:
         # the contraction runs on tcgen05 (3xTF32 for the FP32 form, BF16): its
-        # algorithmic flops (3 nb)^2 nq 2 per cell, times the passes of the split,
-        # against the dtype's peak (TF32: the measured BF16 burst x 1.1 / 2.25)
+        # algorithmic flops per cell, 2 nl^2 K for the Gram of nl rows over K
+        # columns (elasticity: 3 nb rows, nq columns; Poisson: nb rows, 3 nq
+        # columns), times the passes of the split, against the dtype's peak (TF32:
+        # the measured BF16 burst x 1.1 / 2.25)
         passes, peak_tf = (3, bf16_tf * 1.1 / 2.25) if args.prec == "fp32" else (1, bf16_tf)
-        flops = sp.n_cells * sp.nl * sp.nl * prob.quad_1d ** 3 * 2
+        kdim = prob.quad_1d ** 3 * (1 if prob.problem == inputs.ELASTICITY else 3)
+        flops = sp.n_cells * sp.nl * sp.nl * kdim * 2
         tflops = passes * flops / (cell_avg / 1e3) / 1e12
         kernels["k_cell"].update({"contraction_flops": int(flops), "tensor_passes": passes,
                                   "tensor_tflops": tflops, "tensor_peak_tflops": peak_tf,

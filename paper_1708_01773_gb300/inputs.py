@@ -27,6 +27,9 @@ problems, all synthetic):
   nu = 0.3, shifts up to 0.2h, u ~ N(0,1) per DOF rescaled to unit RMS.
 * ``stokes_q2q1_32``   Stokes, Taylor-Hood Q2/Q1, 32^3 cells of the unit cube,
   shifts up to 0.15h, viscosity mu ~ U[0.5, 2], f = (0, 0, -1), 3^3 Gauss.
+* ``poisson_q3_40``    Poisson Q3, 40^3 cells of the unit cube (the largest Q3
+  mesh of the batched recipe), shifts up to 0.2h, conductivity 10^U[-1,1],
+  f = 1, 4^3 Gauss (``poisson_q3_24``: the same on 24^3 cells).
 """
 from __future__ import annotations
 
@@ -230,6 +233,15 @@ def dg_q2_32(n: int = 32, seed_offset: int = 7) -> Mesh:
     return perturb_interior(brick(n, n, n), 0.15, rng)
 
 
+def poisson_q3(n: int = 40, seed_offset: int = 8) -> Problem:
+    """Poisson Q3 on n^3 cells of the unit cube (40^3 is the largest Q3 mesh of
+    the batched recipe), interior shifts up to 0.2h, conductivity 10^U[-1,1],
+    f = 1, 4^3 Gauss."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    mesh = perturb_interior(brick(n, n, n), 0.2, rng)
+    return Problem(f"poisson_q3_{n}", mesh, 3, 4, POISSON, _log_uniform(rng, 0.1, 10.0, mesh.n_cells), np.array([1.0]))
+
+
 def unit_rms_field(n_dofs: int, seed: int) -> np.ndarray:
     """u_i ~ N(0,1) i.i.d., rescaled so that sqrt(mean(u^2)) = 1."""
     rng = np.random.default_rng(seed)
@@ -260,4 +272,6 @@ WORKLOADS = {
     "elasticity_q1_128": elasticity_q1_128,
     "cantilever_q1_64": cantilever_q1_64,
     "stokes_q2q1_32": stokes_q2q1_32,
+    "poisson_q3_40": poisson_q3,
+    "poisson_q3_24": lambda: poisson_q3(24),
 }
