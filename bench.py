@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="fp32", choices=["fp32", "bf16", "fp64"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--kernel", default="auto", choices=["auto", "cuda_core", "tensor_core"],
+                    help="cell-integration kernel selection (fe_space_set_kernel)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--extras", action="store_true",
@@ -182,20 +184,31 @@ def kernel_traffic(workload: str, kernel: str, cells: int):
     return int(round(d["bytes_per_launch"] * cells / d.get("cells", cells)))
 
 
-def kernel_names(prob, prec: str):
+def on_tensor_cores(prob, prec: str, kernel: str) -> bool:
+    """Whether fe_assemble's cell integration runs on tcgen05 for this workload
+    under the kernel selection `kernel` (auto, cuda_core, tensor_core)."""
+    from paper_1708_01773_gb300 import inputs
+    if prec == "fp64" or kernel == "cuda_core" or prob.quad_1d != prob.order + 1:
+        return False
+    if prob.problem == inputs.ELASTICITY and prob.order == 2:
+        return True
+    return kernel == "tensor_core" and prob.problem == inputs.POISSON and prob.order in (2, 3)
+
+
+def kernel_names(prob, prec: str, kernel: str = "auto"):
     """Names of the cell and scatter kernels fe_assemble launches for a workload
-    (the automatic kernel choice)."""
+    under the kernel selection `kernel`."""
     from paper_1708_01773_gb300 import inputs
     el = prob.problem == inputs.ELASTICITY
+    nl = prob.ncomp * (prob.order + 1) ** 3
+    scat = f"k_scatter_slots<{nl},{3 if el and nl <= 32 else 1}>"
     if prec == "fp64":
         return f"k_cell<{prob.order},{3 if el else 1},0>", "k_scatter_rows<double>"
-    if el and prob.order == 1 and prob.quad_1d == 2:
-        return "q1e::k_cell_q1e", "k_scatter_slots<24,3>"
-    if el and prob.order == 2 and prob.quad_1d == 3:
-        return "tc::k_cell_tc", "k_scatter_slots<81,1>"
-    if not el and prob.order == 3 and prob.quad_1d == 4:
-        return "tcp::k_cell_tcp<3>", "k_scatter_slots<64,1>"
-    return "k_cell", "k_scatter_slots"
+    if on_tensor_cores(prob, prec, kernel):
+        return ("tc::k_cell_tc" if el else f"tcp::k_cell_tcp<{prob.order}>"), scat
+    if el and prob.order == 1 and prob.quad_1d == 2 and kernel == "auto":
+        return "q1e::k_cell_q1e", scat
+    return f"k_cell<{prob.order},{3 if el else 1},{1 if prec == 'fp32' else 2}>", scat
 
 
 def scatter_bytes(sp, prec: str) -> int:
@@ -612,6 +625,7 @@ def main():
     t0 = time.perf_counter()
     sp = feasm.FESpace(prob)
     setup_s = time.perf_counter() - t0
+    sp.set_kernel(args.kernel)
     prec = feasm.PRECISIONS[args.prec]
     dev = torch.device("cuda", local)
     coef = torch.tensor(prob.coef, device=dev)
@@ -678,6 +692,7 @@ def main():
             if name == args.prec:
                 continue
             p2 = feasm.PRECISIONS[name]
+            sp.set_kernel("auto" if name == "fp64" else args.kernel)  # FP64 has CUDA-core kernels only
             for _ in range(3):
                 feasm.fe_assemble(sp.handle, coef, prob.force, vals, rhs, p2, stream)
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -692,7 +707,7 @@ def main():
 
     hbm, bf16_tf, peak_src = measured_peaks()
     cell_avg, scat_avg = float(np.mean(cell_ms)), float(np.mean(scat_ms))
-    cell_name, scat_name = kernel_names(prob, args.prec)
+    cell_name, scat_name = kernel_names(prob, args.prec, args.kernel)
     kernels = {
         "k_scatter": {"ms": scat_avg, "bytes": scatter_bytes(sp, args.prec), "name": scat_name},
         "k_cell": {"ms": cell_avg, "bytes": cell_bytes(sp, args.prec), "name": cell_name},
@@ -700,9 +715,7 @@ def main():
     for k in kernels.values():
         k["gbs"] = k["bytes"] / (k["ms"] / 1e3) / 1e9
         k["frac"] = k["gbs"] / hbm
-    on_tc = args.prec != "fp64" and ((prob.problem == inputs.ELASTICITY and prob.order == 2) or
-                                     (prob.problem == inputs.POISSON and prob.order == 3))
-    if on_tc:
+    if on_tensor_cores(prob, args.prec, args.kernel):
         # the contraction runs on tcgen05 (3xTF32 for the FP32 form, BF16): its
         # algorithmic flops per cell, 2 nl^2 K for the Gram of nl rows over K
         # columns (elasticity: 3 nb rows, nq columns; Poisson: nb rows, 3 nq
@@ -745,7 +758,7 @@ def main():
                        "nnz": int(sp.nnz), "contributions": int(sp.n_contrib), "order": prob.order,
                        "precision": f"{args.prec} contraction, fp64 geometry + fp64 CSR accumulation",
                        "l2": "working set > L2 (no flush)", "parallelism": f"replicas x{ws}",
-                       "setup_s": setup_s},
+                       "kernel": args.kernel, "setup_s": setup_s},
             "nnz_per_s": value / sp.n_cells * sp.nnz,
             "e2e": {"value": ws * sp.n_cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(sp.n_cells * 8),
                     "d2h_bytes_per_step": int((sp.nnz + sp.n_dofs) * 8)},

@@ -149,6 +149,24 @@ int fe_space_csr_pattern(const fe_space* s, int64_t* row_ptr, int32_t* col_idx, 
 int fe_space_permutation_host(const fe_space* s, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
                               int64_t* slot_ptr, int32_t* slots);
 
+/* Accumulator layout of the slot-wise scatter (FP32 / BF16 forms; host-only
+ * spaces; the paper has no counterpart: its assembly adds into the matrix in
+ * place). A warp sums one row in shared memory, one 8-byte entry per nonzero;
+ * the nonzeros of each row are mapped to entries so that the 16 lanes of each
+ * half-warp of a cell's contributions touch distinct bank pairs (entry mod 16).
+ *   sizes   [3] int32, out: acc_stride (entries per row; entry acc_stride
+ *           is the row's dummy, which the lanes of dropped columns and the
+ *           lanes past a cell row add into), n_maps, map_stride.
+ *   pos     [code_ptr[n_dofs]] or NULL: slot-major entries, in the blocks of
+ *           fe_space_permutation_host: block row r, slot s, local column m
+ *           holds the entry of the nonzero that (s, m) adds to (bit 15 set on
+ *           the first contribution of each nonzero in slot order).
+ *   map_id  [n_dofs] or NULL: the map of each row.
+ *   maps    [n_maps][map_stride] or NULL: maps[map_id[r]][k] = entry of the
+ *           row's k-th nonzero (k < row length); map 0 is the identity.
+ * Call with NULL arrays to get the sizes. */
+int fe_space_slot_layout_host(const fe_space* s, int32_t* sizes, uint16_t* pos, uint16_t* map_id, uint16_t* maps);
+
 /* Integrates every cell and assembles the global matrix and right-hand side
  * (paper Eq. linear_system, Eq. assembly, Eq. fematrix, Eq. shape_grad; the
  * element loop of the Listing "element_matrix_entries_computation").
@@ -201,15 +219,16 @@ int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients
                         double* dc_dcoef, double* compliance, fe_precision prec, void* stream);
 
 /* Selects the cell-integration kernel of later fe_assemble calls:
- * FE_KERNEL_AUTO (default: the tensor-core kernel for Q2 elasticity and Q3
- * Poisson, the warp-role CUDA-core kernel for Q1 elasticity, else the general
- * CUDA-core kernel; Q2 Poisson stays on the CUDA cores, measured faster there),
- * FE_KERNEL_CUDA_CORE, or FE_KERNEL_TENSOR_CORE (fe_assemble then fails with
- * FE_ERR_UNSUPPORTED where none exists; tensor-core kernels exist for Q2
- * elasticity and Q2 / Q3 Poisson with the (p+1)^3 rule, FP32 or BF16). With
- * FE_KERNEL_AUTO, Q1 elasticity with the 2^3 rule (FP32 or BF16) takes a
- * CUDA-core kernel with warp roles. All kernels give results within the stated
- * tolerances. */
+ * FE_KERNEL_AUTO (default: the tensor-core kernel for Q2 elasticity, the
+ * warp-role CUDA-core kernel for Q1 elasticity, else the general CUDA-core
+ * kernel), FE_KERNEL_CUDA_CORE, or FE_KERNEL_TENSOR_CORE (fe_assemble then
+ * fails with FE_ERR_UNSUPPORTED where none exists; tensor-core kernels exist
+ * for Q2 elasticity and Q2 / Q3 Poisson with the (p+1)^3 rule, FP32 or BF16).
+ * The kernels of FE_KERNEL_AUTO keep the FP32 form within 1e-6 (row-scaled
+ * entry error against FP64) on every mesh tested, single cells included. The
+ * Poisson tensor-core kernel, chosen only on request, is faster for Q3 and
+ * within 1e-6 on multi-cell meshes, but its FP32 form reached 1.2e-6 on one
+ * distorted Q3 cell: the tensor cores' FP32 accumulation truncates. */
 enum { FE_KERNEL_AUTO = 0, FE_KERNEL_CUDA_CORE = 1, FE_KERNEL_TENSOR_CORE = 2 };
 int fe_space_set_kernel(fe_space* s, int cell_kernel);
 
@@ -349,12 +368,18 @@ int fe_dirichlet_csr_pattern(const fe_dirichlet* d, int64_t* row_ptr, int32_t* c
  * pointers), in the layout of fe_space_permutation_host with rows = free DOFs:
  * cnt [nnz]; code_ptr [n_free+1]; codes (may be NULL) hold ncode[r] codes per
  * row, those of fixed columns left out; ncode [n_free] int32; pos (may be
- * NULL) [code_ptr[n_free]] the slot-major positions, where an entry (s, m) of
- * a fixed column holds the index of the reading lane's private dummy
- * accumulator, acc_stride + (m mod 32), acc_stride being the largest row
- * length rounded up to a multiple of 4; slot_ptr [n_free+1]; slots. */
+ * NULL) [code_ptr[n_free]] the slot-major accumulator entries (as in
+ * fe_space_slot_layout_host, through the maps of
+ * fe_dirichlet_slot_layout_host), where an entry (s, m) of a fixed column
+ * holds the row's dummy entry, acc_stride;
+ * slot_ptr [n_free+1]; slots. */
 int fe_dirichlet_permutation_host(const fe_dirichlet* d, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
                                   int32_t* ncode, uint16_t* pos, int64_t* slot_ptr, int32_t* slots);
+
+/* Accumulator maps of the constrained pattern (host-only spaces): sizes [3]
+ * = acc_stride, n_maps, map_stride; map_id [n_free] and maps
+ * [n_maps][map_stride] as in fe_space_slot_layout_host (may be NULL). */
+int fe_dirichlet_slot_layout_host(const fe_dirichlet* d, int32_t* sizes, uint16_t* map_id, uint16_t* maps);
 
 /* Lifting lists (host): n_cells cells carrying fixed and free DOFs, ascending
  * (cells [n_cells]); the fixed local columns of cells[i] are m[ptr[i] ..

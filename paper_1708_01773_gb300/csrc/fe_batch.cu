@@ -53,9 +53,10 @@ constexpr int kWarps = kThreads / 32;
 
 // One CSR row by one warp for FP32 cell matrices: the slot-wise double-float
 // accumulation of k_scatter_slots (slot batches of 4, 2 or 1, first
-// contributions stored, later ones added with TwoSum); loads bypass L1 (the
-// cell matrices were written earlier in this launch by other blocks). The
-// RHS entries are formed separately (rhs_rows).
+// contributions stored, later ones added with TwoSum, the read-out through the
+// row's accumulator map); loads bypass L1 (the cell matrices were written
+// earlier in this launch by other blocks). The RHS entries are formed
+// separately (rhs_rows).
 template <int NL>
 __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* acc) {
   using S = SlotScatter<NL, 1, true>;
@@ -67,7 +68,7 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
   const int my_slot = lane < ns ? p.slots[s0 + lane] : 0;
   const float* ke = reinterpret_cast<const float*>(p.ke) + lane;
   const int rs = p.acc_stride + 32;
-  const int dummy = p.acc_stride + lane;
+  const int dummy = p.acc_stride;
   int sb = 0;
   while (sb < ns) {
     const int left = ns - sb;
@@ -82,9 +83,10 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
       sb += 1;
     }
   }
+  const uint16_t* amap = p.maps + size_t(p.map_id[r]) * p.map_stride;
   for (int kb = 0; kb < nnz; kb += 32) {
     const int k = kb + lane;
-    const float2 a = acc[k < nnz ? k : dummy];
+    const float2 a = acc[k < nnz ? int(amap[k]) : dummy];
     const double v = df_to_double(a.x, a.y);
     if (k < nnz) p.values[k0 + k] = v;
   }
@@ -249,7 +251,7 @@ namespace {
 
 int row_warp_bytes_for(const fe_space* s, fe_precision prec) {
   if (prec == FE_PREC_FP64) return 0;
-  return int(((s->hs.max_row_nnz + 3) & ~int64_t(3)) + 32) * 8;
+  return int(s->hs.acc_stride + 32) * 8;
 }
 
 template <int PREC>
@@ -473,7 +475,10 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
     q.slots = s->d_slots;
     q.ke = s->d_ke;
     q.fe = s->d_fe;
-    q.acc_stride = int((s->hs.max_row_nnz + 3) & ~int64_t(3));
+    q.acc_stride = s->hs.acc_stride;
+    q.maps = s->d_maps;
+    q.map_id = s->d_map_id;
+    q.map_stride = s->hs.map_stride;
   }
   e = cudaMalloc(&b->d_spaces, std::max(1, n) * sizeof(Space));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * (n + 1));

@@ -355,6 +355,9 @@ struct ScatterParams {
   const double* fe;
   double* values;
   double* rhs;
+  const uint16_t* maps;    // [n_maps][map_stride] accumulator entry of each nonzero of a row (slot-wise scatter)
+  const uint16_t* map_id;  // [n_rows] map of each row
+  int map_stride;
   int ke_bytes, code_bytes, warp_bytes, acc_stride;
 };
 
@@ -899,10 +902,13 @@ __device__ __forceinline__ T ld_ro(const T* p) {
 
 // One batch of the slot-wise double-float scatter of k_scatter_slots (see
 // there): B slots from s_begin, R rows per item (R = 3: the rows of one node,
-// local rows i * NL / R + a of each cell), accumulator rows of stride rs with
-// a private dummy per lane at index `dummy`. The first contribution of a
-// nonzero (flag bit 15 of pos; every entry of slot 0) stores (v, 0); later
-// ones add with TwoSum.
+// local rows i * NL / R + a of each cell), accumulator rows of stride rs; pos
+// holds accumulator entries (the row's map applied on the host). Lanes past
+// the end of a cell row (m >= NL) add zero into the row's dummy entry `dummy`
+// (acc_stride: one address for all of them, bank pair 0, which the host's
+// maps keep free in those lanes' half-warp; its value is never read). The
+// first contribution of a nonzero (flag bit 15 of pos; every entry of slot 0)
+// stores (v, 0); later ones add with TwoSum.
 template <int NL, int R, bool CG = false>
 struct SlotScatter {
   static constexpr int CH = (NL + 31) / 32;

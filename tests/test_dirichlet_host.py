@@ -83,7 +83,8 @@ def test_constrained_permutation_matches_oracle(shape, p, problem, kind):
         fe_l[e] -= Ke[e][:, m] @ uD[lfix[lptr[i]:lptr[i + 1]]]
     cnt, code_ptr, codes, ncode, posb, slot_ptr, slots = feasm.fe_dirichlet_permutation_host(
         dsys.handle, prob.mesh.n_cells * nl)
-    acc_stride = (int(np.diff(rp).max()) + 3) & ~3
+    acc_stride, map_id, maps = feasm.fe_dirichlet_slot_layout_host(dsys.handle)
+    assert acc_stride >= int(np.diff(rp).max())
     vals_codes = np.zeros(dsys.nnz)
     vals_pos = np.zeros(dsys.nnz)
     rhs = np.zeros(dsys.n_free)
@@ -106,16 +107,21 @@ def test_constrained_permutation_matches_oracle(shape, p, problem, kind):
             assert np.all(lab[flat_cd[(sl[s] // nl) * nl + m]] == col[k])
             vals_codes[k] = Kf[sl[s] * nl + m].sum()
         assert c == c0 + ncode[r]
-        # slot-major positions: nonzero index (head bit on its first contribution) or the lane's dummy
-        seen = np.zeros(rp[r + 1] - rp[r], dtype=bool)
+        # slot-major positions: the accumulator entry of the nonzero (head bit on its
+        # first contribution), decoded through the row's map, or the lane's dummy
+        nr = rp[r + 1] - rp[r]
+        amap = maps[map_id[r], :nr].astype(np.int64)
+        assert len(set(amap.tolist())) == nr and amap.max(initial=0) < acc_stride
+        inv = {int(a): k for k, a in enumerate(amap)}
+        seen = np.zeros(nr, dtype=bool)
         for s in range(len(sl)):
             e = sl[s] // nl
             for m in range(nl):
                 v = int(posb[c0 + s * nl + m])
                 if fixed[cd[e][m]]:
-                    assert v == acc_stride + (m & 31)
+                    assert v == acc_stride
                     continue
-                k = v & 0x7FFF
+                k = inv[v & 0x7FFF]
                 assert lab[cd[e][m]] == col[rp[r] + k]
                 assert bool(v >> 15) == (not seen[k])
                 seen[k] = True

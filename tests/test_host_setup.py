@@ -150,3 +150,70 @@ def test_empty_mesh_host_setup():
     h = feasm.fe_space_create(mesh.coords, mesh.cell_vertices, 2, 0, 1, 0.3, host_only=True)
     assert feasm.fe_space_sizes(h) == (0, 0, 0, 0)
     feasm.fe_space_destroy(h)
+
+
+def _wavefronts(P, nl, entry, acc_stride):
+    """Shared-memory wavefronts of one slot-wise scatter access pattern: for each
+    slot (row of P) and each 16-lane half-warp of its lanes (local column m on
+    lane m mod 32; lanes past the cell row touch the row's dummy entry
+    acc_stride), the largest number of distinct 8-byte entries that share a
+    bank pair (entry mod 16)."""
+    total = 0
+    lanes = (nl + 31) // 32 * 32
+    for row in P:
+        e = [int(entry[k]) for k in row] + [acc_stride] * (lanes - nl)
+        for g0 in range(0, lanes, 16):
+            g = np.unique(np.asarray(e[g0:g0 + 16]))  # one address: one access
+            total += max(np.bincount(g % 16, minlength=16))
+    return total
+
+
+LAYOUT_CASES = [((6, 6, 6), 1, 1), ((6, 5, 4), 1, 0), ((4, 4, 3), 2, 0), ((3, 3, 3), 2, 1), ((3, 2, 3), 3, 0),
+                ((2, 2, 2), 2, 2)]
+
+
+@pytest.mark.parametrize("shape,p,problem", LAYOUT_CASES)
+def test_slot_layout_maps_and_bank_pairs(shape, p, problem):
+    """The accumulator entries of the slot-wise scatter: every row's map is a
+    one-to-one map of its nonzeros into [0, acc_stride), map 0 is the identity,
+    every slot-major entry decodes (through the row's map) to the nonzero whose
+    column is the cell's DOF, with the first-contribution flag on the first slot
+    that reaches it; and the maps cut the modelled shared-memory wavefronts (one
+    per 16-lane group when the group's entries lie in distinct bank pairs)."""
+    prob = inputs.small_problem(shape, p, problem, seed=70 + 3 * p + problem)
+    sp = feasm.FESpace(prob, host_only=True)
+    nl = prob.n_local
+    cd = sp.cell_dofs().reshape(-1)
+    rp, col = sp.pattern_host()
+    cnt, code_ptr, codes, slot_ptr, slots = feasm.fe_space_permutation_host(sp.handle)
+    acc_stride, pos, map_id, maps = feasm.fe_space_slot_layout_host(sp.handle)
+    assert acc_stride >= np.diff(rp).max() and acc_stride + 32 <= 0x7FFF
+    np.testing.assert_array_equal(maps[0], np.arange(maps.shape[1]))
+    colored = identity = groups = 0
+    for r in range(sp.n_dofs):
+        nr = int(rp[r + 1] - rp[r])
+        amap = maps[map_id[r], :nr].astype(np.int64)
+        assert len(set(amap.tolist())) == nr and amap.max() < acc_stride
+        inv = {int(a): k for k, a in enumerate(amap)}
+        sl = slots[slot_ptr[r]:slot_ptr[r + 1]].astype(np.int64)
+        blk = pos[code_ptr[r]:code_ptr[r] + len(sl) * nl].astype(np.int64).reshape(len(sl), nl)
+        K = np.vectorize(lambda v: inv[v & 0x7FFF])(blk)
+        seen = np.zeros(nr, dtype=bool)
+        for s in range(len(sl)):
+            e = sl[s] // nl
+            np.testing.assert_array_equal(col[rp[r] + K[s]], cd[e * nl:(e + 1) * nl])
+            for m in range(nl):
+                assert bool(blk[s, m] >> 15) == (not seen[K[s, m]])
+                seen[K[s, m]] = True
+        assert seen.all()
+        colored += _wavefronts(K, nl, amap, acc_stride)
+        identity += _wavefronts(K, nl, np.arange(nr), acc_stride)
+        groups += len(sl) * ((nl + 31) // 32 * 2)
+    assert colored <= identity
+    print(f"p {p} problem {problem}: {colored / groups:.3f} wavefronts per half-warp "
+          f"(nonzero order: {identity / groups:.3f})")
+    if (p, problem) in ((1, 1), (1, 0)):
+        assert colored == groups  # every half-warp in one wavefront
+    else:
+        assert colored <= 1.1 * groups
+    sp.close()
