@@ -41,7 +41,7 @@ cudaError_t upload(T** dst, const T* src, size_t n) {
 
 void free_device(fe_space* s) {
   void* ptrs[] = {s->d_xv, s->d_w, s->d_xq, s->d_phi, s->d_dphi, s->d_dphi32, s->d_phi2, s->d_cell_dofs, s->d_row_ptr,
-                  s->d_col, s->d_cnt, s->d_code_ptr, s->d_codes, s->d_pos, s->d_maps, s->d_map_id, s->d_slot_ptr, s->d_slots, s->d_ke, s->d_fe,
+                  s->d_col, s->d_cnt, s->d_code_ptr, s->d_codes, s->d_pos, s->d_slot_ptr, s->d_slots, s->d_ke, s->d_fe,
                   s->d_err, s->d_partials, s->d_stage_coef, s->d_stage_vals, s->d_stage_rhs, s->d_sched, s->d_psi};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -137,8 +137,6 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     if (e == cudaSuccess) e = upload(&s->d_code_ptr, hs.code_ptr.data(), hs.code_ptr.size());
     if (e == cudaSuccess) e = upload(&s->d_codes, hs.codes.data(), hs.codes.size());
     if (e == cudaSuccess) e = upload(&s->d_pos, hs.pos.data(), hs.pos.size());
-    if (e == cudaSuccess) e = upload(&s->d_maps, hs.maps.data(), hs.maps.size());
-    if (e == cudaSuccess) e = upload(&s->d_map_id, hs.map_id.data(), hs.map_id.size());
     if (e == cudaSuccess) e = upload(&s->d_slot_ptr, hs.slot_ptr.data(), hs.slot_ptr.size());
     if (e == cudaSuccess) e = upload(&s->d_slots, hs.slots.data(), hs.slots.size());
     // FP64-sized (the FP32 forms use the first half); 256 bytes of padding for the
@@ -255,16 +253,14 @@ int fe_space_permutation_host(const fe_space* s, uint8_t* cnt, int64_t* code_ptr
   return FE_OK;
 }
 
-int fe_space_slot_layout_host(const fe_space* s, int32_t* sizes, uint16_t* pos, uint16_t* map_id, uint16_t* maps) {
-  if (!s || !sizes) return fail(FE_ERR_INVALID_ARG, "NULL argument");
+int fe_space_slot_layout_host(const fe_space* s, int32_t* acc_stride, uint16_t* pos, uint16_t* entry) {
+  if (!s || !acc_stride) return fail(FE_ERR_INVALID_ARG, "NULL argument");
   if (!s->host_only) return fail(FE_ERR_INVALID_ARG, "the slot layout is kept on the host only for host-only spaces");
   const auto& hs = s->hs;
-  sizes[0] = hs.acc_stride;
-  sizes[1] = hs.map_stride ? int32_t(hs.maps.size() / hs.map_stride) : 0;
-  sizes[2] = hs.map_stride;
+  *acc_stride = hs.acc_stride;
   if (pos) std::memcpy(pos, hs.pos.data(), hs.n_codes * sizeof(uint16_t));
-  if (map_id) std::memcpy(map_id, hs.map_id.data(), hs.map_id.size() * sizeof(uint16_t));
-  if (maps) std::memcpy(maps, hs.maps.data(), hs.maps.size() * sizeof(uint16_t));
+  if (entry)
+    for (int64_t k = 0; k < hs.max_row_nnz; ++k) entry[k] = uint16_t(feasm::slot_entry(s->nl == 24, int(k)));
   return FE_OK;
 }
 

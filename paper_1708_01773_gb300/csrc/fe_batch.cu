@@ -54,7 +54,7 @@ constexpr int kWarps = kThreads / 32;
 // One CSR row by one warp for FP32 cell matrices: the slot-wise double-float
 // accumulation of k_scatter_slots (slot batches of 4, 2 or 1, first
 // contributions stored, later ones added with TwoSum, the read-out through the
-// row's accumulator map); loads bypass L1 (the cell matrices were written
+// row's entry map); loads bypass L1 (the cell matrices were written
 // earlier in this launch by other blocks). The RHS entries are formed
 // separately (rhs_rows).
 template <int NL>
@@ -83,10 +83,10 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
       sb += 1;
     }
   }
-  const uint16_t* amap = p.maps + size_t(p.map_id[r]) * p.map_stride;
+  const bool mapped = NL == 24 && (p.pos[p.code_ptr[r]] & kPosMapped) != 0;
   for (int kb = 0; kb < nnz; kb += 32) {
     const int k = kb + lane;
-    const float2 a = acc[k < nnz ? int(amap[k]) : dummy];
+    const float2 a = acc[k < nnz ? slot_entry(mapped, k) : dummy];
     const double v = df_to_double(a.x, a.y);
     if (k < nnz) p.values[k0 + k] = v;
   }
@@ -476,9 +476,6 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
     q.ke = s->d_ke;
     q.fe = s->d_fe;
     q.acc_stride = s->hs.acc_stride;
-    q.maps = s->d_maps;
-    q.map_id = s->d_map_id;
-    q.map_stride = s->hs.map_stride;
   }
   e = cudaMalloc(&b->d_spaces, std::max(1, n) * sizeof(Space));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * (n + 1));

@@ -35,8 +35,6 @@ struct fe_dirichlet {
   int64_t* d_code_ptr = nullptr;
   uint16_t* d_codes = nullptr;
   uint16_t* d_pos = nullptr;
-  uint16_t* d_maps = nullptr;
-  uint16_t* d_map_id = nullptr;
   int64_t* d_slot_ptr = nullptr;
   int32_t* d_slots = nullptr;
   int32_t* d_ncode = nullptr;
@@ -117,7 +115,7 @@ cudaError_t upload(T** dst, const std::vector<T>& src, size_t extra = 0) {
 void free_device(fe_dirichlet* d) {
   void* ptrs[] = {d->d_row_ptr, d->d_col,   d->d_cnt,       d->d_code_ptr, d->d_codes,   d->d_pos,     d->d_slot_ptr,
                   d->d_slots,   d->d_ncode, d->d_lift_cell, d->d_lift_ptr, d->d_lift_m, d->d_lift_fix,
-                  d->d_sched,   d->d_label, d->d_maps,   d->d_map_id};
+                  d->d_sched,   d->d_label};
   for (void* p : ptrs)
     if (p) cudaFree(p);
 }
@@ -128,9 +126,6 @@ feasm::ScatterPattern pattern_of(const fe_dirichlet* d) {
   pt.nnz = d->hs.nnz;
   pt.max_row_nnz = d->hs.max_row_nnz;
   pt.acc_stride = d->hs.acc_stride;
-  pt.map_stride = d->hs.map_stride;
-  pt.maps = d->d_maps;
-  pt.map_id = d->d_map_id;
   pt.max_slots = d->hs.max_slots;
   pt.node_rows = d->hs.node_rows;
   pt.pos_ok = d->hs.pos_ok;
@@ -241,8 +236,6 @@ int fe_dirichlet_create(fe_space* s, const uint8_t* fixed, fe_dirichlet** out) {
     if (e == cudaSuccess) e = upload(&d->d_code_ptr, hs.code_ptr);
     if (e == cudaSuccess) e = upload(&d->d_codes, hs.codes);
     if (e == cudaSuccess) e = upload(&d->d_pos, hs.pos);
-    if (e == cudaSuccess) e = upload(&d->d_maps, hs.maps);
-    if (e == cudaSuccess) e = upload(&d->d_map_id, hs.map_id);
     if (e == cudaSuccess) e = upload(&d->d_slot_ptr, hs.slot_ptr);
     if (e == cudaSuccess) e = upload(&d->d_slots, hs.slots);
     if (e == cudaSuccess) e = upload(&d->d_ncode, hs.ncode);
@@ -319,16 +312,14 @@ int fe_dirichlet_permutation_host(const fe_dirichlet* d, uint8_t* cnt, int64_t* 
   return FE_OK;
 }
 
-int fe_dirichlet_slot_layout_host(const fe_dirichlet* d, int32_t* sizes, uint16_t* map_id, uint16_t* maps) {
-  if (!d || !sizes) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
+int fe_dirichlet_slot_layout_host(const fe_dirichlet* d, int32_t* acc_stride, uint16_t* entry) {
+  if (!d || !acc_stride) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
   if (!d->s->host_only)
     return feasm::set_error(FE_ERR_INVALID_ARG, "the slot layout is kept on the host only for host-only spaces");
   const auto& hs = d->hs;
-  sizes[0] = hs.acc_stride;
-  sizes[1] = hs.map_stride ? int32_t(hs.maps.size() / hs.map_stride) : 0;
-  sizes[2] = hs.map_stride;
-  if (map_id) std::memcpy(map_id, hs.map_id.data(), hs.map_id.size() * sizeof(uint16_t));
-  if (maps) std::memcpy(maps, hs.maps.data(), hs.maps.size() * sizeof(uint16_t));
+  *acc_stride = hs.acc_stride;
+  if (entry)
+    for (int64_t k = 0; k < hs.max_row_nnz; ++k) entry[k] = uint16_t(feasm::slot_entry(d->s->nl == 24, int(k)));
   return FE_OK;
 }
 

@@ -44,12 +44,9 @@ struct HostSetup {
   std::vector<int32_t> ncode;       // [n_dofs] codes of each row (constrained patterns only; empty: ns * nl)
   bool pos_ok = true;               // the positions of dropped columns fit the 15-bit dummy index
   // accumulator layout of the slot-wise scatter: pos holds accumulator entries
-  // (a row's nonzero k sits at entry maps[map_id[row]][k]; dropped columns at
-  // the dummy entry acc_stride)
+  // (nonzero k of a row at entry slot_entry(nl, k); dropped columns at the
+  // dummy entry acc_stride)
   int acc_stride = 0;               // accumulator entries per row before the dummy
-  int map_stride = 0;               // entries per map (max_row_nnz rounded up to 8)
-  std::vector<uint16_t> maps;       // [n_maps][map_stride]; map 0 is the identity
-  std::vector<uint16_t> map_id;     // [n_dofs]
 };
 
 void build_ref_tables(int p, int nq1d, RefTables* t);
@@ -99,8 +96,6 @@ struct fe_space {
   int64_t* d_code_ptr = nullptr;
   uint16_t* d_codes = nullptr;
   uint16_t* d_pos = nullptr;
-  uint16_t* d_maps = nullptr;    // accumulator maps of the slot-wise scatter
-  uint16_t* d_map_id = nullptr;  // [n_dofs]
   int64_t* d_slot_ptr = nullptr;
   int32_t* d_slots = nullptr;
   void* d_ke = nullptr;          // cell matrices, [n_cells][nl][nlp] FP64 or FP32

@@ -235,11 +235,11 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 // pattern (R = 3). For each cell around the DOF in ascending order ("slot"),
 // the lanes read that cell's matrix row(s) (coalesced) and the slot-major
 // positions pos[s][m]: the accumulator entry of the nonzero that entry (s, m)
-// contributes to (one position block serves all R rows). The host maps each
-// row's nonzeros to accumulator entries so that the 16 lanes of each half-warp
-// of a slot touch distinct shared-memory bank pairs (one wavefront per half
-// instead of about two); the read-out takes nonzero k from entry
-// maps[map_id[row]][k]. The first contribution of each nonzero (flag bit
+// contributes to (one position block serves all R rows); on the Q1 elasticity
+// rows marked by bit 14 the entries follow the bank-pair map of
+// fe_slot_layout.h, so that the 16 lanes of each half-warp of a slot touch
+// distinct shared-memory bank pairs, and the read-out takes nonzero k from
+// entry slot_entry(mapped, k). The first contribution of each nonzero (flag bit
 // 15 of pos; every entry of slot 0) stores (v, 0) into the row's double-float
 // accumulator in shared memory; later ones add with Knuth's TwoSum, whose
 // rounding error is kept exactly in the low part. The entries of one cell row
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 // (fixed) columns also add into the dummy entry. Slots are processed
 // in batches of 8, 4, 2 or 1 (the largest that fits the slots left and the
 // register budget), all loads of a batch issued before its additions; the item
-// descriptors (pointers, slot ids, map) of the warp's next item are fetched
+// descriptors (pointers, slot ids) of the warp's next item are fetched
 // while the current one is reduced. Items
 // go to warps on demand, kSlotGrab at a time (ItemStream). The RHS entries are
 // formed first, in a static pass of 32 consecutive items per warp, one item per
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
   }
   int64_t u = items.u;
   int64_t s0 = 0, k0 = 0, c0 = 0;
-  int ns = 0, nnz = 0, my_slot = 0, mid = 0;
+  int ns = 0, nnz = 0, my_slot = 0;
   if (u < n_items) {
     const int64_t r = u * R;
     s0 = p.slot_ptr[r];
@@ -311,7 +311,6 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
     k0 = p.row_ptr[r];
     nnz = int(p.row_ptr[r + 1] - k0);
     c0 = p.code_ptr[r];
-    mid = p.map_id[r];
     my_slot = lane < ns ? p.slots[s0 + lane] : 0;
   }
   while (u < n_items) {
@@ -344,18 +343,18 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
         sb += 1;
       }
     }
-    // second-level descriptors of the next item (its slot ids, its map)
+    // second-level descriptors of the next item (its slot ids); the current
+    // item's entry map (bit 14 of its positions, read while they are in L1)
     const int nsn = int(s1n - s0n);
     const int my_slot_n = (un < n_items && lane < nsn) ? p.slots[s0n + lane] : 0;
-    const int midn = un < n_items ? int(p.map_id[rn]) : 0;
-    const uint16_t* amap = p.maps + size_t(mid) * p.map_stride;
+    const bool mapped = NL == 24 && (__ldg(p.pos + c0) & kPosMapped) != 0;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int64_t ki = k0 + int64_t(i) * nnz;  // the rows of one node are consecutive and equally long
       const float2* ai = acc + i * rs;
       for (int kb = 0; kb < nnz; kb += 32) {
         const int k = kb + lane;
-        const float2 a = ai[k < nnz ? int(__ldg(amap + k)) : dummy];
+        const float2 a = ai[k < nnz ? slot_entry(mapped, k) : dummy];
         const double v = df_to_double(a.x, a.y);
         if (k < nnz) p.values[ki + k] = v;
       }
@@ -366,7 +365,6 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
     k0 = k0n;
     nnz = int(k1n - k0n);
     c0 = c0n;
-    mid = midn;
     my_slot = my_slot_n;
     u = un;
   }
@@ -381,9 +379,6 @@ ScatterPattern space_pattern(const fe_space* s) {
   pt.nnz = s->hs.nnz;
   pt.max_row_nnz = s->hs.max_row_nnz;
   pt.acc_stride = s->hs.acc_stride;
-  pt.map_stride = s->hs.map_stride;
-  pt.maps = s->d_maps;
-  pt.map_id = s->d_map_id;
   pt.max_slots = s->hs.max_slots;
   pt.node_rows = s->hs.node_rows;
   pt.pos_ok = s->hs.pos_ok;
@@ -412,7 +407,6 @@ cudaError_t launch_scatter_rows(const fe_space* s, const ScatterPattern& pt, fe_
   q.row_ptr = pt.row_ptr + r0;
   q.code_ptr = pt.code_ptr + r0;
   q.slot_ptr = pt.slot_ptr + r0;
-  q.map_id = pt.map_id + r0;
   if (pt.ncode) q.ncode = pt.ncode + r0;
   return launch_scatter_pattern(s, q, prec, values, rhs ? rhs + r0 : nullptr, st);
 }
@@ -437,9 +431,6 @@ cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, 
   p.fe = s->d_fe;
   p.values = values;
   p.rhs = rhs;
-  p.maps = pt.maps;
-  p.map_id = pt.map_id;
-  p.map_stride = pt.map_stride;
   const int tk = prec == FE_PREC_FP64 ? 8 : 4;
   p.ke_bytes = align16(long(pt.max_slots) * s->nlp * tk);
   p.code_bytes = align16(((long(pt.max_slots) * s->nl + 7) & ~7L) * 2);

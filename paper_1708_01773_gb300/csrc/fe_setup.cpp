@@ -2,8 +2,6 @@
 // global DOF numbering, CSR sparsity pattern and the cell-to-nonzero assembly
 // permutation consumed by the scatter kernel.
 #include <algorithm>
-#include <array>
-#include <tuple>
 #include <functional>
 #include <cmath>
 #include <cstring>
@@ -11,6 +9,7 @@
 #include <unordered_map>
 
 #include "fe_internal.h"
+#include "fe_slot_layout.h"
 
 namespace feasm {
 
@@ -246,7 +245,7 @@ static int number_dofs(int p, int ncomp, int64_t n_cells, const int32_t* cv, std
 // each (slot, local column) contributes to ("pos", bit 15 set on the first
 // contribution of each nonzero in slot order), for the slot-wise scatter.
 static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body);
-void build_slot_maps(int nl, HostSetup* hs);
+void build_slot_layout(int nl, HostSetup* hs);
 
 int build_host_setup(int p, int problem, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
                      HostSetup* hs, std::string* err) {
@@ -359,7 +358,7 @@ int build_pattern(int nl, int nb, int ncomp, int64_t n_cells, const int32_t* cel
   // Contributions of fixed columns (label only) are left out of the codes and
   // sent, in the slot-major positions, to a dummy accumulator entry of the
   // slot-wise scatter: entry acc_stride + (m mod 32) of the row here, the
-  // row's single dummy entry once build_slot_maps has run.
+  // row's single dummy entry once build_slot_layout has run.
   const int64_t acc_stride = (hs->max_row_nnz + 3) & ~int64_t(3);
   hs->pos_ok = acc_stride + 32 <= 0x7fff;
   hs->col.assign(hs->nnz, 0);
@@ -426,175 +425,65 @@ int build_pattern(int nl, int nb, int ncomp, int64_t n_cells, const int32_t* cel
     }
     hs->node_rows = ok;
   }
-  build_slot_maps(nl, hs);
+  build_slot_layout(nl, hs);
   return FE_OK;
 }
 
 // ---------------------------------------------------------------------------
-// Accumulator maps of the slot-wise scatter. A warp accumulates a row in
-// shared memory, one 8-byte (FP32 pair) entry per nonzero; the lanes of one
-// slot (one cell) touch the row's entries pos[s][m], lane m mod 32 in pass
-// m / 32. Shared memory serves 16 such 8-byte entries per wavefront when they
-// lie in distinct bank pairs (entry index mod 16), so a group of 16 lanes
-// whose entries share a bank pair is replayed. With the entries stored in
-// nonzero order the 24 entries of a Q1 elasticity cell row fall into about 3
-// wavefronts instead of 2 (the eight nodes of a cell are ranks x + 3y + 9z of
-// the 27 neighbours, 3 components each). Here every distinct position block
-// gets its own injective map from nonzero index to accumulator entry: a greedy
-// colouring of the conflict graph (nonzeros that share a 16-lane group of any
-// slot; the dummy entry that the group's other lanes touch counts as a
-// neighbour already coloured) with 16 colours, one per bank pair (the row
-// stride is a multiple of 16 entries), taking the most constrained
-// nonzero first (DSatur) and, for it, the bank pair with the fewest
-// conflicting neighbours, then the fewest conflicts with the other nonzeros of
-// its 16-wide block of indices (the rows' final read-out), then the lightest
-// load. Entry = colour + 16 * (rank among the nonzeros of that colour). At
-// most kMaxSlotMaps distinct blocks get a map; other rows keep the identity
-// (map 0). The summation order of every nonzero is unchanged.
-constexpr int kMaxSlotMaps = 1 << 14;
-
-static void colour_block(const uint16_t* blk, int ns, int nl, int nnz, int cap, uint16_t* out) {
-  std::vector<std::vector<int32_t>> nbr(nnz);
-  std::vector<int> col(nnz, -1), load(16, 0);
-  std::vector<uint16_t> sat(nnz, 0);
-  std::vector<std::array<int16_t, 16>> ncnt(nnz), ecnt((nnz + 15) / 16);
-  for (auto& a : ncnt) a.fill(0);
-  for (auto& a : ecnt) a.fill(0);
-  {
-    const int W = (nnz + 63) / 64;
-    std::vector<uint64_t> seen(size_t(nnz) * W, 0);
-    const int lanes = (nl + 31) & ~31;
-    int grp[16];
-    for (int s = 0; s < ns; ++s)
-      for (int g0 = 0; g0 < lanes; g0 += 16) {
-        // the group's real entries; its other lanes (past the cell row, or of
-        // dropped columns) touch the row's dummy entry acc_stride, bank pair 0
-        int n = 0;
-        uint16_t taken = 0;
-        for (int m = g0; m < g0 + 16; ++m) {
-          const int k = m < nl ? blk[s * nl + m] & 0x7fff : nnz;
-          if (k < nnz)
-            grp[n++] = k;
-          else
-            taken = 1;
-        }
-        for (int i = 0; i < n; ++i) {
-          const int a = grp[i];
-          sat[a] |= taken;
-          for (int b = 0; b < 16; ++b) ncnt[a][b] += int16_t(taken >> b & 1);
-          for (int j = 0; j < n; ++j) {
-            const int c = grp[j];
-            if (a == c || (seen[size_t(a) * W + c / 64] >> (c % 64) & 1)) continue;
-            seen[size_t(a) * W + c / 64] |= uint64_t(1) << (c % 64);
-            nbr[a].push_back(c);
-          }
-        }
+// Accumulator entries of the slot-wise scatter (fe_slot_layout.h). The
+// slot-major positions hold nonzero indices k after pass 2; here each becomes
+// its accumulator entry: q1e_entry(k), with bit 14 set, on the Q1 elasticity
+// rows whose slots that map serves in fewer shared-memory wavefronts than
+// nonzero order (a model: per slot and 16-lane half-warp, the largest number
+// of distinct entries in one bank pair, entry mod 16, the lanes past the cell
+// row on the dummy entry), else k. Dropped columns of constrained patterns go
+// to the row's dummy entry acc_stride. Summation orders are unchanged.
+static int slot_wavefronts(const uint16_t* b, int ns, int nl, int nnz, bool mapped, int stride) {
+  int total = 0;
+  const int lanes = (nl + 31) & ~31;
+  for (int s = 0; s < ns; ++s)
+    for (int g0 = 0; g0 < lanes; g0 += 16) {
+      int e[16], n = 0, worst = 0;
+      for (int m = g0; m < g0 + 16; ++m) {
+        const int k = m < nl ? b[s * nl + m] & 0x7fff : nnz;
+        const int x = k < nnz ? slot_entry(mapped, k) : stride;
+        bool dup = false;
+        for (int j = 0; j < n; ++j) dup |= e[j] == x;
+        if (!dup) e[n++] = x;
       }
-  }
-  for (int step = 0; step < nnz; ++step) {
-    int v = -1, vs = -1, vd = -1;
-    for (int k = 0; k < nnz; ++k) {
-      if (col[k] >= 0) continue;
-      const int sk = __builtin_popcount(sat[k]), dk = int(nbr[k].size());
-      if (sk > vs || (sk == vs && dk > vd)) { v = k; vs = sk; vd = dk; }
+      for (int j = 0; j < n; ++j) {
+        int c = 0;
+        for (int i = 0; i < n; ++i) c += (e[i] - e[j]) % 16 == 0;
+        worst = std::max(worst, c);
+      }
+      total += worst;
     }
-    int best = -1;
-    for (int b = 0; b < 16; ++b) {
-      if (load[b] >= cap) continue;
-      if (best < 0) { best = b; continue; }
-      const auto key = std::make_tuple(ncnt[v][b], ecnt[v / 16][b], load[b]);
-      const auto kb = std::make_tuple(ncnt[v][best], ecnt[v / 16][best], load[best]);
-      if (key < kb) best = b;
-    }
-    col[v] = best;
-    ++load[best];
-    ++ecnt[v / 16][best];
-    for (int u : nbr[v]) {
-      ++ncnt[u][best];
-      sat[u] |= uint16_t(1u << best);
-    }
-  }
-  int rank[16] = {0};
-  for (int k = 0; k < nnz; ++k) out[k] = uint16_t(col[k] + 16 * rank[col[k]]++);
+  return total;
 }
 
-void build_slot_maps(int nl, HostSetup* hs) {
+void build_slot_layout(int nl, HostSetup* hs) {
   const int64_t nd = hs->n_dofs;
   const int64_t old_stride = (hs->max_row_nnz + 3) & ~int64_t(3);
-  hs->map_stride = int((hs->max_row_nnz + 7) & ~int64_t(7));
-  hs->maps.assign(hs->map_stride, 0);
-  for (int k = 0; k < hs->map_stride; ++k) hs->maps[k] = uint16_t(k);
-  hs->map_id.assign(nd, 0);
+  const int stride = slot_acc_stride(nl, hs->max_row_nnz);
   hs->acc_stride = int(old_stride);
-  if (!hs->pos_ok || hs->max_slots > 32 || nd == 0 || hs->max_row_nnz == 0) return;
-  const int cap = int((hs->max_row_nnz + 15) / 16) + 2;  // entries per bank pair
-  const int64_t stride = int64_t(16) * cap;
-  if (stride + 32 > 0x7fff) return;
-  auto block = [&](int64_t r) { return hs->pos.data() + hs->code_ptr[r]; };
-  auto block_len = [&](int64_t r) { return (hs->slot_ptr[r + 1] - hs->slot_ptr[r]) * nl; };
-  auto row_len = [&](int64_t r) { return hs->row_ptr[r + 1] - hs->row_ptr[r]; };
-  auto same = [&](int64_t a, int64_t b) {
-    return block_len(a) == block_len(b) && row_len(a) == row_len(b) &&
-           std::memcmp(block(a), block(b), size_t(block_len(a)) * sizeof(uint16_t)) == 0;
-  };
-  // hash of each row's block (with its lengths)
-  std::vector<uint64_t> h(nd);
+  if (!hs->pos_ok) return;
+  if (stride + 32 > kPosEntry) {
+    hs->pos_ok = false;  // no slot-wise scatter for this pattern
+    return;
+  }
+  hs->acc_stride = stride;
   const int nthreads = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
   parallel_for(nd, nthreads, [&](int, int64_t r0, int64_t r1) {
     for (int64_t r = r0; r < r1; ++r) {
-      uint64_t x = 0x9e3779b97f4a7c15ull ^ uint64_t(row_len(r)) ^ (uint64_t(block_len(r)) << 32);
-      const uint16_t* b = block(r);
-      for (int64_t i = 0; i < block_len(r); ++i) {
-        x ^= b[i];
-        x *= 0x100000001b3ull;
-        x ^= x >> 29;
-      }
-      h[r] = x;
-    }
-  });
-  // distinct blocks: representative rows, in order of first appearance
-  std::unordered_map<uint64_t, std::vector<int32_t>> by_hash;
-  std::vector<int64_t> rep;  // rep[id - 1] = first row with map id
-  for (int64_t r = 0; r < nd; ++r) {
-    if (row_len(r) == 0) continue;
-    if (r > 0 && h[r] == h[r - 1] && row_len(r - 1) > 0 && same(r - 1, r)) {
-      hs->map_id[r] = hs->map_id[r - 1];  // the rows of one node share their block
-      continue;
-    }
-    auto& cand = by_hash[h[r]];
-    int32_t id = 0;
-    for (int32_t c : cand)
-      if (same(rep[c - 1], r)) { id = c; break; }
-    if (id == 0 && int64_t(rep.size()) + 1 < kMaxSlotMaps) {
-      rep.push_back(r);
-      id = int32_t(rep.size());
-      cand.push_back(id);
-    }
-    hs->map_id[r] = uint16_t(id);
-  }
-  const int64_t n_maps = int64_t(rep.size()) + 1;
-  hs->maps.resize(size_t(n_maps) * hs->map_stride, 0);
-  parallel_for(n_maps - 1, nthreads, [&](int, int64_t i0, int64_t i1) {
-    for (int64_t i = i0; i < i1; ++i) {
-      const int64_t r = rep[i];
-      colour_block(block(r), int(hs->slot_ptr[r + 1] - hs->slot_ptr[r]), nl, int(row_len(r)), cap,
-                   hs->maps.data() + (i + 1) * hs->map_stride);
-    }
-  });
-  // rewrite the positions: nonzero index -> accumulator entry; dropped columns
-  // -> the row's dummy entry (the new stride)
-  hs->acc_stride = int(stride);
-  parallel_for(nd, nthreads, [&](int, int64_t r0, int64_t r1) {
-    for (int64_t r = r0; r < r1; ++r) {
-      const uint16_t* mp = hs->maps.data() + size_t(hs->map_id[r]) * hs->map_stride;
       uint16_t* b = hs->pos.data() + hs->code_ptr[r];
-      const int64_t nnz = row_len(r), len = block_len(r);
-      for (int64_t i = 0; i < len; ++i) {
+      const int nnz = int(hs->row_ptr[r + 1] - hs->row_ptr[r]);
+      const int ns = int(hs->slot_ptr[r + 1] - hs->slot_ptr[r]);
+      const bool mapped = nl == 24 && slot_wavefronts(b, ns, nl, nnz, true, stride) <
+                                          slot_wavefronts(b, ns, nl, nnz, false, stride);
+      for (int64_t i = 0; i < int64_t(ns) * nl; ++i) {
         const int k = b[i] & 0x7fff;
-        if (k < nnz)
-          b[i] = uint16_t((b[i] & 0x8000) | mp[k]);
-        else
-          b[i] = uint16_t(stride);
+        const int flag = mapped ? kPosMapped : 0;
+        b[i] = k < nnz ? uint16_t((b[i] & kPosFirst) | flag | slot_entry(mapped, k)) : uint16_t(flag | stride);
       }
     }
   });

@@ -68,7 +68,7 @@ def lib() -> ctypes.CDLL:
         L.fe_space_csr_pattern_host.argtypes = [V, V, V]
         L.fe_space_csr_pattern.argtypes = [V, V, V, V]
         L.fe_space_permutation_host.argtypes = [V, V, V, V, V, V]
-        L.fe_space_slot_layout_host.argtypes = [V, V, V, V, V]
+        L.fe_space_slot_layout_host.argtypes = [V, V, V, V]
         L.fe_assemble.argtypes = [V, V, V, V, V, I, V]
         L.fe_assemble_host.argtypes = [V, V, V, V, V, I, V]
         L.fe_assemble_ex.argtypes = [V, V, V, V, V, I, V, V]
@@ -93,7 +93,7 @@ def lib() -> ctypes.CDLL:
         L.fe_dirichlet_csr_pattern_host.argtypes = [V, V, V]
         L.fe_dirichlet_csr_pattern.argtypes = [V, V, V, V]
         L.fe_dirichlet_permutation_host.argtypes = [V, V, V, V, V, V, V, V]
-        L.fe_dirichlet_slot_layout_host.argtypes = [V, V, V, V]
+        L.fe_dirichlet_slot_layout_host.argtypes = [V, V, V]
         L.fe_dirichlet_lift_host.argtypes = [V, P(I64), P(I64), V, V, V, V]
         L.fe_assemble_dirichlet.argtypes = [V, V, V, V, V, V, I, V]
         L.fe_compliance_work_size.argtypes = [V, P(I64)]
@@ -192,31 +192,24 @@ def fe_space_permutation_host(space: int):
 
 
 def fe_space_slot_layout_host(space: int):
-    """(acc_stride, pos, map_id, maps) of a host-only space: the slot-major
-    accumulator entries of the slot-wise scatter and the maps from each row's
-    nonzero index to its accumulator entry (maps[map_id[r]][k])."""
-    n_dofs = fe_space_sizes(space)[0]
-    sizes = np.zeros(3, dtype=np.int32)
-    _check(lib().fe_space_slot_layout_host(space, sizes.ctypes.data, None, None, None), "fe_space_slot_layout_host")
+    """(acc_stride, pos, entry) of a host-only space: the slot-major accumulator
+    entries of the slot-wise scatter and the entry of each nonzero index k."""
+    rp, _ = fe_space_csr_pattern_host(space)
     code_ptr = fe_space_permutation_host(space)[1]
+    acc = np.zeros(1, dtype=np.int32)
     pos = np.zeros(int(code_ptr[-1]), dtype=np.uint16)
-    map_id = np.zeros(n_dofs, dtype=np.uint16)
-    maps = np.zeros((int(sizes[1]), int(sizes[2])), dtype=np.uint16)
-    _check(lib().fe_space_slot_layout_host(space, sizes.ctypes.data, pos.ctypes.data, map_id.ctypes.data,
-                                           maps.ctypes.data), "fe_space_slot_layout_host")
-    return int(sizes[0]), pos, map_id, maps
+    entry = np.zeros(max(1, int(np.diff(rp).max(initial=0))), dtype=np.uint16)
+    _check(lib().fe_space_slot_layout_host(space, acc.ctypes.data, pos.ctypes.data, entry.ctypes.data),
+           "fe_space_slot_layout_host")
+    return int(acc[0]), pos, entry
 
 
-def fe_dirichlet_slot_layout_host(d: int):
-    """(acc_stride, map_id, maps) of a host-only space's constrained system."""
-    n_free = fe_dirichlet_sizes(d)[0]
-    sizes = np.zeros(3, dtype=np.int32)
-    _check(lib().fe_dirichlet_slot_layout_host(d, sizes.ctypes.data, None, None), "fe_dirichlet_slot_layout_host")
-    map_id = np.zeros(n_free, dtype=np.uint16)
-    maps = np.zeros((int(sizes[1]), int(sizes[2])), dtype=np.uint16)
-    _check(lib().fe_dirichlet_slot_layout_host(d, sizes.ctypes.data, map_id.ctypes.data, maps.ctypes.data),
-           "fe_dirichlet_slot_layout_host")
-    return int(sizes[0]), map_id, maps
+def fe_dirichlet_slot_layout_host(d: int, max_row_nnz: int):
+    """(acc_stride, entry) of a host-only space's constrained system."""
+    acc = np.zeros(1, dtype=np.int32)
+    entry = np.zeros(max(1, max_row_nnz), dtype=np.uint16)
+    _check(lib().fe_dirichlet_slot_layout_host(d, acc.ctypes.data, entry.ctypes.data), "fe_dirichlet_slot_layout_host")
+    return int(acc[0]), entry
 
 
 def slot_count(space: int) -> int:

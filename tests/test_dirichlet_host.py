@@ -83,7 +83,7 @@ def test_constrained_permutation_matches_oracle(shape, p, problem, kind):
         fe_l[e] -= Ke[e][:, m] @ uD[lfix[lptr[i]:lptr[i + 1]]]
     cnt, code_ptr, codes, ncode, posb, slot_ptr, slots = feasm.fe_dirichlet_permutation_host(
         dsys.handle, prob.mesh.n_cells * nl)
-    acc_stride, map_id, maps = feasm.fe_dirichlet_slot_layout_host(dsys.handle)
+    acc_stride, entry = feasm.fe_dirichlet_slot_layout_host(dsys.handle, int(np.diff(rp).max()))
     assert acc_stride >= int(np.diff(rp).max())
     vals_codes = np.zeros(dsys.nnz)
     vals_pos = np.zeros(dsys.nnz)
@@ -108,9 +108,10 @@ def test_constrained_permutation_matches_oracle(shape, p, problem, kind):
             vals_codes[k] = Kf[sl[s] * nl + m].sum()
         assert c == c0 + ncode[r]
         # slot-major positions: the accumulator entry of the nonzero (head bit on its
-        # first contribution), decoded through the row's map, or the lane's dummy
+        # first contribution), decoded through the entry map, or the row's dummy
         nr = rp[r + 1] - rp[r]
-        amap = maps[map_id[r], :nr].astype(np.int64)
+        mapped = bool(posb[c0] & 0x4000)
+        amap = entry[:nr].astype(np.int64) if mapped else np.arange(nr)
         assert len(set(amap.tolist())) == nr and amap.max(initial=0) < acc_stride
         inv = {int(a): k for k, a in enumerate(amap)}
         seen = np.zeros(nr, dtype=bool)
@@ -119,9 +120,9 @@ def test_constrained_permutation_matches_oracle(shape, p, problem, kind):
             for m in range(nl):
                 v = int(posb[c0 + s * nl + m])
                 if fixed[cd[e][m]]:
-                    assert v == acc_stride
+                    assert v & 0x3FFF == acc_stride and bool(v & 0x4000) == mapped
                     continue
-                k = inv[v & 0x7FFF]
+                k = inv[v & 0x3FFF]
                 assert lab[cd[e][m]] == col[rp[r] + k]
                 assert bool(v >> 15) == (not seen[k])
                 seen[k] = True
