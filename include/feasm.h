@@ -149,25 +149,6 @@ int fe_space_csr_pattern(const fe_space* s, int64_t* row_ptr, int32_t* col_idx, 
 int fe_space_permutation_host(const fe_space* s, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
                               int64_t* slot_ptr, int32_t* slots);
 
-/* Accumulator layout of the slot-wise scatter (FP32 / BF16 forms; host-only
- * spaces; the paper has no counterpart: its assembly adds into the matrix in
- * place). A warp sums one row in shared memory, one 8-byte entry per nonzero:
- * the k-th nonzero of a row at entry k, or, on the rows whose positions carry
- * bit 14, at entry[k]: a Q1 elasticity map that puts the 16 lanes of each
- * half-warp of a cell's contributions in distinct shared-memory bank pairs
- * (entry mod 16) on interior rows.
- *   acc_stride  out: entries per row; entry acc_stride is the row's dummy,
- *               which the lanes of dropped columns and the lanes past a cell
- *               row add into.
- *   pos     [code_ptr[n_dofs]] or NULL: slot-major positions, in the blocks of
- *           fe_space_permutation_host: block row r, slot s, local column m
- *           holds the entry of the nonzero that (s, m) adds to (bits 0-13),
- *           bit 14 if the row uses the map, bit 15 on the first contribution
- *           of each nonzero in slot order.
- *   entry   [max row length] or NULL: the map (the identity for other
- *           elements). */
-int fe_space_slot_layout_host(const fe_space* s, int32_t* acc_stride, uint16_t* pos, uint16_t* entry);
-
 /* Integrates every cell and assembles the global matrix and right-hand side
  * (paper Eq. linear_system, Eq. assembly, Eq. fematrix, Eq. shape_grad; the
  * element loop of the Listing "element_matrix_entries_computation").
@@ -369,18 +350,12 @@ int fe_dirichlet_csr_pattern(const fe_dirichlet* d, int64_t* row_ptr, int32_t* c
  * pointers), in the layout of fe_space_permutation_host with rows = free DOFs:
  * cnt [nnz]; code_ptr [n_free+1]; codes (may be NULL) hold ncode[r] codes per
  * row, those of fixed columns left out; ncode [n_free] int32; pos (may be
- * NULL) [code_ptr[n_free]] the slot-major accumulator entries (as in
- * fe_space_slot_layout_host, through the entry map of
- * fe_dirichlet_slot_layout_host), where an entry (s, m) of a fixed column
- * holds the row's dummy entry, acc_stride;
- * slot_ptr [n_free+1]; slots. */
+ * NULL) [code_ptr[n_free]] the slot-major positions, where an entry (s, m) of
+ * a fixed column holds the index of the reading lane's private dummy
+ * accumulator, acc_stride + (m mod 32), acc_stride being the largest row
+ * length rounded up to a multiple of 4; slot_ptr [n_free+1]; slots. */
 int fe_dirichlet_permutation_host(const fe_dirichlet* d, uint8_t* cnt, int64_t* code_ptr, uint16_t* codes,
                                   int32_t* ncode, uint16_t* pos, int64_t* slot_ptr, int32_t* slots);
-
-/* Accumulator layout of the constrained pattern (host-only spaces):
- * acc_stride and entry [max row length] (may be NULL) as in
- * fe_space_slot_layout_host. */
-int fe_dirichlet_slot_layout_host(const fe_dirichlet* d, int32_t* acc_stride, uint16_t* entry);
 
 /* Lifting lists (host): n_cells cells carrying fixed and free DOFs, ascending
  * (cells [n_cells]); the fixed local columns of cells[i] are m[ptr[i] ..

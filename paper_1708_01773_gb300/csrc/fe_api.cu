@@ -253,17 +253,6 @@ int fe_space_permutation_host(const fe_space* s, uint8_t* cnt, int64_t* code_ptr
   return FE_OK;
 }
 
-int fe_space_slot_layout_host(const fe_space* s, int32_t* acc_stride, uint16_t* pos, uint16_t* entry) {
-  if (!s || !acc_stride) return fail(FE_ERR_INVALID_ARG, "NULL argument");
-  if (!s->host_only) return fail(FE_ERR_INVALID_ARG, "the slot layout is kept on the host only for host-only spaces");
-  const auto& hs = s->hs;
-  *acc_stride = hs.acc_stride;
-  if (pos) std::memcpy(pos, hs.pos.data(), hs.n_codes * sizeof(uint16_t));
-  if (entry)
-    for (int64_t k = 0; k < hs.max_row_nnz; ++k) entry[k] = uint16_t(feasm::slot_entry(s->nl == 24, int(k)));
-  return FE_OK;
-}
-
 int fe_space_csr_pattern(const fe_space* s, int64_t* row_ptr, int32_t* col_idx, void* stream) {
   if (!s || !row_ptr || (!col_idx && s->hs.nnz)) return fail(FE_ERR_INVALID_ARG, "NULL argument");
   if (s->host_only) return fail(FE_ERR_INVALID_ARG, "host-only space");

@@ -53,10 +53,9 @@ constexpr int kWarps = kThreads / 32;
 
 // One CSR row by one warp for FP32 cell matrices: the slot-wise double-float
 // accumulation of k_scatter_slots (slot batches of 4, 2 or 1, first
-// contributions stored, later ones added with TwoSum, the read-out through the
-// row's entry map); loads bypass L1 (the cell matrices were written
-// earlier in this launch by other blocks). The RHS entries are formed
-// separately (rhs_rows).
+// contributions stored, later ones added with TwoSum); loads bypass L1 (the
+// cell matrices were written earlier in this launch by other blocks). The
+// RHS entries are formed separately (rhs_rows).
 template <int NL>
 __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* acc) {
   using S = SlotScatter<NL, 1, true>;
@@ -68,7 +67,7 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
   const int my_slot = lane < ns ? p.slots[s0 + lane] : 0;
   const float* ke = reinterpret_cast<const float*>(p.ke) + lane;
   const int rs = p.acc_stride + 32;
-  const int dummy = p.acc_stride;
+  const int dummy = p.acc_stride + lane;
   int sb = 0;
   while (sb < ns) {
     const int left = ns - sb;
@@ -83,10 +82,9 @@ __device__ void row_slots(const ScatterParams& p, int64_t r, int lane, float2* a
       sb += 1;
     }
   }
-  const bool mapped = NL == 24 && (p.pos[p.code_ptr[r]] & kPosMapped) != 0;
   for (int kb = 0; kb < nnz; kb += 32) {
     const int k = kb + lane;
-    const float2 a = acc[k < nnz ? slot_entry(mapped, k) : dummy];
+    const float2 a = acc[k < nnz ? k : dummy];
     const double v = df_to_double(a.x, a.y);
     if (k < nnz) p.values[k0 + k] = v;
   }
@@ -251,7 +249,7 @@ namespace {
 
 int row_warp_bytes_for(const fe_space* s, fe_precision prec) {
   if (prec == FE_PREC_FP64) return 0;
-  return int(s->hs.acc_stride + 32) * 8;
+  return int(((s->hs.max_row_nnz + 3) & ~int64_t(3)) + 32) * 8;
 }
 
 template <int PREC>
@@ -475,7 +473,7 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
     q.slots = s->d_slots;
     q.ke = s->d_ke;
     q.fe = s->d_fe;
-    q.acc_stride = s->hs.acc_stride;
+    q.acc_stride = int((s->hs.max_row_nnz + 3) & ~int64_t(3));
   }
   e = cudaMalloc(&b->d_spaces, std::max(1, n) * sizeof(Space));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * (n + 1));

@@ -899,13 +899,10 @@ __device__ __forceinline__ T ld_ro(const T* p) {
 
 // One batch of the slot-wise double-float scatter of k_scatter_slots (see
 // there): B slots from s_begin, R rows per item (R = 3: the rows of one node,
-// local rows i * NL / R + a of each cell), accumulator rows of stride rs; pos
-// holds accumulator entries (applied on the host, fe_slot_layout.h). Lanes past
-// the end of a cell row (m >= NL) add zero into the row's dummy entry `dummy`
-// (acc_stride: one address for all of them, in bank pair 0; its value is
-// never read). The
-// first contribution of a nonzero (flag bit 15 of pos; every entry of slot 0)
-// stores (v, 0); later ones add with TwoSum.
+// local rows i * NL / R + a of each cell), accumulator rows of stride rs with
+// a private dummy per lane at index `dummy`. The first contribution of a
+// nonzero (flag bit 15 of pos; every entry of slot 0) stores (v, 0); later
+// ones add with TwoSum.
 template <int NL, int R, bool CG = false>
 struct SlotScatter {
   static constexpr int CH = (NL + 31) / 32;
@@ -938,7 +935,7 @@ struct SlotScatter {
 #pragma unroll
       for (int c = 0; c < CH; ++c) {
         const int raw = kk[t][c];
-        const int k = raw & kPosEntry;
+        const int k = raw & 0x7fff;
 #pragma unroll
         for (int i = 0; i < R; ++i) {
           float2* ai = acc + i * rs;
@@ -946,7 +943,7 @@ struct SlotScatter {
           if (s_begin + t == 0) {
             ai[k] = make_float2(v, 0.f);
           } else {
-            const float2 a = (raw & kPosFirst) ? make_float2(0.f, 0.f) : ai[k];
+            const float2 a = (raw & 0x8000) ? make_float2(0.f, 0.f) : ai[k];
             const float sum = a.x + v;
             const float bp = sum - a.x;
             const float err = (a.x - (sum - bp)) + (v - bp);

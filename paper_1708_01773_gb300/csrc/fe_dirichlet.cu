@@ -125,7 +125,6 @@ feasm::ScatterPattern pattern_of(const fe_dirichlet* d) {
   pt.n_rows = d->hs.n_dofs;
   pt.nnz = d->hs.nnz;
   pt.max_row_nnz = d->hs.max_row_nnz;
-  pt.acc_stride = d->hs.acc_stride;
   pt.max_slots = d->hs.max_slots;
   pt.node_rows = d->hs.node_rows;
   pt.pos_ok = d->hs.pos_ok;
@@ -309,17 +308,6 @@ int fe_dirichlet_permutation_host(const fe_dirichlet* d, uint8_t* cnt, int64_t* 
   if (pos) std::memcpy(pos, hs.pos.data(), hs.n_codes * sizeof(uint16_t));
   std::memcpy(slot_ptr, hs.slot_ptr.data(), hs.slot_ptr.size() * sizeof(int64_t));
   std::memcpy(slots, hs.slots.data(), hs.slots.size() * sizeof(int32_t));
-  return FE_OK;
-}
-
-int fe_dirichlet_slot_layout_host(const fe_dirichlet* d, int32_t* acc_stride, uint16_t* entry) {
-  if (!d || !acc_stride) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
-  if (!d->s->host_only)
-    return feasm::set_error(FE_ERR_INVALID_ARG, "the slot layout is kept on the host only for host-only spaces");
-  const auto& hs = d->hs;
-  *acc_stride = hs.acc_stride;
-  if (entry)
-    for (int64_t k = 0; k < hs.max_row_nnz; ++k) entry[k] = uint16_t(feasm::slot_entry(d->s->nl == 24, int(k)));
   return FE_OK;
 }
 

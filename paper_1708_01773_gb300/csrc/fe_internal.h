@@ -43,10 +43,6 @@ struct HostSetup {
   std::vector<int32_t> slots;       // [n_cells*nl] e*nl + local row, cells ascending
   std::vector<int32_t> ncode;       // [n_dofs] codes of each row (constrained patterns only; empty: ns * nl)
   bool pos_ok = true;               // the positions of dropped columns fit the 15-bit dummy index
-  // accumulator layout of the slot-wise scatter: pos holds accumulator entries
-  // (nonzero k of a row at entry slot_entry(nl, k); dropped columns at the
-  // dummy entry acc_stride)
-  int acc_stride = 0;               // accumulator entries per row before the dummy
 };
 
 void build_ref_tables(int p, int nq1d, RefTables* t);

@@ -234,28 +234,21 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 // lie in the same cells at local rows i * nb + a and share their column
 // pattern (R = 3). For each cell around the DOF in ascending order ("slot"),
 // the lanes read that cell's matrix row(s) (coalesced) and the slot-major
-// positions pos[s][m]: the accumulator entry of the nonzero that entry (s, m)
-// contributes to (one position block serves all R rows); on the Q1 elasticity
-// rows marked by bit 14 the entries follow the bank-pair map of
-// fe_slot_layout.h, so that the 16 lanes of each half-warp of a slot touch
-// distinct shared-memory bank pairs, and the read-out takes nonzero k from
-// entry slot_entry(mapped, k). The first contribution of each nonzero (flag bit
+// positions pos[s][m] of the entries among the row's nonzeros (one position
+// block serves all R rows). The first contribution of each nonzero (flag bit
 // 15 of pos; every entry of slot 0) stores (v, 0) into the row's double-float
 // accumulator in shared memory; later ones add with Knuth's TwoSum, whose
 // rounding error is kept exactly in the low part. The entries of one cell row
 // go to distinct nonzeros, so the lanes never collide; a __syncwarp between
 // slots orders the additions, so every nonzero sums its terms in ascending cell
 // order. Each accumulator is rounded once to FP64 (df_to_double) and stored
-// coalesced. Lanes past the end of a cell row (m >= NL) read padding and add
-// into the row's dummy entry (acc_stride, the same address for all of them),
-// so the inner loop has no divergent branches (the position array and the
-// cell-matrix scratch are allocated with padding for those reads); the maps
-// keep the dummy's bank pair free in their half-warps. The lanes of dropped
-// (fixed) columns also add into the dummy entry. Slots are processed
-// in batches of 8, 4, 2 or 1 (the largest that fits the slots left and the
-// register budget), all loads of a batch issued before its additions; the item
-// descriptors (pointers, slot ids) of the warp's next item are fetched
-// while the current one is reduced. Items
+// coalesced. Lanes past the end of a cell row (m >= NL) read padding and touch
+// a private dummy accumulator, so the inner loop has no divergent branches
+// (the position array and the cell-matrix scratch are allocated with padding
+// for those reads). Slots are processed in batches of 8, 4, 2 or 1 (the
+// largest that fits the slots left and the register budget), all loads of a
+// batch issued before its additions; the item descriptors (pointers, slot ids)
+// of the warp's next item are fetched while the current one is reduced. Items
 // go to warps on demand, kSlotGrab at a time (ItemStream). The RHS entries are
 // formed first, in a static pass of 32 consecutive items per warp, one item per
 // lane (exact fixed-point sum of its cells' FP64 cell-vector entries).
@@ -267,8 +260,8 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
   extern __shared__ __align__(16) unsigned char sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* acc = reinterpret_cast<float2*>(sm + size_t(warp) * p.warp_bytes);
-  const int rs = p.acc_stride + 32;  // accumulator row: acc_stride entries, then the dummy entries
-  const int dummy = p.acc_stride;     // within each accumulator row
+  const int rs = p.acc_stride + 32;       // accumulator row: acc_stride nonzeros, then one dummy per lane
+  const int dummy = p.acc_stride + lane;  // within each accumulator row
   const float* ke = reinterpret_cast<const float*>(p.ke) + lane;
   const bool want_rhs = p.rhs != nullptr;
   const int64_t n_items = p.n_rows / R;
@@ -343,18 +336,16 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
         sb += 1;
       }
     }
-    // second-level descriptors of the next item (its slot ids); the current
-    // item's entry map (bit 14 of its positions, read while they are in L1)
+    // second-level descriptors of the next item (its slot ids)
     const int nsn = int(s1n - s0n);
     const int my_slot_n = (un < n_items && lane < nsn) ? p.slots[s0n + lane] : 0;
-    const bool mapped = NL == 24 && (__ldg(p.pos + c0) & kPosMapped) != 0;
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int64_t ki = k0 + int64_t(i) * nnz;  // the rows of one node are consecutive and equally long
       const float2* ai = acc + i * rs;
       for (int kb = 0; kb < nnz; kb += 32) {
         const int k = kb + lane;
-        const float2 a = ai[k < nnz ? slot_entry(mapped, k) : dummy];
+        const float2 a = ai[k < nnz ? k : dummy];
         const double v = df_to_double(a.x, a.y);
         if (k < nnz) p.values[ki + k] = v;
       }
@@ -378,7 +369,6 @@ ScatterPattern space_pattern(const fe_space* s) {
   pt.n_rows = s->hs.n_dofs;
   pt.nnz = s->hs.nnz;
   pt.max_row_nnz = s->hs.max_row_nnz;
-  pt.acc_stride = s->hs.acc_stride;
   pt.max_slots = s->hs.max_slots;
   pt.node_rows = s->hs.node_rows;
   pt.pos_ok = s->hs.pos_ok;
@@ -451,11 +441,11 @@ cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, 
   };
   if (prec != FE_PREC_FP64 && pt.max_slots <= 32 && pt.pos_ok) {
     const bool idx32 = int64_t(s->n_cells) * s->nl * s->nlp < (int64_t(1) << 32);
-    p.acc_stride = pt.acc_stride;
+    p.acc_stride = int((pt.max_row_nnz + 3) & ~int64_t(3));
     // rows of one node together (3-component problems), else one row per warp
     // (measured: pays for Q1, 24-entry cell rows; for wider rows one row per warp is faster)
-    const int R = (pt.node_rows && s->ncomp == 3 && s->nl <= 32) ? 3 : 1;  // 3: nl = 24 only
-    p.warp_bytes = R * (p.acc_stride + 32) * 8;  // R accumulator rows (entries, dummy, padding)
+    const int R = (pt.node_rows && s->ncomp == 3 && s->nl <= 32) ? 3 : 1;
+    p.warp_bytes = R * (p.acc_stride + 32) * 8;  // R accumulator rows, each with one dummy per lane
     const long bytes = long(p.warp_bytes) * kScatterWarps;
     if (bytes <= 200 * 1024) {
       switch (s->nl * 4 + (R == 3 ? 2 : 0) + (idx32 ? 1 : 0)) {
@@ -471,10 +461,14 @@ cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, 
         case 257: return launch(k_scatter_slots<64, 1, true>, bytes);
         case 324: return launch(k_scatter_slots<81, 1, false>, bytes);
         case 325: return launch(k_scatter_slots<81, 1, true>, bytes);
+        case 326: return launch(k_scatter_slots<81, 3, false>, bytes);
+        case 327: return launch(k_scatter_slots<81, 3, true>, bytes);
         case 356: return launch(k_scatter_slots<89, 1, false>, bytes);   // Stokes Q2/Q1
         case 357: return launch(k_scatter_slots<89, 1, true>, bytes);
         case 768: return launch(k_scatter_slots<192, 1, false>, bytes);
         case 769: return launch(k_scatter_slots<192, 1, true>, bytes);
+        case 770: return launch(k_scatter_slots<192, 3, false>, bytes);
+        case 771: return launch(k_scatter_slots<192, 3, true>, bytes);
         default: break;
       }
     }

@@ -4,7 +4,6 @@
 #include <cuda_runtime.h>
 
 #include "fe_internal.h"
-#include "fe_slot_layout.h"
 
 namespace feasm {
 
@@ -43,7 +42,6 @@ cudaError_t launch_cell_q1e(const fe_space* s, const double* coef, const double 
 struct ScatterPattern {
   int64_t n_rows = 0, nnz = 0, max_row_nnz = 0;
   int max_slots = 0;
-  int acc_stride = 0;                    // accumulator entries per row of the slot-wise scatter
   bool node_rows = false, pos_ok = true;
   const int64_t* row_ptr = nullptr;
   const uint8_t* cnt = nullptr;

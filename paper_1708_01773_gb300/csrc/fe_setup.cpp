@@ -9,7 +9,6 @@
 #include <unordered_map>
 
 #include "fe_internal.h"
-#include "fe_slot_layout.h"
 
 namespace feasm {
 
@@ -245,7 +244,6 @@ static int number_dofs(int p, int ncomp, int64_t n_cells, const int32_t* cv, std
 // each (slot, local column) contributes to ("pos", bit 15 set on the first
 // contribution of each nonzero in slot order), for the slot-wise scatter.
 static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body);
-void build_slot_layout(int nl, HostSetup* hs);
 
 int build_host_setup(int p, int problem, int64_t n_cells, int64_t n_vertices, const int32_t* cell_vertices,
                      HostSetup* hs, std::string* err) {
@@ -356,9 +354,8 @@ int build_pattern(int nl, int nb, int ncomp, int64_t n_cells, const int32_t* cel
     return FE_ERR_UNSUPPORTED;
   }
   // Contributions of fixed columns (label only) are left out of the codes and
-  // sent, in the slot-major positions, to a dummy accumulator entry of the
-  // slot-wise scatter: entry acc_stride + (m mod 32) of the row here, the
-  // row's single dummy entry once build_slot_layout has run.
+  // sent, in the slot-major positions, to the lane's private dummy accumulator
+  // of the slot-wise scatter: entry acc_stride + (m mod 32) of the row.
   const int64_t acc_stride = (hs->max_row_nnz + 3) & ~int64_t(3);
   hs->pos_ok = acc_stride + 32 <= 0x7fff;
   hs->col.assign(hs->nnz, 0);
@@ -425,68 +422,7 @@ int build_pattern(int nl, int nb, int ncomp, int64_t n_cells, const int32_t* cel
     }
     hs->node_rows = ok;
   }
-  build_slot_layout(nl, hs);
   return FE_OK;
-}
-
-// ---------------------------------------------------------------------------
-// Accumulator entries of the slot-wise scatter (fe_slot_layout.h). The
-// slot-major positions hold nonzero indices k after pass 2; here each becomes
-// its accumulator entry: q1e_entry(k), with bit 14 set, on the Q1 elasticity
-// rows whose slots that map serves in fewer shared-memory wavefronts than
-// nonzero order (a model: per slot and 16-lane half-warp, the largest number
-// of distinct entries in one bank pair, entry mod 16, the lanes past the cell
-// row on the dummy entry), else k. Dropped columns of constrained patterns go
-// to the row's dummy entry acc_stride. Summation orders are unchanged.
-static int slot_wavefronts(const uint16_t* b, int ns, int nl, int nnz, bool mapped, int stride) {
-  int total = 0;
-  const int lanes = (nl + 31) & ~31;
-  for (int s = 0; s < ns; ++s)
-    for (int g0 = 0; g0 < lanes; g0 += 16) {
-      int e[16], n = 0, worst = 0;
-      for (int m = g0; m < g0 + 16; ++m) {
-        const int k = m < nl ? b[s * nl + m] & 0x7fff : nnz;
-        const int x = k < nnz ? slot_entry(mapped, k) : stride;
-        bool dup = false;
-        for (int j = 0; j < n; ++j) dup |= e[j] == x;
-        if (!dup) e[n++] = x;
-      }
-      for (int j = 0; j < n; ++j) {
-        int c = 0;
-        for (int i = 0; i < n; ++i) c += (e[i] - e[j]) % 16 == 0;
-        worst = std::max(worst, c);
-      }
-      total += worst;
-    }
-  return total;
-}
-
-void build_slot_layout(int nl, HostSetup* hs) {
-  const int64_t nd = hs->n_dofs;
-  const int64_t old_stride = (hs->max_row_nnz + 3) & ~int64_t(3);
-  const int stride = slot_acc_stride(nl, hs->max_row_nnz);
-  hs->acc_stride = int(old_stride);
-  if (!hs->pos_ok) return;
-  if (stride + 32 > kPosEntry) {
-    hs->pos_ok = false;  // no slot-wise scatter for this pattern
-    return;
-  }
-  hs->acc_stride = stride;
-  const int nthreads = std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
-  parallel_for(nd, nthreads, [&](int, int64_t r0, int64_t r1) {
-    for (int64_t r = r0; r < r1; ++r) {
-      uint16_t* b = hs->pos.data() + hs->code_ptr[r];
-      const int nnz = int(hs->row_ptr[r + 1] - hs->row_ptr[r]);
-      const int ns = int(hs->slot_ptr[r + 1] - hs->slot_ptr[r]);
-      const bool mapped = nl == 24 && slot_wavefronts(b, ns, nl, nnz, true, stride) <
-                                          slot_wavefronts(b, ns, nl, nnz, false, stride);
-      for (int64_t i = 0; i < int64_t(ns) * nl; ++i) {
-        const int k = b[i] & 0x7fff;
-        const int flag = mapped ? kPosMapped : 0;
-        b[i] = k < nnz ? uint16_t((b[i] & kPosFirst) | flag | slot_entry(mapped, k)) : uint16_t(flag | stride);
-      }
-    }
-  });
 }
 
 static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body) {

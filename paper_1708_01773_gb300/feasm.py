@@ -27,11 +27,11 @@ ERRORS = {
 # every entry point declared in include/feasm.h
 EXPORTS = [
     "fe_space_create", "fe_space_create_host", "fe_space_sizes", "fe_space_cell_dofs_host",
-    "fe_space_csr_pattern_host", "fe_space_permutation_host", "fe_space_slot_layout_host", "fe_space_csr_pattern", "fe_assemble", "fe_assemble_ex", "fe_assemble_host",
+    "fe_space_csr_pattern_host", "fe_space_permutation_host", "fe_space_csr_pattern", "fe_assemble", "fe_assemble_ex", "fe_assemble_host",
     "fe_assemble_adjoint", "fe_assemble_adjoint_noalloc", "fe_space_set_kernel", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
     "fe_batch_assemble", "fe_batch_set_wait", "fe_batch_destroy", "fe_selftest_conversions", "fe_space_dof_points_host", "fe_dirichlet_create", "fe_dirichlet_sizes",
     "fe_dirichlet_labels_host", "fe_dirichlet_csr_pattern_host", "fe_dirichlet_csr_pattern",
-    "fe_dirichlet_permutation_host", "fe_dirichlet_slot_layout_host", "fe_dirichlet_lift_host", "fe_assemble_dirichlet", "fe_dirichlet_destroy",
+    "fe_dirichlet_permutation_host", "fe_dirichlet_lift_host", "fe_assemble_dirichlet", "fe_dirichlet_destroy",
     "fe_compliance_work_size", "fe_compliance", "fe_space_block_offset", "fe_dg_create", "fe_dg_create_host",
     "fe_dg_sizes", "fe_dg_csr_pattern_host", "fe_dg_csr_pattern", "fe_dg_facets_host", "fe_dg_assemble",
     "fe_dg_destroy",
@@ -68,7 +68,6 @@ def lib() -> ctypes.CDLL:
         L.fe_space_csr_pattern_host.argtypes = [V, V, V]
         L.fe_space_csr_pattern.argtypes = [V, V, V, V]
         L.fe_space_permutation_host.argtypes = [V, V, V, V, V, V]
-        L.fe_space_slot_layout_host.argtypes = [V, V, V, V]
         L.fe_assemble.argtypes = [V, V, V, V, V, I, V]
         L.fe_assemble_host.argtypes = [V, V, V, V, V, I, V]
         L.fe_assemble_ex.argtypes = [V, V, V, V, V, I, V, V]
@@ -93,7 +92,6 @@ def lib() -> ctypes.CDLL:
         L.fe_dirichlet_csr_pattern_host.argtypes = [V, V, V]
         L.fe_dirichlet_csr_pattern.argtypes = [V, V, V, V]
         L.fe_dirichlet_permutation_host.argtypes = [V, V, V, V, V, V, V, V]
-        L.fe_dirichlet_slot_layout_host.argtypes = [V, V, V]
         L.fe_dirichlet_lift_host.argtypes = [V, P(I64), P(I64), V, V, V, V]
         L.fe_assemble_dirichlet.argtypes = [V, V, V, V, V, V, I, V]
         L.fe_compliance_work_size.argtypes = [V, P(I64)]
@@ -189,27 +187,6 @@ def fe_space_permutation_host(space: int):
     _check(lib().fe_space_permutation_host(space, cnt.ctypes.data, code_ptr.ctypes.data, codes.ctypes.data,
                                            slot_ptr.ctypes.data, slots.ctypes.data), "fe_space_permutation_host")
     return cnt, code_ptr, codes, slot_ptr, slots
-
-
-def fe_space_slot_layout_host(space: int):
-    """(acc_stride, pos, entry) of a host-only space: the slot-major accumulator
-    entries of the slot-wise scatter and the entry of each nonzero index k."""
-    rp, _ = fe_space_csr_pattern_host(space)
-    code_ptr = fe_space_permutation_host(space)[1]
-    acc = np.zeros(1, dtype=np.int32)
-    pos = np.zeros(int(code_ptr[-1]), dtype=np.uint16)
-    entry = np.zeros(max(1, int(np.diff(rp).max(initial=0))), dtype=np.uint16)
-    _check(lib().fe_space_slot_layout_host(space, acc.ctypes.data, pos.ctypes.data, entry.ctypes.data),
-           "fe_space_slot_layout_host")
-    return int(acc[0]), pos, entry
-
-
-def fe_dirichlet_slot_layout_host(d: int, max_row_nnz: int):
-    """(acc_stride, entry) of a host-only space's constrained system."""
-    acc = np.zeros(1, dtype=np.int32)
-    entry = np.zeros(max(1, max_row_nnz), dtype=np.uint16)
-    _check(lib().fe_dirichlet_slot_layout_host(d, acc.ctypes.data, entry.ctypes.data), "fe_dirichlet_slot_layout_host")
-    return int(acc[0]), entry
 
 
 def slot_count(space: int) -> int:

@@ -83,8 +83,7 @@ def test_constrained_permutation_matches_oracle(shape, p, problem, kind):
         fe_l[e] -= Ke[e][:, m] @ uD[lfix[lptr[i]:lptr[i + 1]]]
     cnt, code_ptr, codes, ncode, posb, slot_ptr, slots = feasm.fe_dirichlet_permutation_host(
         dsys.handle, prob.mesh.n_cells * nl)
-    acc_stride, entry = feasm.fe_dirichlet_slot_layout_host(dsys.handle, int(np.diff(rp).max()))
-    assert acc_stride >= int(np.diff(rp).max())
+    acc_stride = (int(np.diff(rp).max()) + 3) & ~3
     vals_codes = np.zeros(dsys.nnz)
     vals_pos = np.zeros(dsys.nnz)
     rhs = np.zeros(dsys.n_free)
@@ -107,22 +106,16 @@ def test_constrained_permutation_matches_oracle(shape, p, problem, kind):
             assert np.all(lab[flat_cd[(sl[s] // nl) * nl + m]] == col[k])
             vals_codes[k] = Kf[sl[s] * nl + m].sum()
         assert c == c0 + ncode[r]
-        # slot-major positions: the accumulator entry of the nonzero (head bit on its
-        # first contribution), decoded through the entry map, or the row's dummy
-        nr = rp[r + 1] - rp[r]
-        mapped = bool(posb[c0] & 0x4000)
-        amap = entry[:nr].astype(np.int64) if mapped else np.arange(nr)
-        assert len(set(amap.tolist())) == nr and amap.max(initial=0) < acc_stride
-        inv = {int(a): k for k, a in enumerate(amap)}
-        seen = np.zeros(nr, dtype=bool)
+        # slot-major positions: nonzero index (head bit on its first contribution) or the lane's dummy
+        seen = np.zeros(rp[r + 1] - rp[r], dtype=bool)
         for s in range(len(sl)):
             e = sl[s] // nl
             for m in range(nl):
                 v = int(posb[c0 + s * nl + m])
                 if fixed[cd[e][m]]:
-                    assert v & 0x3FFF == acc_stride and bool(v & 0x4000) == mapped
+                    assert v == acc_stride + (m & 31)
                     continue
-                k = inv[v & 0x3FFF]
+                k = v & 0x7FFF
                 assert lab[cd[e][m]] == col[rp[r] + k]
                 assert bool(v >> 15) == (not seen[k])
                 seen[k] = True

@@ -150,88 +150,3 @@ def test_empty_mesh_host_setup():
     h = feasm.fe_space_create(mesh.coords, mesh.cell_vertices, 2, 0, 1, 0.3, host_only=True)
     assert feasm.fe_space_sizes(h) == (0, 0, 0, 0)
     feasm.fe_space_destroy(h)
-
-
-def _wavefronts(P, nl, entry, acc_stride):
-    """Shared-memory wavefronts of one slot-wise scatter access pattern: for each
-    slot (row of P) and each 16-lane half-warp of its lanes (local column m on
-    lane m mod 32; lanes past the cell row touch the row's dummy entry
-    acc_stride), the largest number of distinct 8-byte entries that share a
-    bank pair (entry mod 16)."""
-    total = 0
-    lanes = (nl + 31) // 32 * 32
-    for row in P:
-        e = [int(entry[k]) for k in row] + [acc_stride] * (lanes - nl)
-        for g0 in range(0, lanes, 16):
-            g = np.unique(np.asarray(e[g0:g0 + 16]))  # one address: one access
-            total += max(np.bincount(g % 16, minlength=16))
-    return total
-
-
-LAYOUT_CASES = [((6, 6, 6), 1, 1), ((6, 5, 4), 1, 0), ((4, 4, 3), 2, 0), ((3, 3, 3), 2, 1), ((3, 2, 3), 3, 0),
-                ((2, 2, 2), 2, 2)]
-
-
-@pytest.mark.parametrize("shape,p,problem", LAYOUT_CASES)
-def test_slot_layout_entries_and_bank_pairs(shape, p, problem):
-    """The accumulator entries of the slot-wise scatter: the entry map is one to
-    one into [0, acc_stride) (the identity except for Q1 elasticity), every
-    slot-major entry decodes to the nonzero whose column is the cell's DOF, with
-    the first-contribution flag on the first slot that reaches it; and for Q1
-    elasticity the map puts every half-warp of an interior node row with the 27
-    neighbours in lexicographic order in one wavefront (the model: the largest
-    number of distinct 8-byte entries sharing a bank pair, entry mod 16)."""
-    prob = inputs.small_problem(shape, p, problem, seed=70 + 3 * p + problem)
-    sp = feasm.FESpace(prob, host_only=True)
-    nl = prob.n_local
-    cd = sp.cell_dofs().reshape(-1)
-    rp, col = sp.pattern_host()
-    cnt, code_ptr, codes, slot_ptr, slots = feasm.fe_space_permutation_host(sp.handle)
-    acc_stride, pos, entry = feasm.fe_space_slot_layout_host(sp.handle)
-    max_nnz = int(np.diff(rp).max())
-    amap = entry[:max_nnz].astype(np.int64)
-    assert len(set(amap.tolist())) == max_nnz and amap.max() < acc_stride and acc_stride % 16 == 0
-    if nl != 24:
-        np.testing.assert_array_equal(amap, np.arange(max_nnz))
-    inv_map = {int(a): k for k, a in enumerate(amap)}
-    inv_id = {k: k for k in range(max_nnz)}
-    # Q1 elasticity local column m = 8 c + a, node a = x + 2y + 4z of the cell
-    lex = np.array([3 * ((a & 1) + 3 * ((a >> 1) & 1) + 9 * (a >> 2)) + c for c in range(3) for a in range(8)])
-    colored = identity = groups = 0
-    lex_rows = 0
-    for r in range(sp.n_dofs):
-        nr = int(rp[r + 1] - rp[r])
-        sl = slots[slot_ptr[r]:slot_ptr[r + 1]].astype(np.int64)
-        blk = pos[code_ptr[r]:code_ptr[r] + len(sl) * nl].astype(np.int64).reshape(len(sl), nl)
-        mapped = bool(blk[0, 0] & 0x4000)
-        assert np.all((blk & 0x4000 != 0) == mapped) and (nl == 24 or not mapped)
-        inv = inv_map if mapped else inv_id
-        K = np.vectorize(lambda v: inv[v & 0x3FFF])(blk)
-        assert K.max() < nr
-        seen = np.zeros(nr, dtype=bool)
-        for s in range(len(sl)):
-            e = sl[s] // nl
-            np.testing.assert_array_equal(col[rp[r] + K[s]], cd[e * nl:(e + 1) * nl])
-            for m in range(nl):
-                assert bool(blk[s, m] >> 15) == (not seen[K[s, m]])
-                seen[K[s, m]] = True
-        assert seen.all()
-        w = _wavefronts(K, nl, amap if mapped else np.arange(nr), acc_stride)
-        colored += w
-        identity += _wavefronts(K, nl, np.arange(nr), acc_stride)
-        groups += len(sl) * ((nl + 31) // 32 * 2)
-        if nl == 24 and nr == 81 and len(sl) == 8:
-            # interior node whose columns are the 27 neighbours in lexicographic
-            # order: local column c * 8 + a of each cell at 3 (r0 + x + 3y + 9z) + c
-            r0 = K[:, :1] // 3
-            if np.array_equal(K, 3 * r0 + lex[None, :]):
-                lex_rows += 1
-                assert mapped and w == 2 * len(sl), r  # every half-warp in one wavefront
-    assert colored <= identity
-    if nl == 24:
-        assert lex_rows > 0 and colored < identity
-        print(f"Q1 elasticity: {colored / groups:.3f} wavefronts per half-warp (nonzero order "
-              f"{identity / groups:.3f}); {lex_rows} conflict-free interior rows")
-    else:
-        assert colored == identity
-    sp.close()
