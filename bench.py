@@ -192,7 +192,9 @@ def on_tensor_cores(prob, prec: str, kernel: str) -> bool:
         return False
     if prob.problem == inputs.ELASTICITY and prob.order == 2:
         return True
-    return kernel == "tensor_core" and prob.problem == inputs.POISSON and prob.order in (2, 3)
+    if prob.problem != inputs.POISSON or prob.order not in (2, 3):
+        return False
+    return kernel == "tensor_core" or (kernel == "auto" and prob.order == 3 and prec == "bf16")
 
 
 def kernel_names(prob, prec: str, kernel: str = "auto"):

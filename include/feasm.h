@@ -201,15 +201,15 @@ int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients
                         double* dc_dcoef, double* compliance, fe_precision prec, void* stream);
 
 /* Selects the cell-integration kernel of later fe_assemble calls:
- * FE_KERNEL_AUTO (default: the tensor-core kernel for Q2 elasticity, the
- * warp-role CUDA-core kernel for Q1 elasticity, else the general CUDA-core
- * kernel), FE_KERNEL_CUDA_CORE, or FE_KERNEL_TENSOR_CORE (fe_assemble then
+ * FE_KERNEL_AUTO (default: the tensor-core kernel for Q2 elasticity and for
+ * the BF16 form of Q3 Poisson, the warp-role CUDA-core kernel for Q1
+ * elasticity, else the general CUDA-core kernel), FE_KERNEL_CUDA_CORE, or FE_KERNEL_TENSOR_CORE (fe_assemble then
  * fails with FE_ERR_UNSUPPORTED where none exists; tensor-core kernels exist
  * for Q2 elasticity and Q2 / Q3 Poisson with the (p+1)^3 rule, FP32 or BF16).
  * The kernels of FE_KERNEL_AUTO keep the FP32 form within 1e-6 (row-scaled
  * entry error against FP64) on every mesh tested, single cells included. The
- * Poisson tensor-core kernel, chosen only on request, is faster for Q3 and
- * within 1e-6 on multi-cell meshes, but its FP32 form reached 1.2e-6 on one
+ * Poisson tensor-core kernel's FP32 form, chosen only on request, is faster
+ * for Q3 and within 1e-6 on multi-cell meshes, but reached 1.2e-6 on one
  * distorted Q3 cell: the tensor cores' FP32 accumulation truncates. */
 enum { FE_KERNEL_AUTO = 0, FE_KERNEL_CUDA_CORE = 1, FE_KERNEL_TENSOR_CORE = 2 };
 int fe_space_set_kernel(fe_space* s, int cell_kernel);
