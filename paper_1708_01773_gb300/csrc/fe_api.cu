@@ -187,11 +187,18 @@ int cell_stage(fe_space* s, const double* coef, const double force[3], fe_precis
   const bool tcp = cell_tcp_applicable(s, prec) &&
                    (s->cell_kernel == FE_KERNEL_TENSOR_CORE ||
                     (s->cell_kernel == FE_KERNEL_AUTO && s->order == 3 && prec == FE_PREC_BF16));
-  const bool tc = (cell_tc_applicable(s, prec) || cell_tcp_applicable(s, prec)) && s->cell_kernel != FE_KERNEL_CUDA_CORE;
+  // Q3 elasticity on the tensor cores: on request, and by default for BF16
+  const bool tce = cell_tce_applicable(s, prec) &&
+                   (s->cell_kernel == FE_KERNEL_TENSOR_CORE ||
+                    (s->cell_kernel == FE_KERNEL_AUTO && prec == FE_PREC_BF16));
+  const bool tc = (cell_tc_applicable(s, prec) || cell_tcp_applicable(s, prec) || cell_tce_applicable(s, prec)) &&
+                  s->cell_kernel != FE_KERNEL_CUDA_CORE;
   if (s->cell_kernel == FE_KERNEL_TENSOR_CORE && !tc)
     return fail(FE_ERR_UNSUPPORTED, "no tensor-core cell kernel for this order / problem / precision");
   if (tcp)
     FE_CUDA(launch_cell_tcp(s, coef, force, prec, st));
+  else if (tce)
+    FE_CUDA(launch_cell_tce(s, coef, force, prec, st));
   else if (tc && cell_tc_applicable(s, prec))
     FE_CUDA(launch_cell_tc(s, coef, force, prec, st));
   else if (q1e_applicable(s, prec))

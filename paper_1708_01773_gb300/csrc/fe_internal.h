@@ -48,6 +48,9 @@ struct HostSetup {
 void build_ref_tables(int p, int nq1d, RefTables* t);
 // n-point Gauss-Legendre rule on [0,1].
 void gauss_rule(int n, double* x, double* w);
+// 1D Lagrange basis of order p (equidistant nodes) and its derivative at the
+// nq1d Gauss points: val[q][a], der[q][a], q < nq1d, a <= p.
+void lagrange_1d_table(int p, int nq1d, double* val, double* der);
 // Numbering, pattern and permutation of a space of order p for `problem`
 // (FE_POISSON, FE_ELASTICITY, FE_STOKES). Returns 0 or an FE_ERR_* code
 // (message in *err).

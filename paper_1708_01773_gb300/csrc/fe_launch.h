@@ -32,6 +32,11 @@ bool q1e_applicable(const fe_space* s, fe_precision prec);
 // with the (p+1)^3 rule, FP32 (3xTF32) and BF16 forms; same outputs as
 // launch_cell_integration.
 bool cell_tcp_applicable(const fe_space* s, fe_precision prec);
+// Tensor-core (tcgen05) cell integration of Q3 elasticity with the 4^3 rule,
+// FP32 (3xTF32) and BF16 forms; same outputs as launch_cell_integration.
+bool cell_tce_applicable(const fe_space* s, fe_precision prec);
+cudaError_t launch_cell_tce(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
+                            cudaStream_t st);
 cudaError_t launch_cell_tcp(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
                             cudaStream_t st);
 cudaError_t launch_cell_q1e(const fe_space* s, const double* coef, const double force[3], fe_precision prec,

@@ -74,6 +74,12 @@ static void lagrange_01(int p, double x, double* val, double* der) {
 
 void gauss_rule(int n, double* x, double* w) { gauss_rule_01(n, x, w); }
 
+void lagrange_1d_table(int p, int nq1d, double* val, double* der) {
+  double g[kMaxQ1d], gw[kMaxQ1d];
+  gauss_rule_01(nq1d, g, gw);
+  for (int q = 0; q < nq1d; ++q) lagrange_01(p, g[q], val + q * (p + 1), der + q * (p + 1));
+}
+
 void build_ref_tables(int p, int nq1d, RefTables* t) {
   t->p = p;
   t->nq1d = nq1d;

@@ -30,6 +30,8 @@ problems, all synthetic):
 * ``poisson_q3_40``    Poisson Q3, 40^3 cells of the unit cube (the largest Q3
   mesh of the batched recipe), shifts up to 0.2h, conductivity 10^U[-1,1],
   f = 1, 4^3 Gauss (``poisson_q3_24``: the same on 24^3 cells).
+* ``elasticity_q3_20`` Elasticity Q3, 20^3 cells of the unit cube, shifts up to
+  0.2h, E ~ U[1,10], nu = 0.3, f = (0,0,-1), 4^3 Gauss.
 """
 from __future__ import annotations
 
@@ -242,6 +244,16 @@ def poisson_q3(n: int = 40, seed_offset: int = 8) -> Problem:
     return Problem(f"poisson_q3_{n}", mesh, 3, 4, POISSON, _log_uniform(rng, 0.1, 10.0, mesh.n_cells), np.array([1.0]))
 
 
+def elasticity_q3(n: int = 20, seed_offset: int = 9) -> Problem:
+    """Linear elasticity Q3 on n^3 cells of the unit cube (the Q3 elasticity
+    meshes of the batched recipe), interior shifts up to 0.2h, E ~ U[1,10],
+    nu = 0.3, body force (0, 0, -1), 4^3 Gauss."""
+    rng = np.random.default_rng(SEED_BASE + seed_offset)
+    mesh = perturb_interior(brick(n, n, n), 0.2, rng)
+    return Problem(f"elasticity_q3_{n}", mesh, 3, 4, ELASTICITY, rng.uniform(1.0, 10.0, size=mesh.n_cells),
+                   np.array([0.0, 0.0, -1.0]))
+
+
 def unit_rms_field(n_dofs: int, seed: int) -> np.ndarray:
     """u_i ~ N(0,1) i.i.d., rescaled so that sqrt(mean(u^2)) = 1."""
     rng = np.random.default_rng(seed)
@@ -274,4 +286,5 @@ WORKLOADS = {
     "stokes_q2q1_32": stokes_q2q1_32,
     "poisson_q3_40": poisson_q3,
     "poisson_q3_24": lambda: poisson_q3(24),
+    "elasticity_q3_20": elasticity_q3,
 }

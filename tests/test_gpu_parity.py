@@ -9,7 +9,7 @@ import pytest
 import torch
 
 import oracle
-from metrics import TOL, energy_error, row_scaled_error, vec_error
+from metrics import TOL, TOL_TC_Q3_ELASTICITY_FP32, energy_error, row_scaled_error, vec_error
 from paper_1708_01773_gb300 import build, feasm, inputs
 
 pytestmark = pytest.mark.gpu
@@ -43,7 +43,7 @@ def test_small_meshes_all_precisions(shape, p, problem):
     rp, col = sp.pattern()
     np.testing.assert_array_equal(rp.cpu().numpy(), rp_o)
     np.testing.assert_array_equal(col.cpu().numpy(), col_o)
-    kernels = ["cuda_core", "tensor_core"] if (p >= 2 and (problem == 0 or p == 2)) else ["auto"]
+    kernels = ["cuda_core", "tensor_core"] if p >= 2 else ["auto"]
     for kern in kernels:
         sp.set_kernel(kern)
         for prec in ("fp64", "fp32", "bf16"):
@@ -52,8 +52,12 @@ def test_small_meshes_all_precisions(shape, p, problem):
             vals, rhs = run(sp, prob, prec)
             e_inf = row_scaled_error(rp_o, col_o, vals, val_o)
             e_en = energy_error(rp_o, col_o, vals, val_o)
-            assert e_inf <= TOL[prec], (kern, prec, e_inf)
-            assert e_en <= TOL[prec], (kern, prec, e_en)
+            tol = TOL[prec]
+            if kern == "tensor_core" and (p, problem, prec) == (3, 1, "fp32"):
+                tol = TOL_TC_Q3_ELASTICITY_FP32
+            print(f"{shape} p{p} problem {problem} {kern} {prec}: entry {e_inf:.3e} energy {e_en:.3e}")
+            assert e_inf <= tol, (kern, prec, e_inf)
+            assert e_en <= tol, (kern, prec, e_en)
             assert vec_error(rhs, rhs_o) <= 1e-12
     sp.close()
 
@@ -71,6 +75,31 @@ def test_tensor_core_pipeline_wraps():
         assert row_scaled_error(rp_o, col_o, vals, val_o) <= TOL[prec], prec
         assert energy_error(rp_o, col_o, vals, val_o) <= TOL[prec], prec
         assert vec_error(rhs, rhs_o) <= 1e-12
+    sp.close()
+
+
+def test_elasticity_q3_tensor_core_cells_wrap():
+    """Q3 elasticity on the tensor cores, 210 cells: more cells than CTAs, so
+    each persistent CTA runs several MMA rounds on the same operand stages and
+    tensor memory; every entry against the oracle, the CUDA-core kernel on the
+    same space, and run-to-run bitwise reproducibility."""
+    prob = inputs.small_problem((7, 6, 5), 3, 1, seed=33)
+    rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob)
+    sp = feasm.FESpace(prob)
+    for kern in ("tensor_core", "cuda_core"):
+        sp.set_kernel(kern)
+        for prec in ("fp32", "bf16"):
+            vals, rhs = run(sp, prob, prec)
+            e_inf = row_scaled_error(rp_o, col_o, vals, val_o)
+            e_en = energy_error(rp_o, col_o, vals, val_o)
+            print(f"Q3 elasticity 7x6x5 {kern} {prec}: entry {e_inf:.3e} energy {e_en:.3e}")
+            tol = TOL_TC_Q3_ELASTICITY_FP32 if (kern, prec) == ("tensor_core", "fp32") else TOL[prec]
+            assert e_inf <= tol, (kern, prec, e_inf)
+            assert e_en <= tol, (kern, prec, e_en)
+            assert vec_error(rhs, rhs_o) <= 1e-12
+            if kern == "tensor_core":
+                again, rhs2 = run(sp, prob, prec)
+                assert np.array_equal(vals, again) and np.array_equal(rhs, rhs2)
     sp.close()
 
 
