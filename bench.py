@@ -192,6 +192,8 @@ def on_tensor_cores(prob, prec: str, kernel: str) -> bool:
         return False
     if prob.problem == inputs.ELASTICITY and prob.order == 2:
         return True
+    if prob.problem == inputs.ELASTICITY and prob.order == 3:
+        return kernel == "tensor_core" or (kernel == "auto" and prec == "bf16")
     if prob.problem != inputs.POISSON or prob.order not in (2, 3):
         return False
     return kernel == "tensor_core" or (kernel == "auto" and prob.order == 3 and prec == "bf16")
@@ -207,7 +209,9 @@ def kernel_names(prob, prec: str, kernel: str = "auto"):
     if prec == "fp64":
         return f"k_cell<{prob.order},{3 if el else 1},0>", "k_scatter_rows<double>"
     if on_tensor_cores(prob, prec, kernel):
-        return ("tc::k_cell_tc" if el else f"tcp::k_cell_tcp<{prob.order}>"), scat
+        if el:
+            return ("tc::k_cell_tc" if prob.order == 2 else "tce::k_cell_tce"), scat
+        return f"tcp::k_cell_tcp<{prob.order}>", scat
     if el and prob.order == 1 and prob.quad_1d == 2 and kernel == "auto":
         return "q1e::k_cell_q1e", scat
     return f"k_cell<{prob.order},{3 if el else 1},{1 if prec == 'fp32' else 2}>", scat

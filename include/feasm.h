@@ -202,15 +202,17 @@ int fe_assemble_adjoint(fe_space* s, const double* u, const double* coefficients
 
 /* Selects the cell-integration kernel of later fe_assemble calls:
  * FE_KERNEL_AUTO (default: the tensor-core kernel for Q2 elasticity and for
- * the BF16 form of Q3 Poisson, the warp-role CUDA-core kernel for Q1
- * elasticity, else the general CUDA-core kernel), FE_KERNEL_CUDA_CORE, or FE_KERNEL_TENSOR_CORE (fe_assemble then
- * fails with FE_ERR_UNSUPPORTED where none exists; tensor-core kernels exist
- * for Q2 elasticity and Q2 / Q3 Poisson with the (p+1)^3 rule, FP32 or BF16).
+ * the BF16 forms of Q3 Poisson and Q3 elasticity, the warp-role CUDA-core
+ * kernel for Q1 elasticity, else the general CUDA-core kernel),
+ * FE_KERNEL_CUDA_CORE, or FE_KERNEL_TENSOR_CORE (fe_assemble then fails with
+ * FE_ERR_UNSUPPORTED where none exists; tensor-core kernels exist for Q2 / Q3
+ * elasticity and Q2 / Q3 Poisson with the (p+1)^3 rule, FP32 or BF16).
  * The kernels of FE_KERNEL_AUTO keep the FP32 form within 1e-6 (row-scaled
  * entry error against FP64) on every mesh tested, single cells included. The
- * Poisson tensor-core kernel's FP32 form, chosen only on request, is faster
- * for Q3 and within 1e-6 on multi-cell meshes, but reached 1.2e-6 on one
- * distorted Q3 cell: the tensor cores' FP32 accumulation truncates. */
+ * Q3 tensor-core kernels' FP32 forms (3xTF32), chosen only on request, are
+ * faster but not within 1e-6 everywhere, because the tensor cores' FP32
+ * accumulation does not round to nearest: Poisson Q3 reached 1.2e-6 on one
+ * distorted cell (within 1e-6 on multi-cell meshes), elasticity Q3 1.9e-6. */
 enum { FE_KERNEL_AUTO = 0, FE_KERNEL_CUDA_CORE = 1, FE_KERNEL_TENSOR_CORE = 2 };
 int fe_space_set_kernel(fe_space* s, int cell_kernel);
 

@@ -1,7 +1,8 @@
 """Accuracy of the mixed forms over every entry of the full-size workloads.
 
-The FP32 (3xTF32 on the tensor cores for Q2 elasticity and Q3 Poisson; FP32
-node blocks for Q1 elasticity) and BF16 forms are compared over all nonzeros with the FP64 GPU path of the same space,
+The FP32 (3xTF32 on the tensor cores for Q2 elasticity, CUDA cores for the
+others) and BF16 (tensor cores for Q2 elasticity and the Q3 elements) forms
+of the automatic kernel choice are compared over all nonzeros with the FP64 GPU path of the same space,
 which the parity tests pin to the oracle on sampled rows (within 1e-14). Row-
 scaled entry error (max_ij |a - a*| / max_j |a*_ij|) and energy error
 (|v^T (A - A*) v| / v^T A* v over seeded unit-RMS vectors) must stay within the
@@ -39,7 +40,7 @@ def _errors(rp, col, vals, ref, n_vec=4, seed=0):
     return entry, energy
 
 
-@pytest.mark.parametrize("workload", ["elasticity_q2_beam", "elasticity_q1_128", "poisson_q3_40"])
+@pytest.mark.parametrize("workload", ["elasticity_q2_beam", "elasticity_q1_128", "poisson_q3_40", "elasticity_q3_20"])
 def test_mixed_forms_every_entry_full_size(workload):
     prob = inputs.WORKLOADS[workload]()
     sp = feasm.FESpace(prob)
