@@ -60,7 +60,9 @@ struct Cfg {
   static constexpr int OFF_X = al16(OFF_GEO + NQ * 12 * 4);          // 24 double
   static constexpr int OFF_A = al16(OFF_X + 24 * 8);                 // 21 double
   static constexpr int OFF_T = al16(OFF_A + 21 * 8);                 // V[16], D[16] float
-  static constexpr int OFF_BAR = al16(OFF_T + 32 * 4);               // mma, drain
+  static constexpr int OFF_JC = al16(OFF_T + 32 * 4);                // [48][3] double: Jacobian columns
+  static constexpr int OFF_VP = al16(OFF_JC + 48 * 3 * 8);           // [THREADS] float2: cell-vector partials
+  static constexpr int OFF_BAR = al16(OFF_VP + THREADS * 8);         // mma, drain
   static constexpr int OFF_TMEM = OFF_BAR + 2 * 8;
   static constexpr int USED = OFF_TMEM + 8;
   // more than half of the SM's shared memory: one CTA (512 tensor-memory columns) per SM
@@ -166,6 +168,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tce(Params p) {
   double* sa = reinterpret_cast<double*>(sm + C::OFF_A);
   float* sv = reinterpret_cast<float*>(sm + C::OFF_T);
   float* sd = sv + 16;
+  double* jc = reinterpret_cast<double*>(sm + C::OFF_JC);
+  float2* vpart = reinterpret_cast<float2*>(sm + C::OFF_VP);
   const uint32_t sbase = smem_u32(sm);
   const uint32_t sop = sbase + C::OFF_OP;
   const uint32_t bar_mma = sbase + C::OFF_BAR, bar_drain = bar_mma + 8;
@@ -219,10 +223,34 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tce(Params p) {
     if (tid < 3) trilinear_coefficients(sx, tid, sa);
     if (tid < 24 && cell + gridDim.x < p.n_cells) xnext = p.xv[(cell + gridDim.x) * 24 + tid];
     __syncthreads();
+    // Jacobian column d at the 16 pairs of 1D points of the two other
+    // directions (it does not depend on its own direction): 48 items
+    if (tid < 48) {
+      const int d = tid >> 4, u = tid & 3, v = (tid >> 2) & 3;
+      const double s = p.xq[3 * u], t = p.xq[3 * v];  // 1D Gauss points
+      const int c0 = 3 * d, cs = d == 2 ? 12 : 9, ct = d == 0 ? 12 : 15;
+      const double st = s * t;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) jc[tid * 3 + k] = sa[c0 + k] + sa[cs + k] * s + sa[ct + k] * t + sa[18 + k] * st;
+    }
+    __syncthreads();
     if (tid < NQ) {
-      const int q = tid;
-      double cof[9], det;
-      geometry_at(sa, p.xq[3 * q], p.xq[3 * q + 1], p.xq[3 * q + 2], cof, &det);
+      const int q = tid, q0 = q & 3, q1 = (q >> 2) & 3, q2 = q >> 4;
+      const double* j0 = jc + (q1 + 4 * q2) * 3;        // column 0 at (y, z)
+      const double* j1 = jc + (16 + q0 + 4 * q2) * 3;   // column 1 at (x, z)
+      const double* j2 = jc + (32 + q0 + 4 * q1) * 3;   // column 2 at (x, y)
+      const double J[3][3] = {{j0[0], j1[0], j2[0]}, {j0[1], j1[1], j2[1]}, {j0[2], j1[2], j2[2]}};
+      double cof[9];
+      cof[0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+      cof[1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+      cof[2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+      cof[3] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+      cof[4] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+      cof[5] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+      cof[6] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+      cof[7] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+      cof[8] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+      const double det = J[0][0] * cof[0] + J[0][1] * cof[1] + J[0][2] * cof[2];
       if (!(det > 0.0)) atomicOr(p.err, kErrNegJacobian);
       const double wq = p.w[q];
       float* g = geo + q * 12;
@@ -236,11 +264,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tce(Params p) {
     }
     __syncthreads();
     // ---- cell vector: f_(i,a) = f_i sum_q (w det J)_q phihat_a(x_q), double-float
-    // products and sums rounded once to FP64
-    if (tid < NB) {
-      const int a = tid;
+    // products and sums (8 points per thread, then the 8 partial sums of a
+    // node in order), rounded once to FP64
+    {
+      const int a = tid & (NB - 1), q0 = (tid >> 6) * 8;
       float sh = 0.f, sl = 0.f;
-      for (int q = 0; q < NQ; ++q) {
+#pragma unroll
+      for (int q = q0; q < q0 + 8; ++q) {
         const float* g = geo + q * 12;
         const float wh = g[10], wl = g[11];
         const float2 b = sphi[q * NB + a];
@@ -251,6 +281,21 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tce(Params p) {
         const float er = (sh - (sum - bp)) + (ph - bp);
         sh = sum;
         sl += er + pe;
+      }
+      vpart[tid] = make_float2(sh, sl);
+    }
+    __syncthreads();
+    if (tid < NB) {
+      const int a = tid;
+      float sh = 0.f, sl = 0.f;
+#pragma unroll
+      for (int k = 0; k < THREADS / NB; ++k) {
+        const float2 v = vpart[k * NB + a];
+        const float sum = sh + v.x;
+        const float bp = sum - sh;
+        const float er = (sh - (sum - bp)) + (v.x - bp);
+        sh = sum;
+        sl += er + v.y;
       }
       const double s = __dadd_rn(f32_to_f64_exact(sh), f32_to_f64_exact(sl));
 #pragma unroll
