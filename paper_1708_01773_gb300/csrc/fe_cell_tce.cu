@@ -333,11 +333,14 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tce(Params p) {
     const float lE = lam * E, mE = mu * E;
     float* kc = p.ke + cell * (NL * NL) + (32 * rt + 8 * rq) * NL + 32 * rh;
     const float lmE = lE + mE;
-#pragma unroll 1
+    // quarter qq + 1 is loaded from tensor memory while quarter qq is formed
+    uint32_t rbuf[2][32];
+    tmem_ld16x2_start(lane_addr, lane_addr + 16u, rbuf[0]);
+    tmem_wait32(rbuf[0]);
+#pragma unroll
     for (int qq = 0; qq < 4; ++qq) {
-      uint32_t r[32];
-      tmem_ld16x2_start(lane_addr + uint32_t(32 * qq), lane_addr + uint32_t(32 * qq + 16), r);
-      tmem_wait32(r);
+      uint32_t(&r)[32] = rbuf[qq & 1];
+      if (qq < 3) tmem_ld16x2_start(lane_addr + uint32_t(32 * qq + 32), lane_addr + uint32_t(32 * qq + 48), rbuf[(qq + 1) & 1]);
 #pragma unroll
       for (int bb = 0; bb < 8; ++bb) {
         // the lane's row (a, i) holds v_m = G[(a,i)][(b,m)]; it needs G[(a,j)][(b,i)]
@@ -359,6 +362,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_tce(Params p) {
           o[cp] = fmaf(lE, vp, mE * tp);
         }
       }
+      if (qq < 3) tmem_wait32(rbuf[(qq + 1) & 1]);
     }
     __syncwarp();
     // the warp's 24 rows x 3 components x 32 column nodes: 72 coalesced 128-byte row segments
