@@ -31,7 +31,8 @@ problems, all synthetic):
   mesh of the batched recipe), shifts up to 0.2h, conductivity 10^U[-1,1],
   f = 1, 4^3 Gauss (``poisson_q3_24``: the same on 24^3 cells).
 * ``elasticity_q3_20`` Elasticity Q3, 20^3 cells of the unit cube, shifts up to
-  0.2h, E ~ U[1,10], nu = 0.3, f = (0,0,-1), 4^3 Gauss.
+  0.2h, E ~ U[1,10], nu = 0.3, f = (0,0,-1), 4^3 Gauss (``elasticity_q3_12``:
+  the same on 12^3 cells).
 """
 from __future__ import annotations
 
@@ -287,4 +288,5 @@ WORKLOADS = {
     "poisson_q3_40": poisson_q3,
     "poisson_q3_24": lambda: poisson_q3(24),
     "elasticity_q3_20": elasticity_q3,
+    "elasticity_q3_12": lambda: elasticity_q3(12),
 }
