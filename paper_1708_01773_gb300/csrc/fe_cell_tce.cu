@@ -24,9 +24,10 @@
 //
 // Read-out: warp w reads tensor-memory lanes 32 (w % 4).. of tile (w / 4) % 2,
 // columns 128 (w / 8).. (32 column nodes b). For each b the four lanes of a node
-// a exchange their G[(a, .)][(b, .)] values with nine shuffles, form K^e rows
-// (i, a) at columns (j, b) in registers, 8 column nodes at a time, stages them
-// in shared memory and stores 128-byte row segments. One persistent CTA per SM (all 512 tensor-memory
+// a exchange their G[(a, .)][(b, .)] values with four shuffles (two rotated
+// transposes, a butterfly for the trace), form K^e rows (i, a) at columns
+// (j, b), 8 column nodes at a time, stage them in shared memory and store
+// 128-byte row segments. One persistent CTA per SM (all 512 tensor-memory
 // columns); every mbarrier wait is bounded, after which the CTA sets
 // FE_ERR_TIMEOUT, waits (bounded) for its issued MMAs and frees the tensor
 // memory.
