@@ -68,3 +68,37 @@ def test_noalloc_adjoint_empty_mesh():
     torch.cuda.synchronize()
     assert float(c) == 0.0
     sp.close()
+
+
+def test_noalloc_adjoint_in_a_cuda_graph():
+    """The allocation-free entry point captured into a CUDA graph (global capture
+    mode, where an allocation would end the capture with an error) and replayed
+    gives the allocating entry point's gradient and compliance bit for bit."""
+    build.build()
+    prob = inputs.small_problem((6, 5, 4), 1, 1, seed=44)
+    sp = feasm.FESpace(prob)
+    u = torch.tensor(inputs.unit_rms_field(sp.n_dofs, 5), device="cuda")
+    E = torch.tensor(prob.coef, device="cuda")
+    pr = feasm.PRECISIONS["fp64"]
+    g_ref = torch.empty(sp.n_cells, dtype=torch.float64, device="cuda")
+    c_ref = torch.empty(1, dtype=torch.float64, device="cuda")
+    feasm.fe_assemble_adjoint(sp.handle, u, E, 1.3, g_ref, c_ref, pr)
+    g = torch.empty_like(g_ref)
+    c = torch.empty_like(c_ref)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):  # warm-up outside the capture
+        feasm.fe_assemble_adjoint_noalloc(sp.handle, u, E, 1.3, g, c, pr, side)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g.fill_(np.nan)
+    c.fill_(np.nan)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, capture_error_mode="global"):
+        feasm.fe_assemble_adjoint_noalloc(sp.handle, u, E, 1.3, g, c, pr, torch.cuda.current_stream())
+    graph.replay()
+    torch.cuda.synchronize()
+    assert sp.status() == 0
+    assert torch.equal(g, g_ref)
+    assert torch.equal(c, c_ref)
+    sp.close()
