@@ -908,7 +908,9 @@ struct SlotScatter {
   static constexpr int CH = (NL + 31) / 32;
   static constexpr int NBR = NL / R;  // local-row offset between the rows of one node
   static constexpr int LOADS = CH * (R + 1);
-  static constexpr int SB = (LOADS <= 4 && R > 1) ? 8 : LOADS <= 8 ? 4 : LOADS <= 16 ? 2 : 1;
+  // slots per batch: 4 where the loads of a batch fit the registers (measured on
+  // the Q1 node rows: 4 slots per batch at five blocks per SM beat 8 at four)
+  static constexpr int SB = LOADS <= 8 ? 4 : LOADS <= 16 ? 2 : 1;
 
   // One batch of B slots starting at slot s_begin.
   template <int B, bool IDX32>

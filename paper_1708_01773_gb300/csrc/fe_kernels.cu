@@ -245,7 +245,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 // coalesced. Lanes past the end of a cell row (m >= NL) read padding and touch
 // a private dummy accumulator, so the inner loop has no divergent branches
 // (the position array and the cell-matrix scratch are allocated with padding
-// for those reads). Slots are processed in batches of 8, 4, 2 or 1 (the
+// for those reads). Slots are processed in batches of 4, 2 or 1 (the
 // largest that fits the slots left and the register budget), all loads of a
 // batch issued before its additions; the item descriptors (pointers, slot ids)
 // of the warp's next item are fetched while the current one is reduced. Items
@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32) k_scatter_rows(ScatterPara
 constexpr int kSlotGrab = 4;  // items per grab of k_scatter_slots
 
 template <int NL, int R, bool IDX32>
-__global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5) : 4) k_scatter_slots(ScatterParams p) {
+__global__ void __launch_bounds__(kScatterWarps * 32, NL >= 128 ? 4 : 5) k_scatter_slots(ScatterParams p) {
   using S = SlotScatter<NL, R>;
   extern __shared__ __align__(16) unsigned char sm[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -322,10 +322,7 @@ __global__ void __launch_bounds__(kScatterWarps * 32, R == 1 ? (NL >= 64 ? 4 : 5
     int sb = 0;
     while (sb < ns) {
       const int left = ns - sb;
-      if (S::SB >= 8 && left >= 8) {
-        S::template batch<8, IDX32>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
-        sb += 8;
-      } else if (S::SB >= 4 && left >= 4) {
+      if (S::SB >= 4 && left >= 4) {
         S::template batch<4, IDX32>(p, ke, pos, my_slot, sb, acc, rs, dummy, lane);
         sb += 4;
       } else if (S::SB >= 2 && left >= 2) {
@@ -444,7 +441,7 @@ cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, 
     p.acc_stride = int((pt.max_row_nnz + 3) & ~int64_t(3));
     // rows of one node together (3-component problems), else one row per warp
     // (measured: pays for Q1, 24-entry cell rows; for wider rows one row per warp is faster)
-    const int R = (pt.node_rows && s->ncomp == 3 && s->nl <= 32) ? 3 : 1;
+    const int R = (pt.node_rows && s->ncomp == 3 && s->nl <= 32) ? 3 : 1;  // 3: nl = 24 only
     p.warp_bytes = R * (p.acc_stride + 32) * 8;  // R accumulator rows, each with one dummy per lane
     const long bytes = long(p.warp_bytes) * kScatterWarps;
     if (bytes <= 200 * 1024) {
@@ -461,14 +458,10 @@ cudaError_t launch_scatter_pattern(const fe_space* s, const ScatterPattern& pt, 
         case 257: return launch(k_scatter_slots<64, 1, true>, bytes);
         case 324: return launch(k_scatter_slots<81, 1, false>, bytes);
         case 325: return launch(k_scatter_slots<81, 1, true>, bytes);
-        case 326: return launch(k_scatter_slots<81, 3, false>, bytes);
-        case 327: return launch(k_scatter_slots<81, 3, true>, bytes);
         case 356: return launch(k_scatter_slots<89, 1, false>, bytes);   // Stokes Q2/Q1
         case 357: return launch(k_scatter_slots<89, 1, true>, bytes);
         case 768: return launch(k_scatter_slots<192, 1, false>, bytes);
         case 769: return launch(k_scatter_slots<192, 1, true>, bytes);
-        case 770: return launch(k_scatter_slots<192, 3, false>, bytes);
-        case 771: return launch(k_scatter_slots<192, 3, true>, bytes);
         default: break;
       }
     }
