@@ -274,6 +274,30 @@ def test_negative_jacobian_reported_without_fault():
     good.close()
 
 
+@pytest.mark.parametrize("p,problem", [(2, 1), (2, 0), (3, 0), (3, 1)])
+def test_negative_jacobian_reported_by_tensor_core_kernels(p, problem):
+    """Inverted cells set FE_ERR_NEG_JACOBIAN in the tensor-core cell kernels
+    (both forms) without a fault; the next assembly on a good mesh is clean."""
+    prob = inputs.small_problem((2, 2, 2), p, problem, seed=2)
+    coords = prob.mesh.coords.copy()
+    coords[13] = [1.2, 1.2, 1.2]  # the interior vertex pushed through the far corner
+    m = inputs.Mesh(coords, prob.mesh.cell_vertices, prob.mesh.shape, prob.mesh.extent)
+    bad = inputs.Problem("bad", m, p, p + 1, problem, prob.coef, prob.force, prob.nu)
+    sp = feasm.FESpace(bad)
+    sp.set_kernel("tensor_core")
+    coef = torch.tensor(bad.coef, device="cuda")
+    for prec in ("fp32", "bf16"):
+        sp.assemble(coef, prec=prec)
+        assert sp.status() == -4, prec
+        assert sp.status() == 0
+    good = feasm.FESpace(prob)
+    good.set_kernel("tensor_core")
+    vals, _ = good.assemble(torch.tensor(prob.coef, device="cuda"), prec="bf16")
+    assert good.status() == 0 and torch.isfinite(vals).all()
+    sp.close()
+    good.close()
+
+
 def test_empty_mesh():
     mesh = inputs.Mesh(np.zeros((0, 3)), np.zeros((0, 8), dtype=np.int32), (0, 0, 0), (1, 1, 1))
     prob = inputs.Problem("empty", mesh, 2, 3, 1, np.zeros(0), np.array([0.0, 0.0, -1.0]))
