@@ -478,8 +478,10 @@ __device__ __forceinline__ float d2f_rn(double x) {
 }
 
 // FP64 -> FP32 round to nearest even on the 32-bit words of x, branch-free, for
-// a result that is zero or an FP32 normal number; `odd` is set where it is not
-// (the tile's geometry is then recomputed with the general conversions).
+// a result that is zero or an FP32 normal number; `odd` is set for inputs
+// outside that range (the tile's geometry is then recomputed with the general
+// conversions). A rounding at the top of the range that carries into infinity
+// comes out exact without the flag.
 __device__ __forceinline__ float d2f_fast(double x, bool& odd) {
   const uint32_t hi = uint32_t(__double2hiint(x)), lo = uint32_t(__double2loint(x));
   const uint32_t ahi = hi & 0x7fffffffu;
