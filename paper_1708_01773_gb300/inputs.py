@@ -33,9 +33,16 @@ problems, all synthetic):
 * ``elasticity_q3_20`` Elasticity Q3, 20^3 cells of the unit cube, shifts up to
   0.2h, E ~ U[1,10], nu = 0.3, f = (0,0,-1), 4^3 Gauss (``elasticity_q3_12``:
   the same on 12^3 cells).
+
+``scramble`` presents any of these meshes as an unstructured one (random vertex
+ids, random cell order, each cell's local vertex order turned by one of the 24
+proper rotations of the reference cube), so that the DOF numbering, the
+assembly maps and the facet matching are exercised without the brick's
+regular numbering.
 """
 from __future__ import annotations
 
+import itertools
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -277,6 +284,49 @@ def small_problem(n: tuple, order: int, problem: int, alpha: float = 0.2, seed: 
         coef = rng.uniform(1.0, 10.0, size=mesh.n_cells)
         force = np.array([0.0, 0.0, -1.0])
     return Problem(f"small_{n}_p{order}_{problem}", mesh, order, order + 1, problem, coef, force)
+
+
+def _cube_rotations() -> np.ndarray:
+    """The 24 proper rotations of the reference cube as permutations of its 8
+    local vertices (x-fastest order, v = x + 2 y + 4 z): row r maps local
+    vertex v to the vertex at R_r applied to v's corner (about the centre)."""
+    rows = []
+    for perm in itertools.permutations(range(3)):
+        for signs in itertools.product((1, -1), repeat=3):
+            R = np.zeros((3, 3), dtype=np.int64)
+            for i in range(3):
+                R[i, perm[i]] = signs[i]
+            if round(np.linalg.det(R)) != 1:
+                continue
+            m = []
+            for v in range(8):
+                c = np.array([2 * (v & 1) - 1, 2 * ((v >> 1) & 1) - 1, 2 * (v >> 2) - 1])
+                r = (R @ c + 1) // 2
+                m.append(int(r[0] + 2 * r[1] + 4 * r[2]))
+            rows.append(m)
+    return np.array(rows, dtype=np.int64)
+
+
+def scramble(mesh: Mesh, rng: np.random.Generator):
+    """The same mesh presented as an unstructured one: vertex ids relabelled at
+    random, cells in random order, and each cell's local vertex order turned by
+    a random proper rotation of the reference cube (the cell map stays
+    orientation-preserving, so det J keeps its sign). Returns (mesh, order):
+    new cell i is old cell order[i]."""
+    vperm = rng.permutation(mesh.n_vertices)        # old vertex i gets id vperm[i]
+    coords = np.empty_like(mesh.coords)
+    coords[vperm] = mesh.coords
+    order = rng.permutation(mesh.n_cells)
+    rot = _cube_rotations()[rng.integers(0, 24, mesh.n_cells)]
+    cv = np.take_along_axis(mesh.cell_vertices[order].astype(np.int64), rot, axis=1)
+    return Mesh(coords, vperm[cv].astype(mesh.cell_vertices.dtype), (), mesh.extent), order
+
+
+def scrambled(prob: Problem, seed: int) -> Problem:
+    """A workload on the scrambled form of its mesh (coefficients follow their cells)."""
+    mesh, order = scramble(prob.mesh, np.random.default_rng(SEED_BASE + 500 + seed))
+    return Problem(prob.name + "_scrambled", mesh, prob.order, prob.quad_1d, prob.problem,
+                   np.asarray(prob.coef)[order], prob.force, prob.nu)
 
 
 WORKLOADS = {

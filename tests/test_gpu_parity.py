@@ -36,14 +36,36 @@ SMALL = [((3, 3, 3), 1, 0), ((3, 3, 3), 1, 1), ((3, 2, 3), 2, 0), ((3, 2, 2), 2,
 
 @pytest.mark.parametrize("shape,p,problem", SMALL)
 def test_small_meshes_all_precisions(shape, p, problem):
-    prob = inputs.small_problem(shape, p, problem, seed=10 * p + problem)
+    check_all_kernels(inputs.small_problem(shape, p, problem, seed=10 * p + problem))
+
+
+# Scrambled bricks: Q1 on 60 cells (two tiles of the Q1 elasticity kernel, the
+# second ragged), Q2 and Q3 on several cells per persistent tensor-core CTA pass
+SCRAMBLED = [((5, 4, 3), 1, 0), ((5, 4, 3), 1, 1), ((3, 3, 2), 2, 0), ((3, 3, 2), 2, 1), ((2, 2, 3), 3, 0),
+             ((2, 2, 2), 3, 1)]
+
+
+@pytest.mark.parametrize("shape,p,problem", SCRAMBLED)
+def test_unstructured_numbering_all_kernels(shape, p, problem):
+    """The small-mesh check on scrambled bricks: random vertex ids and cell
+    order, every cell's local vertex order turned by a random proper rotation of
+    the reference cube. The DOF numbering and pattern bit for bit, every entry of
+    every kernel and precision, and the RHS against the oracle on the same mesh."""
+    base = inputs.small_problem(shape, p, problem, seed=60 + 10 * p + problem)
+    check_all_kernels(inputs.scrambled(base, seed=70 + 10 * p + problem))
+
+
+def check_all_kernels(prob):
+    p, problem = prob.order, prob.problem
+    shape = prob.mesh.shape or prob.mesh.n_cells
     cd, n = oracle.dof_numbering(prob.mesh, p, prob.ncomp)
     rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob, cd, n)
     sp = feasm.FESpace(prob)
+    np.testing.assert_array_equal(sp.cell_dofs(), cd)
     rp, col = sp.pattern()
     np.testing.assert_array_equal(rp.cpu().numpy(), rp_o)
     np.testing.assert_array_equal(col.cpu().numpy(), col_o)
-    kernels = ["cuda_core", "tensor_core"] if p >= 2 else ["auto"]
+    kernels = ["cuda_core", "tensor_core"] if p >= 2 else ["auto", "cuda_core"]
     for kern in kernels:
         sp.set_kernel(kern)
         for prec in ("fp64", "fp32", "bf16"):

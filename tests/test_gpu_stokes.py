@@ -36,9 +36,12 @@ def velocity_energy_error(rp, col, val, val_ref, nv, seed=0, n_vec=8):
     return worst
 
 
-@pytest.mark.parametrize("shape,p", [((3, 3, 2), 2), ((4, 2, 3), 2), ((2, 2, 2), 3)])
-def test_small_stokes_meshes(shape, p):
+@pytest.mark.parametrize("shape,p,scramble", [((3, 3, 2), 2, False), ((4, 2, 3), 2, False), ((2, 2, 2), 3, False),
+                                              ((3, 2, 2), 2, True), ((2, 2, 2), 3, True)])
+def test_small_stokes_meshes(shape, p, scramble):
     prob = inputs.small_problem(shape, p, inputs.STOKES, seed=700 + p)
+    if scramble:  # random vertex ids and cell order, rotated local vertex orders
+        prob = inputs.scrambled(prob, seed=710 + p)
     cd_o, n_o, nv = oracle.stokes_dof_numbering(prob.mesh, p)
     rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob, cd_o, n_o)
     sp = feasm.FESpace(prob)

@@ -38,14 +38,19 @@ def test_library_exports_every_declared_symbol():
 
 
 CASES = [
-    ((3, 2, 2), 1, 0), ((2, 2, 3), 1, 1), ((2, 3, 2), 2, 0), ((3, 2, 2), 2, 1), ((2, 2, 2), 3, 0), ((2, 1, 2), 3, 1),
-    ((3, 2, 2), 2, 2), ((2, 1, 2), 3, 2),
+    ((3, 2, 2), 1, 0, False), ((2, 2, 3), 1, 1, False), ((2, 3, 2), 2, 0, False), ((3, 2, 2), 2, 1, False),
+    ((2, 2, 2), 3, 0, False), ((2, 1, 2), 3, 1, False), ((3, 2, 2), 2, 2, False), ((2, 1, 2), 3, 2, False),
+    # scrambled bricks: random vertex ids and cell order, rotated local vertex orders
+    ((3, 3, 2), 1, 1, True), ((3, 2, 2), 2, 0, True), ((2, 2, 2), 2, 1, True), ((2, 2, 2), 3, 1, True),
+    ((3, 2, 2), 2, 2, True),
 ]
 
 
-@pytest.mark.parametrize("shape,p,problem", CASES)
-def test_numbering_pattern_permutation_match_oracle(shape, p, problem):
+@pytest.mark.parametrize("shape,p,problem,scramble", CASES)
+def test_numbering_pattern_permutation_match_oracle(shape, p, problem, scramble):
     prob = inputs.small_problem(shape, p, problem, seed=3 * p + problem)
+    if scramble:
+        prob = inputs.scrambled(prob, seed=20 + 3 * p + problem)
     sp = feasm.FESpace(prob, host_only=True)
     cd_o, n_o = oracle.numbering(prob)
     cd = sp.cell_dofs()

@@ -382,6 +382,54 @@ def test_dof_numbering_rotated_cells():
     node_positions(prob2, cd, n)
 
 
+def dof_correspondence(prob_a, cd_a, n_a, prob_b, cd_b, n_b):
+    """perm with DOF m of space a = DOF perm[m] of space b, matched by node
+    position and component (both spaces on the same geometry)."""
+    assert n_a == n_b
+    xa, ca = node_positions(prob_a, cd_a, n_a)
+    xb, cb = node_positions(prob_b, cd_b, n_b)
+
+    def order(x, c):
+        r = np.round(x, 9)
+        return np.lexsort((c, r[:, 2], r[:, 1], r[:, 0]))
+
+    ia, ib = order(xa, ca), order(xb, cb)
+    np.testing.assert_allclose(xa[ia], xb[ib], atol=1e-12)
+    np.testing.assert_array_equal(ca[ia], cb[ib])
+    perm = np.empty(n_a, dtype=np.int64)
+    perm[ia] = ib
+    return perm
+
+
+@pytest.mark.parametrize("p,problem,shape", [(1, 0, (3, 3, 2)), (1, 1, (3, 2, 2)), (2, 0, (3, 2, 2)),
+                                             (2, 1, (2, 2, 2)), (3, 0, (2, 2, 2)), (3, 1, (2, 1, 2))])
+def test_assembly_invariant_under_unstructured_numbering(p, problem, shape):
+    """The scrambled brick (random vertex ids and cell order, every cell's local
+    vertex order turned by a random proper rotation) is the same discrete
+    problem: its matrix and RHS equal the brick's under the DOF correspondence
+    of node positions and components. This pins the orientation-free node keys
+    of list_dofs and the cell matrix's covariance with the cell's local frame
+    (the tensor Gauss rule is invariant under the cube's rotations), and that
+    the coefficient of a cell follows the cell."""
+    prob = inputs.small_problem(shape, p, problem, seed=40 + 2 * p + problem)
+    scr = inputs.scrambled(prob, seed=p + 3 * problem)
+    cd0, n0 = oracle.dof_numbering(prob.mesh, p, prob.ncomp)
+    cd1, n1 = oracle.dof_numbering(scr.mesh, p, scr.ncomp)
+    perm = dof_correspondence(prob, cd0, n0, scr, cd1, n1)
+    assert not np.array_equal(perm, np.arange(n0))
+    rp0, col0, val0, rhs0 = oracle.assemble_csr(prob, cd0, n0)
+    rp1, col1, val1, rhs1 = oracle.assemble_csr(scr, cd1, n1)
+    A0 = csr_to_dense(rp0, col0, val0, n0)
+    A1 = csr_to_dense(rp1, col1, val1, n1)
+    np.testing.assert_allclose(A1[np.ix_(perm, perm)], A0, rtol=0, atol=1e-12 * np.abs(A0).max())
+    np.testing.assert_allclose(rhs1[perm], rhs0, rtol=0, atol=1e-12 * np.abs(rhs0).max())
+    # the same sparsity pattern, up to the renumbering
+    assert rp0[-1] == rp1[-1]
+    S0 = csr_to_dense(rp0, col0, np.ones(col0.size), n0) != 0
+    S1 = csr_to_dense(rp1, col1, np.ones(col1.size), n1) != 0
+    np.testing.assert_array_equal(S1[np.ix_(perm, perm)], S0)
+
+
 # ---------------------------------------------------------------- assembled-system invariants
 def assembled(prob):
     cd, n = oracle.dof_numbering(prob.mesh, prob.order, prob.ncomp)
