@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--kernel", default="auto", choices=["auto", "cuda_core", "tensor_core"],
                     help="cell-integration kernel selection (fe_space_set_kernel)")
+    ap.add_argument("--reorder", action="store_true",
+                    help="give the cells in the locality order of fe_mesh_locality_order (Morton order of "
+                         "the cell centroids) before creating the space")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-comparators", action="store_true")
     ap.add_argument("--extras", action="store_true",
@@ -629,6 +632,8 @@ def main():
 
     prob = inputs.WORKLOADS[args.workload]()
     t0 = time.perf_counter()
+    if args.reorder:
+        prob = inputs.reordered(prob, feasm.fe_mesh_locality_order(prob.mesh.coords, prob.mesh.cell_vertices))
     sp = feasm.FESpace(prob)
     setup_s = time.perf_counter() - t0
     sp.set_kernel(args.kernel)
@@ -764,7 +769,8 @@ def main():
                        "nnz": int(sp.nnz), "contributions": int(sp.n_contrib), "order": prob.order,
                        "precision": f"{args.prec} contraction, fp64 geometry + fp64 CSR accumulation",
                        "l2": "working set > L2 (no flush)", "parallelism": f"replicas x{ws}",
-                       "kernel": args.kernel, "setup_s": setup_s},
+                       "kernel": args.kernel, "setup_s": setup_s,
+                       "cell_order": "morton (fe_mesh_locality_order)" if args.reorder else "as generated"},
             "nnz_per_s": value / sp.n_cells * sp.nnz,
             "e2e": {"value": ws * sp.n_cells / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(sp.n_cells * 8),
                     "d2h_bytes_per_step": int((sp.nnz + sp.n_dofs) * 8)},

@@ -112,6 +112,21 @@ int fe_space_create(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_
 int fe_space_create_host(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem,
                          double nu, fe_space** out);
 
+/* Cell order for memory locality (host only, touches no GPU): order[i] = the
+ * input cell placed at position i, the cells sorted by the Morton (Z-order)
+ * code of their vertex centroids, quantised to 21 bits per axis over the
+ * bounding box of the centroids; equal codes keep the input order. list_dofs
+ * numbers DOFs in cell order (Sect. "Global DOF numbering generation"), so a
+ * mesh whose cells are given in this order (cell_vertices and any per-cell
+ * coefficients permuted alike) gets a numbering and assembly maps in which the
+ * cells around a node, and the rows of neighbouring nodes, lie close in
+ * memory. The paper leaves the cell order to the mesh generator (its
+ * structured generator numbers cells lexicographically); this serves meshes
+ * that arrive in arbitrary order. `order` is host [n_cells], caller-owned.
+ * Errors: FE_ERR_INVALID_ARG (NULL pointers with n_cells > 0, vertex ids out
+ * of range, non-finite coordinates). */
+int fe_mesh_locality_order(const fe_mesh_desc* mesh, int64_t* order);
+
 /* Sizes of the space: number of global DOFs, CSR nonzeros, cells, and
  * per-contribution counts (n_cells * n_loc^2). Any pointer may be NULL. */
 int fe_space_sizes(const fe_space* s, int64_t* n_dofs, int64_t* nnz, int64_t* n_cells,

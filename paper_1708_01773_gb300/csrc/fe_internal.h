@@ -14,6 +14,9 @@ constexpr int kMaxOrder = 3;
 constexpr int kMaxQ1d = 6;
 constexpr int kMaxSlots = 127;  // cells around one DOF (7 bits of a code)
 
+// Records the message returned by fe_last_error and returns `code`.
+int set_error(int code, const char* msg);
+
 // Reference tables of the Q_p element at a tensor Gauss-Legendre rule on
 // [0,1]^3. Point q = q0 + n q1 + n^2 q2, node a = a0 + (p+1) a1 + (p+1)^2 a2.
 struct RefTables {

@@ -445,3 +445,64 @@ static void parallel_for(int64_t n, int nthreads, const std::function<void(int, 
 }
 
 }  // namespace feasm
+
+// ---------------------------------------------------------------------------
+// Cell order for memory locality: cells sorted by the Morton (Z-order) code of
+// their vertex centroids, quantised to 21 bits per axis over the bounding box
+// of the centroids; equal codes keep the input order.
+
+namespace {
+
+// The 21 low bits of v spread to every third bit of a 63-bit word.
+uint64_t spread3(uint64_t v) {
+  v &= 0x1fffffull;
+  v = (v | (v << 32)) & 0x1f00000000ffffull;
+  v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+  v = (v | (v << 8)) & 0x100f00f00f00f00full;
+  v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+  v = (v | (v << 2)) & 0x1249249249249249ull;
+  return v;
+}
+
+}  // namespace
+
+int fe_mesh_locality_order(const fe_mesh_desc* mesh, int64_t* order) {
+  if (!mesh || mesh->n_cells < 0 || mesh->n_vertices < 0)
+    return feasm::set_error(FE_ERR_INVALID_ARG, "invalid mesh descriptor");
+  const int64_t nc = mesh->n_cells, nv = mesh->n_vertices;
+  if (nc == 0) return FE_OK;
+  if (!order || !mesh->cell_vertices || !mesh->coords)
+    return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
+  std::vector<double> cen(size_t(nc) * 3);
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int64_t e = 0; e < nc; ++e) {
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int v = 0; v < 8; ++v) {
+      const int32_t id = mesh->cell_vertices[e * 8 + v];
+      if (id < 0 || id >= nv) return feasm::set_error(FE_ERR_INVALID_ARG, "cell_vertices entry out of range");
+      for (int k = 0; k < 3; ++k) c[k] += mesh->coords[int64_t(id) * 3 + k];
+    }
+    for (int k = 0; k < 3; ++k) {
+      c[k] *= 0.125;
+      if (!std::isfinite(c[k])) return feasm::set_error(FE_ERR_INVALID_ARG, "non-finite vertex coordinate");
+      cen[size_t(e) * 3 + k] = c[k];
+      lo[k] = std::min(lo[k], c[k]);
+      hi[k] = std::max(hi[k], c[k]);
+    }
+  }
+  const double top = double((1 << 21) - 1);
+  std::vector<std::pair<uint64_t, int64_t>> key(static_cast<size_t>(nc));
+  for (int64_t e = 0; e < nc; ++e) {
+    uint64_t code = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double span = hi[k] - lo[k];
+      const double t = span > 0.0 ? (cen[size_t(e) * 3 + k] - lo[k]) / span : 0.0;
+      const uint64_t q = uint64_t(std::min(top, std::max(0.0, std::floor(t * top))));
+      code |= spread3(q) << k;
+    }
+    key[size_t(e)] = {code, e};
+  }
+  std::sort(key.begin(), key.end());
+  for (int64_t i = 0; i < nc; ++i) order[i] = key[size_t(i)].second;
+  return FE_OK;
+}

@@ -29,7 +29,7 @@ EXPORTS = [
     "fe_space_create", "fe_space_create_host", "fe_space_sizes", "fe_space_cell_dofs_host",
     "fe_space_csr_pattern_host", "fe_space_permutation_host", "fe_space_csr_pattern", "fe_assemble", "fe_assemble_ex", "fe_assemble_host",
     "fe_assemble_adjoint", "fe_assemble_adjoint_noalloc", "fe_space_set_kernel", "fe_status", "fe_space_destroy", "fe_last_error", "fe_batch_create",
-    "fe_batch_assemble", "fe_batch_set_wait", "fe_batch_destroy", "fe_selftest_conversions", "fe_space_dof_points_host", "fe_dirichlet_create", "fe_dirichlet_sizes",
+    "fe_batch_assemble", "fe_batch_set_wait", "fe_batch_destroy", "fe_selftest_conversions", "fe_space_dof_points_host", "fe_mesh_locality_order", "fe_dirichlet_create", "fe_dirichlet_sizes",
     "fe_dirichlet_labels_host", "fe_dirichlet_csr_pattern_host", "fe_dirichlet_csr_pattern",
     "fe_dirichlet_permutation_host", "fe_dirichlet_lift_host", "fe_assemble_dirichlet", "fe_dirichlet_destroy",
     "fe_compliance_work_size", "fe_compliance", "fe_space_block_offset", "fe_dg_create", "fe_dg_create_host",
@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
         L.fe_batch_destroy.argtypes = [V]
         L.fe_batch_destroy.restype = None
         L.fe_space_dof_points_host.argtypes = [V, P(MeshDesc), V]
+        L.fe_mesh_locality_order.argtypes = [P(MeshDesc), V]
         L.fe_dirichlet_create.argtypes = [V, V, P(V)]
         L.fe_dirichlet_sizes.argtypes = [V, P(I64), P(I64), P(I64)]
         L.fe_dirichlet_labels_host.argtypes = [V, V]
@@ -285,6 +286,16 @@ def fe_space_dof_points_host(space: int, coords, cell_vertices) -> np.ndarray:
     d, keep = _mesh_desc(coords, cell_vertices)
     out = np.zeros((n_dofs, 3), dtype=np.float64)
     _check(lib().fe_space_dof_points_host(space, ctypes.byref(d), out.ctypes.data), "fe_space_dof_points_host")
+    del keep
+    return out
+
+
+def fe_mesh_locality_order(coords, cell_vertices) -> np.ndarray:
+    """Cell order for memory locality (Morton order of the cell centroids),
+    [n_cells] int64 (host): new cell i = input cell order[i]."""
+    d, keep = _mesh_desc(coords, cell_vertices)
+    out = np.zeros(d.n_cells, dtype=np.int64)
+    _check(lib().fe_mesh_locality_order(ctypes.byref(d), out.ctypes.data), "fe_mesh_locality_order")
     del keep
     return out
 

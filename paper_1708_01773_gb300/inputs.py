@@ -38,7 +38,8 @@ problems, all synthetic):
 ids, random cell order, each cell's local vertex order turned by one of the 24
 proper rotations of the reference cube), so that the DOF numbering, the
 assembly maps and the facet matching are exercised without the brick's
-regular numbering.
+regular numbering (``elasticity_q1_128_scrambled``: the 128^3 workload so
+presented, the worst case of memory locality for the assembly maps).
 """
 from __future__ import annotations
 
@@ -329,6 +330,15 @@ def scrambled(prob: Problem, seed: int) -> Problem:
                    np.asarray(prob.coef)[order], prob.force, prob.nu)
 
 
+def reordered(prob: Problem, order) -> Problem:
+    """The workload with its cells in the given order (new cell i = old cell
+    order[i]); coefficients follow their cells, vertices keep their ids."""
+    order = np.asarray(order, dtype=np.int64)
+    mesh = Mesh(prob.mesh.coords, prob.mesh.cell_vertices[order], (), prob.mesh.extent)
+    return Problem(prob.name + "_reordered", mesh, prob.order, prob.quad_1d, prob.problem,
+                   np.asarray(prob.coef)[order], prob.force, prob.nu)
+
+
 WORKLOADS = {
     "poisson_q1_8": poisson_q1_8,
     "elasticity_q2_beam": elasticity_q2_beam,
@@ -339,4 +349,5 @@ WORKLOADS = {
     "poisson_q3_24": lambda: poisson_q3(24),
     "elasticity_q3_20": elasticity_q3,
     "elasticity_q3_12": lambda: elasticity_q3(12),
+    "elasticity_q1_128_scrambled": lambda: scrambled(elasticity_q1_128(), seed=1),
 }

@@ -55,6 +55,15 @@ def test_unstructured_numbering_all_kernels(shape, p, problem):
     check_all_kernels(inputs.scrambled(base, seed=70 + 10 * p + problem))
 
 
+@pytest.mark.parametrize("p,problem", [(1, 1), (2, 1)])
+def test_locality_ordered_mesh_all_kernels(p, problem):
+    """A scrambled brick given in the cell order of fe_mesh_locality_order (the
+    order bench.py --reorder uses): the same checks against the oracle."""
+    scr = inputs.scrambled(inputs.small_problem((5, 4, 3), p, problem, seed=90 + p), seed=91 + p)
+    order = feasm.fe_mesh_locality_order(scr.mesh.coords, scr.mesh.cell_vertices)
+    check_all_kernels(inputs.reordered(scr, order))
+
+
 def check_all_kernels(prob):
     p, problem = prob.order, prob.problem
     shape = prob.mesh.shape or prob.mesh.n_cells

@@ -155,3 +155,67 @@ def test_empty_mesh_host_setup():
     h = feasm.fe_space_create(mesh.coords, mesh.cell_vertices, 2, 0, 1, 0.3, host_only=True)
     assert feasm.fe_space_sizes(h) == (0, 0, 0, 0)
     feasm.fe_space_destroy(h)
+
+
+def _morton_model(mesh):
+    """Morton codes of the cell centroids written out bit by bit (21 bits per
+    axis over the centroids' bounding box, x in the lowest bit of each triple)."""
+    cen = mesh.coords[mesh.cell_vertices].mean(axis=1)
+    lo, hi = cen.min(axis=0), cen.max(axis=0)
+    span = np.where(hi > lo, hi - lo, 1.0)
+    top = (1 << 21) - 1
+    q = np.clip(np.floor((cen - lo) / span * top), 0, top).astype(np.int64)
+    q[:, hi <= lo] = 0
+    code = np.zeros(mesh.n_cells, dtype=np.uint64)
+    for b in range(21):
+        for k in range(3):
+            code |= (((q[:, k] >> b) & 1).astype(np.uint64)) << np.uint64(3 * b + k)
+    return code
+
+
+def _locality(mesh):
+    """Mean distance in cell position between cells that share a face."""
+    faces = {}
+    for e, cv in enumerate(mesh.cell_vertices):
+        for d in range(3):
+            for s in range(2):
+                f = tuple(sorted(int(cv[v]) for v in range(8) if ((v >> d) & 1) == s))
+                faces.setdefault(f, []).append(e)
+    pairs = np.array([v for v in faces.values() if len(v) == 2])
+    return float(np.abs(pairs[:, 0] - pairs[:, 1]).mean())
+
+
+def test_locality_order_sorts_centroid_morton_codes():
+    """fe_mesh_locality_order returns a permutation that sorts the Morton codes of
+    the cell centroids (ties in input order), and on a scrambled brick it brings
+    face neighbours close again: the mean position distance of face-sharing cells
+    drops far below the scrambled one, to the order of the lexicographic brick's."""
+    base = inputs.small_problem((12, 10, 8), 1, 1, seed=5)
+    scr = inputs.scrambled(base, seed=6)
+    order = feasm.fe_mesh_locality_order(scr.mesh.coords, scr.mesh.cell_vertices)
+    assert order.dtype == np.int64 and np.array_equal(np.sort(order), np.arange(scr.mesh.n_cells))
+    code = _morton_model(scr.mesh)
+    np.testing.assert_array_equal(order, np.lexsort((np.arange(scr.mesh.n_cells), code)))
+    np.testing.assert_array_equal(order, feasm.fe_mesh_locality_order(scr.mesh.coords, scr.mesh.cell_vertices))
+    re = inputs.reordered(scr, order)
+    brick, scrambled, morton = _locality(base.mesh), _locality(scr.mesh), _locality(re.mesh)
+    assert morton < 0.2 * scrambled and morton < 1.5 * brick, (brick, scrambled, morton)
+    # the reordered mesh is the same problem: coefficients follow their cells
+    np.testing.assert_array_equal(re.coef, scr.coef[order])
+
+
+def test_locality_order_edge_cases():
+    m = inputs.brick(1, 1, 1)
+    assert feasm.fe_mesh_locality_order(m.coords, m.cell_vertices).tolist() == [0]
+    empty = feasm.fe_mesh_locality_order(m.coords, m.cell_vertices[:0])
+    assert empty.size == 0
+    flat = inputs.brick(5, 1, 1)               # all centroids on one line: two degenerate axes
+    np.testing.assert_array_equal(feasm.fe_mesh_locality_order(flat.coords, flat.cell_vertices), np.arange(5))
+    bad = m.cell_vertices.copy()
+    bad[0, 3] = m.n_vertices                    # vertex id out of range
+    with pytest.raises(feasm.FEError):
+        feasm.fe_mesh_locality_order(m.coords, bad)
+    nan = m.coords.copy()
+    nan[0, 0] = np.nan
+    with pytest.raises(feasm.FEError):
+        feasm.fe_mesh_locality_order(nan, m.cell_vertices)
