@@ -37,6 +37,12 @@ struct CellParams {
 };
 
 __device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+// Two values rounded to BF16 (nearest even) by one paired conversion.
+__device__ __forceinline__ void round_bf16_pair(float& x, float& y) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x, y);
+  x = __low2float(h);
+  y = __high2float(h);
+}
 
 // Trilinear map Phi(x) = a0 + a1 x + a2 y + a3 z + a4 xy + a5 xz + a6 yz + a7 xyz
 // (the Q1 geometry of the cell written in monomials). Its Jacobian at a
@@ -696,8 +702,9 @@ __device__ __forceinline__ void cell_block_mixed(const CellParams& prm, int64_t 
       const float s = c2.y;
       float a0 = s * g0, a1 = s * g1, a2 = s * g2;
       if (PREC == 2) {
-        a0 = round_bf16(a0), a1 = round_bf16(a1), a2 = round_bf16(a2);
-        g0 = round_bf16(g0), g1 = round_bf16(g1), g2 = round_bf16(g2);
+        round_bf16_pair(a0, a1);
+        round_bf16_pair(a2, g0);
+        round_bf16_pair(g1, g2);
       }
       gA[i] = make_float4(a0, a1, a2, 0.f);
       gB[i] = make_float4(g0, g1, g2, 0.f);
@@ -803,7 +810,7 @@ __device__ __forceinline__ void cell_block_mixed(const CellParams& prm, int64_t 
         for (int k = 0; k < 3; ++k) {
           ga[k] = s * gq[k * NB + a];
           gb[k] = gq[k * NB + b];
-          if (PREC == 2) ga[k] = round_bf16(ga[k]), gb[k] = round_bf16(gb[k]);
+          if (PREC == 2) round_bf16_pair(ga[k], gb[k]);
         }
       }
     };
