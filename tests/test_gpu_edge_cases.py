@@ -1,8 +1,12 @@
 """GPU edge cases of the constrained, Stokes and DG paths: every DOF fixed
 (an empty system), nothing fixed (the unconstrained system, bit for bit), a
-single cell (DG: boundary facets only; Stokes), an empty mesh; and the
-largest single mesh of the batched recipe (Q3 elasticity on 40^3 cells: more
-contributions than an int32 can index)."""
+single cell (DG: boundary facets only; Stokes), an empty mesh; the largest
+single mesh of the batched recipe (Q3 elasticity on 40^3 cells: more
+contributions than an int32 can index); and for every cell kernel void cells
+(zero and 1e-9 coefficients) on a strongly distorted mesh, and flat cells of
+aspect ratio ~1e-3."""
+import dataclasses
+
 import numpy as np
 import pytest
 import torch
@@ -10,7 +14,7 @@ import torch
 import oracle
 from metrics import TOL, row_scaled_error, vec_error
 from paper_1708_01773_gb300 import build, feasm, inputs
-from test_gpu_parity import check_rows, sampled_rows
+from test_gpu_parity import check_all_kernels, check_rows, sampled_rows
 
 pytestmark = pytest.mark.gpu
 
@@ -96,3 +100,32 @@ def test_maximum_size_q3_elasticity_int64():
     assert sp.status() == 0
     check_rows(prob, sp, vals.cpu().numpy(), rhs.cpu().numpy(), "fp32", sampled_rows(sp.n_dofs, k=12))
     sp.close()
+
+
+SHAPES = {1: (4, 4, 3), 2: (3, 3, 2), 3: (2, 2, 2)}
+
+
+@pytest.mark.parametrize("p,problem", [(1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1)])
+def test_void_cells_on_a_strongly_distorted_mesh(p, problem):
+    """SIMP-like coefficients: half the cells at 1e-9 of their value and a fifth
+    exactly zero (void cells have zero cell matrices; rows inside the void are
+    zero, and the row-scaled comparison then demands exact zeros), on a mesh
+    whose interior vertices move by up to 0.3h per coordinate. Every entry of
+    every kernel and precision against the oracle."""
+    prob = inputs.small_problem(SHAPES[p], p, problem, alpha=0.3, seed=120 + 2 * p + problem)
+    assert oracle.min_det_jacobian(prob.mesh, prob.quad_1d) > 0
+    rng = np.random.default_rng(130 + 2 * p + problem)
+    coef = np.where(rng.random(prob.mesh.n_cells) < 0.5, 1e-9, 1.0) * prob.coef
+    coef[rng.random(prob.mesh.n_cells) < 0.2] = 0.0
+    assert (coef == 0).any() and (coef > 0.5).any()
+    check_all_kernels(dataclasses.replace(prob, coef=coef))
+
+
+@pytest.mark.parametrize("p,problem", [(1, 1), (2, 0), (2, 1), (3, 1)])
+def test_flat_cells(p, problem):
+    """Cells of aspect ratio ~1e-3 (a 1 x 1 x 1e-3 slab, interior shifts up to
+    0.2h_d): cofactors and 1/det J span six orders of magnitude before their
+    rounding to FP32. Every entry of every kernel and precision against the oracle."""
+    prob = inputs.small_problem(SHAPES[p], p, problem, seed=140 + 2 * p + problem, extent=(1.0, 1.0, 1e-3))
+    assert oracle.min_det_jacobian(prob.mesh, prob.quad_1d) > 0
+    check_all_kernels(prob)
