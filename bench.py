@@ -603,7 +603,7 @@ def batched(dev, stream):
     cells = sum(s.n_cells for s in spaces)
     nnz = sum(s.nnz for s in spaces)
     rec = {}
-    for prec in ("fp32", "fp64"):
+    for prec in ("fp32", "bf16", "fp64"):
         b = feasm.fe_batch_create([s.handle for s in spaces])
         ms = time_events(lambda: feasm.fe_batch_assemble(b, coefs, [p.force for p in probs], vals, rhss,
                                                          feasm.PRECISIONS[prec], stream), 3, stream)

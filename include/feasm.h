@@ -272,8 +272,14 @@ const char* fe_last_error(void);
  * block) and (space, row block) items, replayed from a CUDA graph. A row item
  * waits (bounded, about one second; FE_ERR_TIMEOUT in the spaces' error
  * words after that) until its space's cells are integrated. Cell items use
- * the CUDA-core cell kernel; results match fe_assemble's CUDA-core path and
- * are deterministic. The batch keeps pointers to the spaces, which must
+ * the CUDA-core cell kernel. A space whose cells fe_assemble would integrate
+ * on the tensor cores in the requested precision (its fe_space_set_kernel
+ * selection; by default Q2 elasticity and the BF16 forms of Q3 Poisson and
+ * Q3 elasticity) has no cell items: its tensor-core cell kernel is launched on
+ * the caller's stream before the persistent launch. Results are
+ * deterministic and match fe_assemble space by space, with the tensor-core
+ * kernel for those spaces and the CUDA-core kernel for the others. The batch
+ * reads each space's kernel selection at every call. The batch keeps pointers to the spaces, which must
  * outlive it; spaces must be on the current device with at most 32 cells
  * around any DOF.
  *   cells_per_item  cells per cell item, 0 = autotuned: the first

@@ -172,6 +172,35 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
 namespace feasm {
 int set_error(int code, const char* msg) { return fail(code, msg); }
 
+// Poisson on the tensor cores: on request, and by default for the BF16 form of
+// Q3 (3x faster there, within its 1e-2 bound). The FP32 form stays on the CUDA
+// cores by default: on the tensor cores it is not within 1e-6 on every single
+// distorted Q3 cell (their FP32 accumulation truncates), and Q2's 27 x 27 cell
+// blocks run faster on the CUDA cores.
+static bool tcp_chosen(const fe_space* s, fe_precision prec) {
+  return cell_tcp_applicable(s, prec) &&
+         (s->cell_kernel == FE_KERNEL_TENSOR_CORE ||
+          (s->cell_kernel == FE_KERNEL_AUTO && s->order == 3 && prec == FE_PREC_BF16));
+}
+
+// Q3 elasticity on the tensor cores: on request, and by default for BF16.
+static bool tce_chosen(const fe_space* s, fe_precision prec) {
+  return cell_tce_applicable(s, prec) &&
+         (s->cell_kernel == FE_KERNEL_TENSOR_CORE || (s->cell_kernel == FE_KERNEL_AUTO && prec == FE_PREC_BF16));
+}
+
+bool cell_on_tensor_cores(const fe_space* s, fe_precision prec) {
+  if (s->problem == FE_STOKES || s->cell_kernel == FE_KERNEL_CUDA_CORE) return false;
+  return tcp_chosen(s, prec) || tce_chosen(s, prec) || cell_tc_applicable(s, prec);
+}
+
+cudaError_t launch_cell_tensor(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
+                               cudaStream_t st) {
+  if (tcp_chosen(s, prec)) return launch_cell_tcp(s, coef, force, prec, st);
+  if (tce_chosen(s, prec)) return launch_cell_tce(s, coef, force, prec, st);
+  return launch_cell_tc(s, coef, force, prec, st);
+}
+
 int cell_stage(fe_space* s, const double* coef, const double force[3], fe_precision prec, cudaStream_t st) {
   if (s->problem == FE_STOKES) {
     if (prec == FE_PREC_BF16) return fail(FE_ERR_UNSUPPORTED, "Stokes cell integration has FP64 and FP32 forms only");
@@ -179,28 +208,11 @@ int cell_stage(fe_space* s, const double* coef, const double force[3], fe_precis
     FE_CUDA(launch_cell_stokes(s, coef, force, prec, st));
     return FE_OK;
   }
-  // Poisson on the tensor cores: on request, and by default for the BF16 form
-  // of Q3 (3x faster there, within its 1e-2 bound). The FP32 form stays on the
-  // CUDA cores by default: on the tensor cores it is not within 1e-6 on every
-  // single distorted Q3 cell (their FP32 accumulation truncates), and Q2's
-  // 27 x 27 cell blocks run faster on the CUDA cores
-  const bool tcp = cell_tcp_applicable(s, prec) &&
-                   (s->cell_kernel == FE_KERNEL_TENSOR_CORE ||
-                    (s->cell_kernel == FE_KERNEL_AUTO && s->order == 3 && prec == FE_PREC_BF16));
-  // Q3 elasticity on the tensor cores: on request, and by default for BF16
-  const bool tce = cell_tce_applicable(s, prec) &&
-                   (s->cell_kernel == FE_KERNEL_TENSOR_CORE ||
-                    (s->cell_kernel == FE_KERNEL_AUTO && prec == FE_PREC_BF16));
-  const bool tc = (cell_tc_applicable(s, prec) || cell_tcp_applicable(s, prec) || cell_tce_applicable(s, prec)) &&
-                  s->cell_kernel != FE_KERNEL_CUDA_CORE;
-  if (s->cell_kernel == FE_KERNEL_TENSOR_CORE && !tc)
+  const bool any_tc = cell_tc_applicable(s, prec) || cell_tcp_applicable(s, prec) || cell_tce_applicable(s, prec);
+  if (s->cell_kernel == FE_KERNEL_TENSOR_CORE && !any_tc)
     return fail(FE_ERR_UNSUPPORTED, "no tensor-core cell kernel for this order / problem / precision");
-  if (tcp)
-    FE_CUDA(launch_cell_tcp(s, coef, force, prec, st));
-  else if (tce)
-    FE_CUDA(launch_cell_tce(s, coef, force, prec, st));
-  else if (tc && cell_tc_applicable(s, prec))
-    FE_CUDA(launch_cell_tc(s, coef, force, prec, st));
+  if (cell_on_tensor_cores(s, prec))
+    FE_CUDA(launch_cell_tensor(s, coef, force, prec, st));
   else if (q1e_applicable(s, prec))
     FE_CUDA(launch_cell_q1e(s, coef, force, prec, st));
   else

@@ -15,8 +15,16 @@
 //
 // Cell items run the CUDA-core cell kernel of the space's order and problem;
 // row items run the slot-wise double-float scatter (FP32 and BF16 forms) or
-// the exact fixed-point scatter (FP64 form), one warp per row. Results are the
-// same as fe_assemble's CUDA-core path for every space and deterministic.
+// the exact fixed-point scatter (FP64 form), one warp per row. A space whose
+// cells fe_assemble integrates on the tensor cores in the requested precision
+// (its kernel selection: by default Q2 elasticity, and the BF16 forms of Q3
+// Poisson and Q3 elasticity) gets no cell items: its tcgen05 cell kernel runs
+// as a launch of its own on the caller's stream just before the persistent
+// launch (outside the graph, whose kernel arguments are fixed at capture,
+// while the coefficient pointers change per call), and its row items do not
+// wait. Results are deterministic and, space by space, the same as
+// fe_assemble's with the tensor-core kernel for those spaces and with the
+// CUDA-core kernel for the others.
 //
 // Autotuning. The first fe_batch_assemble of a precision times each candidate
 // (cells per item, rows per item) twice on the caller's buffers, keeps the
@@ -242,7 +250,9 @@ struct fe_batch {
     int grid = 0, row_warp_bytes = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    std::vector<char> tensor;  // per space: cells integrated on the tensor cores (no cell items)
   } plan[3];
+  int extra_cells = 0;       // test hook: row items wait for this many cells more than exist
 };
 
 namespace {
@@ -262,10 +272,18 @@ cudaError_t occupancy(int* per_sm, size_t smem) {
 }
 
 // Builds the work list of one plan and uploads it.
+std::vector<char> tensor_spaces(const fe_batch* b, fe_precision prec) {
+  std::vector<char> t(b->spaces.size());
+  for (size_t i = 0; i < t.size(); ++i) t[i] = feasm::cell_on_tensor_cores(b->spaces[i], prec) ? 1 : 0;
+  return t;
+}
+
 int build_plan(fe_batch* b, fe_precision prec, int cell_mult, int rows_per_item, fe_batch::Plan* pl) {
   std::vector<Item> items;
   const int n = int(b->spaces.size());
+  pl->tensor = tensor_spaces(b, prec);
   auto add_cells = [&](int i) {
+    if (pl->tensor[i]) return;
     const fe_space* s = b->spaces[i];
     const int64_t step = int64_t(feasm::cells_per_block(s->nb, s->nq)) *
                          (b->cells_per_item > 0 ? std::max(1, b->cells_per_item / feasm::cells_per_block(s->nb, s->nq))
@@ -504,9 +522,23 @@ int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const doub
     S.scat.rhs = rhs ? rhs[i] : nullptr;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  fe_batch::Plan& pl = b->plan[prec];
+  const std::vector<char> tensor = tensor_spaces(b, prec);
+  if (pl.ready && pl.tensor != tensor) free_plan(&pl);  // a space's kernel selection changed
+  for (int i = 0; i < n; ++i) {
+    Space& S = b->h_spaces[i];
+    S.wait_target = (tensor[i] ? 0 : S.n_cells) + b->extra_cells;
+  }
   cudaError_t e = cudaMemcpyAsync(b->d_spaces, b->h_spaces.data(), n * sizeof(Space), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return feasm::set_error(FE_ERR_CUDA, cudaGetErrorString(e));
-  fe_batch::Plan& pl = b->plan[prec];
+  // the tensor-core cell kernels first, on the same stream
+  for (int i = 0; i < n; ++i) {
+    if (!tensor[i] || b->spaces[i]->n_cells == 0) continue;
+    double f[3] = {0.0, 0.0, 0.0};
+    for (int k = 0; k < b->spaces[i]->ncomp && k < 3; ++k) f[k] = body_force[3 * i + k];
+    e = feasm::launch_cell_tensor(b->spaces[i], coefficients[i], f, prec, st);
+    if (e != cudaSuccess) return feasm::set_error(FE_ERR_CUDA, cudaGetErrorString(e));
+  }
   if (!pl.ready) {
     const int rc = tune_and_capture(b, prec, st);
     if (rc) return rc;
@@ -519,10 +551,11 @@ int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const doub
 int fe_batch_set_wait(fe_batch* b, long long wait_cycles, int extra_cells) {
   if (!b) return feasm::set_error(FE_ERR_INVALID_ARG, "batch is NULL");
   if (wait_cycles < 0 || extra_cells < 0) return feasm::set_error(FE_ERR_INVALID_ARG, "negative wait or extra cells");
+  b->extra_cells = extra_cells;
   for (size_t i = 0; i < b->h_spaces.size(); ++i) {
     Space& S = b->h_spaces[i];
     S.wait_cycles = wait_cycles > 0 ? wait_cycles : feasm::batch::kDefaultWaitCycles;
-    S.wait_target = S.n_cells + extra_cells;
+    S.wait_target = S.n_cells + extra_cells;  // (the tensor-core spaces' share is set per call)
   }
   return FE_OK;
 }

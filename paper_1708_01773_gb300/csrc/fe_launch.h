@@ -23,6 +23,14 @@ bool cell_tc_applicable(const fe_space* s, fe_precision prec);
 cudaError_t launch_cell_tc(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
                            cudaStream_t st);
 
+// Whether fe_assemble integrates the cells of `s` on the tensor cores in
+// `prec` under the space's kernel selection (FE_KERNEL_AUTO: Q2 elasticity,
+// and the BF16 forms of Q3 Poisson and Q3 elasticity; FE_KERNEL_TENSOR_CORE:
+// every case a tensor-core kernel covers), and the launch of that kernel.
+bool cell_on_tensor_cores(const fe_space* s, fe_precision prec);
+cudaError_t launch_cell_tensor(const fe_space* s, const double* coef, const double force[3], fe_precision prec,
+                               cudaStream_t st);
+
 // Q1 elasticity (2^3 rule), FP32 and BF16 forms, with the automatic kernel
 // choice: the warp-role cell kernel (FP64 geometry on its own warps); same
 // outputs as launch_cell_integration.

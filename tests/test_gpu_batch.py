@@ -36,6 +36,14 @@ def batch_run(batch, probs, spaces, prec):
     return vals, rhs
 
 
+def on_tensor_cores(p, prec):
+    """fe_assemble's automatic kernel choice: tcgen05 for Q2 elasticity and for
+    the BF16 forms of Q3 Poisson and Q3 elasticity ((p+1)^3 rules)."""
+    if prec == "fp64" or p.quad_1d != p.order + 1:
+        return False
+    return (p.order == 2 and p.problem == inputs.ELASTICITY) or (p.order == 3 and prec == "bf16")
+
+
 @pytest.mark.parametrize("prec", ["fp32", "fp64", "bf16"])
 def test_batch_matches_oracle_and_single_space(small_batch, prec):
     probs, spaces = small_batch
@@ -49,11 +57,34 @@ def test_batch_matches_oracle_and_single_space(small_batch, prec):
         assert row_scaled_error(rp_o, col_o, v, val_o) <= TOL[prec], (p.name, prec)
         assert energy_error(rp_o, col_o, v, val_o) <= TOL[prec], (p.name, prec)
         assert vec_error(rhs[i].cpu().numpy(), rhs_o) <= 1e-12
-        # the same CUDA-core arithmetic as a single-space assembly
-        s.set_kernel("cuda_core")
+        # the same arithmetic as a single-space assembly: the tensor-core kernel
+        # where fe_assemble's automatic choice takes it, else the CUDA-core one
+        s.set_kernel("auto" if on_tensor_cores(p, prec) else "cuda_core")
         sv, sr = s.assemble(torch.tensor(p.coef, device="cuda"), prec=prec)
         s.set_kernel("auto")
         assert torch.equal(sv, vals[i]) and torch.equal(sr, rhs[i]), p.name
+    feasm.fe_batch_destroy(batch)
+
+
+def test_batch_follows_kernel_selection(small_batch):
+    """The BF16 batch runs the Q3 spaces' tensor-core cell kernels; after one Q3
+    space is switched to the CUDA cores the next call rebuilds its work list with
+    that space's cell items and matches the single-space CUDA-core assembly bit
+    for bit, and switching back restores the tensor-core result."""
+    probs, spaces = small_batch
+    i = next(k for k, p in enumerate(probs) if p.order == 3)
+    batch = feasm.fe_batch_create([s.handle for s in spaces])
+    coef = torch.tensor(probs[i].coef, device="cuda")
+    v_tc, _ = batch_run(batch, probs, spaces, "bf16")
+    sv, _ = spaces[i].assemble(coef, prec="bf16")
+    assert torch.equal(sv, v_tc[i])
+    spaces[i].set_kernel("cuda_core")
+    v_cc, _ = batch_run(batch, probs, spaces, "bf16")
+    sv, _ = spaces[i].assemble(coef, prec="bf16")
+    assert torch.equal(sv, v_cc[i]) and not torch.equal(v_cc[i], v_tc[i])
+    spaces[i].set_kernel("auto")
+    v_back, _ = batch_run(batch, probs, spaces, "bf16")
+    assert torch.equal(v_back[i], v_tc[i])
     feasm.fe_batch_destroy(batch)
 
 
