@@ -287,6 +287,69 @@ def small_problem(n: tuple, order: int, problem: int, alpha: float = 0.2, seed: 
     return Problem(f"small_{n}_p{order}_{problem}", mesh, order, order + 1, problem, coef, force)
 
 
+def o_grid(m: int, k: int, nz: int, a: float = 0.45, radius: float = 1.0, height: float = 1.0) -> Mesh:
+    """A hexahedral O-grid: in the xy-plane an inner square [-a, a]^2 of m x m
+    cells inside four blocks of m x k cells that run out to the circle of the
+    given radius, extruded over nz layers of [0, height]. The four edges through
+    the inner square's corners are shared by three cells per layer (six per
+    vertex between layers) instead of a brick's four (eight), so vertex
+    valence, row lengths and cells per DOF vary over the mesh. Coincident points
+    of the blocks are merged; every cell is orientation-preserving."""
+    pts2, quads = [], []
+
+    def block(f, ni, nj):
+        base = len(pts2)
+        for j in range(nj + 1):
+            for i in range(ni + 1):
+                pts2.append(f(i / ni, j / nj))
+        for j in range(nj):
+            for i in range(ni):
+                q = [base + j * (ni + 1) + i, base + j * (ni + 1) + i + 1,
+                     base + (j + 1) * (ni + 1) + i, base + (j + 1) * (ni + 1) + i + 1]
+                quads.append(q)
+
+    block(lambda s, t: (-a + 2 * a * s, -a + 2 * a * t), m, m)
+    for side in range(4):
+        ang0 = -np.pi / 4 + side * np.pi / 2
+        rot = np.array([[np.cos(side * np.pi / 2), -np.sin(side * np.pi / 2)],
+                        [np.sin(side * np.pi / 2), np.cos(side * np.pi / 2)]])
+
+        def f(s, t, rot=rot, ang0=ang0):
+            inner = rot @ np.array([a, -a + 2 * a * s])
+            th = ang0 + s * np.pi / 2
+            outer = radius * np.array([np.cos(th), np.sin(th)])
+            return tuple((1 - t) * inner + t * outer)
+        block(f, m, k)
+    P = np.array(pts2)
+    key = np.round(P, 9)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    P = P[first]
+    Q = inv.reshape(-1)[np.array(quads)]
+    # orientation: (p10 - p00) x (p01 - p00) > 0, else swap the local x and y
+    d1 = P[Q[:, 1]] - P[Q[:, 0]]
+    d2 = P[Q[:, 2]] - P[Q[:, 0]]
+    neg = d1[:, 0] * d2[:, 1] - d1[:, 1] * d2[:, 0] < 0
+    Q[neg] = Q[neg][:, [0, 2, 1, 3]]
+    n2 = P.shape[0]
+    zs = np.linspace(0.0, height, nz + 1)
+    coords = np.concatenate([np.column_stack([P, np.full(n2, z)]) for z in zs])
+    cells = [np.concatenate([Q + l * n2, Q + (l + 1) * n2], axis=1) for l in range(nz)]
+    return Mesh(coords.astype(np.float64), np.concatenate(cells).astype(np.int32), (), (2 * radius, 2 * radius, height))
+
+
+def o_grid_problem(m: int, k: int, nz: int, order: int, problem: int, seed: int = 0) -> Problem:
+    """A seeded problem on an O-grid: coefficients as in small_problem."""
+    rng = np.random.default_rng(SEED_BASE + 700 + seed)
+    mesh = o_grid(m, k, nz)
+    if problem == POISSON:
+        coef, force = _log_uniform(rng, 0.1, 10.0, mesh.n_cells), np.array([1.0])
+    elif problem == STOKES:
+        coef, force = rng.uniform(0.5, 2.0, size=mesh.n_cells), np.array([0.3, -0.2, -1.0])
+    else:
+        coef, force = rng.uniform(1.0, 10.0, size=mesh.n_cells), np.array([0.0, 0.0, -1.0])
+    return Problem(f"o_grid_{m}_{k}_{nz}_p{order}_{problem}", mesh, order, order + 1, problem, coef, force)
+
+
 def _cube_rotations() -> np.ndarray:
     """The 24 proper rotations of the reference cube as permutations of its 8
     local vertices (x-fastest order, v = x + 2 y + 4 z): row r maps local

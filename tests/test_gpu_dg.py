@@ -45,6 +45,26 @@ def test_small_dg_meshes(p, shape, rotate):
     g.close()
 
 
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_dg_o_grid(p):
+    """IP-DG on an O-grid (facets between cells of irregular valence, a curved
+    polygonal outer boundary): pattern and every entry against the oracle, both
+    tau, three forms."""
+    mesh = inputs.o_grid(3, 2, 2)
+    g = feasm.DGSpace(mesh, p)
+    rp, col = g.pattern()
+    for tau in (1.0, -1.0):
+        rp_o, col_o, val_o, rhs_o = oracle.dg_assemble(mesh, p, tau, 8.0, 1.5)
+        np.testing.assert_array_equal(rp.cpu().numpy(), rp_o)
+        np.testing.assert_array_equal(col.cpu().numpy(), col_o)
+        for prec in ("fp64", "fp32", "bf16"):
+            vals, rhs = g.assemble(tau, 8.0, 1.5, prec=prec)
+            torch.cuda.synchronize()
+            assert row_scaled_error(rp_o, col_o, vals.cpu().numpy(), val_o) <= TOL[prec], (tau, prec)
+            assert vec_error(rhs.cpu().numpy(), rhs_o) <= 1e-12
+    g.close()
+
+
 @pytest.mark.parametrize("p,n,taus", [(2, 14, (1.0, -1.0)), (1, 16, (1.0, -1.0)), (3, 11, (1.0,))])
 def test_dg_every_entry_with_several_facets_per_block(p, n, taus):
     """Rotated n^3 meshes: k_dg_facets runs one wave of at most 152 x 16 resident

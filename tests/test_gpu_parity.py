@@ -55,6 +55,14 @@ def test_unstructured_numbering_all_kernels(shape, p, problem):
     check_all_kernels(inputs.scrambled(base, seed=70 + 10 * p + problem))
 
 
+@pytest.mark.parametrize("p,problem", [(1, 0), (1, 1), (2, 0), (2, 1), (3, 0), (3, 1)])
+def test_o_grid_all_kernels(p, problem):
+    """An O-grid (66 cells; six cells around the inner square's corner vertices,
+    three on the end faces, eight elsewhere): numbering, pattern, every entry of
+    every kernel and precision and the RHS against the oracle."""
+    check_all_kernels(inputs.o_grid_problem(3, 2, 2, p, problem, seed=40 + 2 * p + problem))
+
+
 @pytest.mark.parametrize("p,problem", [(1, 1), (2, 1)])
 def test_locality_ordered_mesh_all_kernels(p, problem):
     """A scrambled brick given in the cell order of fe_mesh_locality_order (the

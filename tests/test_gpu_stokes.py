@@ -42,6 +42,17 @@ def test_small_stokes_meshes(shape, p, scramble):
     prob = inputs.small_problem(shape, p, inputs.STOKES, seed=700 + p)
     if scramble:  # random vertex ids and cell order, rotated local vertex orders
         prob = inputs.scrambled(prob, seed=710 + p)
+    check_stokes(prob)
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_stokes_o_grid(p):
+    """Taylor-Hood on an O-grid (irregular vertex valence)."""
+    check_stokes(inputs.o_grid_problem(3, 2, 2, p, inputs.STOKES, seed=720 + p))
+
+
+def check_stokes(prob):
+    p = prob.order
     cd_o, n_o, nv = oracle.stokes_dof_numbering(prob.mesh, p)
     rp_o, col_o, val_o, rhs_o = oracle.assemble_csr(prob, cd_o, n_o)
     sp = feasm.FESpace(prob)

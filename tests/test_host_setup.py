@@ -51,6 +51,18 @@ def test_numbering_pattern_permutation_match_oracle(shape, p, problem, scramble)
     prob = inputs.small_problem(shape, p, problem, seed=3 * p + problem)
     if scramble:
         prob = inputs.scrambled(prob, seed=20 + 3 * p + problem)
+    check_host_setup(prob)
+
+
+@pytest.mark.parametrize("p,problem", [(1, 0), (1, 1), (2, 0), (2, 1), (3, 1), (2, 2)])
+def test_o_grid_numbering_pattern_permutation(p, problem):
+    """The same checks on an O-grid (irregular vertex valence: six cells around
+    the inner square's corner vertices, three on the end faces)."""
+    check_host_setup(inputs.o_grid_problem(3, 2, 2, p, problem, seed=20 + p))
+
+
+def check_host_setup(prob):
+    p, problem = prob.order, prob.problem
     sp = feasm.FESpace(prob, host_only=True)
     cd_o, n_o = oracle.numbering(prob)
     cd = sp.cell_dofs()

@@ -513,6 +513,71 @@ def test_elasticity_rigid_modes_and_patch(p, shape):
     assert abs(zsum + 1.0) < 1e-13 and abs(rhs[comp == 0].sum()) < 1e-14 and abs(rhs[comp == 1].sum()) < 1e-14
 
 
+def _o_grid_ring(mesh):
+    """The outer boundary of an O-grid's cross-section: its vertices on the
+    circle (z = 0), in angular order."""
+    xy = mesh.coords[mesh.coords[:, 2] == 0.0][:, :2]
+    r = np.hypot(xy[:, 0], xy[:, 1])
+    ring = xy[np.abs(r - r.max()) < 1e-12]
+    return ring[np.argsort(np.arctan2(ring[:, 1], ring[:, 0]))]
+
+
+def _o_grid_boundary(pos, ring, height):
+    """DOFs on the boundary: the end faces z = 0, height, and the polygon edges
+    between consecutive ring vertices (the trilinear cells' straight sides)."""
+    b = (np.abs(pos[:, 2]) < 1e-12) | (np.abs(pos[:, 2] - height) < 1e-12)
+    a, c = ring, np.roll(ring, -1, axis=0)
+    for p0, p1 in zip(a, c):
+        d = p1 - p0
+        t = np.clip(((pos[:, :2] - p0) @ d) / (d @ d), 0.0, 1.0)
+        dist = np.linalg.norm(pos[:, :2] - (p0 + t[:, None] * d), axis=1)
+        b |= dist < 1e-12
+    return b
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_o_grid_invariants(p):
+    """On an O-grid (irregular vertex valence: three cells per layer around the
+    inner square's corner edges) the assembled Poisson matrix has zero row sums,
+    reproduces linear fields on interior rows with the energy |a|^2 vol, and its
+    RHS sums to vol (vol = the polygonal cross-section's area x height, by the
+    shoelace formula); the elasticity matrix is symmetric with the six rigid
+    modes in its kernel and z-rows of the RHS summing to -vol."""
+    po = inputs.o_grid_problem(3, 2, 2, p, inputs.POISSON, seed=p)
+    assert oracle.min_det_jacobian(po.mesh, po.quad_1d) > 0
+    ring = _o_grid_ring(po.mesh)
+    area = 0.5 * abs(np.sum(ring[:, 0] * np.roll(ring[:, 1], -1) - np.roll(ring[:, 0], -1) * ring[:, 1]))
+    vol = area * po.mesh.extent[2]
+    po.coef[:] = 2.0
+    cd, n, rp, col, val, rhs = assembled(po)
+    A = csr_to_dense(rp, col, val, n)
+    pos, comp = node_positions(po, cd, n)
+    sc = np.abs(A).max()
+    assert np.abs(A.sum(axis=1)).max() < 1e-13 * sc
+    a = np.array([0.3, -1.1, 0.7])
+    u = pos @ a + 0.5
+    inner = ~_o_grid_boundary(pos, ring, po.mesh.extent[2])
+    assert inner.sum() > 0
+    assert np.abs((A @ u)[inner]).max() < 1e-12 * sc
+    assert abs(u @ A @ u - 2.0 * (a @ a) * vol) < 1e-12 * 2.0 * (a @ a) * vol
+    assert abs(rhs.sum() - vol) < 1e-13
+    el = inputs.o_grid_problem(3, 2, 2, p, inputs.ELASTICITY, seed=10 + p)
+    cd, n, rp, col, val, rhs = assembled(el)
+    A = csr_to_dense(rp, col, val, n)
+    sc = np.abs(A).max()
+    assert np.abs(A - A.T).max() < 1e-15 * sc
+    pos, comp = node_positions(el, cd, n)
+    for c in range(3):
+        assert np.abs(A @ (comp == c).astype(float)).max() < 1e-12 * sc
+    for w in np.eye(3):
+        r = np.zeros(n)
+        disp = np.cross(w[None, :], pos)
+        for c in range(3):
+            r[comp == c] = disp[comp == c, c]
+        assert np.abs(A @ r).max() < 1e-12 * sc
+    assert abs(rhs[comp == 2].sum() + vol) < 1e-13
+
+
 def test_assemble_rows_matches_full():
     prob = inputs.small_problem((3, 2, 2), 2, 1, seed=41)
     cd, n, rp, col, val, rhs = assembled(prob)
