@@ -337,10 +337,32 @@ def o_grid(m: int, k: int, nz: int, a: float = 0.45, radius: float = 1.0, height
     return Mesh(coords.astype(np.float64), np.concatenate(cells).astype(np.int32), (), (2 * radius, 2 * radius, height))
 
 
-def o_grid_problem(m: int, k: int, nz: int, order: int, problem: int, seed: int = 0) -> Problem:
-    """A seeded problem on an O-grid: coefficients as in small_problem."""
+def flower(k: int, nz: int, tip: float = 1.25, height: float = 1.0) -> Mesh:
+    """A hexahedral "flower": in the xy-plane k quadrilaterals around the
+    origin, quad i with corners (origin, spoke i, tip i, spoke i + 1), spokes
+    on the unit circle at angles 2 pi i / k and tips at radius `tip` halfway
+    between, extruded over nz layers. The vertices on the z-axis between two
+    layers belong to 2k cells (a brick's interior vertices to 8), so k > 16
+    exceeds 32 cells around a DOF."""
+    ang = 2 * np.pi * np.arange(k) / k
+    spokes = np.column_stack([np.cos(ang), np.sin(ang)])
+    tips = tip * np.column_stack([np.cos(ang + np.pi / k), np.sin(ang + np.pi / k)])
+    P = np.concatenate([[[0.0, 0.0]], spokes, tips])
+    i = np.arange(k)
+    # local order (x fastest): (0,0) origin, (1,0) spoke i, (0,1) spoke i+1, (1,1) tip i
+    Q = np.column_stack([np.zeros(k, dtype=np.int64), 1 + i, 1 + (i + 1) % k, 1 + k + i])
+    n2 = P.shape[0]
+    zs = np.linspace(0.0, height, nz + 1)
+    coords = np.concatenate([np.column_stack([P, np.full(n2, z)]) for z in zs])
+    cells = [np.concatenate([Q + l * n2, Q + (l + 1) * n2], axis=1) for l in range(nz)]
+    return Mesh(coords.astype(np.float64), np.concatenate(cells).astype(np.int32), (), (2 * tip, 2 * tip, height))
+
+
+def o_grid_problem(m: int, k: int, nz: int, order: int, problem: int, seed: int = 0, mesh: Mesh | None = None) -> Problem:
+    """A seeded problem on an O-grid (or on the given mesh): coefficients as in
+    small_problem."""
     rng = np.random.default_rng(SEED_BASE + 700 + seed)
-    mesh = o_grid(m, k, nz)
+    mesh = o_grid(m, k, nz) if mesh is None else mesh
     if problem == POISSON:
         coef, force = _log_uniform(rng, 0.1, 10.0, mesh.n_cells), np.array([1.0])
     elif problem == STOKES:

@@ -63,6 +63,20 @@ def test_o_grid_all_kernels(p, problem):
     check_all_kernels(inputs.o_grid_problem(3, 2, 2, p, problem, seed=40 + 2 * p + problem))
 
 
+@pytest.mark.parametrize("p,problem", [(1, 0), (1, 1), (2, 0), (2, 1), (3, 0)])
+def test_flower_all_kernels(p, problem):
+    """A flower mesh (34 cells around its axis vertex between the two layers:
+    more than 32 cells around a DOF, so the scatter takes its general path, not
+    the slot-wise one): every kernel and precision against the oracle; the
+    batched driver refuses the space."""
+    prob = inputs.o_grid_problem(0, 0, 0, p, problem, seed=50 + 2 * p + problem, mesh=inputs.flower(17, 2))
+    check_all_kernels(prob)
+    sp = feasm.FESpace(prob)
+    with pytest.raises(feasm.FEError):
+        feasm.fe_batch_create([sp.handle])
+    sp.close()
+
+
 @pytest.mark.parametrize("p,problem", [(1, 1), (2, 1)])
 def test_locality_ordered_mesh_all_kernels(p, problem):
     """A scrambled brick given in the cell order of fe_mesh_locality_order (the

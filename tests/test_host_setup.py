@@ -61,6 +61,14 @@ def test_o_grid_numbering_pattern_permutation(p, problem):
     check_host_setup(inputs.o_grid_problem(3, 2, 2, p, problem, seed=20 + p))
 
 
+@pytest.mark.parametrize("p,problem", [(1, 1), (2, 0), (3, 0)])
+def test_flower_numbering_pattern_permutation(p, problem):
+    """The same checks on a flower mesh: 34 cells around the axis vertex between
+    its two layers (more than the 32 of the slot-wise scatter)."""
+    prob = inputs.o_grid_problem(0, 0, 0, p, problem, seed=30 + p, mesh=inputs.flower(17, 2))
+    check_host_setup(prob)
+
+
 def check_host_setup(prob):
     p, problem = prob.order, prob.problem
     sp = feasm.FESpace(prob, host_only=True)
