@@ -4,7 +4,9 @@ factor, a wrong index), compiles that copy and runs the pin file against it;
 at least one pin must fail. The oracle source itself is not changed. Every
 slip changes the computed result (an unsymmetrised trial strain, for one,
 would not: sigma(u) : eps(v) only sees the symmetric part of grad u, since
-eps(v) is symmetric and tr grad u = div u)."""
+eps(v) is symmetric and tr grad u = div u; nor would mirrored bilinear weights
+in the node keys: the keys only match nodes between cells, and any injective
+orientation-free key gives the same list_dofs numbering)."""
 import concurrent.futures
 import os
 import subprocess
@@ -46,6 +48,9 @@ MUTANTS = [
     ("DG tau term with the other side's derivative", "- tau * gb * phi[sb][b] * half * gn[sa][a]",
      "- tau * gb * phi[sb][b] * half * gn[sb][a]", 0),
     ("DG penalty not divided by the facet area", "pen = gamma / area;", "pen = gamma;", 0),
+    ("node keys: vef corners left in the cell's local order",
+     "    while (j >= 0 && k->g[j] > gg) { k->g[j + 1] = k->g[j]; k->w[j + 1] = k->w[j]; --j; }",
+     "    while (0) { k->g[j + 1] = k->g[j]; k->w[j + 1] = k->w[j]; --j; }", 0),
     ("smallest det J: vertices not sampled", "for (int q = 0; q < 8; ++q) { jacobian(V, q, xv, J);",
      "for (int q = 0; q < 0; ++q) { jacobian(V, q, xv, J);", 0),
     ("smallest det J: corner table left at the Gauss points",
