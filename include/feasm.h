@@ -14,9 +14,13 @@
  *     pattern, assembly permutation, cell-matrix scratch), allocated at create
  *     time and freed by the matching destroy.
  *   - `stream` is a cudaStream_t (NULL = legacy default stream). Compute calls
- *     are asynchronous on it and allocate nothing.
- *   - Compute calls on one space (fe_assemble*, and fe_assemble_dirichlet on
- *     its constrained systems) must not overlap on the GPU: they share the
+ *     are asynchronous on it and allocate nothing (the exceptions say so: the
+ *     first fe_assemble_host call of a space and the first fe_batch_assemble
+ *     of each precision allocate, and fe_assemble_host returns when its
+ *     results are in host memory).
+ *   - Compute calls on one space (fe_assemble*, fe_assemble_dirichlet on its
+ *     constrained systems, fe_batch_assemble of a batch holding it) must not
+ *     overlap on the GPU: they share the
  *     space's cell-matrix scratch and the scatter's work counters (which the
  *     scatter leaves at zero when it completes). Issue them on one stream, or
  *     order them with events.
