@@ -938,6 +938,18 @@ def test_dg_consistency_with_linear_solution(p, shape, rotate, tau):
     assert np.abs(r - rhs).max() <= 1e-11 * np.abs(rhs).max()
 
 
+@pytest.mark.parametrize("p", [1, 2, 3])
+@pytest.mark.parametrize("tau", [1.0, -1.0])
+def test_dg_consistency_on_an_o_grid(p, tau):
+    """The same consistency on an O-grid: facets between cells of irregular
+    valence and a polygonal outer boundary."""
+    mesh = inputs.o_grid(3, 2, 2)
+    ud = np.array([-0.3, 0.8, 1.7, -0.6])
+    rp, col, val, rhs = oracle.dg_assemble(mesh, p, tau, 7.0, 0.0, ud)
+    u = ud[0] + dg_node_positions(mesh, p) @ ud[1:]
+    assert np.abs(csr_matvec(rp, col, val, u) - rhs).max() <= 1e-11 * np.abs(rhs).max()
+
+
 def csr_matvec(rp, col, val, v):
     rows = np.repeat(np.arange(rp.size - 1), np.diff(rp))
     out = np.zeros(rp.size - 1)
