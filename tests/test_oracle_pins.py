@@ -859,6 +859,41 @@ def test_stokes_assembled_invariants():
     assert np.all(rhs[nv:] == 0)
 
 
+@pytest.mark.parametrize("p", [2, 3])
+def test_stokes_invariants_on_an_o_grid(p):
+    """On an O-grid: symmetry, the zero pressure block, the six rigid velocity
+    modes in the kernel, a constant pressure orthogonal to the interior velocity
+    rows (the divergence of an interior velocity basis function integrates to
+    zero) and the body force summing to f vol on the velocity rows."""
+    prob = inputs.o_grid_problem(3, 2, 2, p, inputs.STOKES, seed=60 + p)
+    cd, n, nv = oracle.stokes_dof_numbering(prob.mesh, p)
+    rp, col, val, rhs = oracle.assemble_csr(prob, cd, n)
+    A = csr_to_dense(rp, col, val, n)
+    sc = np.abs(A).max()
+    assert np.abs(A - A.T).max() <= 1e-15 * sc
+    assert np.all(A[nv:, nv:] == 0)
+    pos_v, comp, _ = stokes_positions(prob, cd, n, nv)
+    for c in range(3):
+        t = np.zeros(n)
+        t[:nv][comp == c] = 1.0
+        assert np.abs(A @ t).max() <= 1e-12 * sc
+    for w in np.eye(3):
+        r = np.zeros(n)
+        r[:nv] = np.cross(w[None, :], pos_v)[np.arange(nv), comp]
+        assert np.abs(A @ r).max() <= 1e-12 * sc
+    one_p = np.zeros(n)
+    one_p[nv:] = 1.0
+    bt = (A @ one_p)[:nv]
+    ring = _o_grid_ring(prob.mesh)
+    inner = ~_o_grid_boundary(pos_v, ring, prob.mesh.extent[2])
+    assert np.abs(bt[inner]).max() <= 1e-12 * sc
+    area = 0.5 * abs(np.sum(ring[:, 0] * np.roll(ring[:, 1], -1) - np.roll(ring[:, 0], -1) * ring[:, 1]))
+    vol = area * prob.mesh.extent[2]
+    for c in range(3):
+        assert abs(rhs[:nv][comp == c].sum() - prob.force[c] * vol) <= 1e-13
+    assert np.all(rhs[nv:] == 0)
+
+
 def test_stokes_linear_velocity_closed_forms():
     """u = Bx + t, zero pressure, constant viscosity mu: the pressure rows give
     -tr(B) int psi_c, summing to -tr(B) vol; the interior velocity rows vanish
