@@ -53,6 +53,9 @@ MUTANTS = [
      "    while (0) { k->g[j + 1] = k->g[j]; k->w[j + 1] = k->w[j]; --j; }", 0),
     ("list_dofs: cell-interior nodes met last instead of first", "    int dkey = (dim == 3) ? 0 : dim + 1;",
      "    int dkey = dim;", 0),
+    ("list_dofs: n-faces of one dimension by anchor before extrusion",
+     "    keys[a] = (((int64_t)dkey * 8 + ext) * 8 + anc) * 4096 + a;",
+     "    keys[a] = (((int64_t)dkey * 8 + anc) * 8 + ext) * 4096 + a;", 0),
     ("smallest det J: vertices not sampled", "for (int q = 0; q < 8; ++q) { jacobian(V, q, xv, J);",
      "for (int q = 0; q < 0; ++q) { jacobian(V, q, xv, J);", 0),
     ("smallest det J: corner table left at the Gauss points",

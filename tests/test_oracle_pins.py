@@ -7,6 +7,7 @@ sign, a transposed J, a swapped index) fails at least one of them.
 """
 import itertools
 import math
+import os
 
 import numpy as np
 import pytest
@@ -334,6 +335,50 @@ def test_dof_numbering_list_dofs_order_single_q2_cell():
     got = np.empty(27, dtype=int)
     got[cd[0]] = np.arange(27)
     assert list(got) == expected_order
+
+
+def _golden(name):
+    """Sections of a text fixture under tests/golden: a keyword line followed by
+    rows of integers, or a keyword and its integers on one line."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    out, key = {}, None
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if not line:
+            continue
+        if line[0].lstrip("-").isdigit():
+            out[key].append([int(v) for v in line])
+        else:
+            key = line[0]
+            out[key] = [[int(v) for v in line[1:]]] if len(line) > 1 else []
+    return out
+
+
+def test_dof_numbering_matches_the_papers_bicubic_example():
+    """The paper's printed bicubic quadrilateral (tests/golden/bicubic_quad_dofs.txt):
+    on the z = 0 face of one Q3 hexahedron (the same 4 x 4 nodes), the node
+    numbering is x-fastest lexicographic, and the order in which list_dofs meets
+    the face's nodes is the concatenation of the owned-DOF lists of its n-faces
+    in the figure's order (vertices, x-edges, y-edges, the face). The nodes of
+    n-face 8 (the edge x = 1) are those with alpha_x = 3."""
+    g = _golden("bicubic_quad_dofs.txt")
+    labels = np.array(g["labels"])
+    for j in range(4):
+        for i in range(4):
+            assert labels[j, i] == 1 + i + 4 * j          # the figure's node at (i, j)
+    ptr, lst = g["p"][0], g["l"][0]
+    assert len(ptr) == 10 and ptr[-1] - 1 == len(lst) == 16
+    mesh = inputs.brick(1, 1, 1)
+    cd, n = oracle.dof_numbering(mesh, 3, 1)
+    order = np.argsort(cd[0])                            # local nodes in the order list_dofs numbers them
+    face = [int(a) + 1 for a in order if a < 16]         # the z = 0 layer, as 1-based 2D labels
+    assert face == lst
+    # each n-face's owned nodes are consecutive in that order
+    for f in range(9):
+        owned = lst[ptr[f] - 1:ptr[f + 1] - 1]
+        pos = [face.index(v) for v in owned]
+        assert pos == list(range(pos[0], pos[0] + len(owned)))
+    assert sorted(a + 1 for a in range(16) if a % 4 == 3) == g["dofs_n_face_8"][0]
 
 
 def test_dof_numbering_two_cells_share_face():
