@@ -381,6 +381,24 @@ def test_dof_numbering_matches_the_papers_bicubic_example():
     assert sorted(a + 1 for a in range(16) if a % 4 == 3) == g["dofs_n_face_8"][0]
 
 
+def test_dof_numbering_matches_the_papers_n_face_numbering():
+    """The paper's printed n-face numbering of the quadrilateral
+    (tests/golden/quad_nface_numbering.txt): each n-face's drawn point is the
+    centroid of its listed vertices, and on the z = 0 face of one Q2 hexahedron
+    (one node per n-face) list_dofs meets the nodes at those points in the
+    figure's n-face order (vertices, the two x-edges, the two y-edges, the face)."""
+    g = _golden("quad_nface_numbering.txt")
+    pts = {row[0]: np.array(row[1:], dtype=float) / 2.0 for row in g["position"]}
+    ptr, lst = g["p"][0], g["l"][0]
+    for k in range(1, 10):
+        verts = lst[ptr[k - 1] - 1:ptr[k] - 1]
+        np.testing.assert_allclose(np.mean([pts[v] for v in verts], axis=0), pts[k])
+    cd, n = oracle.dof_numbering(inputs.brick(1, 1, 1), 2, 1)
+    layer = [int(a) for a in np.argsort(cd[0]) if a < 9]   # z = 0 nodes in numbering order
+    got = [np.array([a % 3, a // 3], dtype=float) / 2.0 for a in layer]
+    np.testing.assert_allclose(np.array(got), np.array([pts[k] for k in range(1, 10)]))
+
+
 def test_dof_numbering_two_cells_share_face():
     mesh = inputs.brick(2, 1, 1)
     cd, n = oracle.dof_numbering(mesh, 1, 3)
