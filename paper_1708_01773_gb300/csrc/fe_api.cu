@@ -50,8 +50,20 @@ void free_device(fe_space* s) {
   if (s->copy_stream) cudaStreamDestroy(static_cast<cudaStream_t>(s->copy_stream));
 }
 
-int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem, double nu,
-                  bool host_only, fe_space** out) {
+// Frees a space under construction unless released (every early return and
+// any exception of create_space).
+struct SpaceGuard {
+  fe_space* s;
+  ~SpaceGuard() {
+    if (s) {
+      free_device(s);
+      delete s;
+    }
+  }
+};
+
+int create_space(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem, double nu,
+                 bool host_only, fe_space** out) {
   if (!out) return fail(FE_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!mesh || mesh->n_cells < 0 || mesh->n_vertices < 0 || (mesh->n_cells > 0 && !mesh->cell_vertices) ||
@@ -68,6 +80,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
   if (mesh->n_vertices > INT32_MAX) return fail(FE_ERR_UNSUPPORTED, "more than 2^31-1 vertices");
   fe_space* s = new (std::nothrow) fe_space();
   if (!s) return fail(FE_ERR_OOM, "host allocation failed");
+  SpaceGuard guard{s};
   s->order = order;
   s->nq1d = nq1d;
   s->problem = problem;
@@ -89,18 +102,16 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
   } catch (const std::bad_alloc&) {
     rc = FE_ERR_OOM;
     err = "host allocation failed during setup";
+  } catch (const std::exception& x) {
+    rc = FE_ERR_UNSUPPORTED;
+    err = std::string("host setup failed: ") + x.what();
   }
-  if (rc) {
-    delete s;
-    return fail(rc, err);
-  }
+  if (rc) return fail(rc, err);
   if (!host_only) {
     const int cpb = feasm::cells_per_block(s->nb, s->nq);
     if (problem != FE_STOKES && (feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP64, cpb) < 0 ||
-                                 feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP32, cpb) < 0)) {
-      delete s;
+                                 feasm::cell_smem_bytes(s->nb, s->nq, FE_PREC_FP32, cpb) < 0))
       return fail(FE_ERR_UNSUPPORTED, "quadrature too large for one block at this order");
-    }
     cudaError_t e = cudaGetDevice(&s->device);
     std::vector<double> xv;
     if (e == cudaSuccess) {
@@ -151,11 +162,7 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     s->n_partials = int((s->n_cells + 127) / 128) + 1;
     if (e == cudaSuccess) e = cudaMalloc(&s->d_partials, size_t(s->n_partials) * sizeof(double));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
-    if (e != cudaSuccess) {
-      free_device(s);
-      delete s;
-      return cuda_fail(e, "fe_space_create upload");
-    }
+    if (e != cudaSuccess) return cuda_fail(e, "fe_space_create upload");
     // the large host arrays are no longer needed (cell_dofs, row_ptr and col are kept for inspection)
     std::vector<uint8_t>().swap(s->hs.cnt);
     std::vector<uint16_t>().swap(s->hs.codes);
@@ -163,8 +170,15 @@ int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_pr
     std::vector<int64_t>().swap(s->hs.code_ptr);
     std::vector<int32_t>().swap(s->hs.slots);
   }
+  guard.s = nullptr;
   *out = s;
   return FE_OK;
+}
+
+int create_common(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem, double nu,
+                  bool host_only, fe_space** out) {
+  return feasm::no_throw("fe_space_create",
+                         [&] { return create_space(mesh, order, quad_points_1d, problem, nu, host_only, out); });
 }
 
 }  // namespace

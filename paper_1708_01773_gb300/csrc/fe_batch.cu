@@ -33,6 +33,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <memory>
 #include <vector>
 
 #include "fe_device.cuh"
@@ -426,7 +427,7 @@ int tune_and_capture(fe_batch* b, fe_precision prec, cudaStream_t st) {
 
 extern "C" {
 
-int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch** out) {
+static int batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch** out) {
   if (!out) return feasm::set_error(FE_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (n < 0 || (n > 0 && !spaces)) return feasm::set_error(FE_ERR_INVALID_ARG, "invalid space list");
@@ -441,7 +442,8 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
     if (s->problem == FE_STOKES) return feasm::set_error(FE_ERR_UNSUPPORTED, "the batch takes Poisson and elasticity spaces");
     if (int64_t(s->n_cells) > INT32_MAX) return feasm::set_error(FE_ERR_UNSUPPORTED, "space too large for a batch");
   }
-  fe_batch* b = new fe_batch();
+  std::unique_ptr<fe_batch, void (*)(fe_batch*)> owner(new fe_batch(), fe_batch_destroy);
+  fe_batch* b = owner.get();
   b->spaces.assign(spaces, spaces + n);
   b->device = device;
   b->cells_per_item = cells_per_item;
@@ -496,16 +498,18 @@ int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch
   e = cudaMalloc(&b->d_spaces, std::max(1, n) * sizeof(Space));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(int) * (n + 1));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-  if (e != cudaSuccess) {
-    fe_batch_destroy(b);
+  if (e != cudaSuccess)
     return feasm::set_error(e == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA, cudaGetErrorString(e));
-  }
-  *out = b;
+  *out = owner.release();
   return FE_OK;
 }
 
-int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const double* body_force,
-                      double* const* csr_values, double* const* rhs, fe_precision prec, void* stream) {
+int fe_batch_create(fe_space* const* spaces, int n, int cells_per_item, fe_batch** out) {
+  return feasm::no_throw("fe_batch_create", [&] { return batch_create(spaces, n, cells_per_item, out); });
+}
+
+static int batch_assemble(fe_batch* b, const double* const* coefficients, const double* body_force,
+                          double* const* csr_values, double* const* rhs, fe_precision prec, void* stream) {
   if (!b) return feasm::set_error(FE_ERR_INVALID_ARG, "batch is NULL");
   if (prec != FE_PREC_FP64 && prec != FE_PREC_FP32 && prec != FE_PREC_BF16)
     return feasm::set_error(FE_ERR_INVALID_ARG, "unknown precision");
@@ -546,6 +550,12 @@ int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const doub
   e = cudaGraphLaunch(pl.exec, st);
   if (e != cudaSuccess) return feasm::set_error(FE_ERR_CUDA, cudaGetErrorString(e));
   return FE_OK;
+}
+
+int fe_batch_assemble(fe_batch* b, const double* const* coefficients, const double* body_force,
+                      double* const* csr_values, double* const* rhs, fe_precision prec, void* stream) {
+  return feasm::no_throw("fe_batch_assemble",
+                         [&] { return batch_assemble(b, coefficients, body_force, csr_values, rhs, prec, stream); });
 }
 
 int fe_batch_set_wait(fe_batch* b, long long wait_cycles, int extra_cells) {

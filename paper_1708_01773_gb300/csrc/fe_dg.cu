@@ -782,8 +782,12 @@ int dg_create(const fe_mesh_desc* mesh, int order, bool host_only, fe_dg** out) 
 
 extern "C" {
 
-int fe_dg_create(const fe_mesh_desc* mesh, int order, fe_dg** out) { return dg_create(mesh, order, false, out); }
-int fe_dg_create_host(const fe_mesh_desc* mesh, int order, fe_dg** out) { return dg_create(mesh, order, true, out); }
+int fe_dg_create(const fe_mesh_desc* mesh, int order, fe_dg** out) {
+  return feasm::no_throw("fe_dg_create", [&] { return dg_create(mesh, order, false, out); });
+}
+int fe_dg_create_host(const fe_mesh_desc* mesh, int order, fe_dg** out) {
+  return feasm::no_throw("fe_dg_create_host", [&] { return dg_create(mesh, order, true, out); });
+}
 
 int fe_dg_sizes(const fe_dg* g, int64_t* n_dofs, int64_t* nnz, int64_t* n_interior, int64_t* n_boundary) {
   if (!g) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");

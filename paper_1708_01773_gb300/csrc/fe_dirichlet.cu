@@ -144,7 +144,7 @@ feasm::ScatterPattern pattern_of(const fe_dirichlet* d) {
 
 extern "C" {
 
-int fe_space_dof_points_host(const fe_space* s, const fe_mesh_desc* mesh, double* points) {
+static int dof_points_host(const fe_space* s, const fe_mesh_desc* mesh, double* points) {
   if (!s || !mesh || !points) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
   if (mesh->n_cells != s->n_cells || mesh->n_vertices != s->n_vertices || (s->n_cells && !mesh->cell_vertices) ||
       (s->n_vertices && !mesh->coords))
@@ -178,7 +178,11 @@ int fe_space_dof_points_host(const fe_space* s, const fe_mesh_desc* mesh, double
   return FE_OK;
 }
 
-int fe_dirichlet_create(fe_space* s, const uint8_t* fixed, fe_dirichlet** out) {
+int fe_space_dof_points_host(const fe_space* s, const fe_mesh_desc* mesh, double* points) {
+  return feasm::no_throw("fe_space_dof_points_host", [&] { return dof_points_host(s, mesh, points); });
+}
+
+static int dirichlet_create(fe_space* s, const uint8_t* fixed, fe_dirichlet** out) {
   if (!out) return feasm::set_error(FE_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!s || (s->hs.n_dofs && !fixed)) return feasm::set_error(FE_ERR_INVALID_ARG, "NULL argument");
@@ -260,6 +264,10 @@ int fe_dirichlet_create(fe_space* s, const uint8_t* fixed, fe_dirichlet** out) {
   }
   *out = d;
   return FE_OK;
+}
+
+int fe_dirichlet_create(fe_space* s, const uint8_t* fixed, fe_dirichlet** out) {
+  return feasm::no_throw("fe_dirichlet_create", [&] { return dirichlet_create(s, fixed, out); });
 }
 
 int fe_dirichlet_sizes(const fe_dirichlet* d, int64_t* n_free, int64_t* n_fixed, int64_t* nnz) {

@@ -3,6 +3,8 @@
 #pragma once
 
 #include <cstdint>
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -16,6 +18,22 @@ constexpr int kMaxSlots = 127;  // cells around one DOF (7 bits of a code)
 
 // Records the message returned by fe_last_error and returns `code`.
 int set_error(int code, const char* msg);
+
+// Runs f() and turns a C++ exception into a status code (std::bad_alloc:
+// FE_ERR_OOM, any other: FE_ERR_UNSUPPORTED), so that no exception leaves an
+// entry point of the C ABI.
+template <typename F>
+int no_throw(const char* what, F&& f) {
+  try {
+    return f();
+  } catch (const std::bad_alloc&) {
+    return set_error(FE_ERR_OOM, (std::string(what) + ": host allocation failed").c_str());
+  } catch (const std::exception& x) {
+    return set_error(FE_ERR_UNSUPPORTED, (std::string(what) + ": " + x.what()).c_str());
+  } catch (...) {
+    return set_error(FE_ERR_UNSUPPORTED, (std::string(what) + ": unexpected exception").c_str());
+  }
+}
 
 // Reference tables of the Q_p element at a tensor Gauss-Legendre rule on
 // [0,1]^3. Point q = q0 + n q1 + n^2 q2, node a = a0 + (p+1) a1 + (p+1)^2 a2.

@@ -2,6 +2,7 @@
 // global DOF numbering, CSR sparsity pattern and the cell-to-nonzero assembly
 // permutation consumed by the scatter kernel.
 #include <algorithm>
+#include <exception>
 #include <functional>
 #include <cmath>
 #include <cstring>
@@ -431,17 +432,36 @@ int build_pattern(int nl, int nb, int ncomp, int64_t n_cells, const int32_t* cel
   return FE_OK;
 }
 
+// Runs body(t, a, b) over [0, n) in chunks on up to nthreads threads. An
+// exception thrown by a chunk (std::bad_alloc when host memory runs out) is
+// carried to the calling thread and rethrown there after every thread has
+// joined, so that the entry point's handler turns it into a status code; a
+// chunk whose thread cannot be started runs on the calling thread.
 static void parallel_for(int64_t n, int nthreads, const std::function<void(int, int64_t, int64_t)>& body) {
   if (n <= 0) return;
   nthreads = int(std::max<int64_t>(1, std::min<int64_t>(nthreads, n / 1024 + 1)));
-  std::vector<std::thread> th;
   const int64_t chunk = (n + nthreads - 1) / nthreads;
+  std::vector<std::exception_ptr> errors(static_cast<size_t>(nthreads));
+  auto run = [&](int t, int64_t a, int64_t b) {
+    try {
+      body(t, a, b);
+    } catch (...) {
+      errors[size_t(t)] = std::current_exception();
+    }
+  };
+  std::vector<std::thread> th;
   for (int t = 0; t < nthreads; ++t) {
     const int64_t a = t * chunk, b = std::min(n, a + chunk);
     if (a >= b) break;
-    th.emplace_back(body, t, a, b);
+    try {
+      th.emplace_back(run, t, a, b);
+    } catch (...) {
+      run(t, a, b);
+    }
   }
   for (auto& x : th) x.join();
+  for (auto& e : errors)
+    if (e) std::rethrow_exception(e);
 }
 
 }  // namespace feasm
@@ -466,7 +486,7 @@ uint64_t spread3(uint64_t v) {
 
 }  // namespace
 
-int fe_mesh_locality_order(const fe_mesh_desc* mesh, int64_t* order) {
+static int locality_order(const fe_mesh_desc* mesh, int64_t* order) {
   if (!mesh || mesh->n_cells < 0 || mesh->n_vertices < 0)
     return feasm::set_error(FE_ERR_INVALID_ARG, "invalid mesh descriptor");
   const int64_t nc = mesh->n_cells, nv = mesh->n_vertices;
@@ -505,4 +525,8 @@ int fe_mesh_locality_order(const fe_mesh_desc* mesh, int64_t* order) {
   std::sort(key.begin(), key.end());
   for (int64_t i = 0; i < nc; ++i) order[i] = key[size_t(i)].second;
   return FE_OK;
+}
+
+int fe_mesh_locality_order(const fe_mesh_desc* mesh, int64_t* order) {
+  return feasm::no_throw("fe_mesh_locality_order", [&] { return locality_order(mesh, order); });
 }
