@@ -103,7 +103,8 @@ typedef struct {
  *   nu              Poisson ratio (elasticity only, 0 <= nu < 0.5).
  *   out             receives the new space; destroy with fe_space_destroy.
  * Uses the current CUDA device. Host work is multi-threaded. Errors:
- * FE_ERR_INVALID_ARG (bad sizes, vertex ids out of range), FE_ERR_UNSUPPORTED
+ * FE_ERR_INVALID_ARG (bad sizes, vertex ids out of range, a cell that repeats
+ * a vertex), FE_ERR_UNSUPPORTED
  * (index widths exceeded, more than 127 cells around one DOF), FE_ERR_OOM,
  * FE_ERR_CUDA. */
 int fe_space_create(const fe_mesh_desc* mesh, int order, int quad_points_1d, fe_problem problem,

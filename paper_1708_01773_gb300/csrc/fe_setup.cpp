@@ -262,6 +262,17 @@ int build_host_setup(int p, int problem, int64_t n_cells, int64_t n_vertices, co
       *err = "cell_vertices entry out of range";
       return FE_ERR_INVALID_ARG;
     }
+  // a hexahedron has 8 distinct vertices (a repeated one would give a cell two
+  // local DOFs with one global id, which the assembly maps do not allow)
+  for (int64_t e = 0; e < n_cells; ++e) {
+    const int32_t* v = cell_vertices + 8 * e;
+    for (int a = 0; a < 8; ++a)
+      for (int b = a + 1; b < 8; ++b)
+        if (v[a] == v[b]) {
+          *err = "cell " + std::to_string(e) + " repeats a vertex";
+          return FE_ERR_INVALID_ARG;
+        }
+  }
   if (n_cells * nl > INT32_MAX) {
     *err = "n_cells * n_loc exceeds int32";
     return FE_ERR_UNSUPPORTED;

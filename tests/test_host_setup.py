@@ -239,3 +239,21 @@ def test_locality_order_edge_cases():
     nan[0, 0] = np.nan
     with pytest.raises(feasm.FEError):
         feasm.fe_mesh_locality_order(nan, m.cell_vertices)
+
+
+def test_cell_repeating_a_vertex_is_rejected():
+    """A hexahedron whose vertex list repeats an id (a collapsed edge) is refused
+    at setup with FE_ERR_INVALID_ARG, as are vertex ids out of range."""
+    m = inputs.brick(2, 1, 1)
+    bad = m.cell_vertices.copy()
+    bad[1, 7] = bad[1, 6]
+    prob = inputs.Problem("bad", inputs.Mesh(m.coords, bad, (), m.extent), 1, 2, 0, np.ones(2), np.ones(1))
+    with pytest.raises(feasm.FEError) as e:
+        feasm.FESpace(prob, host_only=True)
+    assert e.value.code == -1 and "repeats a vertex" in str(e.value)
+    bad = m.cell_vertices.copy()
+    bad[0, 0] = -1
+    prob = inputs.Problem("bad", inputs.Mesh(m.coords, bad, (), m.extent), 1, 2, 0, np.ones(2), np.ones(1))
+    with pytest.raises(feasm.FEError) as e:
+        feasm.FESpace(prob, host_only=True)
+    assert e.value.code == -1
