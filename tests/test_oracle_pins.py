@@ -393,10 +393,51 @@ def test_dof_numbering_matches_the_papers_n_face_numbering():
     for k in range(1, 10):
         verts = lst[ptr[k - 1] - 1:ptr[k] - 1]
         np.testing.assert_allclose(np.mean([pts[v] for v in verts], axis=0), pts[k])
+    # n-faces numbered by dimension: 4 vertices, 4 edges, 1 cell (the paper's
+    # ptr_n_faces_x_dim = {1, 5, 9, 10}), read off the vertex counts
+    dims = [int(np.log2(ptr[k] - ptr[k - 1])) for k in range(1, 10)]
+    assert dims == [0] * 4 + [1] * 4 + [2]
+    ptr_x_dim = [1 + sum(1 for d in dims if d < m) for m in range(4)]
+    assert ptr_x_dim == g["ptr_n_faces_x_dim"][0]
     cd, n = oracle.dof_numbering(inputs.brick(1, 1, 1), 2, 1)
     layer = [int(a) for a in np.argsort(cd[0]) if a < 9]   # z = 0 nodes in numbering order
     got = [np.array([a % 3, a // 3], dtype=float) / 2.0 for a in layer]
     np.testing.assert_allclose(np.array(got), np.array([pts[k] for k in range(1, 10)]))
+
+
+def test_node_sharing_matches_the_papers_cube_n_face_codes():
+    """The paper's printed [extrusion|anchor] codes of the 3-cube's n-faces
+    (tests/golden/cube_nface_codes.txt): 26 distinct codes, 8 vertices, 12
+    edges and 6 faces, anchor bits only in directions not extruded. A node
+    alpha of a Q2 cell lies on the n-face extruded where alpha_d = 1 and
+    anchored where alpha_d = 2; in a 3 x 3 x 3 brick the oracle's numbering
+    gives each node of the centre cell to 2^(3 - |ext|) cells, and the codes of
+    the centre cell's 26 boundary nodes are the printed ones."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cube_nface_codes.txt")
+    printed = set()
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line.startswith("["):
+            e, a = line.strip("[]").split("|")
+            printed.add((tuple(int(c) for c in e), tuple(int(c) for c in a)))
+    assert len(printed) == 26
+    assert sorted(sum(e) for e, _ in printed) == [0] * 8 + [1] * 12 + [2] * 6
+    assert all(not (x and y) for e, a in printed for x, y in zip(e, a))
+    cd, n = oracle.dof_numbering(inputs.brick(3, 3, 3), 2, 1)
+    centre = 1 + 3 + 9
+    count = np.bincount(cd.ravel(), minlength=n)
+    codes = set()
+    for a in range(27):
+        al = (a % 3, (a // 3) % 3, a // 9)
+        e = tuple(int(x == 1) for x in al)
+        anc = tuple(int(x == 2) for x in al)
+        assert count[cd[centre, a]] == 2 ** (3 - sum(e))
+        if sum(e) < 3:
+            codes.add((e, anc))
+    # the printed strings' direction order is not stated; the set is the same
+    # under either reading of the bit order
+    flip = {(e[::-1], a[::-1]) for e, a in printed}
+    assert codes == printed == flip
 
 
 def test_dof_numbering_two_cells_share_face():
